@@ -1,0 +1,202 @@
+/*
+ * lmosem: list-mode OS-LM-MLEM attenuation and scatter compensation for 2-D
+ * SPECT on one GB300 (sm_103a).
+ *
+ * Method: Rahman, Laforest, Jha, "A list-mode OSEM-based attenuation and
+ * scatter compensation method for SPECT", ISBI 2020 (arXiv:2002.12471).
+ *
+ * C ABI.  Plain pointers and sizes only.  Conventions:
+ *  - Pointers named d_* are CUDA device memory owned by the caller; h_* are
+ *    host memory owned by the caller.  The context copies what it keeps and
+ *    owns every buffer it allocates (freed by lmosem_destroy).
+ *  - All device work is enqueued on the stream given to lmosem_create.  A
+ *    call returns once its work is enqueued, except where it must read a
+ *    result back (noted per function); those calls synchronise the stream.
+ *  - Every function returns a status code; none throws or aborts.  After an
+ *    error lmosem_last_error(ctx) holds a one-line message.  A context is not
+ *    thread-safe.
+ *  - The image is a vector over the emission support: d_f[q] is the activity
+ *    of pixel support[q] (see lmosem_support).  Support and scatter pixels are
+ *    listed in increasing row-major pixel index (pixel n = iy * nx + ix).
+ *
+ * Geometry (the model's frozen reading of the scanner, paper Section 3):
+ *  pixel (ix, iy) has centre ((ix + 1/2 - nx/2) D, (iy + 1/2 - ny/2) D);
+ *  detector angle a has theta_a = angle0 + 2 pi a / n_angles, photons reach
+ *  it travelling along omega_a = (cos, sin) theta_a; the event position is
+ *  u = p . (-sin theta_a, cos theta_a), continuous, |u| <= n_bins bin_mm / 2;
+ *  depth d = R - p . omega_a sets the collimator response
+ *  FWHM_u = coll_fwhm0 + coll_fwhm_slope d.  Energy resolution is
+ *  FWHM_E(E) = fwhm_frac_e0 sqrt(E0 E); events outside [e_lo, e_hi] are not
+ *  acquired.
+ */
+#ifndef LMOSEM_H
+#define LMOSEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LMOSEM_OK = 0,
+    LMOSEM_EINVAL = 1,   /* an argument is out of range; nothing was enqueued      */
+    LMOSEM_ENOMEM = 2,   /* a device allocation failed                              */
+    LMOSEM_ECUDA = 3,    /* a CUDA call failed (message holds the CUDA error)       */
+    LMOSEM_ETIMEOUT = 4, /* a bounded device wait ran out                           */
+    LMOSEM_ENUMERIC = 5, /* a non-finite value appeared in the image                */
+    LMOSEM_ESTATE = 6,   /* called out of order (e.g. iterate before build_model)   */
+    LMOSEM_ENOTIMPL = 7  /* the requested form is not built                         */
+} lmosem_status;
+
+typedef struct lmosem_ctx lmosem_ctx; /* opaque; owns all device buffers */
+
+/* Object: the mu-map at the photopeak energy (a CT-derived attenuation map;
+ * paper Section 1) and the emission support (paper Section 2.2: the cost scales
+ * with the number of non-zero voxels N_nz). */
+typedef struct {
+    int32_t nx, ny;          /* grid size, 1..2048 each                           */
+    double pixel_mm;         /* pixel pitch D > 0                                 */
+    const double* h_mu_per_mm; /* host, ny*nx row-major, finite, >= 0             */
+    const uint8_t* h_support;  /* host, ny*nx, nonzero = emission pixel;
+                                  NULL selects {mu > 0}                            */
+} lmosem_object;
+
+typedef struct {
+    int32_t n_angles;        /* >= 1                                              */
+    double angle0_rad;
+    int32_t n_bins;          /* detector extent n_bins * bin_mm                   */
+    double bin_mm;
+    double radius_mm;        /* > distance of every support/scatter pixel centre  */
+    double coll_fwhm0_mm;    /* > 0                                               */
+    double coll_fwhm_slope;  /* >= 0                                              */
+} lmosem_geometry;
+
+typedef struct {
+    double e0_kev;           /* photopeak (159 keV for I-123)                      */
+    double fwhm_frac_e0;     /* energy FWHM at E0 / E0, > 0                        */
+    double e_lo_kev, e_hi_kev; /* acquisition window, e_lo < e_hi                  */
+} lmosem_energy;
+
+typedef struct {
+    /* Scatter paths (n, m) whose position kernel is evaluated farther than
+     * k_sigma collimator sigmas from the event are left out of p_jn.
+     * 0 selects the default 6 (entries change by < 3e-7 of the row maximum). */
+    float k_sigma;
+    /* Upper bound (bytes) of the per-angle scatter-weight tables kept on the
+     * device while a model is built; 0 selects 4 GiB. */
+    int64_t table_budget_bytes;
+    /* Nonzero: bracket every kernel launch with CUDA events on the context
+     * stream so that lmosem_profile_read can report device time per kernel
+     * class (for benchmarks; adds two event records per launch). */
+    int32_t profile;
+} lmosem_options;
+
+/* Kernel classes reported by lmosem_profile_read. */
+typedef enum {
+    LMOSEM_K_TABLES = 0,   /* attenuation line integrals and per-angle parameters */
+    LMOSEM_K_SORT = 1,     /* event check and (subset, angle, position) sort      */
+    LMOSEM_K_WTABLE = 2,   /* per-angle scatter weight tables                     */
+    LMOSEM_K_PATHSUM = 3,  /* per-event path-sum model build                      */
+    LMOSEM_K_QUANTIZE = 4, /* row scaling to FP16/BF16                            */
+    LMOSEM_K_SENS = 5,     /* subset sensitivities                                */
+    LMOSEM_K_PASS = 6,     /* streaming OSEM pass (forward, back-projection, LL)  */
+    LMOSEM_K_UPDATE = 7,   /* per-subset reduction and multiplicative update      */
+    LMOSEM_K_OTHER = 8,
+    LMOSEM_K_COUNT = 9
+} lmosem_kernel_class;
+
+typedef enum {
+    LMOSEM_MODEL_FP32 = 0,        /* p_jn cached as FP32                           */
+    LMOSEM_MODEL_FP16_SCALED = 1, /* p_jn = c_j h_jn, h FP16 with max_n h = 2^15   */
+    LMOSEM_MODEL_BF16_SCALED = 2  /* p_jn = c_j h_jn, h BF16 with max_n h = 1      */
+} lmosem_model_fmt;
+
+/* Create a context: validate the problem, copy the mu-map and support to the
+ * device and build the attenuation tables (integrals of mu along omega_a from
+ * every pixel centre to the grid edge, and between every support and scatter
+ * pixel centre; Siddon's ray parametrisation).  Synchronises the stream.
+ * opts may be NULL.  stream is a cudaStream_t (NULL = legacy default stream).
+ * EINVAL: any field out of the ranges above, empty support, radius too small. */
+lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geom,
+                            const lmosem_energy* energy, const lmosem_options* opts,
+                            void* stream, lmosem_ctx** out);
+
+void lmosem_destroy(lmosem_ctx* ctx);
+
+const char* lmosem_last_error(const lmosem_ctx* ctx);
+const char* lmosem_status_string(lmosem_status st);
+
+/* Number of emission-support pixels N_nz and of scatter pixels {mu > 0}. */
+int32_t lmosem_n_support(const lmosem_ctx* ctx);
+int32_t lmosem_n_scatter(const lmosem_ctx* ctx);
+
+/* Copy the support pixel indices (N_nz int32, increasing) to host memory. */
+lmosem_status lmosem_support(const lmosem_ctx* ctx, int32_t* h_out);
+
+/* Subset sensitivities s^i_q (denominator of paper Eq. 7, without T): the
+ * probability that a photon emitted in support pixel q is acquired at an
+ * angle of subset i, summed over the primary path and every first-order
+ * in-plane scatter path.  Subset i holds the angles a with a mod n_subsets
+ * == i.  Terms in FP32, accumulation in FP64.  Kept in the context; also
+ * copied to d_sens (n_subsets x N_nz FP64, row-major) when d_sens != NULL.
+ * EINVAL: n_subsets not in [1, n_angles]. */
+lmosem_status lmosem_sensitivity(lmosem_ctx* ctx, int32_t n_subsets, double* d_sens);
+
+/* Build and cache the list-mode system model for J events (paper Eq. 2 with
+ * Eq. 4: p_jq = sum over paths P from pixel q of pr(A_j|P) s_eff(P), the
+ * primary path plus every first-order in-plane Compton path (q, m) with
+ * attenuation, Klein-Nishina weight, energy blur and collimator response).
+ * Events are three device arrays of length n_events (angle index, position
+ * in mm, energy in keV).  The context sorts them by (subset, angle, u) and
+ * keeps the sorted copy; the caller's arrays are not modified and may be
+ * freed on return.  Synchronises the stream (input check).
+ * EINVAL: n_events < 1 or >= 2^31, n_subsets not in [1, n_angles], an angle
+ * outside [0, n_angles), |u| > extent/2, E outside [e_lo, e_hi], NaN.
+ * ENOMEM: the model does not fit.  Any earlier model is released first. */
+lmosem_status lmosem_build_model(lmosem_ctx* ctx, const int32_t* d_angle, const float* d_u_mm,
+                                 const float* d_e_kev, int64_t n_events, int32_t n_subsets,
+                                 lmosem_model_fmt fmt);
+
+/* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz).
+ * ESTATE: no model or sensitivity. */
+lmosem_status lmosem_init_image(lmosem_ctx* ctx, double acq_time, float* d_f);
+
+/* n_iters global OS-LM-MLEM iterations (paper Eqs. 7-9): for every subset i
+ * in index order, y_j = sum_q p_jq f_q over the subset's events, then
+ * f_q <- f_q sum_j p_jq / y_j / (T s^i_q) (events with y_j = 0 add nothing;
+ * f_q = 0 where s^i_q = 0).  d_f (N_nz FP32) is updated in place.  When
+ * d_loglik != NULL, d_loglik[t] (FP64, device) receives the log-likelihood
+ * of paper Eq. 3 (without log J!) of the image after iteration t; this costs
+ * one extra read of the model per iteration.
+ * ESTATE: no model, or the sensitivity was computed for another subset count. */
+lmosem_status lmosem_iterate(lmosem_ctx* ctx, int32_t n_iters, double acq_time, float* d_f,
+                             double* d_loglik);
+
+/* Log-likelihood of paper Eq. 3 (without log J!) of the image d_f:
+ * sum_j log(T y_j) - T sum_q s_q f_q, FP64 reduction, into d_out[0]. */
+lmosem_status lmosem_loglik(lmosem_ctx* ctx, double acq_time, const float* d_f, double* d_out);
+
+/* Copy model rows back as FP32 (dequantised for the scaled forms):
+ * d_out[k * N_nz + q] = p_{j_k, q} for the caller's original event indices
+ * j_k = d_event_ids[k] (device int64, each in [0, J)).  For tests and tools. */
+lmosem_status lmosem_model_rows(lmosem_ctx* ctx, const int64_t* d_event_ids, int64_t n,
+                                float* d_out);
+
+/* Bytes of the cached model (rows x padded columns x element size + scales). */
+int64_t lmosem_model_bytes(const lmosem_ctx* ctx);
+
+/* Number of kernel launches this context has enqueued so far. */
+int64_t lmosem_launch_count(const lmosem_ctx* ctx);
+
+/* Device time (ms) and launch count per kernel class since the last read,
+ * from the CUDA events of a context created with opts->profile != 0.
+ * h_ms and h_launches hold LMOSEM_K_COUNT entries.  Synchronises the stream.
+ * ESTATE: profiling is off. */
+lmosem_status lmosem_profile_read(lmosem_ctx* ctx, double* h_ms, int64_t* h_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMOSEM_H */

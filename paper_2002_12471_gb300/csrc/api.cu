@@ -1,0 +1,369 @@
+// C ABI of the lmosem library: argument validation, context ownership and
+// the order of the hot-path steps.  Every numerical step runs in the
+// kernels of the other translation units; this file only checks arguments,
+// allocates, and enqueues.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <new>
+
+#include "lmosem_internal.cuh"
+
+namespace lmosem {
+
+lmosem_status fail(lmosem_ctx* c, lmosem_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+lmosem_status cuda_fail(lmosem_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LMOSEM_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                     cudaGetErrorString(e) + ")");
+}
+
+static cudaEvent_t prof_event(lmosem_ctx* c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(lmosem_ctx* c) {
+    c->prof_open = prof_event(c);
+    cudaEventRecord(c->prof_open, c->stream);
+}
+
+void prof_end(lmosem_ctx* c, int cls) {
+    if (!c->prof_open) return;
+    cudaEvent_t b = prof_event(c);
+    cudaEventRecord(b, c->stream);
+    c->prof.push_back({cls, c->prof_open, b});
+    c->prof_open = nullptr;
+}
+
+namespace {
+
+__global__ void k_count_nonfinite(const float* __restrict__ f, int n, int* __restrict__ bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(f[i])) atomicAdd(bad, 1);
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+void free_model(lmosem_ctx* c) {
+    dev_free(&c->d_model);
+    dev_free(&c->d_scale);
+    dev_free(&c->d_stage);
+    dev_free(&c->d_perm);
+    dev_free(&c->d_rank);
+    dev_free(&c->d_u_s);
+    dev_free(&c->d_e_s);
+    dev_free(&c->d_a_s);
+    dev_free(&c->d_angle_row0);
+    dev_free(&c->d_angle_cnt);
+    dev_free(&c->d_tile_prefix);
+    dev_free(&c->d_wtab);
+    c->fmt = -1;
+    c->J = 0;
+    c->n_subsets = 0;
+}
+
+}  // namespace
+}  // namespace lmosem
+
+using namespace lmosem;
+
+extern "C" {
+
+const char* lmosem_status_string(lmosem_status st) {
+    switch (st) {
+        case LMOSEM_OK: return "ok";
+        case LMOSEM_EINVAL: return "invalid argument";
+        case LMOSEM_ENOMEM: return "out of device memory";
+        case LMOSEM_ECUDA: return "CUDA error";
+        case LMOSEM_ETIMEOUT: return "device wait timed out";
+        case LMOSEM_ENUMERIC: return "non-finite value";
+        case LMOSEM_ESTATE: return "called out of order";
+        case LMOSEM_ENOTIMPL: return "not implemented";
+    }
+    return "unknown status";
+}
+
+const char* lmosem_last_error(const lmosem_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int32_t lmosem_n_support(const lmosem_ctx* ctx) { return ctx ? ctx->n_sup : 0; }
+int32_t lmosem_n_scatter(const lmosem_ctx* ctx) { return ctx ? ctx->n_scat : 0; }
+int64_t lmosem_launch_count(const lmosem_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t lmosem_model_bytes(const lmosem_ctx* ctx) {
+    if (!ctx || ctx->fmt < 0) return 0;
+    int64_t elem = ctx->fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
+    return ctx->J * ctx->ld_model * elem + (ctx->fmt == LMOSEM_MODEL_FP32 ? 0 : ctx->J * 4);
+}
+
+lmosem_status lmosem_support(const lmosem_ctx* ctx, int32_t* h_out) {
+    if (!ctx || !h_out) return LMOSEM_EINVAL;
+    std::copy(ctx->h_sup.begin(), ctx->h_sup.end(), h_out);
+    return LMOSEM_OK;
+}
+
+void lmosem_destroy(lmosem_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_model(c);
+    dev_free(&c->d_mu);
+    dev_free(&c->d_sup);
+    dev_free(&c->d_scat);
+    dev_free(&c->d_trig);
+    dev_free(&c->d_l_edge);
+    dev_free(&c->d_l_pair);
+    dev_free(&c->d_compton);
+    dev_free(&c->d_mpar);
+    dev_free(&c->d_ppar);
+    dev_free(&c->d_du_m);
+    dev_free(&c->d_sens);
+    dev_free(&c->d_sens_angle);
+    dev_free(&c->d_bpart);
+    dev_free(&c->d_llpart);
+    dev_free(&c->d_scalar);
+    for (auto& r : c->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->prof_pool) cudaEventDestroy(e);
+    if (c->prof_open) cudaEventDestroy(c->prof_open);
+    delete c;
+}
+
+lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geom,
+                            const lmosem_energy* en, const lmosem_options* opts, void* stream,
+                            lmosem_ctx** out) {
+    if (!out) return LMOSEM_EINVAL;
+    *out = nullptr;
+    if (!obj || !geom || !en || !obj->h_mu_per_mm) return LMOSEM_EINVAL;
+    if (obj->nx < 1 || obj->ny < 1 || obj->nx > 2048 || obj->ny > 2048 || !finite_pos(obj->pixel_mm))
+        return LMOSEM_EINVAL;
+    if (geom->n_angles < 1 || geom->n_angles > 1536 || geom->n_bins < 1 || !finite_pos(geom->bin_mm) ||
+        !finite_pos(geom->radius_mm) || !finite_pos(geom->coll_fwhm0_mm) ||
+        !isfinite(geom->coll_fwhm_slope) || geom->coll_fwhm_slope < 0 || !isfinite(geom->angle0_rad))
+        return LMOSEM_EINVAL;
+    if (!finite_pos(en->e0_kev) || !finite_pos(en->fwhm_frac_e0) || !finite_pos(en->e_lo_kev) ||
+        !isfinite(en->e_hi_kev) || en->e_hi_kev <= en->e_lo_kev)
+        return LMOSEM_EINVAL;
+    float ks = opts && opts->k_sigma != 0.0f ? opts->k_sigma : 6.0f;
+    if (!(ks > 0.0f && ks <= 20.0f)) return LMOSEM_EINVAL;
+
+    lmosem_ctx* c = new (std::nothrow) lmosem_ctx();
+    if (!c) return LMOSEM_ENOMEM;
+    c->stream = (cudaStream_t)stream;
+    c->nx = obj->nx;
+    c->ny = obj->ny;
+    c->npix = obj->nx * obj->ny;
+    c->dpx = obj->pixel_mm;
+    c->n_angles = geom->n_angles;
+    c->angle0 = geom->angle0_rad;
+    c->n_bins = geom->n_bins;
+    c->bin_mm = geom->bin_mm;
+    c->radius = geom->radius_mm;
+    c->fwhm0 = geom->coll_fwhm0_mm;
+    c->fwhm_slope = geom->coll_fwhm_slope;
+    c->e0 = en->e0_kev;
+    c->fwhm_frac = en->fwhm_frac_e0;
+    c->e_lo = en->e_lo_kev;
+    c->e_hi = en->e_hi_kev;
+    c->k_sigma = ks;
+    if (opts && opts->table_budget_bytes > 0) c->table_budget = opts->table_budget_bytes;
+    c->profile = opts && opts->profile != 0;
+
+    std::vector<float> mu(c->npix);
+    double rmax = 0.0;
+    for (int p = 0; p < c->npix; ++p) {
+        double v = obj->h_mu_per_mm[p];
+        if (!isfinite(v) || v < 0.0) {
+            delete c;
+            return LMOSEM_EINVAL;
+        }
+        mu[p] = (float)v;
+        bool sup = obj->h_support ? obj->h_support[p] != 0 : v > 0.0;
+        if (sup) c->h_sup.push_back(p);
+        if (v > 0.0) c->h_scat.push_back(p);
+        if (sup || v > 0.0) {
+            double x = (p % c->nx + 0.5 - 0.5 * c->nx) * c->dpx;
+            double y = (p / c->nx + 0.5 - 0.5 * c->ny) * c->dpx;
+            rmax = std::max(rmax, sqrt(x * x + y * y));
+        }
+    }
+    c->n_sup = (int)c->h_sup.size();
+    c->n_scat = (int)c->h_scat.size();
+    if (c->n_sup == 0) {
+        lmosem_status st = fail(c, LMOSEM_EINVAL, "empty emission support");
+        delete c;
+        return st;
+    }
+    if (c->n_scat > 32768) {
+        delete c;
+        return LMOSEM_EINVAL;
+    }
+    if (geom->radius_mm <= rmax) {
+        delete c;
+        return LMOSEM_EINVAL;
+    }
+    c->ld_w = (c->n_sup + kTN - 1) / kTN * kTN;
+
+    lmosem_status st;
+    if ((st = dev_alloc(c, &c->d_mu, c->npix)) || (st = dev_alloc(c, &c->d_sup, c->n_sup)) ||
+        (st = dev_alloc(c, &c->d_scat, std::max(1, c->n_scat)))) {
+        lmosem_destroy(c);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_mu, mu.data(), mu.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_sup, c->h_sup.data(), c->n_sup * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->n_scat)
+        e = cudaMemcpyAsync(c->d_scat, c->h_scat.data(), c->n_scat * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "copy of the mu-map");
+        lmosem_destroy(c);
+        return LMOSEM_ECUDA;
+    }
+    if ((st = build_tables(c))) {
+        fprintf(stderr, "lmosem_create: %s\n", c->err.c_str());
+        lmosem_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_sensitivity(lmosem_ctx* c, int32_t n_subsets, double* d_sens) {
+    if (!c) return LMOSEM_EINVAL;
+    if (n_subsets < 1 || n_subsets > c->n_angles)
+        return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
+    lmosem_status st = compute_sensitivity(c, n_subsets);
+    if (st) return st;
+    if (d_sens)
+        LMOSEM_CK(c, cudaMemcpyAsync(d_sens, c->d_sens, sizeof(double) * (size_t)n_subsets * c->n_sup,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_build_model(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
+                                 const float* d_e_kev, int64_t n_events, int32_t n_subsets,
+                                 lmosem_model_fmt fmt) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_angle || !d_u_mm || !d_e_kev) return fail(c, LMOSEM_EINVAL, "null event array");
+    if (n_events < 1 || n_events >= (int64_t(1) << 31))
+        return fail(c, LMOSEM_EINVAL, "n_events must be in [1, 2^31)");
+    if (n_subsets < 1 || n_subsets > c->n_angles)
+        return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
+    if (fmt != LMOSEM_MODEL_FP32 && fmt != LMOSEM_MODEL_FP16_SCALED && fmt != LMOSEM_MODEL_BF16_SCALED)
+        return fail(c, LMOSEM_EINVAL, "unknown model format");
+    free_model(c);
+    c->fmt = fmt;
+    c->J = n_events;
+    c->n_subsets = n_subsets;
+    c->ld_model = (c->n_sup + 31) / 32 * 32;
+    lmosem_status st;
+    size_t elem = fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
+    {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)n_events * c->ld_model * elem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_model(c);
+            return fail(c, LMOSEM_ENOMEM, "model of " +
+                                              std::to_string((size_t)n_events * c->ld_model * elem) +
+                                              " bytes does not fit: " + cudaGetErrorString(e));
+        }
+        c->d_model = p;
+    }
+    if (fmt != LMOSEM_MODEL_FP32 && (st = dev_alloc(c, &c->d_scale, n_events))) {
+        free_model(c);
+        return st;
+    }
+    if ((st = sort_events(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets))) {
+        free_model(c);
+        return st;
+    }
+    if ((st = build_model_rows(c))) {
+        free_model(c);
+        return st;
+    }
+    if (!c->d_bpart && (st = setup_pass(c))) return st;
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_init_image(lmosem_ctx* c, double T, float* d_f) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad image pointer or acquisition time");
+    if (c->fmt < 0 || !c->sens_subsets) return fail(c, LMOSEM_ESTATE, "needs a model and a sensitivity");
+    return run_init_image(c, T, d_f);
+}
+
+lmosem_status lmosem_iterate(lmosem_ctx* c, int32_t n_iters, double T, float* d_f, double* d_ll) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || n_iters < 0 || !finite_pos(T))
+        return fail(c, LMOSEM_EINVAL, "bad image pointer, iteration count or acquisition time");
+    if (c->fmt < 0) return fail(c, LMOSEM_ESTATE, "no model built");
+    if (c->sens_subsets != c->n_subsets)
+        return fail(c, LMOSEM_ESTATE, "sensitivity missing or for another subset count");
+    lmosem_status st = run_iterations(c, n_iters, T, d_f, d_ll);
+    if (st) return st;
+    lmosem_status st2;
+    if (!c->d_scalar && (st2 = dev_alloc(c, &c->d_scalar, 4))) return st2;
+    int* bad = reinterpret_cast<int*>(c->d_scalar);
+    LMOSEM_CK(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    LMOSEM_PROF_BEGIN(c);
+    k_count_nonfinite<<<(c->n_sup + 255) / 256, 256, 0, c->stream>>>(d_f, c->n_sup, bad);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
+    int h = 0;
+    LMOSEM_CK(c, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h) return fail(c, LMOSEM_ENUMERIC, std::to_string(h) + " non-finite image values");
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || !d_out || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad arguments");
+    if (c->fmt < 0 || c->sens_subsets != c->n_subsets)
+        return fail(c, LMOSEM_ESTATE, "needs a model and a matching sensitivity");
+    return run_loglik(c, T, d_f, d_out);
+}
+
+lmosem_status lmosem_profile_read(lmosem_ctx* c, double* h_ms, int64_t* h_launches) {
+    if (!c || !h_ms || !h_launches) return LMOSEM_EINVAL;
+    if (!c->profile) return fail(c, LMOSEM_ESTATE, "profiling is off");
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < LMOSEM_K_COUNT; ++k) {
+        h_ms[k] = 0.0;
+        h_launches[k] = 0;
+    }
+    for (auto& r : c->prof) {
+        float ms = 0.0f;
+        LMOSEM_CK(c, cudaEventElapsedTime(&ms, r.a, r.b));
+        h_ms[r.cls] += ms;
+        h_launches[r.cls] += 1;
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    c->prof.clear();
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_model_rows(lmosem_ctx* c, const int64_t* d_ids, int64_t n, float* d_out) {
+    if (!c) return LMOSEM_EINVAL;
+    if (n < 0 || (n > 0 && (!d_ids || !d_out))) return fail(c, LMOSEM_EINVAL, "bad arguments");
+    if (c->fmt < 0) return fail(c, LMOSEM_ESTATE, "no model built");
+    return run_model_rows(c, d_ids, n, d_out);
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// Internal declarations of the lmosem CUDA library (sm_103a only).
+//
+// Method: list-mode OS-LM-MLEM with attenuation and first-order in-plane
+// scatter compensation (Rahman, Laforest, Jha, ISBI 2020, Sections 2.1-2.2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lmosem.h"
+
+namespace lmosem {
+
+constexpr double kMec2Kev = 510.99895;
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kComptonNodes = 16385;  // nodes of the cos(psi) table on [-1, 1]
+
+// Path-sum tile: TJ events x TN support pixels per CTA, MC scatter pixels
+// staged per step, 256 threads each holding 8 events x 4 pixels.
+constexpr int kTJ = 64;
+constexpr int kTN = 128;
+constexpr int kMC = 32;
+constexpr int kBuildThreads = 256;
+
+}  // namespace lmosem
+
+struct lmosem_ctx {
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+
+    // problem statement
+    int nx = 0, ny = 0, npix = 0;
+    double dpx = 0;
+    int n_angles = 0, n_bins = 0;
+    double angle0 = 0, bin_mm = 0, radius = 0, fwhm0 = 0, fwhm_slope = 0;
+    double e0 = 0, fwhm_frac = 0, e_lo = 0, e_hi = 0;
+    float k_sigma = 6.0f;
+    int64_t table_budget = int64_t(4) << 30;
+
+    int n_sup = 0, n_scat = 0, ld_w = 0;  // ld_w: support padded to kTN
+    std::vector<int32_t> h_sup, h_scat;
+    double kbar = 0;      // circle mean of the Klein-Nishina shape at E0
+    double de0 = 0;       // energy-window mass of the photopeak
+
+    // device: problem and attenuation tables
+    float* d_mu = nullptr;        // npix
+    int32_t* d_sup = nullptr;     // n_sup
+    int32_t* d_scat = nullptr;    // n_scat
+    float2* d_trig = nullptr;     // n_angles: (cos, sin) theta_a
+    float* d_l_edge = nullptr;    // n_angles x npix: mu(E0) integral pixel centre -> edge
+    float* d_l_pair = nullptr;    // n_scat x n_sup: integral scatter centre <-> support centre
+    float2* d_compton = nullptr;  // kComptonNodes: (sigma_KN(E')/sigma_KN(E0), window mass at E')
+    float4* d_mpar = nullptr;     // n_angles x n_scat: (u_m, q_m, lq_m, cut_m)
+    float4* d_ppar = nullptr;     // n_angles x ld_w:  (u_n, q_n, lp_n, D_u(n))
+    float* d_du_m = nullptr;      // n_angles x n_scat: detector-extent mass D_u at m
+
+    // sensitivity
+    int sens_subsets = 0;
+    double* d_sens = nullptr;     // sens_subsets x n_sup
+    double* d_sens_angle = nullptr;  // n_angles x n_sup (per-angle partials)
+
+    // model
+    int fmt = -1;
+    int64_t J = 0;
+    int n_subsets = 0;
+    int64_t ld_model = 0;         // row stride in elements
+    void* d_model = nullptr;
+    float* d_scale = nullptr;     // J row scales (scaled forms)
+    float* d_stage = nullptr;     // FP32 staging rows for the scaled forms
+    int64_t stage_rows = 0;
+    int32_t* d_perm = nullptr;    // sorted row -> caller's event index
+    int64_t* d_rank = nullptr;    // caller's event index -> sorted row
+    float* d_u_s = nullptr;       // sorted positions
+    float* d_e_s = nullptr;       // sorted energies
+    int32_t* d_a_s = nullptr;     // sorted angles
+    std::vector<int64_t> h_angle_row0, h_angle_cnt;  // per angle (sorted rows)
+    std::vector<int64_t> h_subset_row0;              // n_subsets + 1
+    int32_t* d_angle_row0 = nullptr;
+    int32_t* d_angle_cnt = nullptr;
+    int32_t* d_tile_prefix = nullptr;                // n_angles + 1 cumulative event tiles
+    std::vector<int32_t> h_tile_prefix;
+    float2* d_wtab = nullptr;     // scatter-weight tables of one angle group
+    int64_t wtab_bytes = 0;
+
+    // iteration scratch
+    int pass_ctas = 0;
+    float* d_bpart = nullptr;     // pass_ctas x n_sup
+    double* d_llpart = nullptr;   // pass_ctas
+    double* d_scalar = nullptr;   // small FP64 scratch
+
+    // kernel timing (opts->profile)
+    bool profile = false;
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> prof_pool;
+    cudaEvent_t prof_open = nullptr;
+};
+
+namespace lmosem {
+
+lmosem_status fail(lmosem_ctx* c, lmosem_status st, const std::string& msg);
+lmosem_status cuda_fail(lmosem_ctx* c, cudaError_t e, const char* what);
+
+#define LMOSEM_CK(ctx, call)                                           \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::lmosem::cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Every kernel launch is followed by LMOSEM_LAUNCHED(ctx, class); with
+// profiling on, LMOSEM_PROF_BEGIN(ctx) precedes it.
+void prof_begin(lmosem_ctx* c);
+void prof_end(lmosem_ctx* c, int cls);
+
+#define LMOSEM_PROF_BEGIN(ctx)                       \
+    do {                                             \
+        if ((ctx)->profile) ::lmosem::prof_begin(ctx); \
+    } while (0)
+
+#define LMOSEM_LAUNCHED(ctx, cls)                                              \
+    do {                                                                       \
+        (ctx)->launches++;                                                     \
+        if ((ctx)->profile) ::lmosem::prof_end(ctx, cls);                      \
+        cudaError_t e_ = cudaGetLastError();                                   \
+        if (e_ != cudaSuccess) return ::lmosem::cuda_fail(ctx, e_, "launch");  \
+    } while (0)
+
+template <typename T>
+lmosem_status dev_alloc(lmosem_ctx* c, T** p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, LMOSEM_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+                                          " bytes failed: " + cudaGetErrorString(e));
+    }
+    return LMOSEM_OK;
+}
+
+template <typename T>
+void dev_free(T** p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+// ---- host entry points implemented in the other translation units
+lmosem_status build_tables(lmosem_ctx* c);                      // siddon.cu
+lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
+                          const float* d_e, int64_t n, int n_subsets);  // sort.cu
+lmosem_status build_model_rows(lmosem_ctx* c);                  // model.cu
+lmosem_status compute_sensitivity(lmosem_ctx* c, int n_subsets);  // sens.cu
+lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll);
+lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out);
+lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f);
+lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float* out);
+lmosem_status setup_pass(lmosem_ctx* c);                        // osem.cu
+
+// ---- device helpers shared by the CUDA translation units
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float pixel_x(int pix, int nx, float dpx) {
+    return ((float)(pix % nx) + 0.5f - 0.5f * (float)nx) * dpx;
+}
+__device__ __forceinline__ float pixel_y(int pix, int nx, int ny, float dpx) {
+    return ((float)(pix / nx) + 0.5f - 0.5f * (float)ny) * dpx;
+}
+
+// Linear interpolation of the cos(psi) table.
+__device__ __forceinline__ float2 compton_lookup(const float2* tab, float c) {
+    float x = (c + 1.0f) * (0.5f * (float)(kComptonNodes - 1));
+    x = fminf(fmaxf(x, 0.0f), (float)(kComptonNodes - 1));
+    int i = min((int)x, kComptonNodes - 2);
+    float fr = x - (float)i;
+    float2 a = __ldg(tab + i), b = __ldg(tab + i + 1);
+    return make_float2(fmaf(fr, b.x - a.x, a.x), fmaf(fr, b.y - a.y, a.y));
+}
+
+// Geometry of one scatter path (n -> m at angle a): cos of the deflection
+// angle and 1/|p_m - p_n|.  Returns false when m == n.
+__device__ __forceinline__ bool path_geometry(int pix_n, int pix_m, int nx, int ny, float dpx,
+                                              float2 trig, float* cpsi, float* rinv) {
+    if (pix_n == pix_m) return false;
+    float vx = pixel_x(pix_m, nx, dpx) - pixel_x(pix_n, nx, dpx);
+    float vy = pixel_y(pix_m, nx, ny, dpx) - pixel_y(pix_n, nx, ny, dpx);
+    float ri = rsqrtf(fmaf(vx, vx, vy * vy));
+    float c = (vx * trig.x + vy * trig.y) * ri;
+    *cpsi = fminf(fmaxf(c, -1.0f), 1.0f);
+    *rinv = ri;
+    return true;
+}
+
+// Compton kinematics at the photopeak: P = E'/E0 and the in-plane
+// Klein-Nishina weight K(psi)/Kbar.
+__device__ __forceinline__ void compton(float cpsi, float eps0, float inv_kbar, float* P, float* kt) {
+    float inv_p = fmaf(eps0, 1.0f - cpsi, 1.0f);
+    float p = 1.0f / inv_p;
+    float sin2 = fmaf(-cpsi, cpsi, 1.0f);
+    *P = p;
+    *kt = 0.5f * p * p * (p + inv_p - sin2) * inv_kbar;
+}
+
+}  // namespace lmosem

@@ -1,0 +1,456 @@
+// System-model build (rows a2-a5 of the hot path): the per-event path sum
+//
+//   p_jn = w_0(n) k_0(u_j, E_j | n)
+//        + sum_{m in strip(j)} U_jm W_a(n, m) phi(E_j; E'_a(n, m), sigma_E(E'))
+//
+// of paper Eq. 2 with Eq. 4 (pr(A_j|P) s_eff(P) summed over the primary path
+// (n) and the first-order in-plane scatter paths (n, m), Section 2.2), where
+// U_jm = phi(u_j; u_a(m), sigma_u(d_a(m))) is the collimator response at the
+// scatter pixel, W_a(n, m) the attenuated, Klein-Nishina-weighted scatter
+// weight and E' the Compton energy.  The denominator of Eq. 8 is y_j =
+// sum_n p_jn f_n, so caching p turns every OSEM sub-iteration into a
+// streaming pass.
+//
+// Per angle a, (E', lw) with lw = log2(W / (sigma_E(E') sqrt(2 pi))) is
+// tabulated for every (m, n); every term is then
+//     U_jm * 2^(lw - ((E_j - E') s)^2),   s = sqrt(log2 e / 2) / sigma_E(E'),
+// i.e. three FP32 FMAs and one MUFU ex2.  A CTA owns 64 events of one angle
+// (consecutive in position) x 128 support pixels and walks the scatter
+// pixels whose kernel reaches any of its events (|u_j - u_m| <= k_sigma
+// sigma_u(m)); terms outside that cut for a given event are set to zero.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "lmosem_internal.cuh"
+
+namespace lmosem {
+
+namespace {
+
+struct WTabArgs {
+    int nx, ny, npix;
+    float dpx;
+    const int32_t* sup;
+    int n_sup, ld_w;
+    const int32_t* scat;
+    int n_scat;
+    const float* mu;
+    const float2* trig;
+    const float* l_edge;
+    const float* l_pair;
+    const float2* compton;
+    const int32_t* slot_angle;  // angle of each sorted slot
+    int s0;                     // first slot of the group
+    float eps0, inv_kbar, e0;
+    float w_const;              // D^2 / (2 pi sqrt(2 pi kappa)), sigma_E^2 = kappa E
+    float2* wtab;               // [slot - s0][m][ld_w]
+};
+
+// (E', lw) of the scatter path (n, m) at the angle of one slot
+__global__ void k_wtable(WTabArgs A) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = blockIdx.y;
+    int g = blockIdx.z;
+    if (n >= A.ld_w) return;
+    float2 out = make_float2(A.e0, -INFINITY);
+    if (n < A.n_sup) {
+        int a = A.slot_angle[A.s0 + g];
+        int pn = A.sup[n], pm = A.scat[k];
+        float cpsi, rinv;
+        if (path_geometry(pn, pm, A.nx, A.ny, A.dpx, A.trig[a], &cpsi, &rinv)) {
+            float P, kt;
+            compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
+            float e1 = A.e0 * P;
+            float ratio = compton_lookup(A.compton, cpsi).x;
+            float att = A.l_pair[(size_t)k * A.n_sup + n] + ratio * A.l_edge[(size_t)a * A.npix + pm];
+            float lw = log2f(A.w_const * A.mu[pm] * kt * rinv * rsqrtf(e1)) - att * kLog2e;
+            out = make_float2(e1, lw);
+        }
+    }
+    A.wtab[((size_t)g * A.n_scat + k) * A.ld_w + n] = out;
+}
+
+struct PathSumArgs {
+    const float* u_s;
+    const float* e_s;
+    const int32_t* slot_angle;
+    const int32_t* tile_prefix;  // per slot, cumulative event tiles
+    const int32_t* angle_row0;
+    const int32_t* angle_cnt;
+    int s0, s1;                  // slot range of the group
+    int n_ptiles;
+    const float2* wtab;
+    int ld_w, n_scat;
+    const float4* mpar;          // [a][m]
+    const float4* ppar;          // [a][n]
+    float cE;                    // s = cE / sqrt(E')
+    float e0, sE0, lE0;          // primary energy factor 2^(lE0 - ((E - e0) sE0)^2)
+    float* out;                  // FP32 rows
+    int64_t ld_out;
+    int64_t row_base;            // out row = sorted row - row_base
+    int n_store;                 // columns to store (padded row width)
+};
+
+__global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    float* sU = sm;                          // [kMC][kTJ]
+    float* sS = sU + kMC * kTJ;              // [kMC][kTN]
+    float* sB = sS + kMC * kTN;
+    float* sW = sB + kMC * kTN;
+    float* ev_u = sW + kMC * kTN;            // [kTJ]
+    float* ev_e = ev_u + kTJ;                // [kTJ]
+    int* misc = reinterpret_cast<int*>(ev_e + kTJ);  // [16]
+    int* mlist = misc + 16;                  // [n_scat]
+    float* red = reinterpret_cast<float*>(misc);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int et = blockIdx.x / A.n_ptiles, pt = blockIdx.x % A.n_ptiles;
+
+    // slot of this event tile
+    const int T = A.tile_prefix[A.s0] + et;
+    int lo = A.s0, hi = A.s1 - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (A.tile_prefix[mid] <= T) lo = mid; else hi = mid - 1;
+    }
+    const int slot = lo;
+    const int a = A.slot_angle[slot];
+    const int tile = T - A.tile_prefix[slot];
+    const int64_t r0 = (int64_t)A.angle_row0[a] + (int64_t)tile * kTJ;
+    const int nr = min(kTJ, A.angle_cnt[a] - tile * kTJ);
+    const int n0 = pt * kTN;
+
+    if (tid < kTJ) {
+        ev_u[tid] = tid < nr ? A.u_s[r0 + tid] : 1e30f;
+        ev_e[tid] = tid < nr ? A.e_s[r0 + tid] : 0.0f;
+    }
+    __syncthreads();
+    // position range of the tile's events
+    if (warp == 0) {
+        float mn = INFINITY, mx = -INFINITY;
+        for (int j = lane; j < nr; j += 32) {
+            mn = fminf(mn, ev_u[j]);
+            mx = fmaxf(mx, ev_u[j]);
+        }
+        for (int o = 16; o; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            red[8] = mn;
+            red[9] = mx;
+        }
+    }
+    __syncthreads();
+    const float umin = red[8], umax = red[9];
+    __syncthreads();
+
+    // scatter pixels whose cut interval reaches the tile (block compaction)
+    const float4* mp_a = A.mpar + (size_t)a * A.n_scat;
+    int nm = 0;
+    for (int m0 = 0; m0 < A.n_scat; m0 += kBuildThreads) {
+        int m = m0 + tid;
+        bool in = false;
+        if (m < A.n_scat) {
+            float4 mp = __ldg(mp_a + m);
+            in = (mp.x + mp.w >= umin) && (mp.x - mp.w <= umax);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) misc[warp] = __popc(bal);
+        __syncthreads();
+        int off = nm, total = 0;
+        for (int w = 0; w < kBuildThreads / 32; ++w) {
+            int cw = misc[w];
+            if (w < warp) off += cw;
+            total += cw;
+        }
+        if (in) mlist[off + __popc(bal & ((1u << lane) - 1u))] = m;
+        __syncthreads();
+        nm += total;
+    }
+
+    // accumulators, initialised with the primary path
+    float E[8];
+    float acc[8][4];
+    {
+        const float4* pp_a = A.ppar + (size_t)a * A.ld_w + n0 + 4 * lane;
+        float4 pp[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pp[q] = __ldg(pp_a + q);
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            float uj = ev_u[8 * warp + jj];
+            float ej = ev_e[8 * warp + jj];
+            E[jj] = ej;
+            float te = (ej - A.e0) * A.sE0;
+            float le = fmaf(-te, te, A.lE0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float t = (uj - pp[q].x) * pp[q].y;
+                acc[jj][q] = ex2_approx(fmaf(-t, t, pp[q].z + le));
+            }
+        }
+    }
+
+    const float2* wt = A.wtab + (size_t)(slot - A.s0) * A.n_scat * A.ld_w + n0;
+    for (int c0 = 0; c0 < nm; c0 += kMC) {
+        // stage U[mc][j]
+        {
+            const int j = tid & (kTJ - 1);
+            const float uj = ev_u[j];
+#pragma unroll
+            for (int k = 0; k < kMC * kTJ / kBuildThreads; ++k) {
+                int mc = (tid >> 6) + 4 * k;
+                float U = 0.0f;
+                if (c0 + mc < nm) {
+                    float4 mp = __ldg(mp_a + mlist[c0 + mc]);
+                    float d = uj - mp.x;
+                    float z = d * mp.y;
+                    U = fabsf(d) <= mp.w ? ex2_approx(fmaf(-z, z, mp.z)) : 0.0f;
+                }
+                sU[mc * kTJ + j] = U;
+            }
+        }
+        // stage s, b, lw for [mc][n]
+        {
+            const int n = tid & (kTN - 1);
+#pragma unroll 4
+            for (int k = 0; k < kMC * kTN / kBuildThreads; ++k) {
+                int mc = (tid >> 7) + 2 * k;
+                float s = 0.0f, b = 0.0f, lw = -INFINITY;
+                if (c0 + mc < nm) {
+                    float2 w2 = __ldg(wt + (size_t)mlist[c0 + mc] * A.ld_w + n);
+                    s = A.cE * rsqrtf(w2.x);
+                    b = -w2.x * s;
+                    lw = w2.y;
+                }
+                sS[mc * kTN + n] = s;
+                sB[mc * kTN + n] = b;
+                sW[mc * kTN + n] = lw;
+            }
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int mc = 0; mc < kMC; ++mc) {
+            float4 u0 = *reinterpret_cast<const float4*>(sU + mc * kTJ + 8 * warp);
+            float4 u1 = *reinterpret_cast<const float4*>(sU + mc * kTJ + 8 * warp + 4);
+            float4 s4 = *reinterpret_cast<const float4*>(sS + mc * kTN + 4 * lane);
+            float4 b4 = *reinterpret_cast<const float4*>(sB + mc * kTN + 4 * lane);
+            float4 w4 = *reinterpret_cast<const float4*>(sW + mc * kTN + 4 * lane);
+            const float U[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            const float S[4] = {s4.x, s4.y, s4.z, s4.w};
+            const float B[4] = {b4.x, b4.y, b4.z, b4.w};
+            const float W[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float t = fmaf(E[jj], S[q], B[q]);
+                    float x = fmaf(-t, t, W[q]);
+                    acc[jj][q] = fmaf(U[jj], ex2_approx(x), acc[jj][q]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // store the tile (columns past the support are exact zeros)
+    const int n = n0 + 4 * lane;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        int j = 8 * warp + jj;
+        if (j >= nr) continue;
+        float* row = A.out + (r0 + j - A.row_base) * A.ld_out;
+        if (n + 3 < A.n_store) {
+            *reinterpret_cast<float4*>(row + n) = make_float4(acc[jj][0], acc[jj][1], acc[jj][2], acc[jj][3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (n + q < A.n_store) row[n + q] = acc[jj][q];
+        }
+    }
+}
+
+// Row scaling and rounding of FP32 staged rows: p_jn = c_j h_jn with
+// max_n h_jn = hmax (2^15 for FP16 keeps entries down to ~2e-9 of the row
+// maximum in the normal range; 1 for BF16).  The scale cancels in the EM
+// update (paper Eq. 8: y_j and p_jq scale together) and enters only the
+// log-likelihood.
+template <typename H>
+__global__ void k_quantize(const float* __restrict__ stage, int64_t ld_stage, int64_t rows,
+                           int n_cols, int64_t ld_out, H* __restrict__ out, int64_t row0,
+                           float* __restrict__ scale, float hmax) {
+    int warps = blockDim.x >> 5;
+    int64_t r = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float* src = stage + r * ld_stage;
+    float mx = 0.0f;
+    for (int n = lane; n < n_cols; n += 32) mx = fmaxf(mx, src[n]);
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float c = mx > 0.0f ? mx / hmax : 1.0f;
+    float ic = 1.0f / c;
+    H* dst = out + (row0 + r) * ld_out;
+    for (int n = lane; n < ld_out; n += 32) {
+        float v = n < n_cols ? src[n] * ic : 0.0f;
+        if constexpr (std::is_same<H, __half>::value)
+            dst[n] = __float2half_rn(v);
+        else
+            dst[n] = __float2bfloat16_rn(v);
+    }
+    if (lane == 0) scale[row0 + r] = c;
+}
+
+}  // namespace
+
+lmosem_status build_model_rows(lmosem_ctx* c) {
+    lmosem_status st;
+    const int n_ptiles = c->ld_w / kTN;
+    const int group = (c->n_angles + c->n_subsets - 1) / c->n_subsets;
+    const int n_slots = c->n_subsets * group;
+
+    // slots in sorted order and their angles (empty slots are skipped)
+    std::vector<int32_t> slot_angle, tile_prefix(1, 0), row0(c->n_angles), cnt(c->n_angles);
+    for (int s = 0; s < n_slots; ++s) {
+        int a = (s / group) + c->n_subsets * (s % group);
+        if (a >= c->n_angles) continue;
+        slot_angle.push_back(a);
+        tile_prefix.push_back(tile_prefix.back() + (int32_t)((c->h_angle_cnt[a] + kTJ - 1) / kTJ));
+    }
+    for (int a = 0; a < c->n_angles; ++a) {
+        row0[a] = (int32_t)c->h_angle_row0[a];
+        cnt[a] = (int32_t)c->h_angle_cnt[a];
+    }
+    const int ns = (int)slot_angle.size();
+    int32_t* d_slot_angle = nullptr;
+    if ((st = dev_alloc(c, &d_slot_angle, ns))) return st;
+    if ((st = dev_alloc(c, &c->d_tile_prefix, ns + 1))) return st;
+    if ((st = dev_alloc(c, &c->d_angle_row0, c->n_angles))) return st;
+    if ((st = dev_alloc(c, &c->d_angle_cnt, c->n_angles))) return st;
+    LMOSEM_CK(c, cudaMemcpyAsync(d_slot_angle, slot_angle.data(), ns * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_tile_prefix, tile_prefix.data(), (ns + 1) * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_angle_row0, row0.data(), c->n_angles * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_angle_cnt, cnt.data(), c->n_angles * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+
+    // angle groups bounded by the scatter-table budget
+    const int64_t per_angle = (int64_t)c->n_scat * c->ld_w * sizeof(float2);
+    int gsz = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
+    if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * c->n_scat * c->ld_w))) return st;
+
+    const bool scaled = c->fmt != LMOSEM_MODEL_FP32;
+    int64_t max_group_rows = 0;
+    for (int s0 = 0; s0 < ns; s0 += gsz) {
+        int s1 = std::min(ns, s0 + gsz);
+        int64_t rows = 0;
+        for (int s = s0; s < s1; ++s) rows += c->h_angle_cnt[slot_angle[s]];
+        max_group_rows = std::max(max_group_rows, rows);
+    }
+    if (scaled) {
+        if ((st = dev_alloc(c, &c->d_stage, (size_t)std::max<int64_t>(1, max_group_rows) * c->ld_model)))
+            return st;
+    }
+
+    const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;  // sigma_E^2 = kappa E
+    const double se0 = sqrt(kappa * c->e0);
+    const size_t smem = sizeof(float) * ((size_t)kMC * kTJ + 3 * (size_t)kMC * kTN + 2 * kTJ) +
+                        sizeof(int) * (16 + (size_t)c->n_scat);
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+
+    for (int s0 = 0; s0 < ns; s0 += gsz) {
+        int s1 = std::min(ns, s0 + gsz);
+        WTabArgs W;
+        W.nx = c->nx;
+        W.ny = c->ny;
+        W.npix = c->npix;
+        W.dpx = (float)c->dpx;
+        W.sup = c->d_sup;
+        W.n_sup = c->n_sup;
+        W.ld_w = c->ld_w;
+        W.scat = c->d_scat;
+        W.n_scat = c->n_scat;
+        W.mu = c->d_mu;
+        W.trig = c->d_trig;
+        W.l_edge = c->d_l_edge;
+        W.l_pair = c->d_l_pair;
+        W.compton = c->d_compton;
+        W.slot_angle = d_slot_angle;
+        W.s0 = s0;
+        W.eps0 = (float)(c->e0 / kMec2Kev);
+        W.inv_kbar = (float)(1.0 / c->kbar);
+        W.e0 = (float)c->e0;
+        W.w_const = (float)(c->dpx * c->dpx / (2.0 * kPi * sqrt(2.0 * kPi * kappa)));
+        W.wtab = c->d_wtab;
+        LMOSEM_PROF_BEGIN(c);
+        k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, s1 - s0), 256, 0, c->stream>>>(W);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
+
+        int tiles = tile_prefix[s1] - tile_prefix[s0];
+        if (tiles == 0) continue;
+        int64_t grow0 = c->h_angle_row0[slot_angle[s0]];
+        int64_t grows = 0;
+        for (int s = s0; s < s1; ++s) grows += c->h_angle_cnt[slot_angle[s]];
+        PathSumArgs P;
+        P.u_s = c->d_u_s;
+        P.e_s = c->d_e_s;
+        P.slot_angle = d_slot_angle;
+        P.tile_prefix = c->d_tile_prefix;
+        P.angle_row0 = c->d_angle_row0;
+        P.angle_cnt = c->d_angle_cnt;
+        P.s0 = s0;
+        P.s1 = s1;
+        P.n_ptiles = n_ptiles;
+        P.wtab = c->d_wtab;
+        P.ld_w = c->ld_w;
+        P.n_scat = c->n_scat;
+        P.mpar = c->d_mpar;
+        P.ppar = c->d_ppar;
+        P.cE = (float)sqrt(1.4426950408889634 / (2.0 * kappa));
+        P.e0 = (float)c->e0;
+        P.sE0 = (float)(0.8493218002880191 / se0);
+        P.lE0 = (float)(-log2(se0 * sqrt(2.0 * kPi)));
+        P.ld_out = c->ld_model;
+        P.n_store = (int)c->ld_model;
+        if (scaled) {
+            P.out = c->d_stage;
+            P.row_base = grow0;
+        } else {
+            P.out = reinterpret_cast<float*>(c->d_model);
+            P.row_base = 0;
+        }
+        LMOSEM_PROF_BEGIN(c);
+        k_pathsum<<<(unsigned)((int64_t)tiles * n_ptiles), kBuildThreads, smem, c->stream>>>(P);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
+        if (scaled) {
+            const int qthreads = 256;
+            unsigned qblocks = (unsigned)((grows + qthreads / 32 - 1) / (qthreads / 32));
+            LMOSEM_PROF_BEGIN(c);
+            if (c->fmt == LMOSEM_MODEL_FP16_SCALED)
+                k_quantize<__half><<<qblocks, qthreads, 0, c->stream>>>(
+                    c->d_stage, c->ld_model, grows, c->n_sup, c->ld_model,
+                    reinterpret_cast<__half*>(c->d_model), grow0, c->d_scale, 32768.0f);
+            else
+                k_quantize<__nv_bfloat16><<<qblocks, qthreads, 0, c->stream>>>(
+                    c->d_stage, c->ld_model, grows, c->n_sup, c->ld_model,
+                    reinterpret_cast<__nv_bfloat16*>(c->d_model), grow0, c->d_scale, 1.0f);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_QUANTIZE);
+        }
+    }
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    dev_free(&d_slot_angle);
+    dev_free(&c->d_wtab);
+    dev_free(&c->d_stage);
+    return LMOSEM_OK;
+}
+
+}  // namespace lmosem

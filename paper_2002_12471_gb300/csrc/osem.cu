@@ -1,0 +1,397 @@
+// OS-LM-MLEM iterations on the cached model (rows a7-a8 of the hot path).
+//
+// Paper Eq. 8 gives the E-step zbar_{j,P_q} = f_q p_jq / y_j with
+// y_j = sum_n p_jn f_n, and Eq. 7 the subset update
+//     f_q <- sum_{j in S_i} zbar_{j,P_q} / (T s^i_q) = f_q b_q / (T s^i_q),
+//     b_q = sum_{j in S_i, y_j > 0} p_jq / y_j.
+// Each sub-iteration is one streaming pass over the subset's model rows:
+// every row is loaded once from HBM into registers, y_j is formed by a CTA
+// reduction, and the same registers are back-projected into the CTA's
+// private b (registers, FP32).  A second kernel reduces the per-CTA b in
+// CTA order (deterministic) and applies the update with T s^i_q formed in
+// FP64.  The log-likelihood of Eq. 3 (without log J!) is reduced in FP64.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "lmosem_internal.cuh"
+
+namespace lmosem {
+
+namespace {
+
+constexpr int kMaxPassThreads = 256;
+
+// 16-byte vector of model elements -> floats
+template <typename H>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int N = 4;
+    __device__ static void load(const float* p, float* out) {
+        float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    }
+};
+template <>
+struct Vec<__half> {
+    static constexpr int N = 8;
+    __device__ static void load(const __half* p, float* out) {
+        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __half22float2(h[k]);
+            out[2 * k] = f.x;
+            out[2 * k + 1] = f.y;
+        }
+    }
+};
+template <>
+struct Vec<__nv_bfloat16> {
+    static constexpr int N = 8;
+    __device__ static void load(const __nv_bfloat16* p, float* out) {
+        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __bfloat1622float2(h[k]);
+            out[2 * k] = f.x;
+            out[2 * k + 1] = f.y;
+        }
+    }
+};
+
+struct PassArgs {
+    const void* model;
+    int64_t ld;              // row stride, elements
+    int64_t r0, r1;          // rows of this pass
+    int64_t rows_per_cta;
+    const float* f;
+    const float* scale;      // row scales (scaled forms) or nullptr
+    int n_sup;
+    double T;
+    int back;                // 1: accumulate b; 0: log-likelihood only
+    float* bpart;            // [cta][n_sup]
+    double* llpart;          // [cta]
+};
+
+// One pass over rows [r0, r1): thread t owns the 16-byte column vectors
+// t, t + NT, ... (VPT of them); R rows are in flight per thread.
+template <typename H, int VPT, int R>
+__global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
+    constexpr int EPV = Vec<H>::N;
+    __shared__ float red[2][R][kMaxPassThreads / 32];
+    __shared__ double llred[kMaxPassThreads / 32];
+    const int NT = blockDim.x, NW = NT >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const H* model = reinterpret_cast<const H*>(A.model);
+
+    float fr[VPT][EPV], br[VPT][EPV];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        int col0 = EPV * (t + NT * v);
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) {
+            int col = col0 + e;
+            fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
+            br[v][e] = 0.0f;
+        }
+    }
+    const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
+    const int64_t re = min(A.r1, rb + A.rows_per_cta);
+    double ll = 0.0;
+    int buf = 0;
+    for (int64_t r = rb; r < re; r += R) {
+        float p[R][VPT][EPV];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const bool ok = r + i < re;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                int64_t col0 = (int64_t)EPV * (t + NT * v);
+                if (ok && col0 < A.ld) {
+                    Vec<H>::load(model + (r + i) * A.ld + col0, p[i][v]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e) p[i][v][e] = 0.0f;
+                }
+            }
+        }
+        float d[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            float s = 0.0f;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v)
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) s = fmaf(p[i][v][e], fr[v][e], s);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            d[i] = s;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) red[buf][i][warp] = d[i];
+        }
+        __syncthreads();
+        float inv[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            float y = 0.0f;
+            for (int w = 0; w < NW; ++w) y += red[buf][i][w];
+            const bool ok = r + i < re && y > 0.0f;
+            inv[i] = ok ? 1.0f / y : 0.0f;
+            if (ok && t == i) {
+                double c = A.scale ? (double)A.scale[r + i] : 1.0;
+                ll += log(A.T * c * (double)y);
+            }
+        }
+        if (A.back) {
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int v = 0; v < VPT; ++v)
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e) br[v][e] = fmaf(p[i][v][e], inv[i], br[v][e]);
+        }
+        buf ^= 1;
+    }
+    if (A.back) {
+        float* bp = A.bpart + (size_t)blockIdx.x * A.n_sup;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            int col0 = EPV * (t + NT * v);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e)
+                if (col0 + e < A.n_sup) bp[col0 + e] = br[v][e];
+        }
+    }
+    // per-CTA log-likelihood partial, fixed order
+    for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+    if (lane == 0) llred[warp] = ll;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += llred[w];
+        A.llpart[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_update(const float* __restrict__ bpart, int nparts, int n_sup,
+                         float* __restrict__ f, const double* __restrict__ sens_i, double T) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_sup) return;
+    float b = 0.0f;
+    for (int c = 0; c < nparts; ++c) b += bpart[(size_t)c * n_sup + n];
+    double s = sens_i[n];
+    float ts = (float)(T * s);
+    f[n] = s > 0.0 ? f[n] * b / ts : 0.0f;
+}
+
+// loglik = sum of the per-CTA partials - T sum_q s_q f_q (FP64, one block)
+__global__ void k_ll_final(const double* __restrict__ llpart, int nparts,
+                           const double* __restrict__ s_total, const float* __restrict__ f,
+                           int n_sup, double T, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < n_sup; n += blockDim.x) acc += s_total[n] * (double)f[n];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sf = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) sf += sh[k];
+        double ll = 0.0;
+        for (int k = 0; k < nparts; ++k) ll += llpart[k];
+        *out = ll - T * sf;
+    }
+}
+
+__global__ void k_init_image(const double* __restrict__ s_total, int n_sup, double J, double T,
+                             float* __restrict__ f) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < n_sup; n += blockDim.x) acc += s_total[n];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) s += sh[k];
+        sh[0] = s;
+    }
+    __syncthreads();
+    float v = (float)(J / (T * sh[0]));
+    for (int n = threadIdx.x; n < n_sup; n += blockDim.x) f[n] = v;
+}
+
+template <typename H>
+__global__ void k_model_rows(const H* __restrict__ model, int64_t ld, const float* __restrict__ scale,
+                             const int64_t* __restrict__ rank, const int64_t* __restrict__ ids,
+                             int64_t n, int n_sup, float* __restrict__ out) {
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n_sup) return;
+    for (int64_t k = blockIdx.y; k < n; k += gridDim.y) {
+        int64_t r = rank[ids[k]];
+        float v;
+        if constexpr (std::is_same<H, float>::value) v = model[r * ld + col];
+        else if constexpr (std::is_same<H, __half>::value) v = __half2float(model[r * ld + col]);
+        else v = __bfloat162float(model[r * ld + col]);
+        if (scale) v *= scale[r];
+        out[k * n_sup + col] = v;
+    }
+}
+
+struct PassShape {
+    int vpt, r, nt;
+};
+
+PassShape pass_shape(const lmosem_ctx* c) {
+    int epv = c->fmt == LMOSEM_MODEL_FP32 ? 4 : 8;
+    int64_t nvec = (c->ld_model + epv - 1) / epv;
+    const int opts[] = {1, 2, 3, 4, 6, 8};
+    int vpt = 8;
+    for (int v : opts)
+        if ((nvec + v - 1) / v <= kMaxPassThreads) {
+            vpt = v;
+            break;
+        }
+    int nt = (int)(((nvec + vpt - 1) / vpt + 31) / 32 * 32);
+    return {vpt, vpt <= 2 ? 4 : 2, nt};
+}
+
+template <typename H, int VPT, int R>
+lmosem_status launch_pass_t(lmosem_ctx* c, const PassArgs& A, int grid, int nt) {
+    LMOSEM_PROF_BEGIN(c);
+    k_pass<H, VPT, R><<<grid, nt, 0, c->stream>>>(A);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
+    return LMOSEM_OK;
+}
+
+template <typename H>
+lmosem_status launch_pass_h(lmosem_ctx* c, const PassArgs& A, int grid, PassShape s) {
+    switch (s.vpt) {
+        case 1: return launch_pass_t<H, 1, 4>(c, A, grid, s.nt);
+        case 2: return launch_pass_t<H, 2, 4>(c, A, grid, s.nt);
+        case 3: return launch_pass_t<H, 3, 2>(c, A, grid, s.nt);
+        case 4: return launch_pass_t<H, 4, 2>(c, A, grid, s.nt);
+        case 6: return launch_pass_t<H, 6, 2>(c, A, grid, s.nt);
+        default: return launch_pass_t<H, 8, 2>(c, A, grid, s.nt);
+    }
+}
+
+lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f, double T, int back) {
+    PassShape s = pass_shape(c);
+    int64_t rows = r1 - r0;
+    int64_t grid = std::min<int64_t>(c->pass_ctas, std::max<int64_t>(1, (rows + s.r - 1) / s.r));
+    PassArgs A;
+    A.model = c->d_model;
+    A.ld = c->ld_model;
+    A.r0 = r0;
+    A.r1 = r1;
+    A.rows_per_cta = (rows + grid - 1) / grid;
+    A.rows_per_cta = (A.rows_per_cta + s.r - 1) / s.r * s.r;
+    grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
+    A.f = f;
+    A.scale = c->fmt == LMOSEM_MODEL_FP32 ? nullptr : c->d_scale;
+    A.n_sup = c->n_sup;
+    A.T = T;
+    A.back = back;
+    A.bpart = c->d_bpart;
+    A.llpart = c->d_llpart;
+    // unused partial slots read as zero by the reduction
+    if (back && grid < c->pass_ctas)
+        LMOSEM_CK(c, cudaMemsetAsync(c->d_bpart + (size_t)grid * c->n_sup, 0,
+                                     sizeof(float) * (size_t)(c->pass_ctas - grid) * c->n_sup,
+                                     c->stream));
+    if (grid < c->pass_ctas)
+        LMOSEM_CK(c, cudaMemsetAsync(c->d_llpart + grid, 0,
+                                     sizeof(double) * (size_t)(c->pass_ctas - grid), c->stream));
+    if (rows <= 0) {
+        if (back)
+            LMOSEM_CK(c, cudaMemsetAsync(c->d_bpart, 0, sizeof(float) * (size_t)c->n_sup, c->stream));
+        LMOSEM_CK(c, cudaMemsetAsync(c->d_llpart, 0, sizeof(double), c->stream));
+        return LMOSEM_OK;
+    }
+    if (c->fmt == LMOSEM_MODEL_FP32) return launch_pass_h<float>(c, A, (int)grid, s);
+    if (c->fmt == LMOSEM_MODEL_FP16_SCALED) return launch_pass_h<__half>(c, A, (int)grid, s);
+    return launch_pass_h<__nv_bfloat16>(c, A, (int)grid, s);
+}
+
+}  // namespace
+
+// grid of the streaming pass: resident CTAs on every SM
+lmosem_status setup_pass(lmosem_ctx* c) {
+    int dev = 0, sms = 0;
+    LMOSEM_CK(c, cudaGetDevice(&dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    c->pass_ctas = sms * 4;
+    lmosem_status st;
+    if ((st = dev_alloc(c, &c->d_bpart, (size_t)c->pass_ctas * c->n_sup))) return st;
+    if ((st = dev_alloc(c, &c->d_llpart, (size_t)c->pass_ctas))) return st;
+    return LMOSEM_OK;
+}
+
+lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll) {
+    lmosem_status st;
+    const double* s_total = c->d_sens + (size_t)c->n_subsets * c->n_sup;
+    for (int it = 0; it < n_iters; ++it) {
+        for (int i = 0; i < c->n_subsets; ++i) {
+            if ((st = launch_pass(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T, 1)))
+                return st;
+            LMOSEM_PROF_BEGIN(c);
+            k_update<<<(c->n_sup + 255) / 256, 256, 0, c->stream>>>(
+                c->d_bpart, c->pass_ctas, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+        }
+        if (d_ll) {
+            if ((st = launch_pass(c, 0, c->J, d_f, T, 0))) return st;
+            LMOSEM_PROF_BEGIN(c);
+            k_ll_final<<<1, 256, 0, c->stream>>>(c->d_llpart, c->pass_ctas, s_total, d_f, c->n_sup,
+                                                 T, d_ll + it);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+        }
+    }
+    return LMOSEM_OK;
+}
+
+lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out) {
+    lmosem_status st;
+    if ((st = launch_pass(c, 0, c->J, d_f, T, 0))) return st;
+    LMOSEM_PROF_BEGIN(c);
+    k_ll_final<<<1, 256, 0, c->stream>>>(c->d_llpart, c->pass_ctas,
+                                         c->d_sens + (size_t)c->n_subsets * c->n_sup, d_f,
+                                         c->n_sup, T, d_out);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+    return LMOSEM_OK;
+}
+
+lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f) {
+    LMOSEM_PROF_BEGIN(c);
+    k_init_image<<<1, 256, 0, c->stream>>>(c->d_sens + (size_t)c->sens_subsets * c->n_sup,
+                                           c->n_sup, (double)c->J, T, d_f);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
+    return LMOSEM_OK;
+}
+
+lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float* out) {
+    if (n <= 0) return LMOSEM_OK;
+    dim3 grid((c->n_sup + 255) / 256, (unsigned)std::min<int64_t>(n, 65535));
+    const float* sc = c->fmt == LMOSEM_MODEL_FP32 ? nullptr : c->d_scale;
+    LMOSEM_PROF_BEGIN(c);
+    if (c->fmt == LMOSEM_MODEL_FP32)
+        k_model_rows<float><<<grid, 256, 0, c->stream>>>((const float*)c->d_model, c->ld_model, sc,
+                                                         c->d_rank, ids, n, c->n_sup, out);
+    else if (c->fmt == LMOSEM_MODEL_FP16_SCALED)
+        k_model_rows<__half><<<grid, 256, 0, c->stream>>>((const __half*)c->d_model, c->ld_model, sc,
+                                                          c->d_rank, ids, n, c->n_sup, out);
+    else
+        k_model_rows<__nv_bfloat16><<<grid, 256, 0, c->stream>>>(
+            (const __nv_bfloat16*)c->d_model, c->ld_model, sc, c->d_rank, ids, n, c->n_sup, out);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
+    return LMOSEM_OK;
+}
+
+}  // namespace lmosem

@@ -1,0 +1,224 @@
+"""Python binding of the lmosem C ABI (``include/lmosem.h``).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of ``liblmosem.so``.  Functions keep the C names; a non-OK status
+raises :class:`LmosemError` with the library's message.  Device arrays are
+passed as torch CUDA tensors (or raw integer addresses); torch supplies
+device memory and streams and nothing else.  There is no CPU fallback: if
+the shared library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblmosem.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE, ENOTIMPL = range(8)
+MODEL_FP32, MODEL_FP16_SCALED, MODEL_BF16_SCALED = 0, 1, 2
+FORMATS = {"fp32": MODEL_FP32, "fp16": MODEL_FP16_SCALED, "bf16": MODEL_BF16_SCALED}
+
+
+class LmosemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_status_name(status), status, msg))
+        self.status = status
+
+
+class Object(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pixel_mm", ctypes.c_double),
+                ("h_mu_per_mm", ctypes.POINTER(ctypes.c_double)),
+                ("h_support", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_angles", ctypes.c_int32), ("angle0_rad", ctypes.c_double),
+                ("n_bins", ctypes.c_int32), ("bin_mm", ctypes.c_double),
+                ("radius_mm", ctypes.c_double), ("coll_fwhm0_mm", ctypes.c_double),
+                ("coll_fwhm_slope", ctypes.c_double)]
+
+
+class Energy(ctypes.Structure):
+    _fields_ = [("e0_kev", ctypes.c_double), ("fwhm_frac_e0", ctypes.c_double),
+                ("e_lo_kev", ctypes.c_double), ("e_hi_kev", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("k_sigma", ctypes.c_float), ("table_budget_bytes", ctypes.c_int64),
+                ("profile", ctypes.c_int32)]
+
+
+KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
+                  "other"]
+
+
+_vp = ctypes.c_void_p
+_i32, _i64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+# name -> (restype, argtypes); mirrors include/lmosem.h
+SIGNATURES = {
+    "lmosem_create": (ctypes.c_int, [ctypes.POINTER(Object), ctypes.POINTER(Geometry),
+                                     ctypes.POINTER(Energy), ctypes.POINTER(Options), _vp,
+                                     ctypes.POINTER(_vp)]),
+    "lmosem_destroy": (None, [_vp]),
+    "lmosem_last_error": (ctypes.c_char_p, [_vp]),
+    "lmosem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lmosem_n_support": (_i32, [_vp]),
+    "lmosem_n_scatter": (_i32, [_vp]),
+    "lmosem_support": (ctypes.c_int, [_vp, _vp]),
+    "lmosem_sensitivity": (ctypes.c_int, [_vp, _i32, _vp]),
+    "lmosem_build_model": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, ctypes.c_int]),
+    "lmosem_init_image": (ctypes.c_int, [_vp, _dbl, _vp]),
+    "lmosem_iterate": (ctypes.c_int, [_vp, _i32, _dbl, _vp, _vp]),
+    "lmosem_loglik": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
+    "lmosem_model_rows": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    "lmosem_model_bytes": (_i64, [_vp]),
+    "lmosem_launch_count": (_i64, [_vp]),
+    "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load ``liblmosem.so`` (built in-tree by ``build.py``).  Raises when it
+    is missing: the library has no other implementation."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("liblmosem.so is not built; run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _status_name(st):
+    try:
+        return load().lmosem_status_string(st).decode()
+    except Exception:  # noqa: BLE001 - message formatting only
+        return "status"
+
+
+def _ptr(x):
+    """Device address of a torch tensor, or an integer address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(ctx, st):
+    if st != OK:
+        msg = load().lmosem_last_error(ctx).decode() if ctx else ""
+        raise LmosemError(st, msg)
+
+
+# ------------------------------------------------------------------ entry points
+
+def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
+                  table_budget_bytes=0, stream=None, profile=False):
+    """Create a context.  ``mu_per_mm`` is an (ny, nx) host array at the
+    photopeak, ``geom`` holds the scanner and energy fields of
+    ``include/lmosem.h``; ``stream`` is a torch.cuda.Stream or a raw handle."""
+    L = load()
+    mu = np.ascontiguousarray(mu_per_mm, dtype=np.float64)
+    ny, nx = mu.shape
+    sup = None
+    if support is not None:
+        sup = np.ascontiguousarray(np.asarray(support).reshape(ny, nx) != 0, dtype=np.uint8)
+    obj = Object(nx, ny, float(pixel_mm), mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                 sup.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if sup is not None else None)
+    g = Geometry(int(geom["n_angles"]), float(geom["angle0_rad"]), int(geom["n_bins"]),
+                 float(geom["bin_mm"]), float(geom["radius_mm"]), float(geom["coll_fwhm0_mm"]),
+                 float(geom["coll_fwhm_slope"]))
+    e = Energy(float(geom["e0_kev"]), float(geom["fwhm_frac_e0"]), float(geom["e_lo_kev"]),
+               float(geom["e_hi_kev"]))
+    o = Options(float(k_sigma), int(table_budget_bytes), int(bool(profile)))
+    h = _vp()
+    s = getattr(stream, "cuda_stream", stream)
+    st = L.lmosem_create(ctypes.byref(obj), ctypes.byref(g), ctypes.byref(e), ctypes.byref(o),
+                         s, ctypes.byref(h))
+    if st != OK:
+        raise LmosemError(st, "lmosem_create rejected the problem")
+    return h.value
+
+
+def lmosem_destroy(ctx):
+    load().lmosem_destroy(ctx)
+
+
+def lmosem_n_support(ctx):
+    return int(load().lmosem_n_support(ctx))
+
+
+def lmosem_n_scatter(ctx):
+    return int(load().lmosem_n_scatter(ctx))
+
+
+def lmosem_support(ctx):
+    out = np.zeros(lmosem_n_support(ctx), dtype=np.int32)
+    _check(ctx, load().lmosem_support(ctx, out.ctypes.data))
+    return out
+
+
+def lmosem_sensitivity(ctx, n_subsets, d_sens=None):
+    _check(ctx, load().lmosem_sensitivity(ctx, int(n_subsets), _ptr(d_sens)))
+
+
+def lmosem_build_model(ctx, d_angle, d_u_mm, d_e_kev, n_subsets, fmt="fp32"):
+    n = int(d_angle.numel()) if hasattr(d_angle, "numel") else int(len(d_angle))
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    _check(ctx, load().lmosem_build_model(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev), n,
+                                          int(n_subsets), f))
+
+
+def lmosem_init_image(ctx, acq_time, d_f):
+    _check(ctx, load().lmosem_init_image(ctx, float(acq_time), _ptr(d_f)))
+
+
+def lmosem_iterate(ctx, n_iters, acq_time, d_f, d_loglik=None):
+    _check(ctx, load().lmosem_iterate(ctx, int(n_iters), float(acq_time), _ptr(d_f),
+                                      _ptr(d_loglik)))
+
+
+def lmosem_loglik(ctx, acq_time, d_f, d_out):
+    _check(ctx, load().lmosem_loglik(ctx, float(acq_time), _ptr(d_f), _ptr(d_out)))
+
+
+def lmosem_model_rows(ctx, d_event_ids, d_out):
+    n = int(d_event_ids.numel())
+    _check(ctx, load().lmosem_model_rows(ctx, _ptr(d_event_ids), n, _ptr(d_out)))
+
+
+def lmosem_model_bytes(ctx):
+    return int(load().lmosem_model_bytes(ctx))
+
+
+def lmosem_launch_count(ctx):
+    return int(load().lmosem_launch_count(ctx))
+
+
+def lmosem_profile_read(ctx):
+    """{kernel class: (device ms, launches)} since the last read."""
+    ms = np.zeros(len(KERNEL_CLASSES), dtype=np.float64)
+    n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+    _check(ctx, load().lmosem_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def header_functions(header_path=None):
+    """Names of the functions declared in include/lmosem.h."""
+    import re
+    if header_path is None:
+        header_path = os.path.join(os.path.dirname(_HERE), "include", "lmosem.h")
+    txt = open(header_path).read()
+    return sorted(set(re.findall(r"\b(lmosem_[a-z0-9_]+)\s*\(", txt)))
