@@ -1,0 +1,483 @@
+#!/usr/bin/env python
+"""Benchmark of the list-mode OS-LM-MLEM attenuation-and-scatter-compensated
+reconstruction on one GB300.
+
+One step is one pass of the whole hot path on the 64 x 64 DaT-like brain
+workload (200k events, 120 angles, 8 subsets x 10 iterations, FP32 model):
+attenuation tables, subset sensitivities, the per-event path-sum model
+build, the initial image, ten OSEM iterations and the FP64 log-likelihood of
+the result, all through the C ABI with the events resident on the device.
+
+Printed (rank 0, one JSON line): the event-pixel model evals/s of the whole
+step (J * N_nz per step / step time), seconds per OSEM iteration with the
+model cached, the end-to-end rate through host buffers, the roofline of the
+dominant kernel (timed live with CUDA events on the library's stream), the
+CPU oracle baseline, SM clocks sampled during the timed region and the
+number of kernel launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank reconstructs its own noise realisation (weak
+scaling, no collective on the data path); rank 0 prints the aggregate.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "event-pixel model evals/s & LM-OSEM s/iter on 1 GB300, exact vs chosen @ error"
+UNIT = "evals/s"
+WORKLOAD = "dat64"
+WORKLOAD_DESC = ("2-D DaT-like brain, 64x64 pixels at 4 mm, 120 angles x 64 bins x 4 mm, R = 150 mm, "
+                 "200,000 list-mode events (100-175 keV, 10% FWHM at 159 keV), 8 subsets x 10 "
+                 "iterations, FP32 model and accumulation")
+# MUFU ex2 throughput of a GB300 SM, measured with independent ex2.approx.ftz.f32
+# chains (4 CTAs x 512 threads per SM): 31.8 per clock, i.e. 32 (twice the 16 of
+# compute capability 10.0).  Each path term needs one ex2 and three FP32 FMAs,
+# so the term rate of the path-sum kernel is bounded by 32 per clock per SM.
+MUFU_EX2_PER_CLK_SM = 32
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fmt", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events", type=int, default=0,
+                    help="override the event count (small cases for profiling)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ_FALLBACK}, "fallback"
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_inputs(seed, events=0):
+    from paper_2002_12471_gb300 import synthetic as S
+    ph, g, J, ns, ni = S.workload(WORKLOAD)
+    J = events or J
+    ev = S.simulate_events(ph, g, J, seed=seed)
+    return ph, g, ev, ns, ni
+
+
+def strip_terms(ph, g, ev, k_sigma=6.0):
+    """Algorithmic count of the model build: sum over events of N_nz (primary)
+    plus N_nz per scatter pixel m with |u_j - u_a(m)| <= k_sigma sigma_u(m)."""
+    mu = ph.mu.reshape(-1)
+    ny, nx = ph.mu.shape
+    scat = np.nonzero(mu > 0)[0]
+    n_nz = len(scat)
+    x = (scat % nx + 0.5 - 0.5 * nx) * ph.pixel_mm
+    y = (scat // nx + 0.5 - 0.5 * ny) * ph.pixel_mm
+    total = 0
+    for a in range(g["n_angles"]):
+        th = g["angle0_rad"] + 2 * np.pi * a / g["n_angles"]
+        um = -x * np.sin(th) + y * np.cos(th)
+        sig = (g["coll_fwhm0_mm"] + g["coll_fwhm_slope"] * (g["radius_mm"] - (x * np.cos(th) + y * np.sin(th)))) / 2.3548200450309493
+        lo, hi = um - k_sigma * sig, um + k_sigma * sig
+        uj = np.sort(ev.u_mm[ev.angle == a].astype(np.float64))
+        # events inside [lo_m, hi_m] for every m
+        cnt = np.searchsorted(uj, hi, side="right") - np.searchsorted(uj, lo, side="left")
+        total += int(cnt.sum()) + len(uj)
+    return total * n_nz, n_nz
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    ph, g, ev, ns, ni = make_inputs(seed=2 + rank, events=args.events)
+    J = len(ev)
+    a_h = torch.from_numpy(ev.angle).pin_memory()
+    u_h = torch.from_numpy(ev.u_mm).pin_memory()
+    e_h = torch.from_numpy(ev.e_kev).pin_memory()
+    a_d, u_d, e_d = a_h.to(dev), u_h.to(dev), e_h.to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB of L2
+    T = 1.0
+
+    def step(a, u, e, profile=False, host_out=None):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            L.lmosem_sensitivity(ctx, ns)
+            L.lmosem_build_model(ctx, a, u, e, ns, args.fmt)
+            f = torch.empty(nsup, dtype=torch.float32, device=dev)
+            ll = torch.empty(1, dtype=torch.float64, device=dev)
+            L.lmosem_init_image(ctx, T, f)
+            L.lmosem_iterate(ctx, ni, T, f)
+            L.lmosem_loglik(ctx, T, f, ll)
+            if host_out is not None:
+                host_out[0][:nsup].copy_(f, non_blocking=True)
+                host_out[1].copy_(ll, non_blocking=True)
+            prof = L.lmosem_profile_read(ctx) if profile else None
+            launches = L.lmosem_launch_count(ctx)
+            return nsup, prof, launches, f, ll
+        finally:
+            L.lmosem_destroy(ctx)
+
+    for _ in range(args.warmup):
+        step(a_d, u_d, e_d)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:  # noqa: BLE001 - the clock sampler then takes every line
+        uuid = None
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, profs, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nsup, prof, nl, f, ll = step(a_d, u_d, e_d, profile=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        profs.append(prof)
+        launches += nl
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total_ms = float(t.item())
+        dist.barrier()
+    ll_final = float(ll.item())
+
+    # ---- end to end through host buffers (H2D of the events, D2H of image + LL)
+    f_h = torch.empty(nsup, dtype=torch.float32).pin_memory()
+    ll_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a2, u2, e2 = a_h.to(dev, non_blocking=True), u_h.to(dev, non_blocking=True), e_h.to(dev, non_blocking=True)
+        step(a2, u2, e2, host_out=(f_h, ll_h))
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+
+    # ---- seconds per OSEM iteration with the model cached
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=True)
+    try:
+        L.lmosem_sensitivity(ctx, ns)
+        L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, args.fmt)
+        f = torch.empty(nsup, dtype=torch.float32, device=dev)
+        L.lmosem_init_image(ctx, T, f)
+        L.lmosem_iterate(ctx, 2, T, f)
+        L.lmosem_profile_read(ctx)
+        model_bytes = L.lmosem_model_bytes(ctx)
+        it_times = []
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.lmosem_iterate(ctx, 1, T, f)
+            e1.record(stream)
+            e1.synchronize()
+            it_times.append(e0.elapsed_time(e1))
+        it_prof = L.lmosem_profile_read(ctx)
+    finally:
+        L.lmosem_destroy(ctx)
+
+    terms, n_nz = strip_terms(ph, g, ev)
+    evals = J * n_nz
+    pk, pk_kind = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = (clk or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK)
+
+    agg = {}
+    for p in profs:
+        for k, (ms, n) in p.items():
+            a = agg.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    tot_kernel_ms = sum(v[0] for v in agg.values())
+    ps_ms, ps_n = agg["pathsum"]
+    ps_launch_ms = ps_ms / max(1, ps_n)
+    terms_per_launch = terms / max(1, ps_n / args.steps)
+    achieved = terms_per_launch / (ps_launch_ms * 1e-3) / 1e9          # Gterm/s
+    peak = MUFU_EX2_PER_CLK_SM * sms * sm_max * 1e6 / 1e9             # Gterm/s (1 ex2 / term)
+    traffic = read_traffic("k_pathsum")
+
+    pass_ms, pass_n = it_prof["pass"]
+    pass_bytes = model_bytes + ns * n_nz * 4          # model rows once + image reads
+    pass_gbs = (pass_bytes / ns) / (pass_ms / max(1, pass_n) * 1e-3) / 1e9
+    ms_step = t_total_ms / args.steps
+    value = world * evals / (ms_step * 1e-3)
+    e2e_ms = statistics.mean(e2e_times)
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.fmt == "fp32" else args.fmt + "+f32",
+        "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events)",
+        "config": {"workload": WORKLOAD_DESC, "events": J, "support_pixels": n_nz,
+                   "model_format": args.fmt, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "model (%.2f GB) larger than L2; 256 MB L2 flush before every step" %
+                         (model_bytes / 1e9)},
+        "s_per_iter": statistics.mean(it_times) * 1e-3,
+        "s_per_iter_detail": {"pass_ms_per_launch": pass_ms / max(1, pass_n),
+                              "pass_gbs": pass_gbs, "hbm_peak_gbs": pk["hbm_gbs"],
+                              "pass_frac_of_%s_hbm" % pk_kind: pass_gbs / pk["hbm_gbs"],
+                              "model_bytes": model_bytes},
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in agg.items() if v[1]},
+        "kernel_share": {k: v[0] / tot_kernel_ms for k, v in agg.items() if v[1]},
+        "model_build_evals_per_s": evals / (ps_launch_ms * ps_n / args.steps * 1e-3),
+        "path_terms_per_step": terms,
+        "loglik_final": ll_final,
+        "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": UNIT,
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(J * 12),
+                "d2h_bytes_per_step": int(nsup * 4 + 8)},
+        "roofline": {"bound": "alu", "kernel": "k_pathsum", "achieved": achieved, "peak": peak,
+                     "unit": "Gterm/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": "%d MUFU ex2 per clock per SM x %d SMs x %.0f MHz; one ex2 and "
+                                   "three FP32 FMAs per path term" % (MUFU_EX2_PER_CLK_SM, sms, sm_max)},
+        "roofline_pass": {"bound": "hbm", "kernel": "k_pass", "achieved": pass_gbs,
+                          "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": pass_gbs / pk["hbm_gbs"],
+                          "peak_kind": pk_kind},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    return out
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if
+    the kernel's source has not changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2002_12471_gb300", "csrc", "model.cu")
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    for ln in open(path):
+        parts = dict(p.split("=", 1) for p in ln.split() if "=" in p)
+        if parts.get("kernel") == kernel and parts.get("source_sha1") == h:
+            try:
+                return float(parts["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_sample_run(ph, g, ev, ns, ni, per_angle):
+    """The FP64 oracle on a bounded sample: full attenuation tables and
+    sensitivity, model rows and OSEM for `per_angle` events of every angle.
+    Returns phase times in seconds."""
+    import oracle
+    rng = np.random.default_rng(per_angle)
+    idx = np.concatenate([rng.choice(np.nonzero(ev.angle == a)[0],
+                                     min(per_angle, int(np.sum(ev.angle == a))), replace=False)
+                          for a in range(g["n_angles"]) if np.any(ev.angle == a)])
+    t0 = time.perf_counter()
+    P = oracle.Problem(dict(g, pixel_mm=ph.pixel_mm), ph.mu)
+    t1 = time.perf_counter()
+    s = P.sensitivity(ns)
+    t2 = time.perf_counter()
+    p = P.model(ev.angle[idx], ev.u_mm[idx], ev.e_kev[idx])
+    t3 = time.perf_counter()
+    f, _ = oracle.osem(p, ev.angle[idx], s, ni, oracle.initial_image(len(idx), s.sum(0)))
+    oracle.loglik(p, f, s.sum(0))
+    t4 = time.perf_counter()
+    return dict(tables=t1 - t0, sens=t2 - t1, model=t3 - t2, osem=t4 - t3, n=len(idx), n_nz=P.n_sup)
+
+
+def oracle_rate(ph, g, ev, ns, ni, fit=None):
+    """Oracle evals/s extrapolated to the full event count.  The model time is
+    fitted as per-angle table cost + per-event cost from two sample sizes."""
+    J = len(ev)
+    if fit is None:
+        r1 = oracle_sample_run(ph, g, ev, ns, ni, 3)
+        r2 = oracle_sample_run(ph, g, ev, ns, ni, 6)
+        b = max(0.0, (r2["model"] - r1["model"]) / (r2["n"] - r1["n"]))
+        a = max(0.0, r2["model"] - b * r2["n"])
+        c = r2["osem"] / r2["n"]
+        fit = dict(model_fixed=a, model_per_event=b, osem_per_event=c)
+        run = r2
+    else:
+        run = oracle_sample_run(ph, g, ev, ns, ni, 6)
+        fit = dict(fit, osem_per_event=run["osem"] / run["n"])
+    t_full = (run["tables"] + run["sens"] + fit["model_fixed"] + fit["model_per_event"] * J
+              + fit["osem_per_event"] * J)
+    value = J * run["n_nz"] / t_full
+    wall = run["tables"] + run["sens"] + run["model"] + run["osem"]
+    return value, fit, run, wall
+
+
+def cores_used():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
+
+
+def cpu_baseline_block(value, run, wall):
+    return {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+            "sample": ("FP64 C/OpenMP oracle: full attenuation tables and 8-subset sensitivity, model "
+                       "rows and 10 OSEM iterations for %d of the %s events (6 per angle); model and "
+                       "OSEM time extrapolated linearly in J (per-angle table cost fitted from a 3-per-"
+                       "angle run); %.1f s of CPU wall time" % (run["n"], "200,000", wall))}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    ph, g, ev, ns, ni = make_inputs(seed=2)
+    J = len(ev)
+    for _ in range(args.warmup):
+        oracle_sample_run(ph, g, ev, ns, ni, 1)
+    _, fit, _, _ = oracle_rate(ph, g, ev, ns, ni)
+    vals, walls = [], []
+    run = None
+    for _ in range(args.steps):
+        v, _, run, wall = oracle_rate(ph, g, ev, ns, ni, fit)
+        vals.append(v)
+        walls.append(wall)
+    value = statistics.mean(vals)
+    ms = J * run["n_nz"] / value * 1e3
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events)",
+            "config": {"workload": WORKLOAD_DESC, "events": J, "support_pixels": run["n_nz"]},
+            "cpu_baseline": cpu_baseline_block(value, run, statistics.mean(walls)),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours" and torch.cuda.is_available():
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            ph, g, ev, ns, ni = make_inputs(seed=2)
+            v, _, run, wall = oracle_rate(ph, g, ev, ns, ni)
+            out["cpu_baseline"] = cpu_baseline_block(v, run, wall)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

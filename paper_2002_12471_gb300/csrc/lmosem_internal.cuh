@@ -84,11 +84,12 @@ struct lmosem_ctx {
     int32_t* d_angle_cnt = nullptr;
     int32_t* d_tile_prefix = nullptr;                // n_angles + 1 cumulative event tiles
     std::vector<int32_t> h_tile_prefix;
-    float2* d_wtab = nullptr;     // scatter-weight tables of one angle group
+    float* d_wtab = nullptr;      // scatter-weight planes (s, b, -lw) of one angle group
     int64_t wtab_bytes = 0;
 
     // iteration scratch
-    int pass_ctas = 0;
+    int pass_ctas = 0;            // capacity of the per-CTA partial buffers
+    int pass_grid = 0;            // CTAs of the last pass (partials to reduce)
     float* d_bpart = nullptr;     // pass_ctas x n_sup
     double* d_llpart = nullptr;   // pass_ctas
     double* d_scalar = nullptr;   // small FP64 scratch

@@ -11,13 +11,20 @@
 // sum_n p_jn f_n, so caching p turns every OSEM sub-iteration into a
 // streaming pass.
 //
-// Per angle a, (E', lw) with lw = log2(W / (sigma_E(E') sqrt(2 pi))) is
-// tabulated for every (m, n); every term is then
-//     U_jm * 2^(lw - ((E_j - E') s)^2),   s = sqrt(log2 e / 2) / sigma_E(E'),
-// i.e. three FP32 FMAs and one MUFU ex2.  A CTA owns 64 events of one angle
-// (consecutive in position) x 128 support pixels and walks the scatter
-// pixels whose kernel reaches any of its events (|u_j - u_m| <= k_sigma
-// sigma_u(m)); terms outside that cut for a given event are set to zero.
+// Per angle a, three planes s, b and -lw are tabulated for every (m, n), with
+// lw = log2(W / (sigma_E(E') sqrt(2 pi))), s = sqrt(log2 e / 2) / sigma_E(E')
+// and b = -E' s, so that every term is
+//     U_jm * 2^-(t^2 - lw),   t = E_j s + b,
+// i.e. one FMA for t, one for t^2 - lw, one MUFU ex2 and one FMA into the
+// accumulator.  The FMAs run as packed FP32x2 instructions (two support
+// pixels per instruction), so a pair of terms costs three FFMA2 and two
+// ex2: the kernel is bound by the MUFU pipe.
+//
+// A CTA owns 64 events of one angle (consecutive in position) x 128 support
+// pixels and walks the scatter pixels whose kernel reaches any of its events
+// (|u_j - u_m| <= k_sigma sigma_u(m)); terms outside that cut for a given
+// event are exactly zero.  The table slices of the next 16 scatter pixels are
+// copied into shared memory with cp.async while the current 16 are summed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -30,6 +37,8 @@
 namespace lmosem {
 
 namespace {
+
+constexpr int kStage = 16;  // scatter pixels per pipeline stage
 
 struct WTabArgs {
     int nx, ny, npix;
@@ -47,16 +56,17 @@ struct WTabArgs {
     int s0;                     // first slot of the group
     float eps0, inv_kbar, e0;
     float w_const;              // D^2 / (2 pi sqrt(2 pi kappa)), sigma_E^2 = kappa E
-    float2* wtab;               // [slot - s0][m][ld_w]
+    float cE;                   // s = cE / sqrt(E')
+    float* wtab;                // [slot - s0][plane s, b, -lw][m][ld_w]
 };
 
-// (E', lw) of the scatter path (n, m) at the angle of one slot
+// planes (s, b, -lw) of the scatter path (n, m) at the angle of one slot
 __global__ void k_wtable(WTabArgs A) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     int k = blockIdx.y;
     int g = blockIdx.z;
     if (n >= A.ld_w) return;
-    float2 out = make_float2(A.e0, -INFINITY);
+    float s = 0.0f, b = 0.0f, nlw = INFINITY;
     if (n < A.n_sup) {
         int a = A.slot_angle[A.s0 + g];
         int pn = A.sup[n], pm = A.scat[k];
@@ -67,11 +77,17 @@ __global__ void k_wtable(WTabArgs A) {
             float e1 = A.e0 * P;
             float ratio = compton_lookup(A.compton, cpsi).x;
             float att = A.l_pair[(size_t)k * A.n_sup + n] + ratio * A.l_edge[(size_t)a * A.npix + pm];
-            float lw = log2f(A.w_const * A.mu[pm] * kt * rinv * rsqrtf(e1)) - att * kLog2e;
-            out = make_float2(e1, lw);
+            float ri = rsqrtf(e1);
+            nlw = att * kLog2e - log2f(A.w_const * A.mu[pm] * kt * rinv * ri);
+            s = A.cE * ri;
+            b = -e1 * s;
         }
     }
-    A.wtab[((size_t)g * A.n_scat + k) * A.ld_w + n] = out;
+    size_t plane = (size_t)A.n_scat * A.ld_w;
+    float* base = A.wtab + (size_t)g * 3 * plane + (size_t)k * A.ld_w + n;
+    base[0] = s;
+    base[plane] = b;
+    base[2 * plane] = nlw;
 }
 
 struct PathSumArgs {
@@ -83,11 +99,10 @@ struct PathSumArgs {
     const int32_t* angle_cnt;
     int s0, s1;                  // slot range of the group
     int n_ptiles;
-    const float2* wtab;
+    const float* wtab;
     int ld_w, n_scat;
     const float4* mpar;          // [a][m]
     const float4* ppar;          // [a][n]
-    float cE;                    // s = cE / sqrt(E')
     float e0, sE0, lE0;          // primary energy factor 2^(lE0 - ((E - e0) sE0)^2)
     float* out;                  // FP32 rows
     int64_t ld_out;
@@ -95,17 +110,48 @@ struct PathSumArgs {
     int n_store;                 // columns to store (padded row width)
 };
 
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// shared-memory layout of k_pathsum, in floats
+constexpr int kPlaneF = kStage * kTN;                 // one plane of one stage
+constexpr int kOffPlanes = 0;                         // [2][3][kStage][kTN]
+constexpr int kOffU = kOffPlanes + 2 * 3 * kPlaneF;   // [kStage][kTJ] float2
+constexpr int kOffMp = kOffU + 2 * kStage * kTJ;      // [2][kStage] float4
+constexpr int kOffEv = kOffMp + 2 * kStage * 4;       // u[kTJ], e[kTJ]
+constexpr int kOffMisc = kOffEv + 2 * kTJ;            // 16 ints
+constexpr int kOffList = kOffMisc + 16;               // n_scat ints
+
 __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
-    float* sU = sm;                          // [kMC][kTJ]
-    float* sS = sU + kMC * kTJ;              // [kMC][kTN]
-    float* sB = sS + kMC * kTN;
-    float* sW = sB + kMC * kTN;
-    float* ev_u = sW + kMC * kTN;            // [kTJ]
-    float* ev_e = ev_u + kTJ;                // [kTJ]
-    int* misc = reinterpret_cast<int*>(ev_e + kTJ);  // [16]
-    int* mlist = misc + 16;                  // [n_scat]
+    float* planes = sm + kOffPlanes;
+    float2* sU = reinterpret_cast<float2*>(sm + kOffU);
+    float4* mp = reinterpret_cast<float4*>(sm + kOffMp);
+    float* ev_u = sm + kOffEv;
+    float* ev_e = ev_u + kTJ;
+    int* misc = reinterpret_cast<int*>(sm + kOffMisc);
+    int* mlist = reinterpret_cast<int*>(sm + kOffList);
     float* red = reinterpret_cast<float*>(misc);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -157,8 +203,8 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         int m = m0 + tid;
         bool in = false;
         if (m < A.n_scat) {
-            float4 mp = __ldg(mp_a + m);
-            in = (mp.x + mp.w >= umin) && (mp.x - mp.w <= umax);
+            float4 q = __ldg(mp_a + m);
+            in = (q.x + q.w >= umin) && (q.x - q.w <= umax);
         }
         unsigned bal = __ballot_sync(0xffffffffu, in);
         if (lane == 0) misc[warp] = __popc(bal);
@@ -174,9 +220,10 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         nm += total;
     }
 
-    // accumulators, initialised with the primary path
-    float E[8];
-    float acc[8][4];
+    // accumulators (pairs of adjacent support pixels), initialised with the
+    // primary path
+    float2 E2[8];
+    float2 acc[8][2];
     {
         const float4* pp_a = A.ppar + (size_t)a * A.ld_w + n0 + 4 * lane;
         float4 pp[4];
@@ -186,74 +233,96 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         for (int jj = 0; jj < 8; ++jj) {
             float uj = ev_u[8 * warp + jj];
             float ej = ev_e[8 * warp + jj];
-            E[jj] = ej;
+            E2[jj] = make_float2(ej, ej);
             float te = (ej - A.e0) * A.sE0;
             float le = fmaf(-te, te, A.lE0);
+            float v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float t = (uj - pp[q].x) * pp[q].y;
-                acc[jj][q] = ex2_approx(fmaf(-t, t, pp[q].z + le));
+                v[q] = ex2_approx(fmaf(-t, t, pp[q].z + le));
             }
+            acc[jj][0] = make_float2(v[0], v[1]);
+            acc[jj][1] = make_float2(v[2], v[3]);
         }
     }
 
-    const float2* wt = A.wtab + (size_t)(slot - A.s0) * A.n_scat * A.ld_w + n0;
-    for (int c0 = 0; c0 < nm; c0 += kMC) {
-        // stage U[mc][j]
-        {
-            const int j = tid & (kTJ - 1);
-            const float uj = ev_u[j];
-#pragma unroll
-            for (int k = 0; k < kMC * kTJ / kBuildThreads; ++k) {
-                int mc = (tid >> 6) + 4 * k;
-                float U = 0.0f;
-                if (c0 + mc < nm) {
-                    float4 mp = __ldg(mp_a + mlist[c0 + mc]);
-                    float d = uj - mp.x;
-                    float z = d * mp.y;
-                    U = fabsf(d) <= mp.w ? ex2_approx(fmaf(-z, z, mp.z)) : 0.0f;
-                }
-                sU[mc * kTJ + j] = U;
+    // strip staging: three table planes and the position parameters of
+    // kStage scatter pixels per stage, double-buffered with cp.async
+    const size_t plane = (size_t)A.n_scat * A.ld_w;
+    const float* tab = A.wtab + (size_t)(slot - A.s0) * 3 * plane + n0;
+    auto issue = [&](int c0, int buf) {
+        for (int k = tid; k < 3 * kStage * (kTN / 4); k += kBuildThreads) {
+            int p = k / (kStage * (kTN / 4));
+            int r = k - p * (kStage * (kTN / 4));
+            int mc = r / (kTN / 4), q = r - mc * (kTN / 4);
+            float* dst = planes + ((buf * 3 + p) * kStage + mc) * kTN + 4 * q;
+            if (c0 + mc < nm) {
+                cp_async16(dst, tab + p * plane + (size_t)mlist[c0 + mc] * A.ld_w + 4 * q);
+            } else {
+                float v = p == 2 ? INFINITY : 0.0f;
+                *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
             }
         }
-        // stage s, b, lw for [mc][n]
-        {
-            const int n = tid & (kTN - 1);
-#pragma unroll 4
-            for (int k = 0; k < kMC * kTN / kBuildThreads; ++k) {
-                int mc = (tid >> 7) + 2 * k;
-                float s = 0.0f, b = 0.0f, lw = -INFINITY;
-                if (c0 + mc < nm) {
-                    float2 w2 = __ldg(wt + (size_t)mlist[c0 + mc] * A.ld_w + n);
-                    s = A.cE * rsqrtf(w2.x);
-                    b = -w2.x * s;
-                    lw = w2.y;
-                }
-                sS[mc * kTN + n] = s;
-                sB[mc * kTN + n] = b;
-                sW[mc * kTN + n] = lw;
-            }
+        if (tid < kStage) {
+            float4* dst = mp + buf * kStage + tid;
+            if (c0 + tid < nm) cp_async16(dst, mp_a + mlist[c0 + tid]);
+            else *dst = make_float4(0.0f, 0.0f, -INFINITY, -1.0f);  // cut < 0: U = 0
+        }
+        cp_async_commit();
+    };
+
+    const int nchunks = (nm + kStage - 1) / kStage;
+    if (nchunks > 0) issue(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) {
+            issue((c + 1) * kStage, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        // U_jm of this stage, duplicated into FP32 pairs
+        for (int k = tid; k < kStage * kTJ; k += kBuildThreads) {
+            int mc = k / kTJ, j = k - mc * kTJ;
+            float4 q = mp[buf * kStage + mc];
+            float d = ev_u[j] - q.x;
+            float z = d * q.y;
+            float U = fabsf(d) <= q.w ? ex2_approx(fmaf(-z, z, q.z)) : 0.0f;
+            sU[mc * kTJ + j] = make_float2(U, U);
+        }
+        __syncthreads();
+        const float* pS = planes + (buf * 3 + 0) * kPlaneF + 4 * lane;
+        const float* pB = planes + (buf * 3 + 1) * kPlaneF + 4 * lane;
+        const float* pW = planes + (buf * 3 + 2) * kPlaneF + 4 * lane;
+        const float4* pU = reinterpret_cast<const float4*>(sU + 8 * warp);
 #pragma unroll 2
-        for (int mc = 0; mc < kMC; ++mc) {
-            float4 u0 = *reinterpret_cast<const float4*>(sU + mc * kTJ + 8 * warp);
-            float4 u1 = *reinterpret_cast<const float4*>(sU + mc * kTJ + 8 * warp + 4);
-            float4 s4 = *reinterpret_cast<const float4*>(sS + mc * kTN + 4 * lane);
-            float4 b4 = *reinterpret_cast<const float4*>(sB + mc * kTN + 4 * lane);
-            float4 w4 = *reinterpret_cast<const float4*>(sW + mc * kTN + 4 * lane);
-            const float U[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-            const float S[4] = {s4.x, s4.y, s4.z, s4.w};
-            const float B[4] = {b4.x, b4.y, b4.z, b4.w};
-            const float W[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (int mc = 0; mc < kStage; ++mc) {
+            const float4 S = *reinterpret_cast<const float4*>(pS + mc * kTN);
+            const float4 B = *reinterpret_cast<const float4*>(pB + mc * kTN);
+            const float4 W = *reinterpret_cast<const float4*>(pW + mc * kTN);
+            const float4* up = pU + mc * (kTJ / 2);
+            float2 U[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 v = up[k];
+                U[2 * k] = make_float2(v.x, v.y);
+                U[2 * k + 1] = make_float2(v.z, v.w);
+            }
+            const float2 S01 = make_float2(S.x, S.y), S23 = make_float2(S.z, S.w);
+            const float2 B01 = make_float2(B.x, B.y), B23 = make_float2(B.z, B.w);
+            const float2 W01 = make_float2(W.x, W.y), W23 = make_float2(W.z, W.w);
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float t = fmaf(E[jj], S[q], B[q]);
-                    float x = fmaf(-t, t, W[q]);
-                    acc[jj][q] = fmaf(U[jj], ex2_approx(x), acc[jj][q]);
-                }
+                float2 t0 = ffma2(E2[jj], S01, B01);
+                float2 t1 = ffma2(E2[jj], S23, B23);
+                float2 z0 = ffma2(t0, t0, W01);
+                float2 z1 = ffma2(t1, t1, W23);
+                float2 e0 = make_float2(ex2_approx(-z0.x), ex2_approx(-z0.y));
+                float2 e1 = make_float2(ex2_approx(-z1.x), ex2_approx(-z1.y));
+                acc[jj][0] = ffma2(U[jj], e0, acc[jj][0]);
+                acc[jj][1] = ffma2(U[jj], e1, acc[jj][1]);
             }
         }
         __syncthreads();
@@ -266,12 +335,13 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         int j = 8 * warp + jj;
         if (j >= nr) continue;
         float* row = A.out + (r0 + j - A.row_base) * A.ld_out;
+        float v[4] = {acc[jj][0].x, acc[jj][0].y, acc[jj][1].x, acc[jj][1].y};
         if (n + 3 < A.n_store) {
-            *reinterpret_cast<float4*>(row + n) = make_float4(acc[jj][0], acc[jj][1], acc[jj][2], acc[jj][3]);
+            *reinterpret_cast<float4*>(row + n) = make_float4(v[0], v[1], v[2], v[3]);
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (n + q < A.n_store) row[n + q] = acc[jj][q];
+                if (n + q < A.n_store) row[n + q] = v[q];
         }
     }
 }
@@ -341,10 +411,10 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     LMOSEM_CK(c, cudaMemcpyAsync(c->d_angle_cnt, cnt.data(), c->n_angles * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, c->stream));
 
-    // angle groups bounded by the scatter-table budget
-    const int64_t per_angle = (int64_t)c->n_scat * c->ld_w * sizeof(float2);
+    // angle groups bounded by the scatter-table budget (three FP32 planes)
+    const int64_t per_angle = (int64_t)3 * c->n_scat * c->ld_w * sizeof(float);
     int gsz = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
-    if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * c->n_scat * c->ld_w))) return st;
+    if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * 3 * c->n_scat * c->ld_w))) return st;
 
     const bool scaled = c->fmt != LMOSEM_MODEL_FP32;
     int64_t max_group_rows = 0;
@@ -362,8 +432,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;  // sigma_E^2 = kappa E
     const double se0 = sqrt(kappa * c->e0);
-    const size_t smem = sizeof(float) * ((size_t)kMC * kTJ + 3 * (size_t)kMC * kTN + 2 * kTJ) +
-                        sizeof(int) * (16 + (size_t)c->n_scat);
+    const size_t smem = sizeof(float) * ((size_t)kOffList + c->n_scat);
     LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
 
@@ -390,6 +459,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         W.inv_kbar = (float)(1.0 / c->kbar);
         W.e0 = (float)c->e0;
         W.w_const = (float)(c->dpx * c->dpx / (2.0 * kPi * sqrt(2.0 * kPi * kappa)));
+        W.cE = (float)sqrt(1.4426950408889634 / (2.0 * kappa));
         W.wtab = c->d_wtab;
         LMOSEM_PROF_BEGIN(c);
         k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, s1 - s0), 256, 0, c->stream>>>(W);
@@ -415,7 +485,6 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.n_scat = c->n_scat;
         P.mpar = c->d_mpar;
         P.ppar = c->d_ppar;
-        P.cE = (float)sqrt(1.4426950408889634 / (2.0 * kappa));
         P.e0 = (float)c->e0;
         P.sE0 = (float)(0.8493218002880191 / se0);
         P.lE0 = (float)(-log2(se0 * sqrt(2.0 * kPi)));

@@ -5,11 +5,13 @@
 //     f_q <- sum_{j in S_i} zbar_{j,P_q} / (T s^i_q) = f_q b_q / (T s^i_q),
 //     b_q = sum_{j in S_i, y_j > 0} p_jq / y_j.
 // Each sub-iteration is one streaming pass over the subset's model rows:
-// every row is loaded once from HBM into registers, y_j is formed by a CTA
-// reduction, and the same registers are back-projected into the CTA's
-// private b (registers, FP32).  A second kernel reduces the per-CTA b in
-// CTA order (deterministic) and applies the update with T s^i_q formed in
-// FP64.  The log-likelihood of Eq. 3 (without log J!) is reduced in FP64.
+// every row is loaded once from HBM into registers (the next rows are
+// already in flight while the current ones are reduced), y_j is formed by a
+// CTA reduction, and the same registers are back-projected into the CTA's
+// private b (registers, FP32).  A second kernel reduces the per-CTA b in CTA
+// order (deterministic) and applies the update with T s^i_q formed in FP64.
+// The log-likelihood of Eq. 3 (without log J!) has its own pass: log(y_j) in
+// FP32, reduced in FP64.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -31,16 +33,17 @@ struct Vec;
 template <>
 struct Vec<float> {
     static constexpr int N = 4;
-    __device__ static void load(const float* p, float* out) {
-        float4 v = __ldcs(reinterpret_cast<const float4*>(p));
-        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    __device__ static void cvt(const uint4& v, float* out) {
+        out[0] = __uint_as_float(v.x);
+        out[1] = __uint_as_float(v.y);
+        out[2] = __uint_as_float(v.z);
+        out[3] = __uint_as_float(v.w);
     }
 };
 template <>
 struct Vec<__half> {
     static constexpr int N = 8;
-    __device__ static void load(const __half* p, float* out) {
-        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    __device__ static void cvt(const uint4& v, float* out) {
         const __half2* h = reinterpret_cast<const __half2*>(&v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -53,8 +56,7 @@ struct Vec<__half> {
 template <>
 struct Vec<__nv_bfloat16> {
     static constexpr int N = 8;
-    __device__ static void load(const __nv_bfloat16* p, float* out) {
-        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    __device__ static void cvt(const uint4& v, float* out) {
         const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -67,28 +69,29 @@ struct Vec<__nv_bfloat16> {
 
 struct PassArgs {
     const void* model;
-    int64_t ld;              // row stride, elements
+    int64_t ld_bytes;        // row stride in bytes
+    int64_t nvec;            // 16-byte vectors per row
     int64_t r0, r1;          // rows of this pass
     int64_t rows_per_cta;
     const float* f;
     const float* scale;      // row scales (scaled forms) or nullptr
     int n_sup;
-    double T;
-    int back;                // 1: accumulate b; 0: log-likelihood only
+    double log_T;
     float* bpart;            // [cta][n_sup]
     double* llpart;          // [cta]
 };
 
 // One pass over rows [r0, r1): thread t owns the 16-byte column vectors
-// t, t + NT, ... (VPT of them); R rows are in flight per thread.
-template <typename H, int VPT, int R>
+// t, t + NT, ... (VPT of them); groups of R rows are double-buffered in
+// registers.  BACK: accumulate b; otherwise accumulate the log-likelihood.
+template <typename H, int VPT, int R, bool BACK>
 __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
     constexpr int EPV = Vec<H>::N;
     __shared__ float red[2][R][kMaxPassThreads / 32];
     __shared__ double llred[kMaxPassThreads / 32];
     const int NT = blockDim.x, NW = NT >> 5;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const H* model = reinterpret_cast<const H*>(A.model);
+    const char* model = reinterpret_cast<const char*>(A.model);
 
     float fr[VPT][EPV], br[VPT][EPV];
 #pragma unroll
@@ -104,63 +107,76 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
     const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
     const int64_t re = min(A.r1, rb + A.rows_per_cta);
     double ll = 0.0;
-    int buf = 0;
-    for (int64_t r = rb; r < re; r += R) {
-        float p[R][VPT][EPV];
+    int npos = 0;
+
+    auto load = [&](int64_t r, uint4 (&dst)[R][VPT]) {
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const bool ok = r + i < re;
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                int64_t col0 = (int64_t)EPV * (t + NT * v);
-                if (ok && col0 < A.ld) {
-                    Vec<H>::load(model + (r + i) * A.ld + col0, p[i][v]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < EPV; ++e) p[i][v][e] = 0.0f;
-                }
+                int64_t vec = t + (int64_t)NT * v;
+                if (r + i < re && vec < A.nvec)
+                    dst[i][v] = __ldcs(reinterpret_cast<const uint4*>(model + (r + i) * A.ld_bytes) + vec);
+                else
+                    dst[i][v] = make_uint4(0u, 0u, 0u, 0u);
             }
         }
+    };
+    auto process = [&](int64_t r, const uint4 (&raw)[R][VPT], int rb_) {
         float d[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             float s = 0.0f;
 #pragma unroll
-            for (int v = 0; v < VPT; ++v)
+            for (int v = 0; v < VPT; ++v) {
+                float p[EPV];
+                Vec<H>::cvt(raw[i][v], p);
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) s = fmaf(p[i][v][e], fr[v][e], s);
+                for (int e = 0; e < EPV; ++e) s = fmaf(p[e], fr[v][e], s);
+            }
 #pragma unroll
             for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             d[i] = s;
         }
         if (lane == 0) {
 #pragma unroll
-            for (int i = 0; i < R; ++i) red[buf][i][warp] = d[i];
+            for (int i = 0; i < R; ++i) red[rb_][i][warp] = d[i];
         }
         __syncthreads();
-        float inv[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             float y = 0.0f;
-            for (int w = 0; w < NW; ++w) y += red[buf][i][w];
+            for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
             const bool ok = r + i < re && y > 0.0f;
-            inv[i] = ok ? 1.0f / y : 0.0f;
-            if (ok && t == i) {
-                double c = A.scale ? (double)A.scale[r + i] : 1.0;
-                ll += log(A.T * c * (double)y);
+            if constexpr (BACK) {
+                const float inv = ok ? 1.0f / y : 0.0f;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    float p[EPV];
+                    Vec<H>::cvt(raw[i][v], p);
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e) br[v][e] = fmaf(p[e], inv, br[v][e]);
+                }
+            } else {
+                if (ok && t == i) {
+                    float c = A.scale ? A.scale[r + i] : 1.0f;
+                    ll += (double)logf(c * y);
+                    ++npos;
+                }
             }
         }
-        if (A.back) {
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-#pragma unroll
-                for (int v = 0; v < VPT; ++v)
-#pragma unroll
-                    for (int e = 0; e < EPV; ++e) br[v][e] = fmaf(p[i][v][e], inv[i], br[v][e]);
-        }
-        buf ^= 1;
+    };
+
+    uint4 P0[R][VPT], P1[R][VPT];
+    if (rb < re) load(rb, P0);
+    for (int64_t r = rb; r < re; r += 2 * R) {
+        if (r + R < re) load(r + R, P1);
+        process(r, P0, 0);
+        if (r + R >= re) break;
+        if (r + 2 * R < re) load(r + 2 * R, P0);
+        process(r + R, P1, 1);
     }
-    if (A.back) {
+    if constexpr (BACK) {
         float* bp = A.bpart + (size_t)blockIdx.x * A.n_sup;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
@@ -169,27 +185,43 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
             for (int e = 0; e < EPV; ++e)
                 if (col0 + e < A.n_sup) bp[col0 + e] = br[v][e];
         }
-    }
-    // per-CTA log-likelihood partial, fixed order
-    for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-    if (lane == 0) llred[warp] = ll;
-    __syncthreads();
-    if (t == 0) {
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += llred[w];
-        A.llpart[blockIdx.x] = s;
+    } else {
+        // per-CTA partial: sum_j log(c_j y_j) + (number of rows) log T, fixed order
+        ll += (double)npos * A.log_T;
+        for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if (lane == 0) llred[warp] = ll;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += llred[w];
+            A.llpart[blockIdx.x] = s;
+        }
     }
 }
 
-__global__ void k_update(const float* __restrict__ bpart, int nparts, int n_sup,
-                         float* __restrict__ f, const double* __restrict__ sens_i, double T) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= n_sup) return;
+// b_q = sum of the per-CTA partials (8 warps over the partials, fixed order),
+// then f_q <- f_q b_q / (T s^i_q)
+__global__ void __launch_bounds__(256) k_update(const float* __restrict__ bpart, int nparts, int n_sup,
+                                                float* __restrict__ f, const double* __restrict__ sens_i,
+                                                double T) {
+    __shared__ float sh[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 32 + lane;
     float b = 0.0f;
-    for (int c = 0; c < nparts; ++c) b += bpart[(size_t)c * n_sup + n];
-    double s = sens_i[n];
-    float ts = (float)(T * s);
-    f[n] = s > 0.0 ? f[n] * b / ts : 0.0f;
+    if (n < n_sup) {
+#pragma unroll 4
+        for (int c = warp; c < nparts; c += 8) b += bpart[(size_t)c * n_sup + n];
+    }
+    sh[warp][lane] = b;
+    __syncthreads();
+    if (warp == 0 && n < n_sup) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += sh[w][lane];
+        double sd = sens_i[n];
+        float ts = (float)(T * sd);
+        f[n] = sd > 0.0 ? f[n] * s / ts : 0.0f;
+    }
 }
 
 // loglik = sum of the per-CTA partials - T sum_q s_q f_q (FP64, one block)
@@ -245,7 +277,8 @@ __global__ void k_model_rows(const H* __restrict__ model, int64_t ld, const floa
 }
 
 struct PassShape {
-    int vpt, r, nt;
+    int vpt, nt;
+    int64_t nvec;
 };
 
 PassShape pass_shape(const lmosem_ctx* c) {
@@ -259,75 +292,85 @@ PassShape pass_shape(const lmosem_ctx* c) {
             break;
         }
     int nt = (int)(((nvec + vpt - 1) / vpt + 31) / 32 * 32);
-    return {vpt, vpt <= 2 ? 4 : 2, nt};
+    return {vpt, nt, nvec};
 }
 
-template <typename H, int VPT, int R>
-lmosem_status launch_pass_t(lmosem_ctx* c, const PassArgs& A, int grid, int nt) {
+template <typename H, int VPT, bool BACK>
+lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
+    constexpr int R = VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4);
+    auto kern = k_pass<H, VPT, R, BACK>;
+    int per_sm = 0, dev = 0, sms = 0;
+    LMOSEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0));
+    LMOSEM_CK(c, cudaGetDevice(&dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = std::max(1, per_sm) * (int64_t)sms;
+    grid = std::min<int64_t>(grid, c->pass_ctas);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, (rows + R - 1) / R));
+    A.rows_per_cta = (rows + grid - 1) / grid;
+    A.rows_per_cta = (A.rows_per_cta + R - 1) / R * R;
+    grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
+    c->pass_grid = (int)grid;
     LMOSEM_PROF_BEGIN(c);
-    k_pass<H, VPT, R><<<grid, nt, 0, c->stream>>>(A);
+    kern<<<(unsigned)grid, nt, 0, c->stream>>>(A);
     LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
     return LMOSEM_OK;
 }
 
-template <typename H>
-lmosem_status launch_pass_h(lmosem_ctx* c, const PassArgs& A, int grid, PassShape s) {
+template <typename H, bool BACK>
+lmosem_status launch_pass_h(lmosem_ctx* c, const PassArgs& A, int64_t rows, PassShape s) {
     switch (s.vpt) {
-        case 1: return launch_pass_t<H, 1, 4>(c, A, grid, s.nt);
-        case 2: return launch_pass_t<H, 2, 4>(c, A, grid, s.nt);
-        case 3: return launch_pass_t<H, 3, 2>(c, A, grid, s.nt);
-        case 4: return launch_pass_t<H, 4, 2>(c, A, grid, s.nt);
-        case 6: return launch_pass_t<H, 6, 2>(c, A, grid, s.nt);
-        default: return launch_pass_t<H, 8, 2>(c, A, grid, s.nt);
+        case 1: return launch_pass_t<H, 1, BACK>(c, A, rows, s.nt);
+        case 2: return launch_pass_t<H, 2, BACK>(c, A, rows, s.nt);
+        case 3: return launch_pass_t<H, 3, BACK>(c, A, rows, s.nt);
+        case 4: return launch_pass_t<H, 4, BACK>(c, A, rows, s.nt);
+        case 6: return launch_pass_t<H, 6, BACK>(c, A, rows, s.nt);
+        default: return launch_pass_t<H, 8, BACK>(c, A, rows, s.nt);
     }
 }
 
-lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f, double T, int back) {
+template <bool BACK>
+lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f, double T) {
     PassShape s = pass_shape(c);
     int64_t rows = r1 - r0;
-    int64_t grid = std::min<int64_t>(c->pass_ctas, std::max<int64_t>(1, (rows + s.r - 1) / s.r));
+    if (rows <= 0) {
+        c->pass_grid = 0;   // the reduction then sees b = 0 / an empty sum
+        return LMOSEM_OK;
+    }
     PassArgs A;
     A.model = c->d_model;
-    A.ld = c->ld_model;
+    A.ld_bytes = c->ld_model * (c->fmt == LMOSEM_MODEL_FP32 ? 4 : 2);
+    A.nvec = s.nvec;
     A.r0 = r0;
     A.r1 = r1;
-    A.rows_per_cta = (rows + grid - 1) / grid;
-    A.rows_per_cta = (A.rows_per_cta + s.r - 1) / s.r * s.r;
-    grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
+    A.rows_per_cta = 0;
     A.f = f;
     A.scale = c->fmt == LMOSEM_MODEL_FP32 ? nullptr : c->d_scale;
     A.n_sup = c->n_sup;
-    A.T = T;
-    A.back = back;
+    A.log_T = log(T);
     A.bpart = c->d_bpart;
     A.llpart = c->d_llpart;
-    // unused partial slots read as zero by the reduction
-    if (back && grid < c->pass_ctas)
-        LMOSEM_CK(c, cudaMemsetAsync(c->d_bpart + (size_t)grid * c->n_sup, 0,
-                                     sizeof(float) * (size_t)(c->pass_ctas - grid) * c->n_sup,
-                                     c->stream));
-    if (grid < c->pass_ctas)
-        LMOSEM_CK(c, cudaMemsetAsync(c->d_llpart + grid, 0,
-                                     sizeof(double) * (size_t)(c->pass_ctas - grid), c->stream));
-    if (rows <= 0) {
-        if (back)
-            LMOSEM_CK(c, cudaMemsetAsync(c->d_bpart, 0, sizeof(float) * (size_t)c->n_sup, c->stream));
-        LMOSEM_CK(c, cudaMemsetAsync(c->d_llpart, 0, sizeof(double), c->stream));
-        return LMOSEM_OK;
-    }
-    if (c->fmt == LMOSEM_MODEL_FP32) return launch_pass_h<float>(c, A, (int)grid, s);
-    if (c->fmt == LMOSEM_MODEL_FP16_SCALED) return launch_pass_h<__half>(c, A, (int)grid, s);
-    return launch_pass_h<__nv_bfloat16>(c, A, (int)grid, s);
+    if (c->fmt == LMOSEM_MODEL_FP32) return launch_pass_h<float, BACK>(c, A, rows, s);
+    if (c->fmt == LMOSEM_MODEL_FP16_SCALED) return launch_pass_h<__half, BACK>(c, A, rows, s);
+    return launch_pass_h<__nv_bfloat16, BACK>(c, A, rows, s);
+}
+
+lmosem_status ll_final(lmosem_ctx* c, double T, const float* d_f, double* out) {
+    LMOSEM_PROF_BEGIN(c);
+    k_ll_final<<<1, 256, 0, c->stream>>>(c->d_llpart, c->pass_grid,
+                                         c->d_sens + (size_t)c->n_subsets * c->n_sup, d_f,
+                                         c->n_sup, T, out);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+    return LMOSEM_OK;
 }
 
 }  // namespace
 
-// grid of the streaming pass: resident CTAs on every SM
+// capacity of the per-CTA partial buffers of the streaming pass
 lmosem_status setup_pass(lmosem_ctx* c) {
     int dev = 0, sms = 0;
     LMOSEM_CK(c, cudaGetDevice(&dev));
     LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    c->pass_ctas = sms * 4;
+    c->pass_ctas = sms * 8;
     lmosem_status st;
     if ((st = dev_alloc(c, &c->d_bpart, (size_t)c->pass_ctas * c->n_sup))) return st;
     if ((st = dev_alloc(c, &c->d_llpart, (size_t)c->pass_ctas))) return st;
@@ -336,22 +379,18 @@ lmosem_status setup_pass(lmosem_ctx* c) {
 
 lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll) {
     lmosem_status st;
-    const double* s_total = c->d_sens + (size_t)c->n_subsets * c->n_sup;
     for (int it = 0; it < n_iters; ++it) {
         for (int i = 0; i < c->n_subsets; ++i) {
-            if ((st = launch_pass(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T, 1)))
+            if ((st = launch_pass<true>(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T)))
                 return st;
             LMOSEM_PROF_BEGIN(c);
-            k_update<<<(c->n_sup + 255) / 256, 256, 0, c->stream>>>(
-                c->d_bpart, c->pass_ctas, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T);
+            k_update<<<(c->n_sup + 31) / 32, 256, 0, c->stream>>>(
+                c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T);
             LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
         }
         if (d_ll) {
-            if ((st = launch_pass(c, 0, c->J, d_f, T, 0))) return st;
-            LMOSEM_PROF_BEGIN(c);
-            k_ll_final<<<1, 256, 0, c->stream>>>(c->d_llpart, c->pass_ctas, s_total, d_f, c->n_sup,
-                                                 T, d_ll + it);
-            LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+            if ((st = launch_pass<false>(c, 0, c->J, d_f, T))) return st;
+            if ((st = ll_final(c, T, d_f, d_ll + it))) return st;
         }
     }
     return LMOSEM_OK;
@@ -359,13 +398,8 @@ lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, d
 
 lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out) {
     lmosem_status st;
-    if ((st = launch_pass(c, 0, c->J, d_f, T, 0))) return st;
-    LMOSEM_PROF_BEGIN(c);
-    k_ll_final<<<1, 256, 0, c->stream>>>(c->d_llpart, c->pass_ctas,
-                                         c->d_sens + (size_t)c->n_subsets * c->n_sup, d_f,
-                                         c->n_sup, T, d_out);
-    LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
-    return LMOSEM_OK;
+    if ((st = launch_pass<false>(c, 0, c->J, d_f, T))) return st;
+    return ll_final(c, T, d_f, d_out);
 }
 
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f) {
