@@ -195,6 +195,38 @@ int64_t lmosem_launch_count(const lmosem_ctx* ctx);
  * ESTATE: profiling is off. */
 lmosem_status lmosem_profile_read(lmosem_ctx* ctx, double* h_ms, int64_t* h_launches);
 
+/* One OS-LM-MLEM sub-iteration that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc or cudaFree, for example an application whose own
+ * allocator owns all device memory, or a processing loop that must not make
+ * calls that can synchronise the whole device.  It needs no context: the
+ * caller passes the model rows of one subset and the image, and the per-CTA
+ * partial back-projections use a 4 MiB array of static device memory that
+ * the library reserves on every GPU that loads it, until the process exits.
+ *
+ *   d_rows     device, n_rows x ld FP32 model rows p_jq of the subset's
+ *              events (row-major, 16-byte aligned, ld a multiple of 4,
+ *              columns n_support..ld-1 ignored if they hold zeros)
+ *   d_f        device, n_support FP32 image, updated in place:
+ *              f_q <- f_q sum_j p_jq / y_j / (T s_q), y_j = sum_q p_jq f_q;
+ *              rows with y_j = 0 add nothing; f_q = 0 where s_q = 0
+ *   d_sens_i   device, n_support FP64 subset sensitivities s_q (without T)
+ *   acq_time   T > 0
+ *   stream     cudaStream_t the work is enqueued on (NULL: legacy stream)
+ *
+ * EINVAL: null pointers, n_rows < 1, n_support < 1 or above 16384 (the
+ * static array holds at least 64 per-CTA partials of that length), ld out of
+ * range or misaligned rows.  ECUDA: a launch or the scratch lookup failed.
+ * The first call on each device looks up the address of the static array
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array and each call overwrites what
+ * it needs, so calls whose work overlaps on the GPU (different streams or
+ * threads) race and must be serialised by the caller. */
+lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_t n_rows, int32_t n_support,
+                                          int64_t ld, float* d_f, const double* d_sens_i,
+                                          double acq_time, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

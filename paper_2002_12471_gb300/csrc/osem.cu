@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "lmosem_internal.cuh"
@@ -410,6 +411,65 @@ lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f) {
     return LMOSEM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free sub-iteration (lmosem_osem_subiter_noalloc).
+//
+// The per-CTA partial back-projections live in one file-scope device array
+// instead of a context buffer.  Its host-side name is only a stand-in, so
+// the device address is looked up once per device with cudaGetSymbolAddress
+// (with that device current) and cached.  Every call shares the array; each
+// CTA overwrites its own slot before the reduction reads it, so nothing needs
+// clearing, but calls that overlap on the GPU race on it.
+namespace {
+
+constexpr int64_t kNoAllocScratchFloats = int64_t(1) << 20;  // 4 MiB
+constexpr int kNoAllocMaxSupport = 16384;                    // >= 64 partial slots
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+cudaError_t noalloc_scratch(float** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+template <int VPT>
+cudaError_t noalloc_pass(const PassArgs& A0, int64_t rows, int nt, cudaStream_t s, int* grid_out) {
+    constexpr int R = VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4);
+    auto kern = k_pass<float, VPT, R, true>;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    PassArgs A = A0;
+    int64_t grid = std::max(1, per_sm) * (int64_t)sms;
+    grid = std::min<int64_t>(grid, kNoAllocScratchFloats / A.n_sup);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, (rows + R - 1) / R));
+    A.rows_per_cta = (rows + grid - 1) / grid;
+    A.rows_per_cta = (A.rows_per_cta + R - 1) / R * R;
+    grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
+    kern<<<(unsigned)grid, nt, 0, s>>>(A);
+    *grid_out = (int)grid;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float* out) {
     if (n <= 0) return LMOSEM_OK;
     dim3 grid((c->n_sup + 255) / 256, (unsigned)std::min<int64_t>(n, 65535));
@@ -429,3 +489,56 @@ lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float
 }
 
 }  // namespace lmosem
+
+extern "C" lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_t n_rows,
+                                                     int32_t n_support, int64_t ld, float* d_f,
+                                                     const double* d_sens_i, double acq_time,
+                                                     void* stream) {
+    using namespace lmosem;
+    if (!d_rows || !d_f || !d_sens_i) return LMOSEM_EINVAL;
+    if (n_rows < 1 || n_support < 1 || n_support > kNoAllocMaxSupport) return LMOSEM_EINVAL;
+    if (ld < n_support || ld % 4 != 0 || (reinterpret_cast<uintptr_t>(d_rows) & 15u) != 0)
+        return LMOSEM_EINVAL;
+    if (!(acq_time > 0.0) || !isfinite(acq_time)) return LMOSEM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return LMOSEM_ECUDA;
+
+    // same column-vector shape as the context path (FP32 rows, 4 per vector)
+    const int64_t nvec = ld / 4;
+    const int opts[] = {1, 2, 3, 4, 6, 8};
+    int vpt = 8;
+    for (int v : opts)
+        if ((nvec + v - 1) / v <= kMaxPassThreads) {
+            vpt = v;
+            break;
+        }
+    if ((nvec + vpt - 1) / vpt > kMaxPassThreads) return LMOSEM_EINVAL;
+    const int nt = (int)(((nvec + vpt - 1) / vpt + 31) / 32 * 32);
+    PassArgs A;
+    A.model = d_rows;
+    A.ld_bytes = ld * 4;
+    A.nvec = nvec;
+    A.r0 = 0;
+    A.r1 = n_rows;
+    A.rows_per_cta = 0;
+    A.f = d_f;
+    A.scale = nullptr;
+    A.n_sup = n_support;
+    A.log_T = 0.0;
+    A.bpart = scratch;
+    A.llpart = nullptr;
+    int grid = 0;
+    cudaError_t e;
+    switch (vpt) {
+        case 1: e = noalloc_pass<1>(A, n_rows, nt, s, &grid); break;
+        case 2: e = noalloc_pass<2>(A, n_rows, nt, s, &grid); break;
+        case 3: e = noalloc_pass<3>(A, n_rows, nt, s, &grid); break;
+        case 4: e = noalloc_pass<4>(A, n_rows, nt, s, &grid); break;
+        case 6: e = noalloc_pass<6>(A, n_rows, nt, s, &grid); break;
+        default: e = noalloc_pass<8>(A, n_rows, nt, s, &grid); break;
+    }
+    if (e != cudaSuccess) return LMOSEM_ECUDA;
+    k_update<<<(n_support + 31) / 32, 256, 0, s>>>(scratch, grid, n_support, d_f, d_sens_i, acq_time);
+    return cudaGetLastError() == cudaSuccess ? LMOSEM_OK : LMOSEM_ECUDA;
+}

@@ -78,6 +78,7 @@ SIGNATURES = {
     "lmosem_model_bytes": (_i64, [_vp]),
     "lmosem_launch_count": (_i64, [_vp]),
     "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lmosem_osem_subiter_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i64, _vp, _vp, _dbl, _vp]),
 }
 
 _lib = None
@@ -213,6 +214,18 @@ def lmosem_profile_read(ctx):
     n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
     _check(ctx, load().lmosem_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def lmosem_osem_subiter_noalloc(d_rows, n_support, d_f, d_sens_i, acq_time, stream=None):
+    """One sub-iteration on caller-provided FP32 rows (a 2-D tensor, row
+    stride = its second dimension) without any device allocation; for
+    callers that cannot allocate device memory."""
+    n_rows, ld = int(d_rows.shape[0]), int(d_rows.stride(0))
+    s = getattr(stream, "cuda_stream", stream)
+    st = load().lmosem_osem_subiter_noalloc(_ptr(d_rows), n_rows, int(n_support), ld, _ptr(d_f),
+                                            _ptr(d_sens_i), float(acq_time), s)
+    if st != OK:
+        raise LmosemError(st, "lmosem_osem_subiter_noalloc rejected the call")
 
 
 def header_functions(header_path=None):
