@@ -90,6 +90,18 @@ typedef struct {
      * stream so that lmosem_profile_read can report device time per kernel
      * class (for benchmarks; adds two event records per launch). */
     int32_t profile;
+    /* Clock-cycle budget of every bounded device wait (the mbarrier waits of
+     * the streaming OSEM pass); 0 selects 2e9 (about one second).  A wait that
+     * runs out abandons the pass and the call returns LMOSEM_ETIMEOUT; the
+     * context stays usable.  Tests set a tiny budget to exercise that path. */
+    int64_t wait_budget_cycles;
+    /* Streaming-pass implementation (tuning knobs; 0 = automatic):
+     * 1 = rows double-buffered in registers, 2 = rows staged in a shared-
+     * memory ring by bulk (TMA) copies, ring_rows rows per stage (1..8) and
+     * ring_stages stages (2..8). */
+    int32_t pass_variant;
+    int32_t ring_rows;
+    int32_t ring_stages;
 } lmosem_options;
 
 /* Kernel classes reported by lmosem_profile_read. */

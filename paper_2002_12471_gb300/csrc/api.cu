@@ -131,6 +131,7 @@ void lmosem_destroy(lmosem_ctx* c) {
     dev_free(&c->d_bpart);
     dev_free(&c->d_llpart);
     dev_free(&c->d_scalar);
+    dev_free(&c->d_status);
     for (auto& r : c->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -179,6 +180,17 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     c->k_sigma = ks;
     if (opts && opts->table_budget_bytes > 0) c->table_budget = opts->table_budget_bytes;
     c->profile = opts && opts->profile != 0;
+    if (opts && opts->wait_budget_cycles > 0) c->wait_budget = opts->wait_budget_cycles;
+    if (opts) {
+        if (opts->pass_variant < 0 || opts->pass_variant > 2 || opts->ring_rows < 0 ||
+            opts->ring_stages < 0) {
+            delete c;
+            return LMOSEM_EINVAL;
+        }
+        c->pass_variant = opts->pass_variant;
+        c->ring_rows = opts->ring_rows;
+        c->ring_stages = opts->ring_stages;
+    }
 
     std::vector<float> mu(c->npix);
     double rmax = 0.0;
@@ -315,19 +327,20 @@ lmosem_status lmosem_iterate(lmosem_ctx* c, int32_t n_iters, double T, float* d_
     if (c->fmt < 0) return fail(c, LMOSEM_ESTATE, "no model built");
     if (c->sens_subsets != c->n_subsets)
         return fail(c, LMOSEM_ESTATE, "sensitivity missing or for another subset count");
+    LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     lmosem_status st = run_iterations(c, n_iters, T, d_f, d_ll);
     if (st) return st;
-    lmosem_status st2;
-    if (!c->d_scalar && (st2 = dev_alloc(c, &c->d_scalar, 4))) return st2;
-    int* bad = reinterpret_cast<int*>(c->d_scalar);
+    // status word and non-finite count: [0] wait timeouts, [1] non-finite pixels
+    int* bad = c->d_status + 1;
     LMOSEM_CK(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
     LMOSEM_PROF_BEGIN(c);
     k_count_nonfinite<<<(c->n_sup + 255) / 256, 256, 0, c->stream>>>(d_f, c->n_sup, bad);
     LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
-    int h = 0;
-    LMOSEM_CK(c, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int h[2] = {0, 0};
+    LMOSEM_CK(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    if (h) return fail(c, LMOSEM_ENUMERIC, std::to_string(h) + " non-finite image values");
+    if (h[0]) return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait ran out; the image is not updated");
+    if (h[1]) return fail(c, LMOSEM_ENUMERIC, std::to_string(h[1]) + " non-finite image values");
     return LMOSEM_OK;
 }
 
@@ -336,7 +349,14 @@ lmosem_status lmosem_loglik(lmosem_ctx* c, double T, const float* d_f, double* d
     if (!d_f || !d_out || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad arguments");
     if (c->fmt < 0 || c->sens_subsets != c->n_subsets)
         return fail(c, LMOSEM_ESTATE, "needs a model and a matching sensitivity");
-    return run_loglik(c, T, d_f, d_out);
+    LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    lmosem_status st = run_loglik(c, T, d_f, d_out);
+    if (st) return st;
+    int h = 0;
+    LMOSEM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h) return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait ran out");
+    return LMOSEM_OK;
 }
 
 lmosem_status lmosem_profile_read(lmosem_ctx* c, double* h_ms, int64_t* h_launches) {

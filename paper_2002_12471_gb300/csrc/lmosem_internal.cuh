@@ -93,6 +93,10 @@ struct lmosem_ctx {
     float* d_bpart = nullptr;     // pass_ctas x n_sup
     double* d_llpart = nullptr;   // pass_ctas
     double* d_scalar = nullptr;   // small FP64 scratch
+    int* d_status = nullptr;      // [0] = 1 after a bounded device wait ran out
+    long long wait_budget = 2000000000LL;  // clock cycles per bounded wait
+    int pass_variant = 0;         // 0 auto, 1 register pipeline, 2 bulk-copy ring
+    int ring_rows = 0, ring_stages = 0;  // ring shape (0: from the row size)
 
     // kernel timing (opts->profile)
     bool profile = false;

@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
 // then f_q <- f_q b_q / (T s^i_q)
 __global__ void __launch_bounds__(256) k_update(const float* __restrict__ bpart, int nparts, int n_sup,
                                                 float* __restrict__ f, const double* __restrict__ sens_i,
-                                                double T) {
+                                                double T, const int* __restrict__ status) {
+    if (status && *status) return;  // the pass was abandoned: keep the image
     __shared__ float sh[8][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * 32 + lane;
@@ -277,6 +278,225 @@ __global__ void k_model_rows(const H* __restrict__ model, int64_t ld, const floa
     }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming pass through a shared-memory ring filled by bulk (TMA) copies.
+//
+// A CTA owns a contiguous chunk of rows.  Its rows come in groups of G
+// consecutive rows (one cp.async.bulk of G row strides each) into S ring
+// stages; every stage has an mbarrier that completes when the copy's bytes
+// have landed.  Up to S groups are in flight while the CTA reduces the
+// current one, so the pass streams at HBM rate without holding rows in
+// registers.  Every wait is bounded: a wait that outlasts its clock budget
+// sets *status = 1, waits (bounded) for the CTA's copies still in flight and
+// returns without writing results.
+constexpr int kRingMaxStages = 8;
+constexpr int kRingMaxG = 8;
+
+struct RingArgs {
+    const char* model;
+    int64_t ld_bytes;        // row stride, bytes (multiple of 16)
+    int64_t nvec;            // 16-byte vectors per row holding the support
+    int64_t r0, r1;          // rows of this pass
+    int64_t rows_per_cta;
+    int G, S;                // rows per stage, stages
+    const float* f;
+    const float* scale;      // row scales (scaled forms) or nullptr
+    int n_sup;
+    double log_T;
+    float* bpart;            // [cta][n_sup]
+    double* llpart;          // [cta]
+    int* status;             // set to 1 on a wait timeout
+    long long wait_budget;   // clock cycles per wait
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arm_and_copy(uint64_t* bar, void* dst, const void* src,
+                                                  unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false when the budget ran out.  The non-blocking test comes
+// before every budget check (try_wait may suspend the thread for a while).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long budget) {
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if (clock64() - t0 > budget) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+    }
+}
+
+template <typename H, int VPT, bool BACK>
+__global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
+    constexpr int EPV = Vec<H>::N;
+    extern __shared__ __align__(128) unsigned char ring[];
+    __shared__ __align__(8) uint64_t bar[kRingMaxStages];
+    __shared__ float red[kRingMaxG][kMaxPassThreads / 32];
+    __shared__ double llred[kMaxPassThreads / 32];
+    const int NT = blockDim.x, NW = NT >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int G = A.G, S = A.S;
+    const int64_t stage_bytes = (int64_t)G * A.ld_bytes;
+
+    float fr[VPT][EPV], br[VPT][EPV];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        int col0 = EPV * (t + NT * v);
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) {
+            int col = col0 + e;
+            fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
+            br[v][e] = 0.0f;
+        }
+    }
+    const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
+    const int64_t re = min(A.r1, rb + A.rows_per_cta);
+    const int64_t ngroups = re > rb ? (re - rb + G - 1) / G : 0;
+
+    if (t == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t g) {  // thread 0 only
+        const int s = (int)(g % S);
+        const int64_t row = rb + g * G;
+        const int64_t nrow = min((int64_t)G, re - row);
+        mbar_arm_and_copy(&bar[s], ring + s * stage_bytes, A.model + row * A.ld_bytes,
+                          (unsigned)(nrow * A.ld_bytes));
+    };
+    if (t == 0)
+        for (int64_t g = 0; g < min((int64_t)S, ngroups); ++g) issue(g);
+
+    double ll = 0.0;
+    int npos = 0;
+    bool aborted = false;
+    int64_t g = 0;
+    for (; g < ngroups; ++g) {
+        const int s = (int)(g % S);
+        const unsigned parity = (unsigned)((g / S) & 1);
+        bool ok = mbar_wait_bounded(&bar[s], parity, A.wait_budget);
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        const int64_t row = rb + g * G;
+        const int nrow = (int)min((int64_t)G, re - row);
+        const unsigned char* st = ring + s * stage_bytes;
+        for (int i = 0; i < nrow; ++i) {
+            const uint4* rp = reinterpret_cast<const uint4*>(st + i * A.ld_bytes);
+            float sdot = 0.0f;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                int64_t vec = t + (int64_t)NT * v;
+                if (vec < A.nvec) {
+                    float p[EPV];
+                    Vec<H>::cvt(rp[vec], p);
+#pragma unroll
+                    for (int e = 0; e < EPV; ++e) sdot = fmaf(p[e], fr[v][e], sdot);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+            if (lane == 0) red[i][warp] = sdot;
+        }
+        __syncthreads();
+        for (int i = 0; i < nrow; ++i) {
+            float y = 0.0f;
+            for (int w = 0; w < NW; ++w) y += red[i][w];
+            if constexpr (BACK) {
+                const float inv = y > 0.0f ? 1.0f / y : 0.0f;
+                const uint4* rp = reinterpret_cast<const uint4*>(st + i * A.ld_bytes);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    int64_t vec = t + (int64_t)NT * v;
+                    if (vec < A.nvec) {
+                        float p[EPV];
+                        Vec<H>::cvt(rp[vec], p);
+#pragma unroll
+                        for (int e = 0; e < EPV; ++e) br[v][e] = fmaf(p[e], inv, br[v][e]);
+                    }
+                }
+            } else {
+                if (t == (i & (kMaxPassThreads - 1)) && y > 0.0f) {
+                    float c = A.scale ? A.scale[row + i] : 1.0f;
+                    ll += (double)logf(c * y);
+                    ++npos;
+                }
+            }
+        }
+        __syncthreads();  // stage s and red[] are free again
+        if (t == 0 && g + S < ngroups) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue(g + S);
+        }
+    }
+    if (aborted) {
+        if (t == 0) {
+            atomicExch(A.status, 1);
+            // copies still in flight target this CTA's shared memory: wait for
+            // them (bounded) before the CTA exits
+            for (int64_t q = g; q < min(ngroups, g + S); ++q)
+                mbar_wait_bounded(&bar[q % S], (unsigned)((q / S) & 1), A.wait_budget * 4 + 4000000000LL);
+        }
+        __syncthreads();
+        return;
+    }
+    if constexpr (BACK) {
+        float* bp = A.bpart + (size_t)blockIdx.x * A.n_sup;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            int col0 = EPV * (t + NT * v);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e)
+                if (col0 + e < A.n_sup) bp[col0 + e] = br[v][e];
+        }
+    } else {
+        ll += (double)npos * A.log_T;
+        for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if (lane == 0) llred[warp] = ll;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += llred[w];
+            A.llpart[blockIdx.x] = s;
+        }
+    }
+}
+
 struct PassShape {
     int vpt, nt;
     int64_t nvec;
@@ -296,8 +516,9 @@ PassShape pass_shape(const lmosem_ctx* c) {
     return {vpt, nt, nvec};
 }
 
+// register-pipelined pass (pass_variant 0 or 1)
 template <typename H, int VPT, bool BACK>
-lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
+lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
     constexpr int R = VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4);
     auto kern = k_pass<H, VPT, R, BACK>;
     int per_sm = 0, dev = 0, sms = 0;
@@ -313,6 +534,52 @@ lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
     c->pass_grid = (int)grid;
     LMOSEM_PROF_BEGIN(c);
     kern<<<(unsigned)grid, nt, 0, c->stream>>>(A);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
+    return LMOSEM_OK;
+}
+
+// bulk-copy ring pass (pass_variant 2)
+template <typename H, int VPT, bool BACK>
+lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
+    if (c->pass_variant != 2) return launch_pass_reg_t<H, VPT, BACK>(c, A0, rows, nt);
+    auto kern = k_pass_ring<H, VPT, BACK>;
+    // ring shape: stages of G rows (~24 KB), ~96 KB of stages per CTA unless set
+    const int64_t rb = A0.ld_bytes;
+    int G = (int)std::max<int64_t>(1, std::min<int64_t>(kRingMaxG, (24 << 10) / rb));
+    if (c->ring_rows > 0) G = std::min(kRingMaxG, c->ring_rows);
+    int S = (int)std::max<int64_t>(2, std::min<int64_t>(kRingMaxStages, (96 << 10) / (G * rb)));
+    if (c->ring_stages > 0) S = std::max(2, std::min(kRingMaxStages, c->ring_stages));
+    const size_t smem = (size_t)S * G * rb;
+    LMOSEM_CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    LMOSEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+    LMOSEM_CK(c, cudaGetDevice(&dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = std::max(1, per_sm) * (int64_t)sms;
+    grid = std::min<int64_t>(grid, c->pass_ctas);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, (rows + G - 1) / G));
+    RingArgs A;
+    A.model = reinterpret_cast<const char*>(A0.model);
+    A.ld_bytes = A0.ld_bytes;
+    A.nvec = A0.nvec;
+    A.r0 = A0.r0;
+    A.r1 = A0.r1;
+    A.rows_per_cta = (rows + grid - 1) / grid;
+    A.rows_per_cta = (A.rows_per_cta + G - 1) / G * G;
+    grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
+    A.G = G;
+    A.S = S;
+    A.f = A0.f;
+    A.scale = A0.scale;
+    A.n_sup = A0.n_sup;
+    A.log_T = A0.log_T;
+    A.bpart = A0.bpart;
+    A.llpart = A0.llpart;
+    A.status = c->d_status;
+    A.wait_budget = c->wait_budget;
+    c->pass_grid = (int)grid;
+    LMOSEM_PROF_BEGIN(c);
+    kern<<<(unsigned)grid, nt, smem, c->stream>>>(A);
     LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
     return LMOSEM_OK;
 }
@@ -375,6 +642,8 @@ lmosem_status setup_pass(lmosem_ctx* c) {
     lmosem_status st;
     if ((st = dev_alloc(c, &c->d_bpart, (size_t)c->pass_ctas * c->n_sup))) return st;
     if ((st = dev_alloc(c, &c->d_llpart, (size_t)c->pass_ctas))) return st;
+    if ((st = dev_alloc(c, &c->d_status, 4))) return st;
+    LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
     return LMOSEM_OK;
 }
 
@@ -386,7 +655,8 @@ lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, d
                 return st;
             LMOSEM_PROF_BEGIN(c);
             k_update<<<(c->n_sup + 31) / 32, 256, 0, c->stream>>>(
-                c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T);
+                c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T,
+                c->d_status);
             LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
         }
         if (d_ll) {
@@ -539,6 +809,7 @@ extern "C" lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_
         default: e = noalloc_pass<8>(A, n_rows, nt, s, &grid); break;
     }
     if (e != cudaSuccess) return LMOSEM_ECUDA;
-    k_update<<<(n_support + 31) / 32, 256, 0, s>>>(scratch, grid, n_support, d_f, d_sens_i, acq_time);
+    k_update<<<(n_support + 31) / 32, 256, 0, s>>>(scratch, grid, n_support, d_f, d_sens_i, acq_time,
+                                                   nullptr);
     return cudaGetLastError() == cudaSuccess ? LMOSEM_OK : LMOSEM_ECUDA;
 }

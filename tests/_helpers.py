@@ -11,7 +11,7 @@ def oracle_problem(ph, g, support=None):
 
 
 def gpu_reconstruct(ph, g, ev, n_subsets, n_iters, fmt="fp32", T=1.0, support=None,
-                    rows=None, loglik=False, k_sigma=0.0):
+                    rows=None, loglik=False, k_sigma=0.0, **opts):
     """Sensitivity, model build and n_iters OSEM iterations on cuda:0.
     Returns a dict with the image, sensitivities, optional model rows (by
     original event index) and optional per-iteration log-likelihoods."""
@@ -22,7 +22,7 @@ def gpu_reconstruct(ph, g, ev, n_subsets, n_iters, fmt="fp32", T=1.0, support=No
     dev = torch.device("cuda:0")
     out = {}
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, support=support, k_sigma=k_sigma,
-                          stream=torch.cuda.current_stream())
+                          stream=torch.cuda.current_stream(), **opts)
     try:
         nsup = L.lmosem_n_support(ctx)
         out["support"] = L.lmosem_support(ctx)

@@ -190,6 +190,53 @@ def test_bitwise_deterministic():
     assert oracle.rel_l2(c["f"], a["f"]) <= 1e-5
 
 
+@pytest.mark.parametrize("rows_stages", [(0, 0), (1, 2), (3, 5), (8, 8)])
+def test_ring_pass_variant_matches_oracle(rows_stages):
+    """The bulk-copy ring pass (several stage shapes, ragged row groups)
+    gives the same reconstruction and log-likelihood as the oracle."""
+    ph, g, J, ns, ni = S.workload("dat32")
+    ev = S.simulate_events(ph, g, 9001, seed=13)
+    P = oracle_problem(ph, g)
+    p, s, f_ref, hist = _oracle_recon(P, ev, ns, 3)
+    out = gpu_reconstruct(ph, g, ev, ns, 3, loglik=True, pass_variant=2,
+                          ring_rows=rows_stages[0], ring_stages=rows_stages[1])
+    assert oracle.rel_l2(out["f"], f_ref) <= 1e-4
+    ll_ref = [oracle.loglik(p, h, s.sum(0)) for h in hist]
+    np.testing.assert_allclose(out["loglik"], ll_ref, rtol=1e-6)
+
+
+def test_wait_timeout_reports_etimeout_and_context_survives():
+    """A bounded device wait that runs out (a one-cycle budget injected through
+    the options; the bulk copies still complete and are drained) makes
+    lmosem_iterate return LMOSEM_ETIMEOUT without touching the image, and the
+    GPU stays usable."""
+    import torch
+
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g, J, ns, ni = S.workload("tiny16")
+    ev = S.simulate_events(ph, g, 500, seed=12)
+    dev = torch.device("cuda:0")
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, wait_budget_cycles=1, pass_variant=2)
+    try:
+        L.lmosem_sensitivity(ctx, 2)
+        L.lmosem_build_model(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                             torch.from_numpy(ev.e_kev).to(dev), 2)
+        f = torch.zeros(L.lmosem_n_support(ctx), dtype=torch.float32, device=dev)
+        L.lmosem_init_image(ctx, 1.0, f)
+        f0 = f.clone()
+        for _ in range(2):
+            with pytest.raises(L.LmosemError) as ei:
+                L.lmosem_iterate(ctx, 1, 1.0, f)
+            assert ei.value.status == L.ETIMEOUT
+            assert torch.equal(f, f0)
+    finally:
+        L.lmosem_destroy(ctx)
+    P = oracle_problem(ph, g)
+    p, s, f_ref, _ = _oracle_recon(P, ev, 2, 2)
+    out = gpu_reconstruct(ph, g, ev, 2, 2)
+    assert oracle.rel_l2(out["f"], f_ref) <= 1e-4
+
+
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 def test_scaled_model_forms(fmt):
     ph, g, J, ns, ni = S.workload("dat32")
