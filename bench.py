@@ -36,10 +36,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "event-pixel model evals/s & LM-OSEM s/iter on 1 GB300, exact vs chosen @ error"
 UNIT = "evals/s"
+WORKLOADS = {
+    "dat64": ("2-D DaT-like brain, 64x64 pixels at 4 mm, 120 angles x 64 bins x 4 mm, R = 150 mm, "
+              "200,000 list-mode events (100-175 keV, 10% FWHM at 159 keV), 8 subsets x 10 "
+              "iterations, FP32 model and accumulation"),
+    "dat128": ("2-D DaT-like brain, 128x128 pixels at 2 mm, 120 angles x 128 bins x 2 mm, R = 150 mm, "
+               "1,000,000 list-mode events (100-175 keV, 10% FWHM at 159 keV), 8 subsets x 10 "
+               "iterations, model cached in the chosen format, FP32 accumulation"),
+    "batch64": ("64 independent noise realisations of the 64x64 DaT phantom (120 angles, R = 150 mm), "
+                "event counts Poisson with means uniform in [50k, 400k], 8 subsets x 10 iterations, "
+                "all realisations in one persistent launch, FP32 model"),
+}
 WORKLOAD = "dat64"
-WORKLOAD_DESC = ("2-D DaT-like brain, 64x64 pixels at 4 mm, 120 angles x 64 bins x 4 mm, R = 150 mm, "
-                 "200,000 list-mode events (100-175 keV, 10% FWHM at 159 keV), 8 subsets x 10 "
-                 "iterations, FP32 model and accumulation")
+WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 # MUFU ex2 throughput of a GB300 SM, measured with independent ex2.approx.ftz.f32
 # chains (4 CTAs x 512 threads per SM): 31.8 per clock, i.e. 32 (twice the 16 of
 # compute capability 10.0).  Each path term needs one ex2 and three FP32 FMAs,
@@ -58,7 +67,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=0,
                     help="override the event count (small cases for profiling)")
-    return ap.parse_args()
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dat64")
+    args = ap.parse_args()
+    global WORKLOAD, WORKLOAD_DESC
+    WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOADS[args.workload]
+    return args
 
 
 def peaks():
@@ -170,7 +183,10 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library replays OSEM iterations as
+    # CUDA graphs on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     ph, g, ev, ns, ni = make_inputs(seed=2 + rank, events=args.events)
     J = len(ev)
     a_h = torch.from_numpy(ev.angle).pin_memory()
@@ -180,7 +196,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB of L2
     T = 1.0
 
-    def step(a, u, e, profile=False, host_out=None):
+    def step(a, u, e, profile=0, host_out=None):
         ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile)
         try:
             nsup = L.lmosem_n_support(ctx)
@@ -221,7 +237,8 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        nsup, prof, nl, f, ll = step(a_d, u_d, e_d, profile=True)
+        # kernel timing of everything but the graph-replayed OSEM iterations
+        nsup, prof, nl, f, ll = step(a_d, u_d, e_d, profile=2)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -253,27 +270,32 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
 
-    # ---- seconds per OSEM iteration with the model cached
-    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=True)
-    try:
-        L.lmosem_sensitivity(ctx, ns)
-        L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, args.fmt)
-        f = torch.empty(nsup, dtype=torch.float32, device=dev)
-        L.lmosem_init_image(ctx, T, f)
-        L.lmosem_iterate(ctx, 2, T, f)
-        L.lmosem_profile_read(ctx)
-        model_bytes = L.lmosem_model_bytes(ctx)
-        it_times = []
-        for _ in range(10):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            L.lmosem_iterate(ctx, 1, T, f)
-            e1.record(stream)
-            e1.synchronize()
-            it_times.append(e0.elapsed_time(e1))
-        it_prof = L.lmosem_profile_read(ctx)
-    finally:
-        L.lmosem_destroy(ctx)
+    # ---- seconds per OSEM iteration with the model cached (graph replay), and
+    # the per-kernel times of the pass and the update from a profiled context
+    it_times = []
+    for prof_level in (0, 1):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=prof_level)
+        try:
+            L.lmosem_sensitivity(ctx, ns)
+            L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, args.fmt)
+            f = torch.empty(nsup, dtype=torch.float32, device=dev)
+            L.lmosem_init_image(ctx, T, f)
+            L.lmosem_iterate(ctx, 2, T, f)
+            if prof_level:
+                L.lmosem_profile_read(ctx)
+                L.lmosem_iterate(ctx, 10, T, f)
+                it_prof = L.lmosem_profile_read(ctx)
+            else:
+                model_bytes = L.lmosem_model_bytes(ctx)
+                for _ in range(10):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    L.lmosem_iterate(ctx, 1, T, f)
+                    e1.record(stream)
+                    e1.synchronize()
+                    it_times.append(e0.elapsed_time(e1))
+        finally:
+            L.lmosem_destroy(ctx)
 
     terms, n_nz = strip_terms(ph, g, ev)
     evals = J * n_nz
@@ -288,6 +310,14 @@ def run_ours(args, rank, world, local_rank):
             a = agg.setdefault(k, [0.0, 0])
             a[0] += ms
             a[1] += n
+    # the timed steps replay the OSEM iterations as CUDA graphs, untimed per
+    # kernel; their pass and update kernels enter the breakdown from the
+    # profiled context (10 iterations), scaled to the step's iterations
+    for k in ("pass", "update"):
+        ms, n = it_prof[k]
+        a = agg.setdefault(k, [0.0, 0])
+        a[0] += ms * ni / 10 * args.steps
+        a[1] += int(round(n * ni / 10 * args.steps))
     tot_kernel_ms = sum(v[0] for v in agg.values())
     ps_ms, ps_n = agg["pathsum"]
     ps_launch_ms = ps_ms / max(1, ps_n)
@@ -448,6 +478,106 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ batching form
+
+def _realisation_events(args):
+    """Worker: events of one realisation (numpy only, no CUDA)."""
+    r, n = args
+    from paper_2002_12471_gb300 import synthetic as S
+    ph, g, _, _, _ = S.workload("dat64")
+    ev = S.simulate_events(ph, g, int(n), seed=4000 + r)
+    return ev.angle, ev.u_mm, ev.e_kev
+
+
+def run_batch_bench(args):
+    """64 noise realisations of the 64x64 DaT phantom with Poisson event counts
+    (lambda uniform in [50k, 400k]) reconstructed together: one step = model
+    build for all realisations + 10 batched iterations (one persistent
+    launch), tiles chosen by the autotuner."""
+    import multiprocessing as mp
+
+    from paper_2002_12471_gb300 import synthetic as S
+    counts = S.realisation_counts(64, seed=4)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any CUDA call
+        parts = pool.map(_realisation_events, list(enumerate(counts)))
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g, _, ns, ni = S.workload("dat64")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    a = torch.from_numpy(np.concatenate([p[0] for p in parts])).to(dev)
+    u = torch.from_numpy(np.concatenate([p[1] for p in parts])).to(dev)
+    e = torch.from_numpy(np.concatenate([p[2] for p in parts])).to(dev)
+    J = int(off[-1])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    choice = None
+
+    def step(tune=False):
+        nonlocal choice
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=2)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            L.lmosem_sensitivity(ctx, ns)
+            L.lmosem_build_model_batch(ctx, a, u, e, off, ns)
+            f = torch.empty((len(counts), nsup), dtype=torch.float32, device=dev)
+            L.lmosem_init_image_batch(ctx, 1.0, f)
+            if tune:
+                choice = L.lmosem_autotune_batch(ctx, 1.0, f)
+            L.lmosem_set_batch_tiles(ctx, *choice)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.lmosem_iterate_batch(ctx, ni, 1.0, f)
+            e1.record(stream)
+            e1.synchronize()
+            prof = L.lmosem_profile_read(ctx)
+            return nsup, e0.elapsed_time(e1), prof, L.lmosem_model_bytes(ctx), L.lmosem_launch_count(ctx)
+        finally:
+            L.lmosem_destroy(ctx)
+
+    step(tune=True)
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    clocks = ClockSampler(None)
+    torch.cuda.synchronize()
+    clocks.start()
+    times, it_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        nsup, ims, prof, model_bytes, nl = step()
+        t1.record(stream)
+        t1.synchronize()
+        times.append(t0.elapsed_time(t1))
+        it_ms.append(ims)
+        launches += nl
+    clk = clocks.stop()
+    pk, pk_kind = peaks()
+    ms_step = statistics.mean(times)
+    s_iter = statistics.mean(it_ms) / ni * 1e-3
+    gbs = model_bytes / s_iter / 1e9
+    return {
+        "metric": METRIC, "value": J * nsup / (ms_step * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events)",
+        "config": {"workload": WORKLOAD_DESC, "events": J, "realisations": len(counts),
+                   "events_min_max": [int(min(counts)), int(max(counts))], "support_pixels": nsup,
+                   "tiles": {"chunk_rows": choice[0], "ctas_per_sm": choice[1]},
+                   "l2": "model (%.1f GB) larger than L2; 256 MB flush before every step" % (model_bytes / 1e9)},
+        "s_per_iter": s_iter,
+        "batched_iteration": {"gbs": gbs, "frac_of_%s_hbm" % pk_kind: gbs / pk["hbm_gbs"],
+                              "model_bytes": model_bytes, "persistent_launches_per_call": 1},
+        "breakdown_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
+        "clocks": clk, "gpu_launches": launches,
+    }
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -465,6 +595,8 @@ def main():
             dist.init_process_group("gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif WORKLOAD == "batch64":
+        out = run_batch_bench(args)
     else:
         out = run_ours(args, rank, world, local_rank)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -86,9 +86,11 @@ typedef struct {
     /* Upper bound (bytes) of the per-angle scatter-weight tables kept on the
      * device while a model is built; 0 selects 4 GiB. */
     int64_t table_budget_bytes;
-    /* Nonzero: bracket every kernel launch with CUDA events on the context
-     * stream so that lmosem_profile_read can report device time per kernel
-     * class (for benchmarks; adds two event records per launch). */
+    /* Kernel timing for benchmarks.  1: bracket every kernel launch with
+     * CUDA events on the context stream so that lmosem_profile_read can
+     * report device time per kernel class (OSEM iterations are then launched
+     * one kernel at a time).  2: the same, except that OSEM iterations keep
+     * their CUDA-graph replay on non-default streams and are not timed. */
     int32_t profile;
     /* Clock-cycle budget of every bounded device wait (the mbarrier waits of
      * the streaming OSEM pass); 0 selects 2e9 (about one second).  A wait that
@@ -169,6 +171,41 @@ lmosem_status lmosem_sensitivity(lmosem_ctx* ctx, int32_t n_subsets, double* d_s
 lmosem_status lmosem_build_model(lmosem_ctx* ctx, const int32_t* d_angle, const float* d_u_mm,
                                  const float* d_e_kev, int64_t n_events, int32_t n_subsets,
                                  lmosem_model_fmt fmt);
+
+/* Batching form: one model for n_real independent list-mode data sets (noise
+ * realisations; the paper repeats its study over multiple noise realisations,
+ * Section 3) of the same object and scanner.  The events of realisation r are
+ * d_*[h_event_offsets[r] .. h_event_offsets[r+1]) (host offsets, n_real + 1,
+ * from 0, not decreasing; realisations may differ in size and may be empty).
+ * The model is FP32 (ENOTIMPL for the scaled formats).  Afterwards use the
+ * *_batch calls; the single-data-set calls return ESTATE.  Synchronises.
+ * EINVAL: as lmosem_build_model, or n_real outside 1..1536, bad offsets. */
+lmosem_status lmosem_build_model_batch(lmosem_ctx* ctx, const int32_t* d_angle, const float* d_u_mm,
+                                       const float* d_e_kev, const int64_t* h_event_offsets,
+                                       int32_t n_real, int32_t n_subsets, lmosem_model_fmt fmt);
+
+/* Starting images of a batched model: d_f[r * N_nz + q] = J_r / (T sum s). */
+lmosem_status lmosem_init_image_batch(lmosem_ctx* ctx, double acq_time, float* d_f);
+
+/* n_iters OS-LM-MLEM iterations (paper Eqs. 7-9) of every realisation, all in
+ * one persistent kernel launch (replayed as a CUDA graph on a non-default
+ * stream).  d_f: n_real x N_nz FP32 images, updated in place.  The rows of a
+ * (realisation, subset) are split into chunks of the tile size set by
+ * lmosem_set_batch_tiles / lmosem_autotune_batch (default 512 rows, 2 CTAs
+ * per SM).  Synchronises.  ETIMEOUT: a bounded wait of the persistent kernel
+ * ran out (images then partly updated). */
+lmosem_status lmosem_iterate_batch(lmosem_ctx* ctx, int32_t n_iters, double acq_time, float* d_f);
+
+/* Autotuner of the batched iterations: times one iteration of every
+ * (chunk rows in {128..2048}, CTAs per SM in {1..4}) candidate on a scratch
+ * copy of d_f (not modified), keeps the fastest for this context and writes
+ * it to h_choice[0..1] (may be NULL).  Synchronises. */
+lmosem_status lmosem_autotune_batch(lmosem_ctx* ctx, double acq_time, const float* d_f,
+                                    int32_t* h_choice);
+
+/* Set the batched tiles directly (e.g. a choice cached from an earlier
+ * autotuning): chunk_rows in [8, 2^20], ctas_per_sm in [1, 16]. */
+lmosem_status lmosem_set_batch_tiles(lmosem_ctx* ctx, int32_t chunk_rows, int32_t ctas_per_sm);
 
 /* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz).
  * ESTATE: no model or sensitivity. */

@@ -34,6 +34,7 @@ static cudaEvent_t prof_event(lmosem_ctx* c) {
 }
 
 void prof_begin(lmosem_ctx* c) {
+    if (c->capturing) return;
     c->prof_open = prof_event(c);
     cudaEventRecord(c->prof_open, c->stream);
 }
@@ -55,7 +56,17 @@ __global__ void k_count_nonfinite(const float* __restrict__ f, int n, int* __res
 
 bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
+void drop_graph(lmosem_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    c->graph_f = nullptr;
+    if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
+    c->bgraph_exec = nullptr;
+    c->bgraph_f = nullptr;
+}
+
 void free_model(lmosem_ctx* c) {
+    drop_graph(c);
     dev_free(&c->d_model);
     dev_free(&c->d_scale);
     dev_free(&c->d_stage);
@@ -68,9 +79,69 @@ void free_model(lmosem_ctx* c) {
     dev_free(&c->d_angle_cnt);
     dev_free(&c->d_tile_prefix);
     dev_free(&c->d_wtab);
+    dev_free(&c->d_bsub_row0);
+    dev_free(&c->d_breal_row0);
+    dev_free(&c->d_bclaim);
+    dev_free(&c->d_bdone);
+    dev_free(&c->d_bpart_batch);
+    c->bpart_batch_floats = 0;
+    c->batch_model = false;
+    c->n_real = 1;
     c->fmt = -1;
     c->J = 0;
     c->n_subsets = 0;
+}
+
+lmosem_status check_events_args(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
+                                const float* d_e, int64_t n_events, int32_t n_subsets,
+                                lmosem_model_fmt fmt) {
+    if (!d_angle || !d_u || !d_e) return fail(c, LMOSEM_EINVAL, "null event array");
+    if (n_events < 1 || n_events >= (int64_t(1) << 31))
+        return fail(c, LMOSEM_EINVAL, "n_events must be in [1, 2^31)");
+    if (n_subsets < 1 || n_subsets > c->n_angles)
+        return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
+    if (fmt != LMOSEM_MODEL_FP32 && fmt != LMOSEM_MODEL_FP16_SCALED && fmt != LMOSEM_MODEL_BF16_SCALED)
+        return fail(c, LMOSEM_EINVAL, "unknown model format");
+    return LMOSEM_OK;
+}
+
+// allocation, sort and row build shared by the single and the batched model
+lmosem_status build_model_common(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
+                                 const float* d_e_kev, int64_t n_events, int32_t n_subsets,
+                                 lmosem_model_fmt fmt, const int64_t* h_offsets, int n_real) {
+    free_model(c);
+    c->fmt = fmt;
+    c->J = n_events;
+    c->n_subsets = n_subsets;
+    c->ld_model = (c->n_sup + 31) / 32 * 32;
+    lmosem_status st;
+    size_t elem = fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
+    {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)n_events * c->ld_model * elem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_model(c);
+            return fail(c, LMOSEM_ENOMEM, "model of " +
+                                              std::to_string((size_t)n_events * c->ld_model * elem) +
+                                              " bytes does not fit: " + cudaGetErrorString(e));
+        }
+        c->d_model = p;
+    }
+    if (fmt != LMOSEM_MODEL_FP32 && (st = dev_alloc(c, &c->d_scale, n_events))) {
+        free_model(c);
+        return st;
+    }
+    if ((st = sort_events(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, h_offsets, n_real))) {
+        free_model(c);
+        return st;
+    }
+    if ((st = build_model_rows(c))) {
+        free_model(c);
+        return st;
+    }
+    if (!c->d_bpart && (st = setup_pass(c))) return st;
+    return LMOSEM_OK;
 }
 
 }  // namespace
@@ -179,7 +250,11 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     c->e_hi = en->e_hi_kev;
     c->k_sigma = ks;
     if (opts && opts->table_budget_bytes > 0) c->table_budget = opts->table_budget_bytes;
-    c->profile = opts && opts->profile != 0;
+    c->profile = opts ? opts->profile : 0;
+    if (c->profile < 0 || c->profile > 2) {
+        delete c;
+        return LMOSEM_EINVAL;
+    }
     if (opts && opts->wait_budget_cycles > 0) c->wait_budget = opts->wait_budget_cycles;
     if (opts) {
         if (opts->pass_variant < 0 || opts->pass_variant > 2 || opts->ring_rows < 0 ||
@@ -259,6 +334,7 @@ lmosem_status lmosem_sensitivity(lmosem_ctx* c, int32_t n_subsets, double* d_sen
     if (!c) return LMOSEM_EINVAL;
     if (n_subsets < 1 || n_subsets > c->n_angles)
         return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
+    drop_graph(c);  // the captured iteration reads the sensitivity buffer
     lmosem_status st = compute_sensitivity(c, n_subsets);
     if (st) return st;
     if (d_sens)
@@ -271,45 +347,76 @@ lmosem_status lmosem_build_model(lmosem_ctx* c, const int32_t* d_angle, const fl
                                  const float* d_e_kev, int64_t n_events, int32_t n_subsets,
                                  lmosem_model_fmt fmt) {
     if (!c) return LMOSEM_EINVAL;
-    if (!d_angle || !d_u_mm || !d_e_kev) return fail(c, LMOSEM_EINVAL, "null event array");
-    if (n_events < 1 || n_events >= (int64_t(1) << 31))
-        return fail(c, LMOSEM_EINVAL, "n_events must be in [1, 2^31)");
-    if (n_subsets < 1 || n_subsets > c->n_angles)
-        return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
-    if (fmt != LMOSEM_MODEL_FP32 && fmt != LMOSEM_MODEL_FP16_SCALED && fmt != LMOSEM_MODEL_BF16_SCALED)
-        return fail(c, LMOSEM_EINVAL, "unknown model format");
-    free_model(c);
-    c->fmt = fmt;
-    c->J = n_events;
-    c->n_subsets = n_subsets;
-    c->ld_model = (c->n_sup + 31) / 32 * 32;
-    lmosem_status st;
-    size_t elem = fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
-    {
-        void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, (size_t)n_events * c->ld_model * elem);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            free_model(c);
-            return fail(c, LMOSEM_ENOMEM, "model of " +
-                                              std::to_string((size_t)n_events * c->ld_model * elem) +
-                                              " bytes does not fit: " + cudaGetErrorString(e));
-        }
-        c->d_model = p;
-    }
-    if (fmt != LMOSEM_MODEL_FP32 && (st = dev_alloc(c, &c->d_scale, n_events))) {
+    lmosem_status st = check_events_args(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, fmt);
+    if (st) return st;
+    return build_model_common(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, fmt, nullptr, 1);
+}
+
+lmosem_status lmosem_build_model_batch(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
+                                       const float* d_e_kev, const int64_t* h_event_offsets,
+                                       int32_t n_real, int32_t n_subsets, lmosem_model_fmt fmt) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!h_event_offsets || n_real < 1 || n_real > 1536)
+        return fail(c, LMOSEM_EINVAL, "need 1..1536 realisations and their event offsets");
+    const int64_t n_events = h_event_offsets[n_real];
+    if (h_event_offsets[0] != 0) return fail(c, LMOSEM_EINVAL, "event offsets must start at 0");
+    for (int r = 0; r < n_real; ++r)
+        if (h_event_offsets[r + 1] < h_event_offsets[r])
+            return fail(c, LMOSEM_EINVAL, "event offsets must not decrease");
+    lmosem_status st = check_events_args(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, fmt);
+    if (st) return st;
+    if (fmt != LMOSEM_MODEL_FP32)
+        return fail(c, LMOSEM_ENOTIMPL, "the batched model is cached as FP32 only");
+    if ((st = build_model_common(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, fmt,
+                                 h_event_offsets, n_real)))
+        return st;
+    if ((st = setup_batch(c))) {
         free_model(c);
         return st;
     }
-    if ((st = sort_events(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets))) {
-        free_model(c);
-        return st;
-    }
-    if ((st = build_model_rows(c))) {
-        free_model(c);
-        return st;
-    }
-    if (!c->d_bpart && (st = setup_pass(c))) return st;
+    c->batch_model = true;
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_init_image_batch(lmosem_ctx* c, double T, float* d_f) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad image pointer or acquisition time");
+    if (!c->batch_model || c->sens_subsets != c->n_subsets)
+        return fail(c, LMOSEM_ESTATE, "needs a batched model and a matching sensitivity");
+    return run_init_batch(c, T, d_f);
+}
+
+lmosem_status lmosem_iterate_batch(lmosem_ctx* c, int32_t n_iters, double T, float* d_f) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || n_iters < 0 || !finite_pos(T))
+        return fail(c, LMOSEM_EINVAL, "bad image pointer, iteration count or acquisition time");
+    if (!c->batch_model || c->sens_subsets != c->n_subsets)
+        return fail(c, LMOSEM_ESTATE, "needs a batched model and a matching sensitivity");
+    if (n_iters == 0) return LMOSEM_OK;
+    LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    lmosem_status st = run_batch(c, n_iters, T, d_f);
+    if (st) return st;
+    int h = 0;
+    LMOSEM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h) return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait of the batched pass ran out");
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int32_t* h_choice) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad image pointer or acquisition time");
+    if (!c->batch_model || c->sens_subsets != c->n_subsets)
+        return fail(c, LMOSEM_ESTATE, "needs a batched model and a matching sensitivity");
+    return run_autotune_batch(c, T, d_f, h_choice);
+}
+
+lmosem_status lmosem_set_batch_tiles(lmosem_ctx* c, int32_t chunk_rows, int32_t ctas_per_sm) {
+    if (!c) return LMOSEM_EINVAL;
+    if (chunk_rows < 8 || chunk_rows > (1 << 20) || ctas_per_sm < 1 || ctas_per_sm > 16)
+        return fail(c, LMOSEM_EINVAL, "chunk_rows in [8, 2^20], ctas_per_sm in [1, 16]");
+    c->batch_chunk_rows = chunk_rows;
+    c->batch_ctas_per_sm = ctas_per_sm;
     return LMOSEM_OK;
 }
 
@@ -317,6 +424,7 @@ lmosem_status lmosem_init_image(lmosem_ctx* c, double T, float* d_f) {
     if (!c) return LMOSEM_EINVAL;
     if (!d_f || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad image pointer or acquisition time");
     if (c->fmt < 0 || !c->sens_subsets) return fail(c, LMOSEM_ESTATE, "needs a model and a sensitivity");
+    if (c->batch_model) return fail(c, LMOSEM_ESTATE, "a batched model takes lmosem_init_image_batch");
     return run_init_image(c, T, d_f);
 }
 
@@ -325,6 +433,7 @@ lmosem_status lmosem_iterate(lmosem_ctx* c, int32_t n_iters, double T, float* d_
     if (!d_f || n_iters < 0 || !finite_pos(T))
         return fail(c, LMOSEM_EINVAL, "bad image pointer, iteration count or acquisition time");
     if (c->fmt < 0) return fail(c, LMOSEM_ESTATE, "no model built");
+    if (c->batch_model) return fail(c, LMOSEM_ESTATE, "a batched model takes lmosem_iterate_batch");
     if (c->sens_subsets != c->n_subsets)
         return fail(c, LMOSEM_ESTATE, "sensitivity missing or for another subset count");
     LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
@@ -349,6 +458,7 @@ lmosem_status lmosem_loglik(lmosem_ctx* c, double T, const float* d_f, double* d
     if (!d_f || !d_out || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad arguments");
     if (c->fmt < 0 || c->sens_subsets != c->n_subsets)
         return fail(c, LMOSEM_ESTATE, "needs a model and a matching sensitivity");
+    if (c->batch_model) return fail(c, LMOSEM_ESTATE, "the log-likelihood takes a single-data-set model");
     LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     lmosem_status st = run_loglik(c, T, d_f, d_out);
     if (st) return st;

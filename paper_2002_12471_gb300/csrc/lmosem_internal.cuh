@@ -78,8 +78,10 @@ struct lmosem_ctx {
     float* d_u_s = nullptr;       // sorted positions
     float* d_e_s = nullptr;       // sorted energies
     int32_t* d_a_s = nullptr;     // sorted angles
-    std::vector<int64_t> h_angle_row0, h_angle_cnt;  // per angle (sorted rows)
-    std::vector<int64_t> h_subset_row0;              // n_subsets + 1
+    int n_real = 1;                                  // independent realisations in the model
+    std::vector<int64_t> h_real_row0;                // n_real + 1
+    std::vector<int64_t> h_angle_row0, h_angle_cnt;  // [r * n_angles + a] (sorted rows)
+    std::vector<int64_t> h_subset_row0;              // [r * (n_subsets + 1) + i]
     int32_t* d_angle_row0 = nullptr;
     int32_t* d_angle_cnt = nullptr;
     int32_t* d_tile_prefix = nullptr;                // n_angles + 1 cumulative event tiles
@@ -96,10 +98,31 @@ struct lmosem_ctx {
     int* d_status = nullptr;      // [0] = 1 after a bounded device wait ran out
     long long wait_budget = 2000000000LL;  // clock cycles per bounded wait
     int pass_variant = 0;         // 0 auto, 1 register pipeline, 2 bulk-copy ring
+    // batching form: per-realisation work words, partial slots, tiles, graph
+    bool batch_model = false;
+    int64_t* d_bsub_row0 = nullptr;           // n_real * (n_subsets + 1)
+    int64_t* d_breal_row0 = nullptr;          // n_real + 1
+    unsigned long long* d_bclaim = nullptr;   // n_real
+    int* d_bdone = nullptr;                   // n_real + 1 (last: finished count)
+    float* d_bpart_batch = nullptr;
+    int64_t bpart_batch_floats = 0;
+    int64_t batch_max_subset_rows = 0;
+    int batch_chunk_rows = 0, batch_ctas_per_sm = 0;
+    cudaGraphExec_t bgraph_exec = nullptr;
+    const float* bgraph_f = nullptr;
+    double bgraph_T = 0.0;
+    int bgraph_iters = 0, bgraph_chunk = 0, bgraph_ctas = 0;
+    int64_t bgraph_launches = 0;
+    // one OSEM iteration captured as a CUDA graph (non-default streams)
+    cudaGraphExec_t graph_exec = nullptr;
+    const float* graph_f = nullptr;
+    double graph_T = 0.0;
+    int64_t graph_launches = 0;
     int ring_rows = 0, ring_stages = 0;  // ring shape (0: from the row size)
 
     // kernel timing (opts->profile)
-    bool profile = false;
+    int profile = 0;              // 0 off, 1 every launch, 2 all but graph-replayed iterations
+    bool capturing = false;       // a CUDA graph is being captured on the stream
     struct ProfRec {
         int cls;
         cudaEvent_t a, b;
@@ -163,8 +186,10 @@ void dev_free(T** p) {
 
 // ---- host entry points implemented in the other translation units
 lmosem_status build_tables(lmosem_ctx* c);                      // siddon.cu
+// h_offsets: n_real + 1 event offsets of the realisations (nullptr: one)
 lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
-                          const float* d_e, int64_t n, int n_subsets);  // sort.cu
+                          const float* d_e, int64_t n, int n_subsets,
+                          const int64_t* h_offsets, int n_real);  // sort.cu
 lmosem_status build_model_rows(lmosem_ctx* c);                  // model.cu
 lmosem_status compute_sensitivity(lmosem_ctx* c, int n_subsets);  // sens.cu
 lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll);
@@ -172,6 +197,10 @@ lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_ou
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f);
 lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float* out);
 lmosem_status setup_pass(lmosem_ctx* c);                        // osem.cu
+lmosem_status setup_batch(lmosem_ctx* c);                       // batch.cu
+lmosem_status run_init_batch(lmosem_ctx* c, double T, float* d_f);
+lmosem_status run_batch(lmosem_ctx* c, int n_iters, double T, float* d_f);
+lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int32_t* h_choice);
 
 // ---- device helpers shared by the CUDA translation units
 

@@ -93,11 +93,13 @@ __global__ void k_wtable(WTabArgs A) {
 struct PathSumArgs {
     const float* u_s;
     const float* e_s;
-    const int32_t* slot_angle;
-    const int32_t* tile_prefix;  // per slot, cumulative event tiles
-    const int32_t* angle_row0;
-    const int32_t* angle_cnt;
-    int s0, s1;                  // slot range of the group
+    // entries (realisation, angle) of this launch, in sorted-row order
+    const int32_t* ent_angle;    // detector angle
+    const int32_t* ent_wpos;     // slot of its scatter tables in the group
+    const int32_t* ent_row0;     // first sorted row
+    const int32_t* ent_cnt;      // rows
+    const int32_t* tile_prefix;  // cumulative event tiles, tile_prefix[0] = 0
+    int n_ent;
     int n_ptiles;
     const float* wtab;
     int ld_w, n_scat;
@@ -157,18 +159,17 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int et = blockIdx.x / A.n_ptiles, pt = blockIdx.x % A.n_ptiles;
 
-    // slot of this event tile
-    const int T = A.tile_prefix[A.s0] + et;
-    int lo = A.s0, hi = A.s1 - 1;
+    // entry (realisation, angle) of this event tile
+    int lo = 0, hi = A.n_ent - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (A.tile_prefix[mid] <= T) lo = mid; else hi = mid - 1;
+        if (A.tile_prefix[mid] <= et) lo = mid; else hi = mid - 1;
     }
-    const int slot = lo;
-    const int a = A.slot_angle[slot];
-    const int tile = T - A.tile_prefix[slot];
-    const int64_t r0 = (int64_t)A.angle_row0[a] + (int64_t)tile * kTJ;
-    const int nr = min(kTJ, A.angle_cnt[a] - tile * kTJ);
+    const int ent = lo;
+    const int a = A.ent_angle[ent];
+    const int tile = et - A.tile_prefix[ent];
+    const int64_t r0 = (int64_t)A.ent_row0[ent] + (int64_t)tile * kTJ;
+    const int nr = min(kTJ, A.ent_cnt[ent] - tile * kTJ);
     const int n0 = pt * kTN;
 
     if (tid < kTJ) {
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     // strip staging: three table planes and the position parameters of
     // kStage scatter pixels per stage, double-buffered with cp.async
     const size_t plane = (size_t)A.n_scat * A.ld_w;
-    const float* tab = A.wtab + (size_t)(slot - A.s0) * 3 * plane + n0;
+    const float* tab = A.wtab + (size_t)A.ent_wpos[ent] * 3 * plane + n0;
     auto issue = [&](int c0, int buf) {
         for (int k = tid; k < 3 * kStage * (kTN / 4); k += kBuildThreads) {
             int p = k / (kStage * (kTN / 4));
@@ -384,49 +385,82 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const int group = (c->n_angles + c->n_subsets - 1) / c->n_subsets;
     const int n_slots = c->n_subsets * group;
 
-    // slots in sorted order and their angles (empty slots are skipped)
-    std::vector<int32_t> slot_angle, tile_prefix(1, 0), row0(c->n_angles), cnt(c->n_angles);
+    // angles in sorted-slot order (empty slots skipped)
+    std::vector<int32_t> slot_angle;
     for (int s = 0; s < n_slots; ++s) {
         int a = (s / group) + c->n_subsets * (s % group);
-        if (a >= c->n_angles) continue;
-        slot_angle.push_back(a);
-        tile_prefix.push_back(tile_prefix.back() + (int32_t)((c->h_angle_cnt[a] + kTJ - 1) / kTJ));
-    }
-    for (int a = 0; a < c->n_angles; ++a) {
-        row0[a] = (int32_t)c->h_angle_row0[a];
-        cnt[a] = (int32_t)c->h_angle_cnt[a];
+        if (a < c->n_angles) slot_angle.push_back(a);
     }
     const int ns = (int)slot_angle.size();
-    int32_t* d_slot_angle = nullptr;
-    if ((st = dev_alloc(c, &d_slot_angle, ns))) return st;
-    if ((st = dev_alloc(c, &c->d_tile_prefix, ns + 1))) return st;
-    if ((st = dev_alloc(c, &c->d_angle_row0, c->n_angles))) return st;
-    if ((st = dev_alloc(c, &c->d_angle_cnt, c->n_angles))) return st;
-    LMOSEM_CK(c, cudaMemcpyAsync(d_slot_angle, slot_angle.data(), ns * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->stream));
-    LMOSEM_CK(c, cudaMemcpyAsync(c->d_tile_prefix, tile_prefix.data(), (ns + 1) * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->stream));
-    LMOSEM_CK(c, cudaMemcpyAsync(c->d_angle_row0, row0.data(), c->n_angles * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->stream));
-    LMOSEM_CK(c, cudaMemcpyAsync(c->d_angle_cnt, cnt.data(), c->n_angles * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->stream));
 
     // angle groups bounded by the scatter-table budget (three FP32 planes)
     const int64_t per_angle = (int64_t)3 * c->n_scat * c->ld_w * sizeof(float);
-    int gsz = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
-    if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * 3 * c->n_scat * c->ld_w))) return st;
+    const int gsz = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
+    const int n_groups = (ns + gsz - 1) / gsz;
 
-    const bool scaled = c->fmt != LMOSEM_MODEL_FP32;
-    int64_t max_group_rows = 0;
-    for (int s0 = 0; s0 < ns; s0 += gsz) {
-        int s1 = std::min(ns, s0 + gsz);
-        int64_t rows = 0;
-        for (int s = s0; s < s1; ++s) rows += c->h_angle_cnt[slot_angle[s]];
-        max_group_rows = std::max(max_group_rows, rows);
+    // launch entries (realisation, angle) of every group, in sorted-row order
+    // within a realisation; one host array for all groups, copied once
+    std::vector<int32_t> e_angle, e_wpos, e_row0, e_cnt, e_tiles, g_first(n_groups + 1, 0);
+    std::vector<int64_t> g_rows(n_groups, 0), g_row0(n_groups, -1);
+    for (int gi = 0; gi < n_groups; ++gi) {
+        const int s0 = gi * gsz, s1 = std::min(ns, s0 + gsz);
+        g_first[gi] = (int32_t)e_angle.size();
+        for (int r = 0; r < c->n_real; ++r) {
+            for (int s = s0; s < s1; ++s) {
+                const int a = slot_angle[s];
+                const size_t k = (size_t)r * c->n_angles + a;
+                const int64_t cnt = c->h_angle_cnt[k];
+                if (cnt == 0) continue;
+                if (g_row0[gi] < 0) g_row0[gi] = c->h_angle_row0[k];
+                e_angle.push_back(a);
+                e_wpos.push_back(s - s0);
+                e_row0.push_back((int32_t)c->h_angle_row0[k]);
+                e_cnt.push_back((int32_t)cnt);
+                e_tiles.push_back((int32_t)((cnt + kTJ - 1) / kTJ));
+                g_rows[gi] += cnt;
+            }
+        }
     }
+    g_first[n_groups] = (int32_t)e_angle.size();
+    const int n_ent = (int)e_angle.size();
+    // per-group exclusive tile prefix, stored per entry (+1 slot per group end)
+    std::vector<int32_t> e_prefix(n_ent + n_groups, 0);
+    std::vector<int32_t> g_tiles(n_groups, 0);
+    for (int gi = 0; gi < n_groups; ++gi) {
+        int32_t acc = 0;
+        for (int e = g_first[gi]; e < g_first[gi + 1]; ++e) {
+            e_prefix[e + gi] = acc;
+            acc += e_tiles[e];
+        }
+        e_prefix[g_first[gi + 1] + gi] = acc;
+        g_tiles[gi] = acc;
+    }
+    std::vector<int32_t> host_all;
+    host_all.reserve((size_t)4 * n_ent + e_prefix.size() + ns);
+    host_all.insert(host_all.end(), e_angle.begin(), e_angle.end());
+    host_all.insert(host_all.end(), e_wpos.begin(), e_wpos.end());
+    host_all.insert(host_all.end(), e_row0.begin(), e_row0.end());
+    host_all.insert(host_all.end(), e_cnt.begin(), e_cnt.end());
+    host_all.insert(host_all.end(), e_prefix.begin(), e_prefix.end());
+    host_all.insert(host_all.end(), slot_angle.begin(), slot_angle.end());
+    int32_t* d_all = nullptr;
+    if ((st = dev_alloc(c, &d_all, host_all.size()))) return st;
+    LMOSEM_CK(c, cudaMemcpyAsync(d_all, host_all.data(), host_all.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    const int32_t* d_ent_angle = d_all;
+    const int32_t* d_ent_wpos = d_all + n_ent;
+    const int32_t* d_ent_row0 = d_all + 2 * n_ent;
+    const int32_t* d_ent_cnt = d_all + 3 * n_ent;
+    const int32_t* d_prefix = d_all + 4 * n_ent;
+    const int32_t* d_slot_angle = d_all + 4 * n_ent + e_prefix.size();
+
+    if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * 3 * c->n_scat * c->ld_w))) return st;
+    const bool scaled = c->fmt != LMOSEM_MODEL_FP32;
     if (scaled) {
-        if ((st = dev_alloc(c, &c->d_stage, (size_t)std::max<int64_t>(1, max_group_rows) * c->ld_model)))
-            return st;
+        // scaled rows are staged per group: one realisation, contiguous rows
+        int64_t max_group_rows = 1;
+        for (int gi = 0; gi < n_groups; ++gi) max_group_rows = std::max(max_group_rows, g_rows[gi]);
+        if ((st = dev_alloc(c, &c->d_stage, (size_t)max_group_rows * c->ld_model))) return st;
     }
 
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
@@ -436,8 +470,8 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
 
-    for (int s0 = 0; s0 < ns; s0 += gsz) {
-        int s1 = std::min(ns, s0 + gsz);
+    for (int gi = 0; gi < n_groups; ++gi) {
+        const int s0 = gi * gsz, s1 = std::min(ns, s0 + gsz);
         WTabArgs W;
         W.nx = c->nx;
         W.ny = c->ny;
@@ -465,20 +499,18 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, s1 - s0), 256, 0, c->stream>>>(W);
         LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
 
-        int tiles = tile_prefix[s1] - tile_prefix[s0];
+        const int tiles = g_tiles[gi];
         if (tiles == 0) continue;
-        int64_t grow0 = c->h_angle_row0[slot_angle[s0]];
-        int64_t grows = 0;
-        for (int s = s0; s < s1; ++s) grows += c->h_angle_cnt[slot_angle[s]];
+        const int e0 = g_first[gi];
         PathSumArgs P;
         P.u_s = c->d_u_s;
         P.e_s = c->d_e_s;
-        P.slot_angle = d_slot_angle;
-        P.tile_prefix = c->d_tile_prefix;
-        P.angle_row0 = c->d_angle_row0;
-        P.angle_cnt = c->d_angle_cnt;
-        P.s0 = s0;
-        P.s1 = s1;
+        P.ent_angle = d_ent_angle + e0;
+        P.ent_wpos = d_ent_wpos + e0;
+        P.ent_row0 = d_ent_row0 + e0;
+        P.ent_cnt = d_ent_cnt + e0;
+        P.tile_prefix = d_prefix + e0 + gi;
+        P.n_ent = g_first[gi + 1] - e0;
         P.n_ptiles = n_ptiles;
         P.wtab = c->d_wtab;
         P.ld_w = c->ld_w;
@@ -490,6 +522,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.lE0 = (float)(-log2(se0 * sqrt(2.0 * kPi)));
         P.ld_out = c->ld_model;
         P.n_store = (int)c->ld_model;
+        const int64_t grow0 = g_row0[gi], grows = g_rows[gi];
         if (scaled) {
             P.out = c->d_stage;
             P.row_base = grow0;
@@ -516,7 +549,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         }
     }
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(&d_slot_angle);
+    dev_free(&d_all);
     dev_free(&c->d_wtab);
     dev_free(&c->d_stage);
     return LMOSEM_OK;

@@ -200,26 +200,37 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
     }
 }
 
-// b_q = sum of the per-CTA partials (8 warps over the partials, fixed order),
-// then f_q <- f_q b_q / (T s^i_q)
-__global__ void __launch_bounds__(256) k_update(const float* __restrict__ bpart, int nparts, int n_sup,
-                                                float* __restrict__ f, const double* __restrict__ sens_i,
-                                                double T, const int* __restrict__ status) {
+// b_q = sum of the per-CTA partials, then f_q <- f_q b_q / (T s^i_q).  One
+// CTA of kUpdWarps warps per 32 support pixels; warp w sums the partials
+// w, w + kUpdWarps, ... with eight loads in flight, then warp 0 adds the warp
+// sums in warp order (fixed order: deterministic).
+constexpr int kUpdWarps = 32;
+__global__ void __launch_bounds__(kUpdWarps * 32) k_update(const float* __restrict__ bpart, int nparts,
+                                                          int n_sup, float* __restrict__ f,
+                                                          const double* __restrict__ sens_i, double T,
+                                                          const int* __restrict__ status) {
     if (status && *status) return;  // the pass was abandoned: keep the image
-    __shared__ float sh[8][32];
+    __shared__ float sh[kUpdWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;  // <= kUpdWarps
     const int n = blockIdx.x * 32 + lane;
     float b = 0.0f;
     if (n < n_sup) {
-#pragma unroll 4
-        for (int c = warp; c < nparts; c += 8) b += bpart[(size_t)c * n_sup + n];
+        int c = warp;
+        for (; c + 7 * nw < nparts; c += 8 * nw) {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = bpart[(size_t)(c + k * nw) * n_sup + n];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b += v[k];
+        }
+        for (; c < nparts; c += nw) b += bpart[(size_t)c * n_sup + n];
     }
     sh[warp][lane] = b;
     __syncthreads();
     if (warp == 0 && n < n_sup) {
         float s = 0.0f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += sh[w][lane];
+        for (int w = 0; w < nw; ++w) s += sh[w][lane];
         double sd = sens_i[n];
         float ts = (float)(T * sd);
         f[n] = sd > 0.0 ? f[n] * s / ts : 0.0f;
@@ -647,18 +658,79 @@ lmosem_status setup_pass(lmosem_ctx* c) {
     return LMOSEM_OK;
 }
 
+namespace {
+
+// the kernels of one global iteration: N_s passes and updates
+lmosem_status enqueue_iteration(lmosem_ctx* c, double T, float* d_f) {
+    lmosem_status st;
+    for (int i = 0; i < c->n_subsets; ++i) {
+        if ((st = launch_pass<true>(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T)))
+            return st;
+        LMOSEM_PROF_BEGIN(c);
+        k_update<<<(c->n_sup + 31) / 32, kUpdWarps * 32, 0, c->stream>>>(
+            c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T,
+            c->d_status);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+    }
+    return LMOSEM_OK;
+}
+
+// One iteration captured as a CUDA graph and replayed (no per-kernel launch
+// overhead between the 2 N_s dependent kernels).  Used on a non-default
+// stream without profiling; the graph is rebuilt when the image or T change.
+lmosem_status iterate_graph(lmosem_ctx* c, int n_iters, double T, float* d_f, bool* done) {
+    *done = false;
+    if (c->profile == 1 || c->stream == nullptr || n_iters < 1) return LMOSEM_OK;
+    if (!c->graph_exec || c->graph_f != d_f || c->graph_T != T) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        const int64_t before = c->launches;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return LMOSEM_OK;  // not capturable: launch directly
+        }
+        c->capturing = true;
+        lmosem_status st = enqueue_iteration(c, T, d_f);
+        c->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->graph_exec = nullptr;
+            return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+        c->graph_launches = c->launches - before;
+        c->launches = before;
+        c->graph_f = d_f;
+        c->graph_T = T;
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        LMOSEM_CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+        c->launches += c->graph_launches;
+    }
+    *done = true;
+    return LMOSEM_OK;
+}
+
+}  // namespace
+
 lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll) {
     lmosem_status st;
+    if (!d_ll) {
+        bool done = false;
+        if ((st = iterate_graph(c, n_iters, T, d_f, &done))) return st;
+        if (done) return LMOSEM_OK;
+    }
     for (int it = 0; it < n_iters; ++it) {
-        for (int i = 0; i < c->n_subsets; ++i) {
-            if ((st = launch_pass<true>(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T)))
-                return st;
-            LMOSEM_PROF_BEGIN(c);
-            k_update<<<(c->n_sup + 31) / 32, 256, 0, c->stream>>>(
-                c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T,
-                c->d_status);
-            LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
-        }
+        if ((st = enqueue_iteration(c, T, d_f))) return st;
         if (d_ll) {
             if ((st = launch_pass<false>(c, 0, c->J, d_f, T))) return st;
             if ((st = ll_final(c, T, d_f, d_ll + it))) return st;

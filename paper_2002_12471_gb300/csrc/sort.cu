@@ -27,22 +27,44 @@ __global__ void k_check_events(const int32_t* __restrict__ a, const float* __res
     if (!ok) atomicAdd(bad, 1);
 }
 
+// realisation of event (or sorted row) i: the last r with off[r] <= i
+__device__ __forceinline__ int realisation_of(const int64_t* off, int n_real, int64_t i) {
+    int lo = 0, hi = n_real - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // digit of the event at original index i
 struct Digit {
-    int mode;  // 0: position bin, 1: subset-major angle slot
+    int mode;  // 0: position bin, 1: subset-major angle slot, 2: realisation
     const int32_t* a;
     const float* u;
     float half;
     int n_subsets, group;
+    const int64_t* off;
+    int n_real;
     __device__ int operator()(int64_t i) const {
         if (mode == 0) {
             int b = (int)floorf((u[i] + half) * ((float)kUBins / (2.0f * half)));
             return min(max(b, 0), kUBins - 1);
         }
+        if (mode == 2) return realisation_of(off, n_real, i);
         int ai = a[i];
         return (ai % n_subsets) * group + ai / n_subsets;
     }
 };
+
+// events per (realisation, angle) of the sorted rows
+__global__ void k_rs_hist(const int32_t* __restrict__ a_s, int64_t n, const int64_t* __restrict__ off,
+                          int n_real, int n_angles, int32_t* __restrict__ cnt) {
+    int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    int r = off ? realisation_of(off, n_real, row) : 0;
+    atomicAdd(&cnt[(size_t)r * n_angles + a_s[row]], 1);
+}
 
 // per-block digit histograms, digit-major: H[d * nblk + b]
 __global__ void k_hist(Digit dg, const int32_t* __restrict__ perm, int64_t n, int ndig,
@@ -151,17 +173,8 @@ __global__ void k_gather_events(const int32_t* __restrict__ perm, int64_t n,
     rank[j] = r;
 }
 
-// digit start offsets: O[d * nblk] for d = 0..ndig-1, plus n
-__global__ void k_digit_starts(const int32_t* __restrict__ O, int nblk, int ndig, int64_t n,
-                               int32_t* __restrict__ starts) {
-    int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d < ndig) starts[d] = O[(size_t)d * nblk];
-    if (d == ndig) starts[d] = (int32_t)n;
-}
-
 lmosem_status counting_pass(lmosem_ctx* c, const Digit& dg, int ndig, const int32_t* perm_in,
-                            int32_t* perm_out, int64_t n, int32_t* H, int32_t* tot,
-                            int32_t* starts) {
+                            int32_t* perm_out, int64_t n, int32_t* H, int32_t* tot) {
     int nblk = (int)((n + kSortThreads - 1) / kSortThreads);
     LMOSEM_PROF_BEGIN(c);
     k_hist<<<nblk, kSortThreads, ndig * sizeof(int32_t), c->stream>>>(dg, perm_in, n, ndig, H);
@@ -181,18 +194,14 @@ lmosem_status counting_pass(lmosem_ctx* c, const Digit& dg, int ndig, const int3
     LMOSEM_PROF_BEGIN(c);
     k_scatter<<<nblk, kSortThreads, smem, c->stream>>>(dg, perm_in, n, ndig, H, perm_out);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SORT);
-    if (starts) {
-        LMOSEM_PROF_BEGIN(c);
-        k_digit_starts<<<(ndig + 1 + 255) / 256, 256, 0, c->stream>>>(H, nblk, ndig, n, starts);
-        LMOSEM_LAUNCHED(c, LMOSEM_K_SORT);
-    }
     return LMOSEM_OK;
 }
 
 }  // namespace
 
 lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
-                          const float* d_e, int64_t n, int n_subsets) {
+                          const float* d_e, int64_t n, int n_subsets, const int64_t* h_offsets,
+                          int n_real) {
     lmosem_status st;
     const float half = (float)(0.5 * c->n_bins * c->bin_mm);
     int32_t* d_bad = nullptr;
@@ -211,50 +220,87 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
 
     const int group = (c->n_angles + n_subsets - 1) / n_subsets;
     const int ndig_a = n_subsets * group;
-    const int ndig = ndig_a > kUBins ? ndig_a : kUBins;
     // the stable scatter keeps one count per (warp, digit) in 48 KB of shared memory
-    if (ndig_a > 1536) return fail(c, LMOSEM_EINVAL, "too many angles for the event sort");
+    if (ndig_a > 1536 || n_real > 1536)
+        return fail(c, LMOSEM_EINVAL, "too many angles or realisations for the event sort");
+    int ndig = ndig_a > kUBins ? ndig_a : kUBins;
+    ndig = ndig > n_real ? ndig : n_real;
     const int nblk = (int)((n + kSortThreads - 1) / kSortThreads);
     const int64_t hn = (int64_t)ndig * nblk;
     const int sblk = (int)((hn + kScanBlock * 4 - 1) / (kScanBlock * 4));
-    int32_t *H = nullptr, *tot = nullptr, *p1 = nullptr, *starts = nullptr;
+    int32_t *H = nullptr, *tot = nullptr, *p1 = nullptr, *p2 = nullptr, *cnt = nullptr;
+    int64_t* d_off = nullptr;
     if ((st = dev_alloc(c, &H, hn))) return st;
     if ((st = dev_alloc(c, &tot, sblk))) return st;
     if ((st = dev_alloc(c, &p1, n))) return st;
-    if ((st = dev_alloc(c, &starts, ndig_a + 1))) return st;
+    if ((st = dev_alloc(c, &cnt, (size_t)n_real * c->n_angles))) return st;
     if ((st = dev_alloc(c, &c->d_perm, n))) return st;
     if ((st = dev_alloc(c, &c->d_rank, n))) return st;
     if ((st = dev_alloc(c, &c->d_a_s, n))) return st;
     if ((st = dev_alloc(c, &c->d_u_s, n))) return st;
     if ((st = dev_alloc(c, &c->d_e_s, n))) return st;
+    if (n_real > 1) {
+        if ((st = dev_alloc(c, &p2, n))) return st;
+        if ((st = dev_alloc(c, &d_off, n_real + 1))) return st;
+        LMOSEM_CK(c, cudaMemcpyAsync(d_off, h_offsets, (n_real + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, c->stream));
+    }
 
-    Digit d0{0, d_angle, d_u, half, n_subsets, group};
-    Digit d1{1, d_angle, d_u, half, n_subsets, group};
-    if ((st = counting_pass(c, d0, kUBins, nullptr, p1, n, H, tot, nullptr))) return st;
-    if ((st = counting_pass(c, d1, ndig_a, p1, c->d_perm, n, H, tot, starts))) return st;
+    // stable passes, least significant key first: position bin, angle slot
+    // and, for several realisations, the realisation
+    Digit d0{0, d_angle, d_u, half, n_subsets, group, d_off, n_real};
+    Digit d1{1, d_angle, d_u, half, n_subsets, group, d_off, n_real};
+    Digit d2{2, d_angle, d_u, half, n_subsets, group, d_off, n_real};
+    if ((st = counting_pass(c, d0, kUBins, nullptr, p1, n, H, tot))) return st;
+    if (n_real > 1) {
+        if ((st = counting_pass(c, d1, ndig_a, p1, p2, n, H, tot))) return st;
+        if ((st = counting_pass(c, d2, n_real, p2, c->d_perm, n, H, tot))) return st;
+    } else {
+        if ((st = counting_pass(c, d1, ndig_a, p1, c->d_perm, n, H, tot))) return st;
+    }
     LMOSEM_PROF_BEGIN(c);
     k_gather_events<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(
         c->d_perm, n, d_angle, d_u, d_e, c->d_a_s, c->d_u_s, c->d_e_s, c->d_rank);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SORT);
+    LMOSEM_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_real * c->n_angles, c->stream));
+    LMOSEM_PROF_BEGIN(c);
+    k_rs_hist<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(c->d_a_s, n, d_off, n_real,
+                                                             c->n_angles, cnt);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SORT);
 
-    std::vector<int32_t> h_starts(ndig_a + 1);
-    LMOSEM_CK(c, cudaMemcpyAsync(h_starts.data(), starts, (ndig_a + 1) * sizeof(int32_t),
+    std::vector<int32_t> h_cnt((size_t)n_real * c->n_angles);
+    LMOSEM_CK(c, cudaMemcpyAsync(h_cnt.data(), cnt, h_cnt.size() * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     dev_free(&H);
     dev_free(&tot);
     dev_free(&p1);
-    dev_free(&starts);
+    dev_free(&p2);
+    dev_free(&cnt);
+    dev_free(&d_off);
 
-    c->h_angle_row0.assign(c->n_angles, 0);
-    c->h_angle_cnt.assign(c->n_angles, 0);
-    for (int a = 0; a < c->n_angles; ++a) {
-        int slot = (a % n_subsets) * group + a / n_subsets;
-        c->h_angle_row0[a] = h_starts[slot];
-        c->h_angle_cnt[a] = h_starts[slot + 1] - h_starts[slot];
+    // rows of (realisation, angle) and of (realisation, subset), in sorted order
+    c->n_real = n_real;
+    c->h_real_row0.assign(n_real + 1, 0);
+    c->h_angle_row0.assign((size_t)n_real * c->n_angles, 0);
+    c->h_angle_cnt.assign((size_t)n_real * c->n_angles, 0);
+    c->h_subset_row0.assign((size_t)n_real * (n_subsets + 1), 0);
+    int64_t row = 0;
+    for (int r = 0; r < n_real; ++r) {
+        c->h_real_row0[r] = row;
+        for (int s = 0; s < ndig_a; ++s) {
+            if (s % group == 0) c->h_subset_row0[(size_t)r * (n_subsets + 1) + s / group] = row;
+            int a = (s / group) + n_subsets * (s % group);
+            if (a >= c->n_angles) continue;
+            size_t k = (size_t)r * c->n_angles + a;
+            c->h_angle_row0[k] = row;
+            c->h_angle_cnt[k] = h_cnt[k];
+            row += h_cnt[k];
+        }
+        c->h_subset_row0[(size_t)r * (n_subsets + 1) + n_subsets] = row;
     }
-    c->h_subset_row0.assign(n_subsets + 1, n);
-    for (int i = 0; i < n_subsets; ++i) c->h_subset_row0[i] = h_starts[i * group];
+    c->h_real_row0[n_real] = row;
+    if (row != n) return fail(c, LMOSEM_ECUDA, "event sort lost events");
     return LMOSEM_OK;
 }
 

@@ -81,6 +81,11 @@ SIGNATURES = {
     "lmosem_launch_count": (_i64, [_vp]),
     "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "lmosem_osem_subiter_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i64, _vp, _vp, _dbl, _vp]),
+    "lmosem_build_model_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int]),
+    "lmosem_init_image_batch": (ctypes.c_int, [_vp, _dbl, _vp]),
+    "lmosem_iterate_batch": (ctypes.c_int, [_vp, _i32, _dbl, _vp]),
+    "lmosem_autotune_batch": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
+    "lmosem_set_batch_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
 }
 
 _lib = None
@@ -146,7 +151,7 @@ def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                  float(geom["coll_fwhm_slope"]))
     e = Energy(float(geom["e0_kev"]), float(geom["fwhm_frac_e0"]), float(geom["e_lo_kev"]),
                float(geom["e_hi_kev"]))
-    o = Options(float(k_sigma), int(table_budget_bytes), int(bool(profile)),
+    o = Options(float(k_sigma), int(table_budget_bytes), int(profile),
                 int(wait_budget_cycles), int(pass_variant), int(ring_rows), int(ring_stages))
     h = _vp()
     s = getattr(stream, "cuda_stream", stream)
@@ -218,6 +223,32 @@ def lmosem_profile_read(ctx):
     n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
     _check(ctx, load().lmosem_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def lmosem_build_model_batch(ctx, d_angle, d_u_mm, d_e_kev, event_offsets, n_subsets, fmt="fp32"):
+    off = np.ascontiguousarray(event_offsets, dtype=np.int64)
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    _check(ctx, load().lmosem_build_model_batch(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev),
+                                                off.ctypes.data, len(off) - 1, int(n_subsets), f))
+
+
+def lmosem_init_image_batch(ctx, acq_time, d_f):
+    _check(ctx, load().lmosem_init_image_batch(ctx, float(acq_time), _ptr(d_f)))
+
+
+def lmosem_iterate_batch(ctx, n_iters, acq_time, d_f):
+    _check(ctx, load().lmosem_iterate_batch(ctx, int(n_iters), float(acq_time), _ptr(d_f)))
+
+
+def lmosem_autotune_batch(ctx, acq_time, d_f):
+    """Returns the chosen (chunk_rows, ctas_per_sm)."""
+    out = np.zeros(2, dtype=np.int32)
+    _check(ctx, load().lmosem_autotune_batch(ctx, float(acq_time), _ptr(d_f), out.ctypes.data))
+    return int(out[0]), int(out[1])
+
+
+def lmosem_set_batch_tiles(ctx, chunk_rows, ctas_per_sm):
+    _check(ctx, load().lmosem_set_batch_tiles(ctx, int(chunk_rows), int(ctas_per_sm)))
 
 
 def lmosem_osem_subiter_noalloc(d_rows, n_support, d_f, d_sens_i, acq_time, stream=None):
