@@ -1,0 +1,93 @@
+"""FP64 reference of the scatter surrogate's multilayer perceptron.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  The surrogate replaces
+the sum over scatter pixels of the path model (paper Eq. 2 restricted to the
+first-order paths of Section 2.2) by a learned function of six inputs:
+
+    pixel x, pixel y, detector angle, event position u, event energy E,
+    attenuation from the pixel to the detector along the detector direction,
+
+each mapped to O(1) by the fixed affine scaling ``FEATURE_SCALE`` below.
+Architecture: 6 -> 256 -> 256 -> 256 -> 256 -> 1, ReLU after every hidden
+layer, linear output; the output is the standardised natural log of the
+scatter part of p_jn.  Parameters: W_l (out x in, row-major), b_l (out).
+Training: mean squared error, Adam (Kingma & Ba 2015: bias-corrected first
+and second moments).
+
+Everything here is plain numpy in float64, one line per formula.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LAYERS = (6, 256, 256, 256, 256, 1)
+
+# x_mm, y_mm, theta_rad, u_mm, e_kev, atten -> (v - shift) / scale
+FEATURE_SHIFT = np.array([0.0, 0.0, np.pi, 0.0, 137.5, 1.5])
+FEATURE_SCALE = np.array([100.0, 100.0, np.pi, 100.0, 37.5, 1.5])
+
+
+def scale_features(raw):
+    return (np.asarray(raw, dtype=np.float64) - FEATURE_SHIFT) / FEATURE_SCALE
+
+
+def init_params(seed=0, layers=LAYERS):
+    """He-normal weights, zero biases (seeded)."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for fan_in, fan_out in zip(layers[:-1], layers[1:]):
+        W = rng.standard_normal((fan_out, fan_in)) * np.sqrt(2.0 / fan_in)
+        params.append([W, np.zeros(fan_out)])
+    return params
+
+
+def forward(params, X):
+    """Returns the output (n,) and the per-layer cache (inputs, pre-activations)."""
+    h = np.asarray(X, dtype=np.float64)
+    cache = []
+    for k, (W, b) in enumerate(params):
+        z = h @ W.T + b
+        cache.append((h, z))
+        h = np.maximum(z, 0.0) if k < len(params) - 1 else z
+    return h[:, 0], cache
+
+
+def backward(params, cache, dy):
+    """Gradients of sum(dy * y) with respect to every W and b."""
+    g = np.asarray(dy, dtype=np.float64)[:, None]
+    grads = [None] * len(params)
+    for k in range(len(params) - 1, -1, -1):
+        h, z = cache[k]
+        if k < len(params) - 1:
+            g = g * (z > 0.0)
+        W, _ = params[k]
+        grads[k] = [g.T @ h, g.sum(axis=0)]
+        g = g @ W
+    return grads
+
+
+def mse_loss_and_grad(params, X, t):
+    """Mean squared error and its gradients."""
+    y, cache = forward(params, X)
+    r = y - np.asarray(t, dtype=np.float64)
+    loss = float(np.mean(r * r))
+    grads = backward(params, cache, 2.0 * r / len(r))
+    return loss, grads
+
+
+def adam_step(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update in place; state = {'t': step, 'm': [...], 'v': [...]}."""
+    if not state:
+        state.update(t=0, m=[[np.zeros_like(p) for p in layer] for layer in params],
+                     v=[[np.zeros_like(p) for p in layer] for layer in params])
+    state["t"] += 1
+    t = state["t"]
+    for l, layer in enumerate(params):
+        for i, p in enumerate(layer):
+            g = grads[l][i]
+            state["m"][l][i] = beta1 * state["m"][l][i] + (1 - beta1) * g
+            state["v"][l][i] = beta2 * state["v"][l][i] + (1 - beta2) * g * g
+            mhat = state["m"][l][i] / (1 - beta1 ** t)
+            vhat = state["v"][l][i] / (1 - beta2 ** t)
+            layer[i] = p - lr * mhat / (np.sqrt(vhat) + eps)
+    return params
