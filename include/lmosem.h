@@ -117,14 +117,28 @@ typedef enum {
     LMOSEM_K_PASS = 6,     /* streaming OSEM pass (forward, back-projection, LL)  */
     LMOSEM_K_UPDATE = 7,   /* per-subset reduction and multiplicative update      */
     LMOSEM_K_OTHER = 8,
-    LMOSEM_K_COUNT = 9
+    LMOSEM_K_SURROGATE = 9, /* scatter surrogate: MLP products and their helpers */
+    LMOSEM_K_COUNT = 10
 } lmosem_kernel_class;
 
 typedef enum {
-    LMOSEM_MODEL_FP32 = 0,        /* p_jn cached as FP32                           */
-    LMOSEM_MODEL_FP16_SCALED = 1, /* p_jn = c_j h_jn, h FP16 with max_n h = 2^15   */
-    LMOSEM_MODEL_BF16_SCALED = 2  /* p_jn = c_j h_jn, h BF16 with max_n h = 1      */
+    LMOSEM_MODEL_FP32 = 0,          /* p_jn cached as FP32                           */
+    LMOSEM_MODEL_FP16_SCALED = 1,   /* p_jn = c_j h_jn, h FP16 with max_n h = 2^15   */
+    LMOSEM_MODEL_BF16_SCALED = 2,   /* p_jn = c_j h_jn, h BF16 with max_n h = 1      */
+    LMOSEM_MODEL_SURROGATE_FP32 = 3 /* FP32; scatter part from the loaded surrogate  */
 } lmosem_model_fmt;
+
+/* Scatter surrogate parameters: one FP32 blob of LMOSEM_SURROGATE_PARAMS
+ * values, in this order: W1 (256 x 6, row-major, out x in), b1 (256), W2, b2,
+ * W3, b3 (256 x 256, 256), W4, b4, W5 (1 x 256), b5 (1), mu, sigma.  The
+ * network (ReLU after every hidden layer) maps six inputs, each scaled as
+ * (v - shift) / scale with shift, scale =
+ *   pixel x (0, 100 mm), pixel y (0, 100 mm), detector angle (pi, pi rad),
+ *   event position u (0, 100 mm), event energy (137.5, 37.5 keV),
+ *   integral of mu(E0) from the pixel centre to the grid edge along the
+ *   detector direction (1.5, 1.5),
+ * to y with log p^scat_jn = mu + sigma y (natural log). */
+#define LMOSEM_SURROGATE_PARAMS 199427
 
 /* Create a context: validate the problem, copy the mu-map and support to the
  * device and build the attenuation tables (integrals of mu along omega_a from
@@ -206,6 +220,52 @@ lmosem_status lmosem_autotune_batch(lmosem_ctx* ctx, double acq_time, const floa
 /* Set the batched tiles directly (e.g. a choice cached from an earlier
  * autotuning): chunk_rows in [8, 2^20], ctas_per_sm in [1, 16]. */
 lmosem_status lmosem_set_batch_tiles(lmosem_ctx* ctx, int32_t chunk_rows, int32_t ctas_per_sm);
+
+/* Scatter surrogate (the learned form of the first-order scatter sum of paper
+ * Eq. 2; the paper itself evaluates that sum exactly).
+ *
+ * Training samples: builds the exact model of the given events with the
+ * primary path left out (replacing any cached model, which is released
+ * afterwards) and writes, for every (event k, support pixel q) at row
+ * k * N_nz + q: the six scaled inputs (d_features, 6 floats per row) and the
+ * natural log of the exact scatter entry (d_log_scatter; entries below 1e-30
+ * are clamped).  Synchronises.  EINVAL as lmosem_build_model. */
+lmosem_status lmosem_surrogate_samples(lmosem_ctx* ctx, const int32_t* d_angle, const float* d_u_mm,
+                                       const float* d_e_kev, int64_t n_events, float* d_features,
+                                       float* d_log_scatter);
+
+typedef struct {
+    int32_t steps;     /* Adam steps (>= 1)                                        */
+    int32_t batch;     /* rows per minibatch, multiple of 64, 64..65536            */
+    float lr;          /* learning rate (the last 20% of the steps use lr / 10)    */
+    uint64_t seed;     /* minibatch sampling (rows drawn with replacement)         */
+} lmosem_train_opts;
+
+/* Train the surrogate on n samples (features n x 6, targets n = log scatter)
+ * with the library's tensor-core forward and backward kernels and Adam (FP32
+ * parameters and moments, BF16 products, FP32 accumulation).  d_weights holds
+ * the initial parameters on entry (mu and sigma are recomputed from the
+ * targets) and the trained ones on return.  h_loss_curve (steps doubles, may
+ * be NULL) receives the minibatch loss of every step.  Synchronises. */
+lmosem_status lmosem_surrogate_train(lmosem_ctx* ctx, const float* d_features, const float* d_targets,
+                                     int64_t n, const lmosem_train_opts* opts, float* d_weights,
+                                     double* h_loss_curve);
+
+/* Gradient of the mean squared error of the network output against the
+ * standardised targets ((t - mu) / sigma with the blob's mu, sigma) over all
+ * n rows (n <= 65536), in the blob layout (mu, sigma entries zero), and the
+ * loss in *h_loss.  Synchronises. */
+lmosem_status lmosem_surrogate_grad(lmosem_ctx* ctx, const float* d_weights, const float* d_features,
+                                    const float* d_targets, int64_t n, float* d_grad, double* h_loss);
+
+/* Network output y for n rows of scaled inputs (log p^scat = mu + sigma y).
+ * Synchronises. */
+lmosem_status lmosem_surrogate_infer(lmosem_ctx* ctx, const float* d_weights, const float* d_features,
+                                     int64_t n, float* d_out);
+
+/* Copy trained parameters into the context for LMOSEM_MODEL_SURROGATE_FP32
+ * model builds. */
+lmosem_status lmosem_surrogate_load(lmosem_ctx* ctx, const float* d_weights);
 
 /* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz).
  * ESTATE: no model or sensitivity. */

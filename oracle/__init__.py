@@ -95,7 +95,8 @@ def lib():
                                            _ip, ctypes.c_int, _dp, _dp]
             L.orc_model.restype = None
             L.orc_model.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
-                                    ctypes.c_int, _dp, _dp, _ip, _dp, _dp, ctypes.c_int64, _dp]
+                                    ctypes.c_int, _dp, _dp, _ip, _dp, _dp, ctypes.c_int64, _dp,
+                                    ctypes.c_int]
             L.orc_sensitivity.restype = None
             L.orc_sensitivity.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
                                           ctypes.c_int, _dp, _dp, ctypes.c_int, _dp]
@@ -193,10 +194,11 @@ class Problem:
         ix, iy = pix % g.nx, pix // g.nx
         return ((ix + 0.5 - 0.5 * g.nx) * g.pixel_mm, (iy + 0.5 - 0.5 * g.ny) * g.pixel_mm)
 
-    def model(self, angle, u_mm, e_kev):
+    def model(self, angle, u_mm, e_kev, primary=True, scatter=True):
         """p[j, q] of every event j and support pixel q (paper Eq. 2 with
         Eq. 4: pr(A_j|P) s_eff(P) summed over the primary path and every
-        first-order in-plane scatter path that starts in pixel q)."""
+        first-order in-plane scatter path that starts in pixel q).  The
+        flags restrict the sum to the primary path or to the scatter paths."""
         angle = np.ascontiguousarray(angle, dtype=np.int32)
         u = np.ascontiguousarray(u_mm, dtype=np.float64)
         e = np.ascontiguousarray(e_kev, dtype=np.float64)
@@ -204,7 +206,7 @@ class Problem:
         p = np.zeros((n, self.n_sup), dtype=np.float64)
         lib().orc_model(ctypes.byref(self.geom), _d(self.mu), _i(self.support), self.n_sup,
                         _i(self.scatter), len(self.scatter), _d(self.l_edge), _d(self.l_pair),
-                        _i(angle), _d(u), _d(e), n, _d(p))
+                        _i(angle), _d(u), _d(e), n, _d(p), int(primary) | (int(scatter) << 1))
         return p
 
     def sensitivity(self, n_subsets: int):

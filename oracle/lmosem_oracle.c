@@ -313,7 +313,7 @@ static int orc_scatter_path(const orc_geom* g, const double* mu, int a, int pix_
 void orc_model(const orc_geom* g, const double* mu, const int32_t* sup, int n_sup,
                const int32_t* scat, int n_scat, const double* l_edge, const double* l_pair,
                const int32_t* ev_angle, const double* ev_u, const double* ev_e, int64_t n_ev,
-               double* p_out)
+               double* p_out, int parts /* bit 0: primary path, bit 1: scatter paths */)
 {
     int npix = g->nx * g->ny;
     double kbar = orc_kn_mean(g->e0_kev);
@@ -350,13 +350,14 @@ void orc_model(const orc_geom* g, const double* mu, const int32_t* sup, int n_su
             double* row = p_out + (size_t)j * n_sup;
             double u = ev_u[j], e = ev_e[j];
             /* primary path (n) */
-            for (int i = 0; i < n_sup; ++i) {
+            for (int i = 0; i < n_sup && (parts & 1); ++i) {
                 double xn, yn;
                 orc_pixel_centre(g, sup[i], &xn, &yn);
                 double su = orc_sigma_u(g, orc_det_depth(g, a, xn, yn));
                 row[i] = exp(-l_edge[(size_t)a * npix + sup[i]]) *
                          orc_gauss(u, orc_det_u(g, a, xn, yn), su) * orc_gauss(e, g->e0_kev, se0);
             }
+            if (!(parts & 2)) continue;
             /* first-order scatter paths (n, m) */
             for (int k = 0; k < n_scat; ++k) {
                 double z = (u - ucen[k]) / usig[k];

@@ -86,6 +86,7 @@ void free_model(lmosem_ctx* c) {
     dev_free(&c->d_bpart_batch);
     c->bpart_batch_floats = 0;
     c->batch_model = false;
+    c->use_surrogate = false;
     c->n_real = 1;
     c->fmt = -1;
     c->J = 0;
@@ -100,8 +101,11 @@ lmosem_status check_events_args(lmosem_ctx* c, const int32_t* d_angle, const flo
         return fail(c, LMOSEM_EINVAL, "n_events must be in [1, 2^31)");
     if (n_subsets < 1 || n_subsets > c->n_angles)
         return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
-    if (fmt != LMOSEM_MODEL_FP32 && fmt != LMOSEM_MODEL_FP16_SCALED && fmt != LMOSEM_MODEL_BF16_SCALED)
+    if (fmt != LMOSEM_MODEL_FP32 && fmt != LMOSEM_MODEL_FP16_SCALED && fmt != LMOSEM_MODEL_BF16_SCALED &&
+        fmt != LMOSEM_MODEL_SURROGATE_FP32)
         return fail(c, LMOSEM_EINVAL, "unknown model format");
+    if (fmt == LMOSEM_MODEL_SURROGATE_FP32 && !c->d_surrogate)
+        return fail(c, LMOSEM_ESTATE, "no surrogate loaded (lmosem_surrogate_load)");
     return LMOSEM_OK;
 }
 
@@ -110,7 +114,11 @@ lmosem_status build_model_common(lmosem_ctx* c, const int32_t* d_angle, const fl
                                  const float* d_e_kev, int64_t n_events, int32_t n_subsets,
                                  lmosem_model_fmt fmt, const int64_t* h_offsets, int n_real) {
     free_model(c);
+    // the surrogate form is stored as FP32 rows; only their scatter part differs
+    const bool sur = fmt == LMOSEM_MODEL_SURROGATE_FP32;
+    if (sur) fmt = LMOSEM_MODEL_FP32;
     c->fmt = fmt;
+    c->use_surrogate = sur;
     c->J = n_events;
     c->n_subsets = n_subsets;
     c->ld_model = (c->n_sup + 31) / 32 * 32;
@@ -203,6 +211,7 @@ void lmosem_destroy(lmosem_ctx* c) {
     dev_free(&c->d_llpart);
     dev_free(&c->d_scalar);
     dev_free(&c->d_status);
+    dev_free(&c->d_surrogate);
     for (auto& r : c->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -494,6 +503,62 @@ lmosem_status lmosem_model_rows(lmosem_ctx* c, const int64_t* d_ids, int64_t n, 
     if (n < 0 || (n > 0 && (!d_ids || !d_out))) return fail(c, LMOSEM_EINVAL, "bad arguments");
     if (c->fmt < 0) return fail(c, LMOSEM_ESTATE, "no model built");
     return run_model_rows(c, d_ids, n, d_out);
+}
+
+lmosem_status lmosem_surrogate_samples(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
+                                       const float* d_e_kev, int64_t n_events, float* d_features,
+                                       float* d_log_scatter) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_features || !d_log_scatter) return fail(c, LMOSEM_EINVAL, "null output");
+    lmosem_status st = check_events_args(c, d_angle, d_u_mm, d_e_kev, n_events, 1, LMOSEM_MODEL_FP32);
+    if (st) return st;
+    c->scatter_only = true;
+    st = build_model_common(c, d_angle, d_u_mm, d_e_kev, n_events, 1, LMOSEM_MODEL_FP32, nullptr, 1);
+    c->scatter_only = false;
+    if (st) return st;
+    st = run_surrogate_samples(c, d_features, d_log_scatter);
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    free_model(c);
+    return st;
+}
+
+lmosem_status lmosem_surrogate_train(lmosem_ctx* c, const float* d_features, const float* d_targets,
+                                     int64_t n, const lmosem_train_opts* opts, float* d_weights,
+                                     double* h_loss_curve) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_features || !d_targets || !d_weights || !opts || n < 1)
+        return fail(c, LMOSEM_EINVAL, "bad training arguments");
+    if (opts->steps < 1 || opts->batch < 64 || opts->batch > 65536 || opts->batch % 64 ||
+        !(opts->lr > 0.0f) || !isfinite(opts->lr))
+        return fail(c, LMOSEM_EINVAL, "steps >= 1, batch a multiple of 64 in [64, 65536], lr > 0");
+    return run_surrogate_train(c, d_features, d_targets, n, opts->steps, opts->batch, opts->lr, opts->seed,
+                               d_weights, h_loss_curve);
+}
+
+lmosem_status lmosem_surrogate_grad(lmosem_ctx* c, const float* d_weights, const float* d_features,
+                                    const float* d_targets, int64_t n, float* d_grad, double* h_loss) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_weights || !d_features || !d_targets || !d_grad || n < 1 || n > 65536)
+        return fail(c, LMOSEM_EINVAL, "bad gradient arguments (1 <= n <= 65536)");
+    return run_surrogate_grad(c, d_weights, d_features, d_targets, n, d_grad, h_loss);
+}
+
+lmosem_status lmosem_surrogate_infer(lmosem_ctx* c, const float* d_weights, const float* d_features,
+                                     int64_t n, float* d_out) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_weights || !d_features || !d_out || n < 1 || n > (int64_t(1) << 26))
+        return fail(c, LMOSEM_EINVAL, "bad inference arguments (1 <= n <= 2^26)");
+    return run_surrogate_infer(c, d_weights, d_features, n, d_out);
+}
+
+lmosem_status lmosem_surrogate_load(lmosem_ctx* c, const float* d_weights) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_weights) return fail(c, LMOSEM_EINVAL, "null weights");
+    lmosem_status st;
+    if (!c->d_surrogate && (st = dev_alloc(c, &c->d_surrogate, LMOSEM_SURROGATE_PARAMS))) return st;
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_surrogate, d_weights, sizeof(float) * LMOSEM_SURROGATE_PARAMS,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    return LMOSEM_OK;
 }
 
 }  // extern "C"

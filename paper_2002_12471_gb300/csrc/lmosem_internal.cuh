@@ -98,6 +98,10 @@ struct lmosem_ctx {
     int* d_status = nullptr;      // [0] = 1 after a bounded device wait ran out
     long long wait_budget = 2000000000LL;  // clock cycles per bounded wait
     int pass_variant = 0;         // 0 auto, 1 register pipeline, 2 bulk-copy ring
+    // scatter surrogate
+    float* d_surrogate = nullptr;             // LMOSEM_SURROGATE_PARAMS FP32 parameters
+    bool scatter_only = false;                // model build leaves the primary path out
+    bool use_surrogate = false;               // model build takes the scatter part from the MLP
     // batching form: per-realisation work words, partial slots, tiles, graph
     bool batch_model = false;
     int64_t* d_bsub_row0 = nullptr;           // n_real * (n_subsets + 1)
@@ -201,6 +205,16 @@ lmosem_status setup_batch(lmosem_ctx* c);                       // batch.cu
 lmosem_status run_init_batch(lmosem_ctx* c, double T, float* d_f);
 lmosem_status run_batch(lmosem_ctx* c, int n_iters, double T, float* d_f);
 lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int32_t* h_choice);
+// mlp.cu
+lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* feat, const float* targ,
+                                 int64_t n, float* grad_out, double* h_loss);
+lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
+                                  int steps, int B, float lr, uint64_t seed, float* blob,
+                                  double* h_loss_curve);
+lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float* feat, int64_t n,
+                                  float* out);
+lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ);
+lmosem_status build_model_surrogate(lmosem_ctx* c);
 
 // ---- device helpers shared by the CUDA translation units
 

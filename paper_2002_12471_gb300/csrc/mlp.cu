@@ -1,0 +1,666 @@
+// Learned scatter surrogate (row a9 of the hot path).
+//
+// The first-order scatter part of the per-event path sum (paper Eq. 2 over
+// the scatter paths of Section 2.2),
+//     p^scat_jn = sum_{m in strip(j)} U_jm W_a(n, m) phi(E_j; E'_a(n, m), sigma_E),
+// is replaced by a multilayer perceptron of six inputs (pixel x, y, detector
+// angle, event position, event energy, attenuation from the pixel to the
+// detector), 6 -> 256 -> 256 -> 256 -> 256 -> 1 with ReLU, whose output is the
+// standardised natural log of p^scat_jn.  The network is trained on exact
+// scatter path sums made by the exact path (k_pathsum with the primary left
+// out) and evaluated inside the model build, where p_jn = primary_jn +
+// exp(mu + sigma y_jn).
+//
+// Matrix products run on the tensor cores in BF16 with FP32 accumulation:
+// C[M x N] = A[M x K] B[N x K]^T with both operands K-contiguous (one kernel;
+// the backward products use explicit transposes), ldmatrix fragments and
+// mma.sync m16n8k16, fused bias / ReLU / ReLU-mask epilogues.  Parameters are
+// kept in FP32 (Adam state too) with BF16 copies for the products.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "lmosem_internal.cuh"
+
+namespace lmosem {
+
+namespace {
+
+constexpr int kIn = 6, kInPad = 16, kH = 256;
+constexpr int64_t kOffW1 = 0;
+constexpr int64_t kOffB1 = kOffW1 + kH * kIn;
+constexpr int64_t kOffW2 = kOffB1 + kH;
+constexpr int64_t kOffB2 = kOffW2 + kH * kH;
+constexpr int64_t kOffW3 = kOffB2 + kH;
+constexpr int64_t kOffB3 = kOffW3 + kH * kH;
+constexpr int64_t kOffW4 = kOffB3 + kH;
+constexpr int64_t kOffB4 = kOffW4 + kH * kH;
+constexpr int64_t kOffW5 = kOffB4 + kH;
+constexpr int64_t kOffB5 = kOffW5 + kH;
+constexpr int64_t kOffMu = kOffB5 + 1;
+constexpr int64_t kOffSigma = kOffMu + 1;
+constexpr int64_t kParams = kOffSigma + 1;
+static_assert(kParams == LMOSEM_SURROGATE_PARAMS, "parameter blob layout");
+
+// input scaling: (raw - shift) / scale for x, y, theta, u, E, attenuation
+__constant__ float c_shift[kIn] = {0.0f, 0.0f, 3.14159265358979f, 0.0f, 137.5f, 1.5f};
+__constant__ float c_scale[kIn] = {100.0f, 100.0f, 3.14159265358979f, 100.0f, 37.5f, 1.5f};
+
+// ---------------------------------------------------------------- GEMM
+
+constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;
+
+enum Epi { EPI_F32 = 0, EPI_RELU_BF16 = 1, EPI_MASK_BF16 = 2 };
+
+__device__ __forceinline__ void cp16_zfill(void* dst, const void* src, bool ok) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    int n = ok ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                        const void* p) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C = A B^T (+ epilogue); K a multiple of 8; M, N arbitrary
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict__ A, int64_t lda,
+                                                 const __nv_bfloat16* __restrict__ B, int64_t ldb,
+                                                 void* __restrict__ C, int64_t ldc,
+                                                 const float* __restrict__ bias,
+                                                 const __nv_bfloat16* __restrict__ mask, int64_t ldm,
+                                                 int64_t M, int N, int K) {
+    __shared__ __align__(16) __nv_bfloat16 As[2][kBM][kLds];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][kBN][kLds];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int64_t m0 = (int64_t)blockIdx.x * kBM;
+    const int n0 = blockIdx.y * kBN;
+
+    auto load = [&](int kt, int buf) {
+        const int k0 = kt * kBK;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c = tid + q * 128;       // 256 chunks of 8 elements per operand
+            const int row = c >> 2, kc = (c & 3) * 8;
+            const bool ka = k0 + kc < K;
+            const int64_t ar = m0 + row;
+            cp16_zfill(&As[buf][row][kc], A + (ar < M && ka ? ar * lda + k0 + kc : 0), ar < M && ka);
+            const int br = n0 + row;
+            cp16_zfill(&Bs[buf][row][kc], B + (br < N && ka ? (int64_t)br * ldb + k0 + kc : 0), br < N && ka);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    float acc[2][4][4] = {};
+    const int nk = (K + kBK - 1) / kBK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) {
+            load(kt + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; kk += 16) {
+            unsigned af[2][4], bf[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3],
+                        &As[buf][wm * 32 + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                ldsm_x4(bf[j][0], bf[j][1], bf[j][2], bf[j][3],
+                        &Bs[buf][wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_bf16(acc[i][j], af[i], bf[j >> 1][(j & 1) * 2], bf[j >> 1][(j & 1) * 2 + 1]);
+        }
+        __syncthreads();
+    }
+    // epilogue: thread holds rows g, g+8 and columns 2t, 2t+1 of every m16n8 tile
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = m0 + wm * 32 + i * 16 + g + h * 8;
+                const int col = n0 + wn * 32 + j * 8 + 2 * t4;
+                if (row >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (col + e >= N) continue;
+                    float v = acc[i][j][2 * h + e];
+                    if constexpr (EPI == EPI_F32) {
+                        reinterpret_cast<float*>(C)[row * ldc + col + e] = v;
+                    } else if constexpr (EPI == EPI_RELU_BF16) {
+                        v += bias[col + e];
+                        reinterpret_cast<__nv_bfloat16*>(C)[row * ldc + col + e] = __float2bfloat16_rn(fmaxf(v, 0.0f));
+                    } else {
+                        const bool on = __bfloat162float(mask[row * ldm + col + e]) > 0.0f;
+                        reinterpret_cast<__nv_bfloat16*>(C)[row * ldc + col + e] = __float2bfloat16_rn(on ? v : 0.0f);
+                    }
+                }
+            }
+}
+
+// out[c][r] = in[r][c] (BF16), 32 x 32 tiles
+__global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int64_t rows, int cols, int64_t ldi,
+                            __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k;
+        const int c = c0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < rows && c < cols) ? in[r * ldi + c] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[(int64_t)c * ldo + r] = tile[threadIdx.x][k];
+    }
+}
+
+// ---------------------------------------------------------------- small kernels
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// minibatch rows (seeded, with replacement): scaled features as BF16 (padded
+// to 16 columns) and standardised targets
+__global__ void k_gather(const float* __restrict__ feat, const float* __restrict__ targ, int64_t n,
+                         int B, uint64_t seed, int step, const float* __restrict__ blob,
+                         __nv_bfloat16* __restrict__ X, float* __restrict__ t) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int64_t i = seed == 0 ? (int64_t)b % n
+                                : (int64_t)(splitmix64(seed ^ ((uint64_t)step * 0x100000001B3ull + b)) % (uint64_t)n);
+#pragma unroll
+    for (int k = 0; k < kInPad; ++k)
+        X[(int64_t)b * kInPad + k] = __float2bfloat16_rn(k < kIn ? feat[i * kIn + k] : 0.0f);
+    t[b] = (targ[i] - blob[kOffMu]) / blob[kOffSigma];
+}
+
+// y = H4 w5 + b5 (one warp per row)
+__global__ void k_out_fwd(const __nv_bfloat16* __restrict__ H, int64_t M, const float* __restrict__ blob,
+                          float* __restrict__ y) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    float s = 0.0f;
+    for (int k = lane; k < kH; k += 32) s = fmaf(__bfloat162float(H[row * kH + k]), blob[kOffW5 + k], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s + blob[kOffB5];
+}
+
+// dy = 2 (y - t) / B; dz4 = dy w5 where H4 > 0; loss sum into *loss (FP64)
+__global__ void k_out_bwd(const float* __restrict__ y, const float* __restrict__ t,
+                          const __nv_bfloat16* __restrict__ H4, int B, const float* __restrict__ blob,
+                          float* __restrict__ dy, __nv_bfloat16* __restrict__ dz4, double* __restrict__ loss) {
+    const int b = blockIdx.x;
+    const float r = y[b] - t[b];
+    const float d = 2.0f * r / (float)B;
+    if (threadIdx.x == 0) {
+        dy[b] = d;
+        atomicAdd(loss, (double)r * (double)r / (double)B);
+    }
+    for (int k = threadIdx.x; k < kH; k += blockDim.x) {
+        const bool on = __bfloat162float(H4[(int64_t)b * kH + k]) > 0.0f;
+        dz4[(int64_t)b * kH + k] = __float2bfloat16_rn(on ? d * blob[kOffW5 + k] : 0.0f);
+    }
+}
+
+// dW5[k] = sum_b dy_b H4[b][k], db5 = sum_b dy_b (fixed order per column)
+__global__ void k_out_wgrad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, int B,
+                            float* __restrict__ grad) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > kH) return;
+    float s = 0.0f;
+    for (int b = 0; b < B; ++b) s += dy[b] * (k < kH ? __bfloat162float(H4[(int64_t)b * kH + k]) : 1.0f);
+    grad[k < kH ? kOffW5 + k : kOffB5] = s;
+}
+
+// db[r] = sum of row r of dZ^T (rows x B), one warp per row, fixed order
+__global__ void k_rowsum(const __nv_bfloat16* __restrict__ ZT, int rows, int B, int64_t ld,
+                         float* __restrict__ out) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.0f;
+    for (int b = lane; b < B; b += 32) s += __bfloat162float(ZT[(int64_t)r * ld + b]);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s;
+}
+
+// copy a gradient block [rows x cols] from a GEMM result with ld into the blob
+__global__ void k_copy_grad(const float* __restrict__ src, int rows, int cols, int64_t lds,
+                            float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    dst[i] = src[(int64_t)(i / cols) * lds + (i % cols)];
+}
+
+// Adam (bias-corrected moments) over the whole blob except (mu, sigma)
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of the weights: W1 padded to 16 columns, W2..W4 and their
+// transposes (for the input gradients)
+__global__ void k_weights_bf16(const float* __restrict__ blob, __nv_bfloat16* __restrict__ w1,
+                               __nv_bfloat16* __restrict__ w234, __nv_bfloat16* __restrict__ w234t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kH * kInPad) {
+        const int o = i / kInPad, k = i % kInPad;
+        w1[i] = __float2bfloat16_rn(k < kIn ? blob[kOffW1 + o * kIn + k] : 0.0f);
+    }
+    if (i < 3 * kH * kH) {
+        const int l = i / (kH * kH), r = i % (kH * kH);
+        const int o = r / kH, k = r % kH;
+        const float val = blob[kOffW2 + (int64_t)l * (kH * kH + kH) + r];
+        w234[i] = __float2bfloat16_rn(val);
+        w234t[(int64_t)l * kH * kH + k * kH + o] = __float2bfloat16_rn(val);
+    }
+}
+
+// mean and standard deviation of the targets (FP64, one block, fixed order)
+__global__ void k_target_stats(const float* __restrict__ t, int64_t n, float* __restrict__ blob) {
+    __shared__ double s1[256], s2[256];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a += t[i];
+        b += (double)t[i] * t[i];
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, Bq = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            A += s1[k];
+            Bq += s2[k];
+        }
+        const double mu = A / n;
+        const double var = fmax(Bq / n - mu * mu, 1e-12);
+        blob[kOffMu] = (float)mu;
+        blob[kOffSigma] = (float)sqrt(var);
+    }
+}
+
+// ---------------------------------------------------------------- features
+
+struct FeatArgs {
+    const int32_t* a_s;      // sorted angles
+    const float* u_s;
+    const float* e_s;
+    const int32_t* sup;
+    int n_sup, nx, ny, npix;
+    float dpx;
+    const float* l_edge;     // [a][pixel]
+    float angle0, dtheta;
+};
+
+__device__ __forceinline__ void features(const FeatArgs& F, int64_t row, int q, float* out) {
+    const int a = F.a_s[row];
+    const int pix = F.sup[q];
+    float raw[kIn] = {pixel_x(pix, F.nx, F.dpx), pixel_y(pix, F.nx, F.ny, F.dpx), F.angle0 + F.dtheta * a,
+                      F.u_s[row], F.e_s[row], F.l_edge[(size_t)a * F.npix + pix]};
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) out[k] = (raw[k] - c_shift[k]) / c_scale[k];
+}
+
+// training samples: scaled features and log of the exact scatter entry for
+// (event ids[k], every support pixel); rows of the caller's order
+__global__ void k_samples(FeatArgs F, const float* __restrict__ model, int64_t ld,
+                          const int64_t* __restrict__ rank, int64_t n_ev, float* __restrict__ feat,
+                          float* __restrict__ targ) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_ev * F.n_sup) return;
+    const int64_t k = i / F.n_sup;
+    const int q = (int)(i % F.n_sup);
+    const int64_t row = rank[k];
+    float f[kIn];
+    features(F, row, q, f);
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) feat[i * kIn + c] = f[c];
+    targ[i] = logf(fmaxf(model[row * ld + q], 1e-30f));
+}
+
+// surrogate inputs of rows [r0, r0 + nrows) x all support pixels, BF16
+__global__ void k_surr_inputs(FeatArgs F, int64_t r0, int64_t nrows, __nv_bfloat16* __restrict__ X) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows * F.n_sup) return;
+    float f[kIn];
+    features(F, r0 + i / F.n_sup, (int)(i % F.n_sup), f);
+#pragma unroll
+    for (int k = 0; k < kInPad; ++k) X[i * kInPad + k] = __float2bfloat16_rn(k < kIn ? f[k] : 0.0f);
+}
+
+// p_jn = primary_jn + exp(mu + sigma y_jn) into the FP32 model rows
+__global__ void k_surr_combine(const float* __restrict__ y, int64_t r0, int64_t nrows, int n_sup,
+                               int64_t ld, const int32_t* __restrict__ a_s, const float* __restrict__ u_s,
+                               const float* __restrict__ e_s, const float4* __restrict__ ppar, int ld_w,
+                               float e0, float sE0, float lE0, const float* __restrict__ blob,
+                               float* __restrict__ model) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows * ld) return;
+    const int64_t row = r0 + i / ld;
+    const int q = (int)(i % ld);
+    float v = 0.0f;
+    if (q < n_sup) {
+        const int a = a_s[row];
+        const float4 pp = ppar[(size_t)a * ld_w + q];
+        const float te = (e_s[row] - e0) * sE0;
+        const float t = (u_s[row] - pp.x) * pp.y;
+        const float prim = ex2_approx(fmaf(-t, t, pp.z + fmaf(-te, te, lE0)));
+        const float ls = blob[kOffMu] + blob[kOffSigma] * y[(i / ld) * n_sup + q];
+        v = prim + expf(ls);
+    }
+    model[row * ld + q] = v;
+}
+
+// ---------------------------------------------------------------- host helpers
+
+struct MlpBufs {
+    __nv_bfloat16 *w1 = nullptr, *w234 = nullptr, *w234t = nullptr;
+};
+
+lmosem_status gemm(lmosem_ctx* c, int epi, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B,
+                   int64_t ldb, void* C, int64_t ldc, const float* bias, const __nv_bfloat16* mask,
+                   int64_t ldm, int64_t M, int N, int K) {
+    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + kBN - 1) / kBN));
+    LMOSEM_PROF_BEGIN(c);
+    if (epi == EPI_F32)
+        k_gemm_tn<EPI_F32><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
+    else if (epi == EPI_RELU_BF16)
+        k_gemm_tn<EPI_RELU_BF16><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
+    else
+        k_gemm_tn<EPI_MASK_BF16><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    return LMOSEM_OK;
+}
+
+lmosem_status transpose(lmosem_ctx* c, const __nv_bfloat16* in, int64_t rows, int cols, int64_t ldi,
+                        __nv_bfloat16* out, int64_t ldo) {
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    LMOSEM_PROF_BEGIN(c);
+    k_transpose<<<grid, dim3(32, 8), 0, c->stream>>>(in, rows, cols, ldi, out, ldo);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    return LMOSEM_OK;
+}
+
+lmosem_status weights_bf16(lmosem_ctx* c, const float* blob, MlpBufs& w) {
+    LMOSEM_PROF_BEGIN(c);
+    k_weights_bf16<<<(3 * kH * kH + 255) / 256, 256, 0, c->stream>>>(blob, w.w1, w.w234, w.w234t);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    return LMOSEM_OK;
+}
+
+// forward of M rows: X (M x 16) -> H[0..3] (M x 256 each) -> y (M)
+lmosem_status forward(lmosem_ctx* c, const float* blob, const MlpBufs& w, const __nv_bfloat16* X,
+                      __nv_bfloat16* const H[4], float* y, int64_t M) {
+    lmosem_status st;
+    if ((st = gemm(c, EPI_RELU_BF16, X, kInPad, w.w1, kInPad, H[0], kH, blob + kOffB1, nullptr, 0, M, kH, kInPad)))
+        return st;
+    for (int l = 0; l < 3; ++l)
+        if ((st = gemm(c, EPI_RELU_BF16, H[l], kH, w.w234 + (int64_t)l * kH * kH, kH, H[l + 1], kH,
+                       blob + kOffB2 + (int64_t)l * (kH * kH + kH), nullptr, 0, M, kH, kH)))
+            return st;
+    LMOSEM_PROF_BEGIN(c);
+    k_out_fwd<<<(unsigned)((M + 7) / 8), 256, 0, c->stream>>>(H[3], M, blob, y);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    return LMOSEM_OK;
+}
+
+struct TrainBufs {
+    __nv_bfloat16 *X = nullptr, *XT = nullptr, *H = nullptr, *HT = nullptr, *dz = nullptr, *dzT = nullptr;
+    float *t = nullptr, *y = nullptr, *dy = nullptr, *gtmp = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    double* loss = nullptr;
+};
+
+// loss and gradient of one minibatch into tb.grad (blob layout)
+lmosem_status loss_grad(lmosem_ctx* c, const float* blob, const MlpBufs& w, TrainBufs& tb, int B) {
+    lmosem_status st;
+    __nv_bfloat16* H[4] = {tb.H, tb.H + (int64_t)B * kH, tb.H + 2 * (int64_t)B * kH, tb.H + 3 * (int64_t)B * kH};
+    if ((st = forward(c, blob, w, tb.X, H, tb.y, B))) return st;
+    __nv_bfloat16* dz = tb.dz;                       // B x 256, current layer
+    LMOSEM_PROF_BEGIN(c);
+    k_out_bwd<<<B, 128, 0, c->stream>>>(tb.y, tb.t, H[3], B, blob, tb.dy, dz, tb.loss);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    LMOSEM_PROF_BEGIN(c);
+    k_out_wgrad<<<2, 256, 0, c->stream>>>(tb.dy, H[3], B, tb.grad);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    for (int l = 3; l >= 0; --l) {                   // hidden layer l + 1 (0-based l)
+        // dW = dz^T h_prev, db = row sums of dz^T
+        if ((st = transpose(c, dz, B, kH, kH, tb.dzT, B))) return st;
+        const int in = l == 0 ? kInPad : kH;
+        const __nv_bfloat16* hprev = l == 0 ? tb.X : H[l - 1];
+        if ((st = transpose(c, hprev, B, in, in, tb.HT, B))) return st;
+        if ((st = gemm(c, EPI_F32, tb.dzT, B, tb.HT, B, tb.gtmp, in, nullptr, nullptr, 0, kH, in, B))) return st;
+        const int64_t offW = l == 0 ? kOffW1 : kOffW2 + (int64_t)(l - 1) * (kH * kH + kH);
+        const int64_t offB = l == 0 ? kOffB1 : offW + kH * kH;
+        const int cols = l == 0 ? kIn : kH;
+        LMOSEM_PROF_BEGIN(c);
+        k_copy_grad<<<(kH * cols + 255) / 256, 256, 0, c->stream>>>(tb.gtmp, kH, cols, in, tb.grad + offW);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        LMOSEM_PROF_BEGIN(c);
+        k_rowsum<<<kH / 8, 256, 0, c->stream>>>(tb.dzT, kH, B, B, tb.grad + offB);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        if (l > 0) {
+            // dz_prev = (dz W_l) where h_prev > 0
+            __nv_bfloat16* nxt = dz == tb.dz ? tb.dz + (int64_t)B * kH : tb.dz;
+            if ((st = gemm(c, EPI_MASK_BF16, dz, kH, w.w234t + (int64_t)(l - 1) * kH * kH, kH, nxt, kH, nullptr,
+                           hprev, kH, B, kH, kH)))
+                return st;
+            dz = nxt;
+        }
+    }
+    return LMOSEM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- entry points
+
+lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* feat, const float* targ,
+                                 int64_t n, float* grad_out, double* h_loss) {
+    lmosem_status st;
+    const int B = (int)n;
+    MlpBufs w;
+    TrainBufs tb;
+    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
+        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &tb.X, (size_t)B * kInPad)) ||
+        (st = dev_alloc(c, &tb.XT, (size_t)B * kInPad)) || (st = dev_alloc(c, &tb.H, (size_t)4 * B * kH)) ||
+        (st = dev_alloc(c, &tb.HT, (size_t)B * kH)) || (st = dev_alloc(c, &tb.dz, (size_t)2 * B * kH)) ||
+        (st = dev_alloc(c, &tb.dzT, (size_t)B * kH)) || (st = dev_alloc(c, &tb.t, B)) ||
+        (st = dev_alloc(c, &tb.y, B)) || (st = dev_alloc(c, &tb.dy, B)) ||
+        (st = dev_alloc(c, &tb.gtmp, (size_t)kH * kH)) || (st = dev_alloc(c, &tb.loss, 1)))
+        return st;
+    LMOSEM_CK(c, cudaMemsetAsync(grad_out, 0, sizeof(float) * kParams, c->stream));
+    LMOSEM_CK(c, cudaMemsetAsync(tb.loss, 0, sizeof(double), c->stream));
+    if ((st = weights_bf16(c, blob, w))) return st;
+    LMOSEM_PROF_BEGIN(c);
+    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, blob, tb.X, tb.t);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    tb.grad = grad_out;
+    if ((st = loss_grad(c, blob, w, tb, B))) return st;
+    double h = 0.0;
+    LMOSEM_CK(c, cudaMemcpyAsync(&h, tb.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h_loss) *h_loss = h;
+    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&tb.X); dev_free(&tb.XT);
+    dev_free(&tb.H); dev_free(&tb.HT); dev_free(&tb.dz); dev_free(&tb.dzT); dev_free(&tb.t);
+    dev_free(&tb.y); dev_free(&tb.dy); dev_free(&tb.gtmp); dev_free(&tb.loss);
+    return LMOSEM_OK;
+}
+
+lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
+                                  int steps, int B, float lr, uint64_t seed, float* blob,
+                                  double* h_loss_curve) {
+    lmosem_status st;
+    MlpBufs w;
+    TrainBufs tb;
+    double* d_curve = nullptr;
+    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
+        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &tb.X, (size_t)B * kInPad)) ||
+        (st = dev_alloc(c, &tb.H, (size_t)4 * B * kH)) || (st = dev_alloc(c, &tb.HT, (size_t)B * kH)) ||
+        (st = dev_alloc(c, &tb.dz, (size_t)2 * B * kH)) || (st = dev_alloc(c, &tb.dzT, (size_t)B * kH)) ||
+        (st = dev_alloc(c, &tb.t, B)) || (st = dev_alloc(c, &tb.y, B)) || (st = dev_alloc(c, &tb.dy, B)) ||
+        (st = dev_alloc(c, &tb.gtmp, (size_t)kH * kH)) || (st = dev_alloc(c, &tb.grad, kParams)) ||
+        (st = dev_alloc(c, &tb.m, kParams)) || (st = dev_alloc(c, &tb.v, kParams)) ||
+        (st = dev_alloc(c, &d_curve, std::max(1, steps))))
+        return st;
+    LMOSEM_CK(c, cudaMemsetAsync(tb.m, 0, sizeof(float) * kParams, c->stream));
+    LMOSEM_CK(c, cudaMemsetAsync(tb.v, 0, sizeof(float) * kParams, c->stream));
+    LMOSEM_CK(c, cudaMemsetAsync(d_curve, 0, sizeof(double) * std::max(1, steps), c->stream));
+    LMOSEM_PROF_BEGIN(c);
+    k_target_stats<<<1, 256, 0, c->stream>>>(targ, n, blob);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    const float b1 = 0.9f, b2 = 0.999f;
+    double p1 = 1.0, p2 = 1.0;
+    for (int s = 0; s < steps; ++s) {
+        if ((st = weights_bf16(c, blob, w))) return st;
+        LMOSEM_PROF_BEGIN(c);
+        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, s, blob, tb.X, tb.t);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        tb.loss = d_curve + s;
+        if ((st = loss_grad(c, blob, w, tb, B))) return st;
+        p1 *= b1;
+        p2 *= b2;
+        const float lr_s = s < steps * 0.8 ? lr : lr * 0.1f;
+        LMOSEM_PROF_BEGIN(c);
+        k_adam<<<(unsigned)((kOffMu + 255) / 256), 256, 0, c->stream>>>(blob, tb.grad, tb.m, tb.v, kOffMu, lr_s,
+                                                                       b1, b2, 1e-8f, (float)(1.0 - p1),
+                                                                       (float)(1.0 - p2));
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    }
+    if (h_loss_curve && steps > 0)
+        LMOSEM_CK(c, cudaMemcpyAsync(h_loss_curve, d_curve, sizeof(double) * steps, cudaMemcpyDeviceToHost,
+                                     c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&tb.X); dev_free(&tb.H);
+    dev_free(&tb.HT); dev_free(&tb.dz); dev_free(&tb.dzT); dev_free(&tb.t); dev_free(&tb.y);
+    dev_free(&tb.dy); dev_free(&tb.gtmp); dev_free(&tb.grad); dev_free(&tb.m); dev_free(&tb.v);
+    dev_free(&d_curve);
+    return LMOSEM_OK;
+}
+
+lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float* feat, int64_t n,
+                                  float* out) {
+    lmosem_status st;
+    MlpBufs w;
+    __nv_bfloat16 *X = nullptr, *H = nullptr;
+    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
+        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)n * kInPad)) ||
+        (st = dev_alloc(c, &H, (size_t)4 * n * kH)))
+        return st;
+    if ((st = weights_bf16(c, blob, w))) return st;
+    LMOSEM_PROF_BEGIN(c);
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, X, out);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
+    if ((st = forward(c, blob, w, X, Hs, out, n))) return st;
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H);
+    return LMOSEM_OK;
+}
+
+FeatArgs feat_args(lmosem_ctx* c) {
+    FeatArgs F;
+    F.a_s = c->d_a_s;
+    F.u_s = c->d_u_s;
+    F.e_s = c->d_e_s;
+    F.sup = c->d_sup;
+    F.n_sup = c->n_sup;
+    F.nx = c->nx;
+    F.ny = c->ny;
+    F.npix = c->npix;
+    F.dpx = (float)c->dpx;
+    F.l_edge = c->d_l_edge;
+    F.angle0 = (float)c->angle0;
+    F.dtheta = (float)(2.0 * kPi / c->n_angles);
+    return F;
+}
+
+// features and log exact scatter of every (event, support pixel) of the
+// current (scatter-only, FP32) model, in the caller's event order
+lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ) {
+    const int64_t total = c->J * c->n_sup;
+    // the sort's rank maps the caller's event k to its model row
+    LMOSEM_PROF_BEGIN(c);
+    k_samples<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
+        feat_args(c), reinterpret_cast<const float*>(c->d_model), c->ld_model, c->d_rank, c->J, feat, targ);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    return LMOSEM_OK;
+}
+
+// model rows with the surrogate scatter term, in chunks of whole rows
+lmosem_status build_model_surrogate(lmosem_ctx* c) {
+    lmosem_status st;
+    const int64_t max_pairs = int64_t(1) << 20;
+    const int64_t rows_per = std::max<int64_t>(1, max_pairs / c->n_sup);
+    const int64_t M = rows_per * c->n_sup;
+    MlpBufs w;
+    __nv_bfloat16 *X = nullptr, *H = nullptr;
+    float* y = nullptr;
+    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
+        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)M * kInPad)) ||
+        (st = dev_alloc(c, &H, (size_t)2 * M * kH)) || (st = dev_alloc(c, &y, M)))
+        return st;
+    if ((st = weights_bf16(c, c->d_surrogate, w))) return st;
+    const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    const double se0 = fw2s * c->fwhm_frac * c->e0;
+    __nv_bfloat16* Hs[4] = {H, H + M * kH, H, H + M * kH};  // ping-pong
+    for (int64_t r0 = 0; r0 < c->J; r0 += rows_per) {
+        const int64_t nr = std::min(rows_per, c->J - r0);
+        const int64_t m = nr * c->n_sup;
+        LMOSEM_PROF_BEGIN(c);
+        k_surr_inputs<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(feat_args(c), r0, nr, X);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        if ((st = forward(c, c->d_surrogate, w, X, Hs, y, m))) return st;
+        LMOSEM_PROF_BEGIN(c);
+        k_surr_combine<<<(unsigned)((nr * c->ld_model + 255) / 256), 256, 0, c->stream>>>(
+            y, r0, nr, c->n_sup, c->ld_model, c->d_a_s, c->d_u_s, c->d_e_s, c->d_ppar, c->ld_w, (float)c->e0,
+            (float)(0.8493218002880191 / se0), (float)(-log2(se0 * sqrt(2.0 * kPi))), c->d_surrogate,
+            reinterpret_cast<float*>(c->d_model));
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    }
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H); dev_free(&y);
+    return LMOSEM_OK;
+}
+
+}  // namespace lmosem

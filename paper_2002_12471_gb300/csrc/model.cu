@@ -110,6 +110,7 @@ struct PathSumArgs {
     int64_t ld_out;
     int64_t row_base;            // out row = sorted row - row_base
     int n_store;                 // columns to store (padded row width)
+    int scatter_only;            // 1: leave the primary path out
 };
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float t = (uj - pp[q].x) * pp[q].y;
-                v[q] = ex2_approx(fmaf(-t, t, pp[q].z + le));
+                v[q] = A.scatter_only ? 0.0f : ex2_approx(fmaf(-t, t, pp[q].z + le));
             }
             acc[jj][0] = make_float2(v[0], v[1]);
             acc[jj][1] = make_float2(v[2], v[3]);
@@ -380,6 +381,7 @@ __global__ void k_quantize(const float* __restrict__ stage, int64_t ld_stage, in
 }  // namespace
 
 lmosem_status build_model_rows(lmosem_ctx* c) {
+    if (c->use_surrogate) return build_model_surrogate(c);
     lmosem_status st;
     const int n_ptiles = c->ld_w / kTN;
     const int group = (c->n_angles + c->n_subsets - 1) / c->n_subsets;
@@ -522,6 +524,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.lE0 = (float)(-log2(se0 * sqrt(2.0 * kPi)));
         P.ld_out = c->ld_model;
         P.n_store = (int)c->ld_model;
+        P.scatter_only = c->scatter_only ? 1 : 0;
         const int64_t grow0 = g_row0[gi], grows = g_rows[gi];
         if (scaled) {
             P.out = c->d_stage;

@@ -54,7 +54,15 @@ class Options(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
-                  "other"]
+                  "other", "surrogate"]
+SURROGATE_PARAMS = 199427
+MODEL_SURROGATE_FP32 = 3
+FORMATS["surrogate"] = MODEL_SURROGATE_FP32
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
 
 
 _vp = ctypes.c_void_p
@@ -86,6 +94,11 @@ SIGNATURES = {
     "lmosem_iterate_batch": (ctypes.c_int, [_vp, _i32, _dbl, _vp]),
     "lmosem_autotune_batch": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
     "lmosem_set_batch_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
+    "lmosem_surrogate_samples": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "lmosem_surrogate_train": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(TrainOpts), _vp, _vp]),
+    "lmosem_surrogate_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "lmosem_surrogate_infer": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
+    "lmosem_surrogate_load": (ctypes.c_int, [_vp, _vp]),
 }
 
 _lib = None
@@ -249,6 +262,60 @@ def lmosem_autotune_batch(ctx, acq_time, d_f):
 
 def lmosem_set_batch_tiles(ctx, chunk_rows, ctas_per_sm):
     _check(ctx, load().lmosem_set_batch_tiles(ctx, int(chunk_rows), int(ctas_per_sm)))
+
+
+def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_scatter):
+    n = int(d_angle.numel())
+    _check(ctx, load().lmosem_surrogate_samples(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev), n,
+                                                _ptr(d_features), _ptr(d_log_scatter)))
+
+
+def lmosem_surrogate_train(ctx, d_features, d_targets, d_weights, steps=2000, batch=4096, lr=1e-3,
+                           seed=1):
+    """Trains in place; returns the per-step minibatch loss curve."""
+    n = int(d_targets.numel())
+    curve = np.zeros(int(steps), dtype=np.float64)
+    o = TrainOpts(int(steps), int(batch), float(lr), int(seed))
+    _check(ctx, load().lmosem_surrogate_train(ctx, _ptr(d_features), _ptr(d_targets), n, ctypes.byref(o),
+                                              _ptr(d_weights), curve.ctypes.data))
+    return curve
+
+
+def lmosem_surrogate_grad(ctx, d_weights, d_features, d_targets, d_grad):
+    loss = ctypes.c_double()
+    n = int(d_targets.numel())
+    _check(ctx, load().lmosem_surrogate_grad(ctx, _ptr(d_weights), _ptr(d_features), _ptr(d_targets), n,
+                                             _ptr(d_grad), ctypes.byref(loss)))
+    return loss.value
+
+
+def lmosem_surrogate_infer(ctx, d_weights, d_features, d_out):
+    n = int(d_out.numel())
+    _check(ctx, load().lmosem_surrogate_infer(ctx, _ptr(d_weights), _ptr(d_features), n, _ptr(d_out)))
+
+
+def lmosem_surrogate_load(ctx, d_weights):
+    _check(ctx, load().lmosem_surrogate_load(ctx, _ptr(d_weights)))
+
+
+def pack_surrogate(params, mu=0.0, sigma=1.0):
+    """Flatten [[W, b], ...] (the oracle's layout) into the library's blob."""
+    parts = [np.asarray(a, dtype=np.float64).ravel() for layer in params for a in layer]
+    blob = np.concatenate(parts + [np.array([mu, sigma])]).astype(np.float32)
+    assert blob.size == SURROGATE_PARAMS, blob.size
+    return blob
+
+
+def unpack_surrogate(blob, layers=(6, 256, 256, 256, 256, 1)):
+    blob = np.asarray(blob, dtype=np.float64)
+    params, k = [], 0
+    for fi, fo in zip(layers[:-1], layers[1:]):
+        W = blob[k:k + fo * fi].reshape(fo, fi)
+        k += fo * fi
+        b = blob[k:k + fo]
+        k += fo
+        params.append([W, b])
+    return params, float(blob[k]), float(blob[k + 1])
 
 
 def lmosem_osem_subiter_noalloc(d_rows, n_support, d_f, d_sens_i, acq_time, stream=None):

@@ -191,3 +191,17 @@ def test_pos_cut_only_drops_negligible_terms():
     full = oracle.Problem(g, ph.mu, pos_cut=1e9).model(ev.angle, ev.u_mm, ev.e_kev)
     cut = oracle.Problem(g, ph.mu).model(ev.angle, ev.u_mm, ev.e_kev)
     np.testing.assert_allclose(cut, full, rtol=1e-14, atol=1e-15 * full.max())
+
+
+def test_model_parts_add_up():
+    """The primary-only and scatter-only restrictions of the path sum add up to
+    the full sum, and the scatter part vanishes without matter."""
+    ph, g, J, ns, ni = S.workload("tiny16")
+    g = dict(g, pixel_mm=ph.pixel_mm)
+    ev = S.simulate_events(ph, g, 60, seed=21)
+    P = oracle.Problem(g, ph.mu)
+    full = P.model(ev.angle, ev.u_mm, ev.e_kev)
+    prim = P.model(ev.angle, ev.u_mm, ev.e_kev, scatter=False)
+    scat = P.model(ev.angle, ev.u_mm, ev.e_kev, primary=False)
+    np.testing.assert_allclose(prim + scat, full, rtol=1e-13, atol=1e-300)
+    assert np.all(scat > 0) and np.all(prim >= 0)

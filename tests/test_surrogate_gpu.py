@@ -1,0 +1,218 @@
+"""Scatter surrogate on the GPU: its tensor-core forward and backward against
+the FP64 MLP oracle, its exact training targets against the oracle's scatter
+path sum, training convergence, and what the trained network gains over
+reconstructing without scatter compensation, measured against the exact
+model."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2002_12471_gb300 import synthetic as S
+from tests._helpers import gpu_reconstruct, oracle_problem, row_close
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(x):
+    """Round to bfloat16 (nearest even), returned as float64."""
+    a = np.asarray(x, dtype=np.float32).copy()
+    u = a.view(np.uint32)
+    u += 0x7FFF + ((u >> 16) & 1)
+    u &= 0xFFFF0000
+    return a.astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    return L
+
+
+def _ctx(L, ph, g):
+    import torch
+    return L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream())
+
+
+def _perturbed_params(seed):
+    rng = np.random.default_rng(seed)
+    params = mlp.init_params(seed)
+    for W, b in params:
+        b += rng.normal(0.0, 0.2, b.shape)
+    return params
+
+
+def test_gradients_match_oracle(L):
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, *_ = S.workload("tiny16")
+    params = _perturbed_params(7)
+    rng = np.random.default_rng(8)
+    n = 512
+    X = rng.normal(0.0, 1.0, (n, 6))
+    t = rng.normal(0.0, 1.0, n)
+    blob = L.pack_surrogate(params)
+    ctx = _ctx(L, ph, g)
+    try:
+        grad = torch.zeros(L.SURROGATE_PARAMS, dtype=torch.float32, device=dev)
+        loss = L.lmosem_surrogate_grad(ctx, torch.from_numpy(blob).to(dev),
+                                       torch.from_numpy(X.astype(np.float32)).to(dev),
+                                       torch.from_numpy(t.astype(np.float32)).to(dev), grad)
+        g_gpu, _, _ = L.unpack_surrogate(grad.cpu().numpy())
+        out = torch.zeros(n, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_infer(ctx, torch.from_numpy(blob).to(dev),
+                                 torch.from_numpy(X.astype(np.float32)).to(dev), out)
+        y_gpu = out.cpu().numpy().astype(np.float64)
+    finally:
+        L.lmosem_destroy(ctx)
+    # the oracle sees the same BF16-rounded weights and inputs as the products
+    pq = [[bf16(W), np.asarray(b, dtype=np.float32).astype(np.float64)] for W, b in params]
+    pq[-1][0] = np.asarray(params[-1][0], dtype=np.float32).astype(np.float64)   # output layer is FP32
+    Xq = bf16(X.astype(np.float32))
+    tq = t.astype(np.float32).astype(np.float64)
+    # (1) the plain FP64 oracle: the GPU also rounds every hidden activation and
+    # every back-propagated delta to BF16 (2^-9 relative each) and ReLU masks of
+    # pre-activations within that rounding of zero can flip, so the bound is 3e-2
+    loss_ref, g_ref = mlp.mse_loss_and_grad(pq, Xq, tq)
+    y_ref, _ = mlp.forward(pq, Xq)
+    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    assert oracle.rel_l2(y_gpu, y_ref) <= 2e-2
+    for l in range(5):
+        for i in range(2):
+            err = oracle.rel_l2(np.ravel(g_gpu[l][i]), np.ravel(g_ref[l][i]))
+            assert err <= 3e-2, (l, i, err)
+    # (2) FP64 with the GPU's BF16 rounding points: only the FP32 accumulation
+    # order remains
+    hs, zs, h = [], [], Xq
+    for k, (W, b) in enumerate(pq):
+        z = h @ W.T + b
+        hs.append(h)
+        zs.append(z)
+        h = bf16(np.maximum(z, 0.0)) if k < 4 else z
+    r = h[:, 0] - tq
+    d = (2.0 * r / n)[:, None]
+    gm = [None] * 5
+    for k in range(4, -1, -1):
+        if k < 4:
+            d = bf16(d * (zs[k] > 0.0))
+        elif k == 4:
+            gm[k] = [d.T @ hs[k], d.sum(axis=0)]
+            d = bf16((d @ pq[k][0]) * (zs[k - 1] > 0.0))
+            continue
+        gm[k] = [d.T @ hs[k], d.sum(axis=0)]
+        if k > 0:
+            d = d @ pq[k][0]
+    for l in range(5):
+        for i in range(2):
+            err = oracle.rel_l2(np.ravel(g_gpu[l][i]), np.ravel(gm[l][i]))
+            assert err <= 2e-3, ("bf16-mirrored", l, i, err)
+
+
+def test_training_targets_match_oracle_scatter(L):
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, J, ns, ni = S.workload("tiny16")
+    ev = S.simulate_events(ph, g, 40, seed=31)
+    P = oracle_problem(ph, g)
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        feat = torch.zeros((len(ev) * nsup, 6), dtype=torch.float32, device=dev)
+        targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                                   torch.from_numpy(ev.e_kev).to(dev), feat, targ)
+        f = feat.cpu().numpy().astype(np.float64).reshape(len(ev), nsup, 6)
+        p_gpu = np.exp(targ.cpu().numpy().astype(np.float64)).reshape(len(ev), nsup)
+    finally:
+        L.lmosem_destroy(ctx)
+    scat = P.model(ev.angle, ev.u_mm, ev.e_kev, primary=False)
+    assert row_close(p_gpu, scat) <= 1.0
+    # inputs: pixel centre, angle, position, energy, attenuation to the edge
+    xs, ys = P.pixel_centres(P.support)
+    th = g["angle0_rad"] + 2 * np.pi * ev.angle / g["n_angles"]
+    raw = np.stack(np.broadcast_arrays(xs[None, :], ys[None, :], th[:, None], ev.u_mm[:, None].astype(np.float64),
+                                       ev.e_kev[:, None].astype(np.float64),
+                                       P.l_edge[ev.angle][:, P.support]), axis=-1)
+    np.testing.assert_allclose(f, mlp.scale_features(raw), rtol=1e-5, atol=1e-5)
+
+
+@pytest.fixture(scope="module")
+def trained(L):
+    """Surrogate trained on exact scatter sums of 400 events of the 32 x 32
+    brain workload, plus 60 held-out events."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, J, ns, ni = S.workload("dat32")
+    ev = S.simulate_events(ph, g, 460, seed=51)
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        feat = torch.zeros((len(ev) * nsup, 6), dtype=torch.float32, device=dev)
+        targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                                   torch.from_numpy(ev.e_kev).to(dev), feat, targ)
+        ntr = 400 * nsup
+        blob = torch.from_numpy(L.pack_surrogate(mlp.init_params(3))).to(dev)
+        curve = L.lmosem_surrogate_train(ctx, feat[:ntr].contiguous(), targ[:ntr].contiguous(), blob,
+                                         steps=3000, batch=2048, lr=1e-3, seed=5)
+        out = torch.zeros(len(ev) * nsup - ntr, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_infer(ctx, blob, feat[ntr:].contiguous(), out)
+        _, mu, sigma = L.unpack_surrogate(blob.cpu().numpy())
+        pred = mu + sigma * out.cpu().numpy().astype(np.float64)
+        held = targ[ntr:].cpu().numpy().astype(np.float64)
+    finally:
+        L.lmosem_destroy(ctx)
+    return dict(ph=ph, g=g, ns=ns, curve=curve, pred=pred, held=held, blob=blob, sigma=sigma)
+
+
+def test_training_converges_and_generalises(trained):
+    c = trained["curve"]
+    assert np.all(np.isfinite(c))
+    assert np.mean(c[-200:]) < 0.1 * np.mean(c[:20])
+    err = trained["pred"] - trained["held"]
+    # held-out events: log scatter within a few tens of percent (the trained
+    # network's own minibatch loss, 0.0085 sigma^2, is an RMS of ~0.09 sigma)
+    assert np.sqrt(np.mean(err ** 2)) < 0.3 * trained["sigma"]
+    assert np.median(np.abs(err)) < 0.35
+
+
+def test_surrogate_model_gains_over_no_scatter_compensation(L, trained):
+    """Reconstructions with the surrogate's scatter term stay close to those
+    of the exact path sum; leaving scatter out altogether does not."""
+    import torch
+    ph, g, ns = trained["ph"], trained["g"], trained["ns"]
+    ev = S.simulate_events(ph, g, 20000, seed=52)
+    exact = gpu_reconstruct(ph, g, ev, ns, 4)
+
+    def with_blob(blob):
+        import paper_2002_12471_gb300.lmosem as Lm
+        dev = torch.device("cuda:0")
+        ctx = Lm.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream())
+        try:
+            Lm.lmosem_surrogate_load(ctx, blob)
+            nsup = Lm.lmosem_n_support(ctx)
+            Lm.lmosem_sensitivity(ctx, ns)
+            Lm.lmosem_build_model(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                                  torch.from_numpy(ev.e_kev).to(dev), ns, "surrogate")
+            f = torch.zeros(nsup, dtype=torch.float32, device=dev)
+            Lm.lmosem_init_image(ctx, 1.0, f)
+            Lm.lmosem_iterate(ctx, 4, 1.0, f)
+            return f.cpu().numpy().astype(np.float64)
+        finally:
+            Lm.lmosem_destroy(ctx)
+
+    f_sur = with_blob(trained["blob"])
+    none = trained["blob"].clone()
+    none[-2] = -1.0e4        # mu: exp(mu + sigma y) = 0, i.e. no scatter paths
+    none[-1] = 0.0
+    f_none = with_blob(none)
+    img = lambda f: np.bincount(exact["support"], weights=f, minlength=ph.mu.size)
+    for name, roi in ph.rois.items():
+        w = roi.reshape(-1)
+        ref = np.dot(w, img(exact["f"]))
+        e_sur = abs(np.dot(w, img(f_sur)) - ref) / ref
+        e_none = abs(np.dot(w, img(f_none)) - ref) / ref
+        assert e_sur < 0.5 * e_none, (name, e_sur, e_none)
+    assert oracle.rel_l2(f_sur, exact["f"]) < 0.5 * oracle.rel_l2(f_none, exact["f"])
