@@ -104,6 +104,10 @@ typedef struct {
     int32_t pass_variant;
     int32_t ring_rows;
     int32_t ring_stages;
+    /* Scatter-surrogate inference: 0 = automatic (2), 1 = BF16 mma.sync
+     * product chain (the training kernels), 2 = fused tcgen05 kernel (one
+     * persistent CTA per SM, activations kept on chip, TMEM accumulators). */
+    int32_t surrogate_kernel;
 } lmosem_options;
 
 /* Kernel classes reported by lmosem_profile_read. */

@@ -274,6 +274,11 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
         c->pass_variant = opts->pass_variant;
         c->ring_rows = opts->ring_rows;
         c->ring_stages = opts->ring_stages;
+        if (opts->surrogate_kernel < 0 || opts->surrogate_kernel > 2) {
+            delete c;
+            return LMOSEM_EINVAL;
+        }
+        c->surrogate_kernel = opts->surrogate_kernel;
     }
 
     std::vector<float> mu(c->npix);

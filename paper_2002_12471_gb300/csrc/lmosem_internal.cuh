@@ -4,6 +4,7 @@
 // scatter compensation (Rahman, Laforest, Jha, ISBI 2020, Sections 2.1-2.2).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -102,6 +103,7 @@ struct lmosem_ctx {
     float* d_surrogate = nullptr;             // LMOSEM_SURROGATE_PARAMS FP32 parameters
     bool scatter_only = false;                // model build leaves the primary path out
     bool use_surrogate = false;               // model build takes the scatter part from the MLP
+    int surrogate_kernel = 0;                 // inference: 0 auto (tcgen05), 1 mma.sync, 2 tcgen05
     // batching form: per-realisation work words, partial slots, tiles, graph
     bool batch_model = false;
     int64_t* d_bsub_row0 = nullptr;           // n_real * (n_subsets + 1)
@@ -215,6 +217,9 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
                                   float* out);
 lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ);
 lmosem_status build_model_surrogate(lmosem_ctx* c);
+// mlp_tc.cu: fused tcgen05 inference of M rows of BF16 inputs (M x 16)
+lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
+                         const __nv_bfloat16* w234, const __nv_bfloat16* X, float* y, int64_t M);
 
 // ---- device helpers shared by the CUDA translation units
 

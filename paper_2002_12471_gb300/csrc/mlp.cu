@@ -445,6 +445,14 @@ lmosem_status forward(lmosem_ctx* c, const float* blob, const MlpBufs& w, const 
     return LMOSEM_OK;
 }
 
+// inference: the tcgen05 kernel (mlp_tc.cu) unless the options select the
+// mma.sync product chain (surrogate_kernel == 1), which the training uses
+lmosem_status forward_infer(lmosem_ctx* c, const float* blob, const MlpBufs& w, const __nv_bfloat16* X,
+                            __nv_bfloat16* const H[4], float* y, int64_t M) {
+    if (c->surrogate_kernel != 1) return forward_tc(c, blob, w.w1, w.w234, X, y, M);
+    return forward(c, blob, w, X, H, y, M);
+}
+
 struct TrainBufs {
     __nv_bfloat16 *X = nullptr, *XT = nullptr, *H = nullptr, *HT = nullptr, *dz = nullptr, *dzT = nullptr;
     float *t = nullptr, *y = nullptr, *dy = nullptr, *gtmp = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
@@ -585,14 +593,14 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     __nv_bfloat16 *X = nullptr, *H = nullptr;
     if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
         (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)n * kInPad)) ||
-        (st = dev_alloc(c, &H, (size_t)4 * n * kH)))
+        (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)4 * n * kH))))
         return st;
     if ((st = weights_bf16(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
     k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, X, out);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
-    if ((st = forward(c, blob, w, X, Hs, out, n))) return st;
+    if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H);
     return LMOSEM_OK;
@@ -638,7 +646,7 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
     float* y = nullptr;
     if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
         (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)M * kInPad)) ||
-        (st = dev_alloc(c, &H, (size_t)2 * M * kH)) || (st = dev_alloc(c, &y, M)))
+        (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)2 * M * kH))) || (st = dev_alloc(c, &y, M)))
         return st;
     if ((st = weights_bf16(c, c->d_surrogate, w))) return st;
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
@@ -650,7 +658,7 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         LMOSEM_PROF_BEGIN(c);
         k_surr_inputs<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(feat_args(c), r0, nr, X);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
-        if ((st = forward(c, c->d_surrogate, w, X, Hs, y, m))) return st;
+        if ((st = forward_infer(c, c->d_surrogate, w, X, Hs, y, m))) return st;
         LMOSEM_PROF_BEGIN(c);
         k_surr_combine<<<(unsigned)((nr * c->ld_model + 255) / 256), 256, 0, c->stream>>>(
             y, r0, nr, c->n_sup, c->ld_model, c->d_a_s, c->d_u_s, c->d_e_s, c->d_ppar, c->ld_w, (float)c->e0,

@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
     _fields_ = [("k_sigma", ctypes.c_float), ("table_budget_bytes", ctypes.c_int64),
                 ("profile", ctypes.c_int32), ("wait_budget_cycles", ctypes.c_int64),
                 ("pass_variant", ctypes.c_int32), ("ring_rows", ctypes.c_int32),
-                ("ring_stages", ctypes.c_int32)]
+                ("ring_stages", ctypes.c_int32), ("surrogate_kernel", ctypes.c_int32)]
 
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
@@ -147,7 +147,7 @@ def _check(ctx, st):
 
 def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                   table_budget_bytes=0, stream=None, profile=False, wait_budget_cycles=0,
-                  pass_variant=0, ring_rows=0, ring_stages=0):
+                  pass_variant=0, ring_rows=0, ring_stages=0, surrogate_kernel=0):
     """Create a context.  ``mu_per_mm`` is an (ny, nx) host array at the
     photopeak, ``geom`` holds the scanner and energy fields of
     ``include/lmosem.h``; ``stream`` is a torch.cuda.Stream or a raw handle."""
@@ -165,7 +165,8 @@ def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
     e = Energy(float(geom["e0_kev"]), float(geom["fwhm_frac_e0"]), float(geom["e_lo_kev"]),
                float(geom["e_hi_kev"]))
     o = Options(float(k_sigma), int(table_budget_bytes), int(profile),
-                int(wait_budget_cycles), int(pass_variant), int(ring_rows), int(ring_stages))
+                int(wait_budget_cycles), int(pass_variant), int(ring_rows), int(ring_stages),
+                int(surrogate_kernel))
     h = _vp()
     s = getattr(stream, "cuda_stream", stream)
     st = L.lmosem_create(ctypes.byref(obj), ctypes.byref(g), ctypes.byref(e), ctypes.byref(o),

@@ -110,6 +110,60 @@ def test_gradients_match_oracle(L):
             assert err <= 2e-3, ("bf16-mirrored", l, i, err)
 
 
+def _mirrored_forward(params, X, round_last):
+    """FP64 forward with the GPU's BF16 rounding points: inputs, hidden
+    weights and the ReLU outputs of the first three hidden layers (and of the
+    fourth where ``round_last``); the 256 -> 1 output layer stays FP32."""
+    pq = [[bf16(W), np.asarray(b, dtype=np.float32).astype(np.float64)] for W, b in params]
+    pq[-1][0] = np.asarray(params[-1][0], dtype=np.float32).astype(np.float64)
+    h = bf16(X.astype(np.float32))
+    for k, (W, b) in enumerate(pq):
+        z = h @ W.T + b
+        if k < 4:
+            h = np.maximum(z, 0.0)
+            if k < 3 or round_last:
+                h = bf16(h)
+        else:
+            h = z
+    return h[:, 0]
+
+
+@pytest.mark.parametrize("n", [1, 129, 10007, 3 * 152 * 128 + 5])
+def test_tcgen05_inference_matches_mma_and_oracle(L, n):
+    """The fused tcgen05 inference kernel (persistent over 128-row tiles, a
+    ragged last tile) against the mma.sync product chain and against the FP64
+    forward with the same BF16 rounding points."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, *_ = S.workload("tiny16")
+    params = _perturbed_params(11)
+    X = np.random.default_rng(12).normal(0.0, 1.0, (n, 6))
+    blob = torch.from_numpy(L.pack_surrogate(params)).to(dev)
+    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+    ys = {}
+    for kern in (0, 1, 2):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream(), surrogate_kernel=kern)
+        try:
+            out = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+            L.lmosem_surrogate_infer(ctx, blob, Xd, out)
+            ys[kern] = out.cpu().numpy().astype(np.float64)
+        finally:
+            L.lmosem_destroy(ctx)
+    assert np.all(np.isfinite(ys[2]))
+    np.testing.assert_array_equal(ys[0], ys[2])          # automatic choice is tcgen05
+    ref_tc = _mirrored_forward(params, X, round_last=False)
+    ref_mma = _mirrored_forward(params, X, round_last=True)
+    scale = max(np.sqrt(np.mean(ref_tc ** 2)), 0.1)
+    err = lambda a, b: np.sqrt(np.mean((a - b) ** 2)) / scale
+    # only the FP32 accumulation order (and the BF16 roundings it tips) remain
+    assert err(ys[2], ref_tc) <= 1e-3
+    assert err(ys[1], ref_mma) <= 1e-3
+    # the two kernels differ by the BF16 rounding of the last hidden layer,
+    # as the two references predict (the sum over 256 terms cancels, so that
+    # rounding can be a percent of a small output)
+    assert err(ys[2] - ys[1], ref_tc - ref_mma) <= 2e-3
+
+
 def test_training_targets_match_oracle_scatter(L):
     import torch
     dev = torch.device("cuda:0")
@@ -176,6 +230,32 @@ def test_training_converges_and_generalises(trained):
     # network's own minibatch loss, 0.0085 sigma^2, is an RMS of ~0.09 sigma)
     assert np.sqrt(np.mean(err ** 2)) < 0.3 * trained["sigma"]
     assert np.median(np.abs(err)) < 0.35
+
+
+def test_surrogate_model_rows_agree_across_kernels(L, trained):
+    """Model rows built with the surrogate scatter term through the tcgen05
+    kernel and through the mma.sync chain agree to the BF16 rounding of the
+    last hidden layer."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, ns = trained["ph"], trained["g"], trained["ns"]
+    ev = S.simulate_events(ph, g, 3000, seed=53)
+    rows = {}
+    for kern in (1, 2):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream(), surrogate_kernel=kern)
+        try:
+            L.lmosem_surrogate_load(ctx, trained["blob"])
+            nsup = L.lmosem_n_support(ctx)
+            L.lmosem_build_model(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                                 torch.from_numpy(ev.e_kev).to(dev), ns, "surrogate")
+            ids = torch.arange(0, len(ev), 7, dtype=torch.int64, device=dev)
+            out = torch.zeros((ids.numel(), nsup), dtype=torch.float32, device=dev)
+            L.lmosem_model_rows(ctx, ids, out)
+            rows[kern] = out.cpu().numpy().astype(np.float64)
+        finally:
+            L.lmosem_destroy(ctx)
+    assert np.all(np.isfinite(rows[2]))
+    assert oracle.rel_l2(rows[2], rows[1]) <= 2e-3
 
 
 def test_surrogate_model_gains_over_no_scatter_compensation(L, trained):
