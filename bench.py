@@ -43,6 +43,11 @@ WORKLOADS = {
     "dat128": ("2-D DaT-like brain, 128x128 pixels at 2 mm, 120 angles x 128 bins x 2 mm, R = 150 mm, "
                "1,000,000 list-mode events (100-175 keV, 10% FWHM at 159 keV), 8 subsets x 10 "
                "iterations, model cached in the chosen format, FP32 accumulation"),
+    "surrogate128": ("scatter surrogate on the 128x128 DaT-like family (2 mm, 120 angles x 128 bins x 2 mm, "
+                     "R = 150 mm): MLP 6 -> 4 x 256 -> 1 with BF16 weights and FP32 accumulation trained "
+                     "on exact scatter path sums of 32 jittered phantoms (~1M event-pixel pairs each); "
+                     "one step = sensitivity, surrogate model build, 8 subsets x 10 iterations on "
+                     "2,000,000 events of a held-out phantom"),
     "batch64": ("64 independent noise realisations of the 64x64 DaT phantom (120 angles, R = 150 mm), "
                 "event counts Poisson with means uniform in [50k, 400k], 8 subsets x 10 iterations, "
                 "all realisations in one persistent launch, FP32 model"),
@@ -578,6 +583,253 @@ def run_batch_bench(args):
     }
 
 
+# ------------------------------------------------------------------ surrogate form
+
+SURR_TRAIN_SEEDS = tuple(range(1000, 1032))
+SURR_TRAIN_EVENTS = 170            # x ~5,900 support pixels = ~1M (event, pixel) pairs per phantom
+SURR_EVAL_SEED = 2000
+SURR_EVAL_EVENTS = 2_000_000
+SURR_EVAL_CHUNKS = 16
+MLP_FLOPS_PER_PAIR = 2 * (6 * 256 + 3 * 256 * 256 + 256)   # the network's multiply-adds x 2
+
+
+def surrogate_phantom(seed):
+    from paper_2002_12471_gb300 import synthetic as S
+    return S.brain_phantom(128, 2.0, jitter=np.random.default_rng(seed))
+
+
+def _surrogate_events(job):
+    """Worker: events of one jittered 128 x 128 phantom (numpy only, no CUDA)."""
+    phantom_seed, n, event_seed = job
+    from paper_2002_12471_gb300 import synthetic as S
+    g = S.workload("dat128")[1]
+    ev = S.simulate_events(surrogate_phantom(phantom_seed), g, int(n), seed=event_seed)
+    return ev.angle, ev.u_mm, ev.e_kev
+
+
+def surrogate_jobs(eval_events):
+    per = -(-eval_events // SURR_EVAL_CHUNKS)
+    sizes = [min(per, eval_events - k * per) for k in range(SURR_EVAL_CHUNKS)]
+    return ([(s, SURR_TRAIN_EVENTS, s) for s in SURR_TRAIN_SEEDS]
+            + [(SURR_EVAL_SEED, n, SURR_EVAL_SEED * 100 + k) for k, n in enumerate(sizes) if n > 0])
+
+
+def run_surrogate_bench(args):
+    """Form (4): the scatter term of the model from the MLP surrogate.  The
+    network is trained (untimed) on exact scatter path sums of 32 jittered
+    128 x 128 phantoms; one timed step is the whole hot path on 2M events of
+    a held-out phantom with the surrogate scatter term: sensitivity, model
+    build (fused tcgen05 inference), 8 subsets x 10 OSEM iterations and the
+    log-likelihood.  The exact model is built and reconstructed beside it, and
+    the surrogate's error is measured against it on model rows, on held-out
+    log scatter values and on the reconstructed image."""
+    import multiprocessing as mp
+
+    from paper_2002_12471_gb300 import synthetic as S
+    n_eval = args.events or SURR_EVAL_EVENTS
+    jobs = surrogate_jobs(n_eval)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any CUDA call
+        parts = pool.map(_surrogate_events, jobs)
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    g = S.workload("dat128")[1]
+    ns, ni = 8, 10
+    T = 1.0
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # ---- training set: exact log scatter of every (event, support pixel)
+    t_samples = time.perf_counter()
+    feats, targs = [], []
+    for (seed, _, _), (a, u, e) in zip(jobs[:len(SURR_TRAIN_SEEDS)], parts):
+        ph = surrogate_phantom(seed)
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            feat = torch.empty((len(a) * nsup, 6), dtype=torch.float32, device=dev)
+            targ = torch.empty(len(a) * nsup, dtype=torch.float32, device=dev)
+            L.lmosem_surrogate_samples(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(u).to(dev),
+                                       torch.from_numpy(e).to(dev), feat, targ)
+            feats.append(feat)
+            targs.append(targ)
+        finally:
+            L.lmosem_destroy(ctx)
+    feat = torch.cat(feats)
+    targ = torch.cat(targs)
+    n_train_pairs = int(targ.numel())
+    del feats, targs
+    torch.cuda.synchronize()
+    t_samples = time.perf_counter() - t_samples
+
+    ph = surrogate_phantom(SURR_EVAL_SEED)
+    ev_parts = parts[len(SURR_TRAIN_SEEDS):]
+    a_h = torch.from_numpy(np.concatenate([p[0] for p in ev_parts])).pin_memory()
+    u_h = torch.from_numpy(np.concatenate([p[1] for p in ev_parts])).pin_memory()
+    e_h = torch.from_numpy(np.concatenate([p[2] for p in ev_parts])).pin_memory()
+    J = len(a_h)
+    a_d, u_d, e_d = a_h.to(dev), u_h.to(dev), e_h.to(dev)
+
+    train_steps, train_batch = 8000, 8192
+    blob = torch.from_numpy(L.surrogate_init(seed=3)).to(dev)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+    try:
+        t_train = time.perf_counter()
+        curve = L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=train_steps, batch=train_batch,
+                                         lr=1e-3, seed=5)
+        t_train = time.perf_counter() - t_train
+        # held out: exact log scatter of 200 events of the evaluation phantom
+        nsup = L.lmosem_n_support(ctx)
+        hold = 200
+        hf = torch.empty((hold * nsup, 6), dtype=torch.float32, device=dev)
+        ht = torch.empty(hold * nsup, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_samples(ctx, a_d[:hold].contiguous(), u_d[:hold].contiguous(),
+                                   e_d[:hold].contiguous(), hf, ht)
+        hy = torch.empty(hold * nsup, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_infer(ctx, blob, hf, hy)
+        _, mu_t, sigma_t = L.unpack_surrogate(blob.cpu().numpy())
+        err = (mu_t + sigma_t * hy.double() - ht.double()).cpu().numpy()
+    finally:
+        L.lmosem_destroy(ctx)
+    del feat, targ
+    torch.cuda.empty_cache()
+
+    support = None
+    rows_ids = torch.arange(0, J, max(1, J // 2000), dtype=torch.int64, device=dev)
+
+    def step(surrogate, a, u, e, profile=0, rows=None, host_out=None):
+        nonlocal support
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            if support is None:
+                support = L.lmosem_support(ctx)
+            if surrogate:
+                L.lmosem_surrogate_load(ctx, blob)
+            L.lmosem_sensitivity(ctx, ns)
+            L.lmosem_build_model(ctx, a, u, e, ns, "surrogate" if surrogate else "fp32")
+            f = torch.empty(nsup, dtype=torch.float32, device=dev)
+            ll = torch.empty(1, dtype=torch.float64, device=dev)
+            L.lmosem_init_image(ctx, T, f)
+            L.lmosem_iterate(ctx, ni, T, f)
+            L.lmosem_loglik(ctx, T, f, ll)
+            if host_out is not None:
+                host_out[0].copy_(f, non_blocking=True)
+                host_out[1].copy_(ll, non_blocking=True)
+            if rows is not None:
+                rows.append(torch.empty((rows_ids.numel(), nsup), dtype=torch.float32, device=dev))
+                L.lmosem_model_rows(ctx, rows_ids, rows[-1])
+            prof = L.lmosem_profile_read(ctx) if profile else None
+            return f, ll, prof, L.lmosem_launch_count(ctx)
+        finally:
+            L.lmosem_destroy(ctx)
+
+    def timed(fn):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    # ---- exact model beside it (same events): image, sampled rows, build time
+    rows_exact, rows_sur = [], []
+    ex_ms, (f_exact, _, prof_ex, _) = timed(lambda: step(False, a_d, u_d, e_d, profile=2, rows=rows_exact))
+    f_exact = f_exact.double().cpu().numpy()
+
+    for _ in range(args.warmup):
+        step(True, a_d, u_d, e_d)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(None)
+    clocks.start()
+    times, profs, launches = [], [], 0
+    for _ in range(args.steps):
+        ms, (f_sur, ll, prof, nl) = timed(lambda: step(True, a_d, u_d, e_d, profile=2))
+        times.append(ms)
+        profs.append(prof)
+        launches += nl
+    clk = clocks.stop()
+    _, (f_sur, ll, _, _) = timed(lambda: step(True, a_d, u_d, e_d, rows=rows_sur))
+    f_sur_np = f_sur.double().cpu().numpy()
+
+    # ---- end to end through host buffers
+    nsup = len(support)
+    f_h = torch.empty(nsup, dtype=torch.float32).pin_memory()
+    ll_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e = []
+    for _ in range(max(1, min(args.steps, 2))):
+        ms, _ = timed(lambda: step(True, a_h.to(dev, non_blocking=True), u_h.to(dev, non_blocking=True),
+                                   e_h.to(dev, non_blocking=True), host_out=(f_h, ll_h)))
+        e2e.append(ms)
+
+    # ---- errors of the surrogate form against the exact model
+    re = rows_exact[0].double()
+    rs = rows_sur[0].double()
+    row_err = float(torch.linalg.vector_norm(rs - re) / torch.linalg.vector_norm(re))
+    img = lambda f: np.bincount(support, weights=f, minlength=ph.mu.size)
+    roi = {}
+    for name, w in ph.rois.items():
+        w = w.reshape(-1)
+        ref = float(np.dot(w, img(f_exact)) / w.sum())
+        roi[name] = (float(np.dot(w, img(f_sur_np)) / w.sum()) - ref) / ref
+    img_err = float(np.linalg.norm(f_sur_np - f_exact) / np.linalg.norm(f_exact))
+
+    agg = {}
+    for p in profs:
+        for k, (ms, n) in p.items():
+            a = agg.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    mlp_ms, mlp_n = agg["mlp"]
+    pairs = J * nsup
+    pk, pk_kind = peaks()
+    achieved = pairs * MLP_FLOPS_PER_PAIR / (mlp_ms / args.steps * 1e-3) / 1e12
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    ms_step = statistics.mean(times)
+    ex_build_ms = prof_ex["pathsum"][0] + prof_ex["wtable"][0]
+    sur_build_ms = (agg["mlp"][0] + agg["surrogate"][0]) / args.steps
+    terms, _ = strip_terms(ph, g, type("E", (), {"u_mm": u_h.numpy(), "angle": a_h.numpy()})())
+    kernel_ms = sum(v[0] for v in agg.values())
+    return {
+        "metric": METRIC, "value": pairs / (ms_step * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+        "data": "synthetic (seeded jittered ellipse phantoms, photon Monte-Carlo list-mode events)",
+        "config": {"workload": WORKLOAD_DESC, "events": J, "support_pixels": nsup,
+                   "train_pairs": n_train_pairs, "train_phantoms": len(SURR_TRAIN_SEEDS),
+                   "train_steps": train_steps, "train_batch": train_batch,
+                   "l2": "model (%.1f GB) larger than L2; 256 MB flush before every step" % (J * nsup * 4 / 1e9)},
+        "model_build_evals_per_s": {"surrogate": pairs / (sur_build_ms * 1e-3),
+                                    "exact": pairs / (ex_build_ms * 1e-3),
+                                    "exact_path_terms": terms},
+        "exact_step_ms": ex_ms,
+        "error_vs_exact": {"model_rows_rel_l2": row_err, "image_rel_l2": img_err,
+                           "roi_mean_rel": roi, "rows_sampled": int(rows_ids.numel()),
+                           "held_out_log_scatter_rms": float(np.sqrt(np.mean(err ** 2))),
+                           "held_out_log_scatter_median_abs": float(np.median(np.abs(err))),
+                           "held_out_pairs": int(err.size)},
+        "training": {"samples_s": t_samples, "train_s": t_train, "loss_first": float(np.mean(curve[:20])),
+                     "loss_last": float(np.mean(curve[-200:]))},
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in agg.items() if v[1]},
+        "kernel_share": {k: v[0] / kernel_ms for k, v in agg.items() if v[1]},
+        "loglik_final": float(ll.item()),
+        "e2e": {"value": pairs / (statistics.mean(e2e) * 1e-3), "unit": UNIT,
+                "ms_per_step": statistics.mean(e2e), "h2d_bytes_per_step": int(J * 12),
+                "d2h_bytes_per_step": int(nsup * 4 + 8)},
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_tc", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": "%s bf16 (sustained)" % pk_kind,
+                     "flops_basis": "%d flops per (event, pixel) pair: 2 x (6x256 + 3x256x256 + 256)"
+                                    % MLP_FLOPS_PER_PAIR},
+        "clocks": clk, "gpu_launches": launches,
+    }
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -597,6 +849,8 @@ def main():
         out = run_reference(args, rank, world)
     elif WORKLOAD == "batch64":
         out = run_batch_bench(args)
+    elif WORKLOAD == "surrogate128":
+        out = run_surrogate_bench(args)
     else:
         out = run_ours(args, rank, world, local_rank)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -121,8 +121,9 @@ typedef enum {
     LMOSEM_K_PASS = 6,     /* streaming OSEM pass (forward, back-projection, LL)  */
     LMOSEM_K_UPDATE = 7,   /* per-subset reduction and multiplicative update      */
     LMOSEM_K_OTHER = 8,
-    LMOSEM_K_SURROGATE = 9, /* scatter surrogate: MLP products and their helpers */
-    LMOSEM_K_COUNT = 10
+    LMOSEM_K_SURROGATE = 9, /* scatter surrogate: features, loss, Adam, combine */
+    LMOSEM_K_MLP = 10,      /* scatter surrogate: the MLP products (tensor cores) */
+    LMOSEM_K_COUNT = 11
 } lmosem_kernel_class;
 
 typedef enum {

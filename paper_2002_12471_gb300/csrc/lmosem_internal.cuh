@@ -202,7 +202,11 @@ lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, d
 lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out);
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f);
 lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float* out);
-lmosem_status setup_pass(lmosem_ctx* c);                        // osem.cu
+lmosem_status setup_pass(lmosem_ctx* c);
+// the device status word (bounded waits that ran out), allocated once and zeroed
+lmosem_status ensure_status(lmosem_ctx* c);
+// ETIMEOUT (and the word cleared) if a bounded wait ran out since the last check
+lmosem_status take_status(lmosem_ctx* c);                        // osem.cu
 lmosem_status setup_batch(lmosem_ctx* c);                       // batch.cu
 lmosem_status run_init_batch(lmosem_ctx* c, double T, float* d_f);
 lmosem_status run_batch(lmosem_ctx* c, int n_iters, double T, float* d_f);

@@ -409,7 +409,7 @@ lmosem_status gemm(lmosem_ctx* c, int epi, const __nv_bfloat16* A, int64_t lda, 
         k_gemm_tn<EPI_RELU_BF16><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
     else
         k_gemm_tn<EPI_MASK_BF16><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
-    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_MLP);
     return LMOSEM_OK;
 }
 
@@ -441,7 +441,7 @@ lmosem_status forward(lmosem_ctx* c, const float* blob, const MlpBufs& w, const 
             return st;
     LMOSEM_PROF_BEGIN(c);
     k_out_fwd<<<(unsigned)((M + 7) / 8), 256, 0, c->stream>>>(H[3], M, blob, y);
-    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_MLP);
     return LMOSEM_OK;
 }
 
@@ -601,9 +601,9 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
     if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;
-    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    st = take_status(c);   // synchronises
     dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H);
-    return LMOSEM_OK;
+    return st;
 }
 
 FeatArgs feat_args(lmosem_ctx* c) {
@@ -638,7 +638,9 @@ lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ) {
 // model rows with the surrogate scatter term, in chunks of whole rows
 lmosem_status build_model_surrogate(lmosem_ctx* c) {
     lmosem_status st;
-    const int64_t max_pairs = int64_t(1) << 20;
+    // pairs per chunk: the mma.sync chain keeps two 256-wide BF16 activations
+    // per pair in HBM, the fused tcgen05 kernel none
+    const int64_t max_pairs = int64_t(1) << (c->surrogate_kernel == 1 ? 20 : 24);
     const int64_t rows_per = std::max<int64_t>(1, max_pairs / c->n_sup);
     const int64_t M = rows_per * c->n_sup;
     MlpBufs w;
@@ -666,9 +668,9 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
             reinterpret_cast<float*>(c->d_model));
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     }
-    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    st = take_status(c);   // synchronises
     dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H); dev_free(&y);
-    return LMOSEM_OK;
+    return st;
 }
 
 }  // namespace lmosem

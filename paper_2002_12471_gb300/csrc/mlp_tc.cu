@@ -23,6 +23,7 @@ namespace lmosem {
 namespace {
 
 constexpr int kH = 256, kInPad = 16, kTileM = 128, kThreads = 128;
+constexpr long long kDrainCycles = 1LL << 31;   // wait for in-flight products after a timeout
 constexpr int64_t kOffB1 = 256 * 6, kOffW2 = kOffB1 + 256, kOffB2 = kOffW2 + 256 * 256;
 constexpr int64_t kLayerStride = 256 * 256 + 256;
 constexpr int64_t kOffW5 = kOffW2 + 3 * kLayerStride, kOffB5 = kOffW5 + 256;
@@ -207,12 +208,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcArgs A) {
             issue(0);
         }
         for (int layer = 0; layer < 4; ++layer) {
-            ok = bar_wait(bar, phase, A.budget);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
+            const bool done = bar_wait(bar, phase, A.budget);
+            if (__syncthreads_or(!done)) {   // all threads agree; the phase stays pending
                 ok = false;
                 break;
             }
+            phase ^= 1u;
             fence_after();
             if (layer < 3) load_w(layer);   // W buffer is free: the last products finished
             // epilogue: accumulator row -> bias, ReLU -> next input (or output)
@@ -256,7 +257,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcArgs A) {
             }
         }
     }
-    if (!ok && tid == 0) atomicExch(A.status, 1);
+    if (!ok) {
+        if (tid == 0) atomicExch(A.status, 1);
+        // the products of the pending phase still write TMEM: let them finish
+        // (bounded again) before the columns are freed
+        bar_wait(bar, phase, kDrainCycles);
+    }
     cp_wait_all();  // no copy may land in shared memory after the CTA has left
     fence_before();
     __syncthreads();
@@ -268,10 +274,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcArgs A) {
 
 }  // namespace
 
-bool surrogate_tc_shape_ok() { return kSmBytes <= 227 * 1024; }
+static_assert(kSmBytes <= 227 * 1024, "shared memory of the fused kernel");
+
+lmosem_status take_status(lmosem_ctx* c) {
+    if (!c->d_status) return LMOSEM_OK;
+    int h = 0;
+    LMOSEM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    if (!h) return LMOSEM_OK;
+    LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait of the surrogate inference ran out");
+}
 
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
                          const __nv_bfloat16* w234, const __nv_bfloat16* X, float* y, int64_t M) {
+    lmosem_status st;
+    if ((st = ensure_status(c))) return st;
     int dev = 0, sms = 0;
     LMOSEM_CK(c, cudaGetDevice(&dev));
     LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -289,7 +307,7 @@ lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* 
     const int grid = (int)std::min<int64_t>(ntiles, sms);
     LMOSEM_PROF_BEGIN(c);
     k_mlp_tc<<<grid, kThreads, kSmBytes, c->stream>>>(A);
-    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_MLP);
     return LMOSEM_OK;
 }
 

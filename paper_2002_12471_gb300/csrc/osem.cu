@@ -653,6 +653,12 @@ lmosem_status setup_pass(lmosem_ctx* c) {
     lmosem_status st;
     if ((st = dev_alloc(c, &c->d_bpart, (size_t)c->pass_ctas * c->n_sup))) return st;
     if ((st = dev_alloc(c, &c->d_llpart, (size_t)c->pass_ctas))) return st;
+    return ensure_status(c);
+}
+
+lmosem_status ensure_status(lmosem_ctx* c) {
+    if (c->d_status) return LMOSEM_OK;
+    lmosem_status st;
     if ((st = dev_alloc(c, &c->d_status, 4))) return st;
     LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream));
     return LMOSEM_OK;

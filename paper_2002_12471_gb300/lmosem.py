@@ -54,7 +54,7 @@ class Options(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
-                  "other", "surrogate"]
+                  "other", "surrogate", "mlp"]
 SURROGATE_PARAMS = 199427
 MODEL_SURROGATE_FP32 = 3
 FORMATS["surrogate"] = MODEL_SURROGATE_FP32
@@ -297,6 +297,16 @@ def lmosem_surrogate_infer(ctx, d_weights, d_features, d_out):
 
 def lmosem_surrogate_load(ctx, d_weights):
     _check(ctx, load().lmosem_surrogate_load(ctx, _ptr(d_weights)))
+
+
+def surrogate_init(seed=0, layers=(6, 256, 256, 256, 256, 1)):
+    """Initial surrogate weights as a blob: He-normal weights (standard
+    deviation sqrt(2 / fan_in)), zero biases, output standardisation (0, 1);
+    training sets the standardisation from its targets."""
+    rng = np.random.default_rng(seed)
+    params = [[rng.standard_normal((fo, fi)) * np.sqrt(2.0 / fi), np.zeros(fo)]
+              for fi, fo in zip(layers[:-1], layers[1:])]
+    return pack_surrogate(params)
 
 
 def pack_surrogate(params, mu=0.0, sigma=1.0):

@@ -164,6 +164,37 @@ def test_tcgen05_inference_matches_mma_and_oracle(L, n):
     assert err(ys[2] - ys[1], ref_tc - ref_mma) <= 2e-3
 
 
+def test_tcgen05_bounded_wait_reports_timeout(L):
+    """With a one-cycle wait budget every CTA of the fused kernel gives up on
+    its first tensor-core wait: the call returns LMOSEM_ETIMEOUT (after the
+    pending products drained and TMEM was freed) and the GPU stays usable."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, *_ = S.workload("tiny16")
+    params = _perturbed_params(13)
+    n = 4 * 128 + 3
+    X = np.random.default_rng(14).normal(0.0, 1.0, (n, 6))
+    blob = torch.from_numpy(L.pack_surrogate(params)).to(dev)
+    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+    out = torch.zeros(n, dtype=torch.float32, device=dev)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream(), surrogate_kernel=2,
+                          wait_budget_cycles=1)
+    try:
+        with pytest.raises(L.LmosemError) as ei:
+            L.lmosem_surrogate_infer(ctx, blob, Xd, out)
+        assert ei.value.status == L.ETIMEOUT
+    finally:
+        L.lmosem_destroy(ctx)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream(), surrogate_kernel=2)
+    try:
+        L.lmosem_surrogate_infer(ctx, blob, Xd, out)
+    finally:
+        L.lmosem_destroy(ctx)
+    ref = _mirrored_forward(params, X, round_last=False)
+    y = out.cpu().numpy().astype(np.float64)
+    assert np.sqrt(np.mean((y - ref) ** 2)) <= 1e-3 * max(np.sqrt(np.mean(ref ** 2)), 0.1)
+
+
 def test_training_targets_match_oracle_scatter(L):
     import torch
     dev = torch.device("cuda:0")
