@@ -244,13 +244,16 @@ typedef struct {
     int32_t batch;     /* rows per minibatch, multiple of 64, 64..65536            */
     float lr;          /* learning rate (the last 20% of the steps use lr / 10)    */
     uint64_t seed;     /* minibatch sampling (rows drawn with replacement)         */
+    float target_floor; /* > 0: targets below (largest target - target_floor) are
+                         * raised to that level, so that the fit is spent on the
+                         * entries that carry the model (log units); 0: none      */
 } lmosem_train_opts;
 
 /* Train the surrogate on n samples (features n x 6, targets n = log scatter)
  * with the library's tensor-core forward and backward kernels and Adam (FP32
  * parameters and moments, BF16 products, FP32 accumulation).  d_weights holds
  * the initial parameters on entry (mu and sigma are recomputed from the
- * targets) and the trained ones on return.  h_loss_curve (steps doubles, may
+ * (floored) targets) and the trained ones on return.  h_loss_curve (steps doubles, may
  * be NULL) receives the minibatch loss of every step.  Synchronises. */
 lmosem_status lmosem_surrogate_train(lmosem_ctx* ctx, const float* d_features, const float* d_targets,
                                      int64_t n, const lmosem_train_opts* opts, float* d_weights,

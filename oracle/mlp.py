@@ -7,7 +7,12 @@ first-order paths of Section 2.2) by a learned function of six inputs:
     pixel x, pixel y, detector angle, event position u, event energy E,
     attenuation from the pixel to the detector along the detector direction,
 
-each mapped to O(1) by the fixed affine scaling ``FEATURE_SCALE`` below.
+encoded in the detector frame of the angle (``features`` below): the event's
+offset from the pixel's projection u - u_a(p), the pixel's coordinate along
+the flight direction p . omega_a, its projection u_a(p) = p . t_a, the
+angle, the energy and the attenuation, each mapped to O(1) by a fixed affine
+scaling.  The encoding is a bijection of the six inputs; it puts the
+quantity the scatter term varies fastest with (the offset) on one axis.
 Architecture: 6 -> 256 -> 256 -> 256 -> 256 -> 1, ReLU after every hidden
 layer, linear output; the output is the standardised natural log of the
 scatter part of p_jn.  Parameters: W_l (out x in, row-major), b_l (out).
@@ -22,13 +27,16 @@ import numpy as np
 
 LAYERS = (6, 256, 256, 256, 256, 1)
 
-# x_mm, y_mm, theta_rad, u_mm, e_kev, atten -> (v - shift) / scale
-FEATURE_SHIFT = np.array([0.0, 0.0, np.pi, 0.0, 137.5, 1.5])
-FEATURE_SCALE = np.array([100.0, 100.0, np.pi, 100.0, 37.5, 1.5])
-
-
-def scale_features(raw):
-    return (np.asarray(raw, dtype=np.float64) - FEATURE_SHIFT) / FEATURE_SCALE
+def features(x_mm, y_mm, theta, u_mm, e_kev, atten):
+    """Scaled network inputs (..., 6) of pixel centres (x, y), angles theta
+    (flight direction omega = (cos, sin), lateral axis t = (-sin, cos)),
+    event positions u, energies E and pixel-to-detector attenuation."""
+    x, y, th = (np.asarray(v, dtype=np.float64) for v in (x_mm, y_mm, theta))
+    u_a = -x * np.sin(th) + y * np.cos(th)
+    s_a = x * np.cos(th) + y * np.sin(th)
+    u, e, att = (np.asarray(v, dtype=np.float64) for v in (u_mm, e_kev, atten))
+    return np.stack(np.broadcast_arrays((u - u_a) / 50.0, s_a / 100.0, u_a / 100.0, (th - np.pi) / np.pi,
+                                        (e - 137.5) / 37.5, (att - 1.5) / 1.5), axis=-1)
 
 
 def init_params(seed=0, layers=LAYERS):

@@ -534,10 +534,12 @@ lmosem_status lmosem_surrogate_train(lmosem_ctx* c, const float* d_features, con
     if (!d_features || !d_targets || !d_weights || !opts || n < 1)
         return fail(c, LMOSEM_EINVAL, "bad training arguments");
     if (opts->steps < 1 || opts->batch < 64 || opts->batch > 65536 || opts->batch % 64 ||
-        !(opts->lr > 0.0f) || !isfinite(opts->lr))
-        return fail(c, LMOSEM_EINVAL, "steps >= 1, batch a multiple of 64 in [64, 65536], lr > 0");
+        !(opts->lr > 0.0f) || !isfinite(opts->lr) || !(opts->target_floor >= 0.0f) ||
+        !isfinite(opts->target_floor))
+        return fail(c, LMOSEM_EINVAL,
+                    "steps >= 1, batch a multiple of 64 in [64, 65536], lr > 0, target_floor >= 0");
     return run_surrogate_train(c, d_features, d_targets, n, opts->steps, opts->batch, opts->lr, opts->seed,
-                               d_weights, h_loss_curve);
+                               opts->target_floor, d_weights, h_loss_curve);
 }
 
 lmosem_status lmosem_surrogate_grad(lmosem_ctx* c, const float* d_weights, const float* d_features,

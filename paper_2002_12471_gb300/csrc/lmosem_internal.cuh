@@ -215,7 +215,7 @@ lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int3
 lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* feat, const float* targ,
                                  int64_t n, float* grad_out, double* h_loss);
 lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
-                                  int steps, int B, float lr, uint64_t seed, float* blob,
+                                  int steps, int B, float lr, uint64_t seed, float floor_below, float* blob,
                                   double* h_loss_curve);
 lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float* feat, int64_t n,
                                   float* out);

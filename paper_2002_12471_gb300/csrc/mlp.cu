@@ -18,6 +18,7 @@
 // kept in FP32 (Adam state too) with BF16 copies for the products.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <float.h>
 
 #include <algorithm>
 
@@ -44,8 +45,6 @@ constexpr int64_t kParams = kOffSigma + 1;
 static_assert(kParams == LMOSEM_SURROGATE_PARAMS, "parameter blob layout");
 
 // input scaling: (raw - shift) / scale for x, y, theta, u, E, attenuation
-__constant__ float c_shift[kIn] = {0.0f, 0.0f, 3.14159265358979f, 0.0f, 137.5f, 1.5f};
-__constant__ float c_scale[kIn] = {100.0f, 100.0f, 3.14159265358979f, 100.0f, 37.5f, 1.5f};
 
 // ---------------------------------------------------------------- GEMM
 
@@ -194,7 +193,8 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // to 16 columns) and standardised targets
 __global__ void k_gather(const float* __restrict__ feat, const float* __restrict__ targ, int64_t n,
                          int B, uint64_t seed, int step, const float* __restrict__ blob,
-                         __nv_bfloat16* __restrict__ X, float* __restrict__ t) {
+                         const float* __restrict__ floor, __nv_bfloat16* __restrict__ X,
+                         float* __restrict__ t) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const int64_t i = seed == 0 ? (int64_t)b % n
@@ -202,7 +202,8 @@ __global__ void k_gather(const float* __restrict__ feat, const float* __restrict
 #pragma unroll
     for (int k = 0; k < kInPad; ++k)
         X[(int64_t)b * kInPad + k] = __float2bfloat16_rn(k < kIn ? feat[i * kIn + k] : 0.0f);
-    t[b] = (targ[i] - blob[kOffMu]) / blob[kOffSigma];
+    const float ti = floor ? fmaxf(targ[i], *floor) : targ[i];
+    t[b] = (ti - blob[kOffMu]) / blob[kOffSigma];
 }
 
 // y = H4 w5 + b5 (one warp per row)
@@ -297,12 +298,27 @@ __global__ void k_weights_bf16(const float* __restrict__ blob, __nv_bfloat16* __
 }
 
 // mean and standard deviation of the targets (FP64, one block, fixed order)
-__global__ void k_target_stats(const float* __restrict__ t, int64_t n, float* __restrict__ blob) {
+// with floor_below > 0 the targets are first raised to (largest - floor_below),
+// that level written to *floor (else -FLT_MAX)
+__global__ void k_target_stats(const float* __restrict__ t, int64_t n, float floor_below,
+                               float* __restrict__ floor, float* __restrict__ blob) {
     __shared__ double s1[256], s2[256];
+    __shared__ float smax[256];
+    float fl = -FLT_MAX;
+    if (floor_below > 0.0f) {
+        float m = -FLT_MAX;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, t[i]);
+        smax[threadIdx.x] = m;
+        __syncthreads();
+        for (int k = 0; k < (int)blockDim.x; ++k) fl = fmaxf(fl, smax[k]);
+        fl -= floor_below;
+    }
+    if (threadIdx.x == 0) *floor = fl;
     double a = 0.0, b = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        a += t[i];
-        b += (double)t[i] * t[i];
+        const double ti = fmaxf(t[i], fl);
+        a += ti;
+        b += ti * ti;
     }
     s1[threadIdx.x] = a;
     s2[threadIdx.x] = b;
@@ -333,13 +349,25 @@ struct FeatArgs {
     float angle0, dtheta;
 };
 
+// network inputs in the detector frame of the event's angle: offset of the
+// event from the pixel's projection, the pixel's coordinate along the flight
+// direction and its projection, the angle, the energy and the pixel-to-
+// detector attenuation, each scaled to O(1)
 __device__ __forceinline__ void features(const FeatArgs& F, int64_t row, int q, float* out) {
     const int a = F.a_s[row];
     const int pix = F.sup[q];
-    float raw[kIn] = {pixel_x(pix, F.nx, F.dpx), pixel_y(pix, F.nx, F.ny, F.dpx), F.angle0 + F.dtheta * a,
-                      F.u_s[row], F.e_s[row], F.l_edge[(size_t)a * F.npix + pix]};
-#pragma unroll
-    for (int k = 0; k < kIn; ++k) out[k] = (raw[k] - c_shift[k]) / c_scale[k];
+    const float x = pixel_x(pix, F.nx, F.dpx), y = pixel_y(pix, F.nx, F.ny, F.dpx);
+    const float th = F.angle0 + F.dtheta * a;
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    const float u_a = -x * sn + y * cs;
+    const float s_a = x * cs + y * sn;
+    out[0] = (F.u_s[row] - u_a) / 50.0f;
+    out[1] = s_a / 100.0f;
+    out[2] = u_a / 100.0f;
+    out[3] = (th - 3.14159265358979f) / 3.14159265358979f;
+    out[4] = (F.e_s[row] - 137.5f) / 37.5f;
+    out[5] = (F.l_edge[(size_t)a * F.npix + pix] - 1.5f) / 1.5f;
 }
 
 // training samples: scaled features and log of the exact scatter entry for
@@ -521,7 +549,7 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     LMOSEM_CK(c, cudaMemsetAsync(tb.loss, 0, sizeof(double), c->stream));
     if ((st = weights_bf16(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, blob, tb.X, tb.t);
+    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, blob, nullptr, tb.X, tb.t);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     tb.grad = grad_out;
     if ((st = loss_grad(c, blob, w, tb, B))) return st;
@@ -536,12 +564,13 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
 }
 
 lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
-                                  int steps, int B, float lr, uint64_t seed, float* blob,
+                                  int steps, int B, float lr, uint64_t seed, float floor_below, float* blob,
                                   double* h_loss_curve) {
     lmosem_status st;
     MlpBufs w;
     TrainBufs tb;
     double* d_curve = nullptr;
+    float* d_floor = nullptr;
     if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
         (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &tb.X, (size_t)B * kInPad)) ||
         (st = dev_alloc(c, &tb.H, (size_t)4 * B * kH)) || (st = dev_alloc(c, &tb.HT, (size_t)B * kH)) ||
@@ -549,20 +578,21 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
         (st = dev_alloc(c, &tb.t, B)) || (st = dev_alloc(c, &tb.y, B)) || (st = dev_alloc(c, &tb.dy, B)) ||
         (st = dev_alloc(c, &tb.gtmp, (size_t)kH * kH)) || (st = dev_alloc(c, &tb.grad, kParams)) ||
         (st = dev_alloc(c, &tb.m, kParams)) || (st = dev_alloc(c, &tb.v, kParams)) ||
-        (st = dev_alloc(c, &d_curve, std::max(1, steps))))
+        (st = dev_alloc(c, &d_curve, std::max(1, steps))) || (st = dev_alloc(c, &d_floor, 1)))
         return st;
     LMOSEM_CK(c, cudaMemsetAsync(tb.m, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(tb.v, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(d_curve, 0, sizeof(double) * std::max(1, steps), c->stream));
     LMOSEM_PROF_BEGIN(c);
-    k_target_stats<<<1, 256, 0, c->stream>>>(targ, n, blob);
+    k_target_stats<<<1, 256, 0, c->stream>>>(targ, n, floor_below, d_floor, blob);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     const float b1 = 0.9f, b2 = 0.999f;
     double p1 = 1.0, p2 = 1.0;
     for (int s = 0; s < steps; ++s) {
         if ((st = weights_bf16(c, blob, w))) return st;
         LMOSEM_PROF_BEGIN(c);
-        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, s, blob, tb.X, tb.t);
+        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, s, blob, d_floor, tb.X,
+                                                         tb.t);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         tb.loss = d_curve + s;
         if ((st = loss_grad(c, blob, w, tb, B))) return st;
@@ -583,6 +613,7 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
     dev_free(&tb.HT); dev_free(&tb.dz); dev_free(&tb.dzT); dev_free(&tb.t); dev_free(&tb.y);
     dev_free(&tb.dy); dev_free(&tb.gtmp); dev_free(&tb.grad); dev_free(&tb.m); dev_free(&tb.v);
     dev_free(&d_curve);
+    dev_free(&d_floor);
     return LMOSEM_OK;
 }
 
@@ -597,7 +628,7 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
         return st;
     if ((st = weights_bf16(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, X, out);
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, nullptr, X, out);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
     if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;

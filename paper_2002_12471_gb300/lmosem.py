@@ -62,7 +62,7 @@ FORMATS["surrogate"] = MODEL_SURROGATE_FP32
 
 class TrainOpts(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("target_floor", ctypes.c_float)]
 
 
 _vp = ctypes.c_void_p
@@ -272,11 +272,11 @@ def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_sc
 
 
 def lmosem_surrogate_train(ctx, d_features, d_targets, d_weights, steps=2000, batch=4096, lr=1e-3,
-                           seed=1):
+                           seed=1, target_floor=0.0):
     """Trains in place; returns the per-step minibatch loss curve."""
     n = int(d_targets.numel())
     curve = np.zeros(int(steps), dtype=np.float64)
-    o = TrainOpts(int(steps), int(batch), float(lr), int(seed))
+    o = TrainOpts(int(steps), int(batch), float(lr), int(seed), float(target_floor))
     _check(ctx, load().lmosem_surrogate_train(ctx, _ptr(d_features), _ptr(d_targets), n, ctypes.byref(o),
                                               _ptr(d_weights), curve.ctypes.data))
     return curve

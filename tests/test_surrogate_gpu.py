@@ -217,10 +217,9 @@ def test_training_targets_match_oracle_scatter(L):
     # inputs: pixel centre, angle, position, energy, attenuation to the edge
     xs, ys = P.pixel_centres(P.support)
     th = g["angle0_rad"] + 2 * np.pi * ev.angle / g["n_angles"]
-    raw = np.stack(np.broadcast_arrays(xs[None, :], ys[None, :], th[:, None], ev.u_mm[:, None].astype(np.float64),
-                                       ev.e_kev[:, None].astype(np.float64),
-                                       P.l_edge[ev.angle][:, P.support]), axis=-1)
-    np.testing.assert_allclose(f, mlp.scale_features(raw), rtol=1e-5, atol=1e-5)
+    ref = mlp.features(xs[None, :], ys[None, :], th[:, None], ev.u_mm[:, None].astype(np.float64),
+                       ev.e_kev[:, None].astype(np.float64), P.l_edge[ev.angle][:, P.support])
+    np.testing.assert_allclose(f, ref, rtol=1e-5, atol=1e-5)
 
 
 @pytest.fixture(scope="module")
