@@ -223,7 +223,9 @@ lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ);
 lmosem_status build_model_surrogate(lmosem_ctx* c);
 // mlp_tc.cu: fused tcgen05 inference of M rows of BF16 inputs (M x 16)
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
-                         const __nv_bfloat16* w234, const __nv_bfloat16* X, float* y, int64_t M);
+                         const unsigned char* w234img, const __nv_bfloat16* X, float* y, int64_t M);
+// hidden weights to the chunked operand layout of forward_tc (3 x 128 KB)
+lmosem_status weights_img(lmosem_ctx* c, const __nv_bfloat16* w234, unsigned char* img);
 
 // ---- device helpers shared by the CUDA translation units
 

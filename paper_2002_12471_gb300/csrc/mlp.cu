@@ -424,7 +424,9 @@ __global__ void k_surr_combine(const float* __restrict__ y, int64_t r0, int64_t 
 
 struct MlpBufs {
     __nv_bfloat16 *w1 = nullptr, *w234 = nullptr, *w234t = nullptr;
+    unsigned char* wimg = nullptr;  // hidden weights in the operand layout of the tcgen05 kernel
 };
+
 
 lmosem_status gemm(lmosem_ctx* c, int epi, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B,
                    int64_t ldb, void* C, int64_t ldc, const float* bias, const __nv_bfloat16* mask,
@@ -457,6 +459,16 @@ lmosem_status weights_bf16(lmosem_ctx* c, const float* blob, MlpBufs& w) {
     return LMOSEM_OK;
 }
 
+// BF16 weights for inference: the row-major copies and, for the tcgen05
+// kernel, the chunked operand image
+lmosem_status infer_weights(lmosem_ctx* c, const float* blob, MlpBufs& w) {
+    lmosem_status st;
+    if ((st = weights_bf16(c, blob, w))) return st;
+    if (c->surrogate_kernel == 1) return LMOSEM_OK;
+    if ((st = dev_alloc(c, &w.wimg, (size_t)3 * kH * kH * 2))) return st;
+    return weights_img(c, w.w234, w.wimg);
+}
+
 // forward of M rows: X (M x 16) -> H[0..3] (M x 256 each) -> y (M)
 lmosem_status forward(lmosem_ctx* c, const float* blob, const MlpBufs& w, const __nv_bfloat16* X,
                       __nv_bfloat16* const H[4], float* y, int64_t M) {
@@ -477,7 +489,7 @@ lmosem_status forward(lmosem_ctx* c, const float* blob, const MlpBufs& w, const 
 // mma.sync product chain (surrogate_kernel == 1), which the training uses
 lmosem_status forward_infer(lmosem_ctx* c, const float* blob, const MlpBufs& w, const __nv_bfloat16* X,
                             __nv_bfloat16* const H[4], float* y, int64_t M) {
-    if (c->surrogate_kernel != 1) return forward_tc(c, blob, w.w1, w.w234, X, y, M);
+    if (c->surrogate_kernel != 1) return forward_tc(c, blob, w.w1, w.wimg, X, y, M);
     return forward(c, blob, w, X, H, y, M);
 }
 
@@ -626,14 +638,14 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
         (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)n * kInPad)) ||
         (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)4 * n * kH))))
         return st;
-    if ((st = weights_bf16(c, blob, w))) return st;
+    if ((st = infer_weights(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
     k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, nullptr, X, out);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
     if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;
     st = take_status(c);   // synchronises
-    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H);
+    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&w.wimg); dev_free(&X); dev_free(&H);
     return st;
 }
 
@@ -681,7 +693,7 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)M * kInPad)) ||
         (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)2 * M * kH))) || (st = dev_alloc(c, &y, M)))
         return st;
-    if ((st = weights_bf16(c, c->d_surrogate, w))) return st;
+    if ((st = infer_weights(c, c->d_surrogate, w))) return st;
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double se0 = fw2s * c->fwhm_frac * c->e0;
     __nv_bfloat16* Hs[4] = {H, H + M * kH, H, H + M * kH};  // ping-pong
@@ -700,7 +712,8 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     }
     st = take_status(c);   // synchronises
-    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&X); dev_free(&H); dev_free(&y);
+    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&w.wimg); dev_free(&X); dev_free(&H);
+    dev_free(&y);
     return st;
 }
 
