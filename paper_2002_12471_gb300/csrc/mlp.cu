@@ -191,17 +191,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 // minibatch rows (seeded, with replacement): scaled features as BF16 (padded
 // to 16 columns) and standardised targets
+// element index of input (row i, column k) in the row-major M x 16 layout of
+// the mma.sync chain or, for the tcgen05 kernel, the tile-major layout:
+// 128-row tiles of 2048 elements, each the K = 16 operand layout (row group g
+// of 8 rows at 128 elements, its two 8-column groups 64 elements apart)
+__device__ __forceinline__ int64_t x_index(int64_t i, int k, bool tiled) {
+    if (!tiled) return i * kInPad + k;
+    const int r = (int)(i & 127);
+    return (i >> 7) * (128 * kInPad) + (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
 __global__ void k_gather(const float* __restrict__ feat, const float* __restrict__ targ, int64_t n,
                          int B, uint64_t seed, int step, const float* __restrict__ blob,
                          const float* __restrict__ floor, __nv_bfloat16* __restrict__ X,
-                         float* __restrict__ t) {
+                         float* __restrict__ t, bool tiled) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const int64_t i = seed == 0 ? (int64_t)b % n
                                 : (int64_t)(splitmix64(seed ^ ((uint64_t)step * 0x100000001B3ull + b)) % (uint64_t)n);
 #pragma unroll
     for (int k = 0; k < kInPad; ++k)
-        X[(int64_t)b * kInPad + k] = __float2bfloat16_rn(k < kIn ? feat[i * kIn + k] : 0.0f);
+        X[x_index(b, k, tiled)] = __float2bfloat16_rn(k < kIn ? feat[i * kIn + k] : 0.0f);
     const float ti = floor ? fmaxf(targ[i], *floor) : targ[i];
     t[b] = (ti - blob[kOffMu]) / blob[kOffSigma];
 }
@@ -388,13 +398,14 @@ __global__ void k_samples(FeatArgs F, const float* __restrict__ model, int64_t l
 }
 
 // surrogate inputs of rows [r0, r0 + nrows) x all support pixels, BF16
-__global__ void k_surr_inputs(FeatArgs F, int64_t r0, int64_t nrows, __nv_bfloat16* __restrict__ X) {
+__global__ void k_surr_inputs(FeatArgs F, int64_t r0, int64_t nrows, __nv_bfloat16* __restrict__ X,
+                              bool tiled) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows * F.n_sup) return;
     float f[kIn];
     features(F, r0 + i / F.n_sup, (int)(i % F.n_sup), f);
 #pragma unroll
-    for (int k = 0; k < kInPad; ++k) X[i * kInPad + k] = __float2bfloat16_rn(k < kIn ? f[k] : 0.0f);
+    for (int k = 0; k < kInPad; ++k) X[x_index(i, k, tiled)] = __float2bfloat16_rn(k < kIn ? f[k] : 0.0f);
 }
 
 // p_jn = primary_jn + exp(mu + sigma y_jn) into the FP32 model rows
@@ -561,7 +572,7 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     LMOSEM_CK(c, cudaMemsetAsync(tb.loss, 0, sizeof(double), c->stream));
     if ((st = weights_bf16(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, blob, nullptr, tb.X, tb.t);
+    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, blob, nullptr, tb.X, tb.t, false);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     tb.grad = grad_out;
     if ((st = loss_grad(c, blob, w, tb, B))) return st;
@@ -604,7 +615,7 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
         if ((st = weights_bf16(c, blob, w))) return st;
         LMOSEM_PROF_BEGIN(c);
         k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, s, blob, d_floor, tb.X,
-                                                         tb.t);
+                                                         tb.t, false);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         tb.loss = d_curve + s;
         if ((st = loss_grad(c, blob, w, tb, B))) return st;
@@ -635,12 +646,13 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     MlpBufs w;
     __nv_bfloat16 *X = nullptr, *H = nullptr;
     if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
-        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)n * kInPad)) ||
+        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)((n + 127) / 128 * 128) * kInPad)) ||
         (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)4 * n * kH))))
         return st;
     if ((st = infer_weights(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, nullptr, X, out);
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, nullptr, X, out,
+                                                                 c->surrogate_kernel != 1);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
     if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;
@@ -690,7 +702,7 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
     __nv_bfloat16 *X = nullptr, *H = nullptr;
     float* y = nullptr;
     if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
-        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)M * kInPad)) ||
+        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)((M + 127) / 128 * 128) * kInPad)) ||
         (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)2 * M * kH))) || (st = dev_alloc(c, &y, M)))
         return st;
     if ((st = infer_weights(c, c->d_surrogate, w))) return st;
@@ -701,7 +713,8 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         const int64_t nr = std::min(rows_per, c->J - r0);
         const int64_t m = nr * c->n_sup;
         LMOSEM_PROF_BEGIN(c);
-        k_surr_inputs<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(feat_args(c), r0, nr, X);
+        k_surr_inputs<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(feat_args(c), r0, nr, X,
+                                                                          c->surrogate_kernel != 1);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         if ((st = forward_infer(c, c->d_surrogate, w, X, Hs, y, m))) return st;
         LMOSEM_PROF_BEGIN(c);

@@ -1,26 +1,26 @@
 // Scatter-surrogate inference on the 5th-generation tensor cores (tcgen05).
 //
-// One persistent CTA per SM takes tiles of 128 rows and runs the whole
-// network on chip.  Roles:
-//   * eight epilogue warps: read a layer's FP32 accumulator from TMEM
-//     (tcgen05.ld; warp w reads lanes 32 (w % 4).. and columns of half w / 4),
-//     add the bias, apply ReLU and write the next layer's BF16 input into
-//     shared memory, 32 columns (one K chunk) at a time; the last hidden
-//     layer's epilogue folds in the 256 -> 1 output layer;
-//   * thread 0 (also an epilogue thread) issues the products: as soon as a
-//     K chunk of the next layer's input is written and the matching chunk of
-//     its weights has landed, the two K = 16 steps of that chunk go to the
-//     tensor core as tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation,
-//     M = 128, N = 256);
-//   * one producer warp streams the weight chunks (16 KB each, pre-arranged
-//     in global memory in the shared-memory operand layout) with
-//     cp.async.bulk into eight slots guarded by full / empty mbarriers.
-// Two 256-column accumulators alternate between layers, so the products of
-// layer l + 1 run while the epilogue of layer l drains its accumulator, and
-// the first layer of the next tile starts while the last epilogue of the
-// current tile runs.  Every wait is bounded: a timeout (or the abort of
-// another role) sets the status word; the CTA then waits (bounded again) for
-// its products and copies in flight, frees its TMEM and returns.
+// One persistent CTA per SM runs the whole network on chip for tiles of 128
+// rows, two tiles at a time ("ping-pong"): each tile has its own 256-column
+// FP32 accumulator in TMEM and its own BF16 activation buffer in shared
+// memory, and while the epilogue drains one tile's accumulator the tensor
+// core computes the other tile's layer.  Roles, handing work to each other
+// through mbarriers only:
+//   * producer warp: streams each tile's inputs (4 KB) and the hidden weights
+//     (16 KB K chunks, pre-arranged in global memory in the shared-memory
+//     operand layout) with cp.async.bulk, the weights through a ring of four
+//     chunk slots in the order the products consume them;
+//   * MMA warp: one thread issues every product as tcgen05.mma (kind::f16,
+//     BF16 operands, FP32 accumulation, M = 128, N = 256), alternating
+//     between the two tiles layer by layer;
+//   * two epilogue groups of four warps, one per tile of the pair: read the
+//     accumulator (warp w: TMEM lanes 32 (w % 4).., all 256 columns), add
+//     the bias, apply ReLU, round to BF16 and write the next layer's input
+//     in place; the last hidden layer's epilogue folds in the 256 -> 1 output
+//     layer.
+// Every wait is bounded: a timeout (or another role's abort) sets the status
+// word; the CTA then waits (bounded again) for its products and copies in
+// flight, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -32,10 +32,12 @@ namespace lmosem {
 namespace {
 
 constexpr int kH = 256, kInPad = 16, kTileM = 128;
-constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32, kThreads = kEpiThreads + 32;
-constexpr int kChunks = 8, kChunkK = 32;
+constexpr int kGroupWarps = 4, kEpiWarps = 2 * kGroupWarps, kGroupThreads = kGroupWarps * 32;
+constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kThreads = kEpiWarps * 32 + 64;
+constexpr int kChunks = 8, kChunkK = 32, kSlots = 4;
 constexpr uint32_t kWChunkBytes = kH * kChunkK * 2;       // 16 KB
 constexpr uint32_t kAChunkBytes = kTileM * kChunkK * 2;   // 8 KB
+constexpr uint32_t kABytes = kChunks * kAChunkBytes;      // 64 KB per tile
 constexpr long long kDrainCycles = 1LL << 31;             // waits for in-flight work after an abort
 constexpr int64_t kOffB1 = 256 * 6, kOffW2 = kOffB1 + 256, kOffB2 = kOffW2 + 256 * 256;
 constexpr int64_t kLayerStride = 256 * 256 + 256;
@@ -57,15 +59,17 @@ __host__ __device__ constexpr uint32_t chunk_offset(int r, int k, int R) {
 }
 
 // shared memory (bytes)
-constexpr uint32_t kSmW = 0;                                   // 8 weight chunks, 128 KB
-constexpr uint32_t kSmA = kSmW + kChunks * kWChunkBytes;       // 128 x 256 activations, 64 KB
-constexpr uint32_t kSmX = kSmA + kChunks * kAChunkBytes;       // 128 x 16 inputs
-constexpr uint32_t kSmW1 = kSmX + kTileM * kInPad * 2;         // 256 x 16 first-layer weights
+constexpr uint32_t kXTileBytes = kTileM * kInPad * 2;          // 4 KB
+constexpr uint32_t kSmW = 0;                                   // weight ring, 4 x 16 KB
+constexpr uint32_t kSmA = kSmW + kSlots * kWChunkBytes;        // 2 x (128 x 256) activations
+constexpr uint32_t kSmX = kSmA + 2 * kABytes;                  // 2 input tiles of 128 x 16
+constexpr uint32_t kSmW1 = kSmX + 2 * kXTileBytes;             // 256 x 16 first-layer weights
 constexpr uint32_t kSmBias = kSmW1 + kH * kInPad * 2;          // 4 x 256 biases
 constexpr uint32_t kSmW5 = kSmBias + 4 * kH * 4;               // output weights
-constexpr uint32_t kSmYp = kSmW5 + kH * 4;                     // output partials of column half 1
-constexpr uint32_t kSmBar = kSmYp + kTileM * 4;                // wfull[8] wempty[8] acc[2] drain
-constexpr uint32_t kSmTmem = kSmBar + 19 * 8;
+// mbarriers: wfull[4] wempty[4] xfull[2] xempty[2] accfull[2] adone[2] drain
+constexpr int kBars = 2 * kSlots + 9;
+constexpr uint32_t kSmBar = kSmW5 + kH * 4;
+constexpr uint32_t kSmTmem = kSmBar + kBars * 8;
 constexpr uint32_t kSmFlag = kSmTmem + 4;
 constexpr uint32_t kSmBytes = kSmFlag + 12;
 
@@ -98,8 +102,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void bar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(bar)) : "memory");
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(bar)) : "memory");
 }
 __device__ __forceinline__ bool bar_test(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -139,36 +146,63 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool ok) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0));
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-// barrier 1 over the eight epilogue warps
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kEpiThreads) : "memory"); }
-__device__ __forceinline__ bool epi_any(bool v) {
+// OR over the four warps of epilogue group g (named barrier 1 + g)
+__device__ __forceinline__ bool group_any(int g, bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(kEpiThreads)
+        : "r"((uint32_t)v), "r"(1 + g), "n"(kGroupThreads)
         : "memory");
     return r != 0;
 }
 
-// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane; the
+// registers are valid after tmem_wait32 (which takes them as operands, so no
+// use can be scheduled before the wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
+                   "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+// (a0 + b0, a1 + b1) in one packed FP32x2 add
+__device__ __forceinline__ uint64_t add2(uint32_t a0, uint32_t a1, float b0, float b1) {
+    uint64_t d;
+    asm("{\n\t.reg .b64 a, b;\n\tmov.b64 a, {%1, %2};\n\tmov.b64 b, {%3, %4};\n\t"
+        "add.rn.f32x2 %0, a, b;\n\t}"
+        : "=l"(d)
+        : "r"(a0), "r"(a1), "f"(b0), "f"(b1));
+    return d;
+}
+// BF16x2 of ReLU of the two halves (low half = first element)
+__device__ __forceinline__ uint32_t relu_bf16x2(uint64_t v) {
+    uint32_t d;
+    asm("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tcvt.rn.relu.bf16x2.f32 %0, hi, lo;\n\t}"
+        : "=r"(d)
+        : "l"(v));
+    return d;
 }
 
 struct TcArgs {
-    const __nv_bfloat16* X;         // M x 16 scaled inputs (BF16)
+    const unsigned char* X;         // inputs, tile-major: 128-row tiles of 4 KB in the K = 16 operand layout
     int64_t M;
     const __nv_bfloat16* w1;        // 256 x 16, row-major
     const unsigned char* w234img;   // 3 x 8 chunks x 16 KB: hidden weights in the operand layout
@@ -182,24 +216,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint64_t* wfull = reinterpret_cast<uint64_t*>(sm + kSmBar);
-    uint64_t* wempty = wfull + kChunks;
-    uint64_t* accbar = wfull + 2 * kChunks;
-    uint64_t* drain = accbar + 2;
+    uint64_t* wempty = wfull + kSlots;
+    uint64_t* xfull = wempty + kSlots;
+    uint64_t* xempty = xfull + 2;
+    uint64_t* accfull = xempty + 2;
+    uint64_t* adone = accfull + 2;   // epilogue of group g done with a layer (count 4 warps)
+    uint64_t* drain = adone + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmTmem);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kSmFlag);
     float* sb = reinterpret_cast<float*>(sm + kSmBias);
     float* sw5 = reinterpret_cast<float*>(sm + kSmW5);
-    float* yp = reinterpret_cast<float*>(sm + kSmYp);
     const uint32_t base = su32(sm);
 
-    // TMEM: two accumulators of 256 FP32 columns x 128 lanes
-    if (warp == 0) {
+    // TMEM: one accumulator of 256 FP32 columns x 128 lanes per tile of the pair
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(su32(tslot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < 2 * kChunks + 3; ++i) bar_init(wfull + i);
+        for (int i = 0; i < kBars; ++i) bar_init(wfull + i, (adone <= wfull + i && wfull + i < drain) ? kGroupWarps : 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -219,156 +255,186 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcArgs A) {
     const float b5 = A.blob[kOffB5];
     const uint32_t idesc = idesc_bf16(kTileM, kH);
     const int64_t ntiles = (A.M + kTileM - 1) / kTileM;
+    // this CTA's tiles j = 0, 1, ... are blockIdx.x + j gridDim.x; tile j belongs to
+    // group j % 2 as that group's tile j / 2; pairs p = (2p, 2p + 1)
+    const int64_t nj = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t npairs = (nj + 1) / 2;
+    auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };
 
-    uint32_t issued[kChunks];  // producer: copies issued per weight slot
-#pragma unroll
-    for (int c = 0; c < kChunks; ++c) issued[c] = 0;
-    if (warp == kEpiWarps) {
-        // ---------------- producer: hidden weight chunks, 3 layers per tile
+    // producer counters: weight chunks and input tiles issued (for the drain after an abort)
+    uint32_t nw = 0, nx0 = 0, nx1 = 0;
+
+    if (warp == kProdWarp) {
+        // ---------------- producer: inputs of a pair, then its weight chunks in product order
         if (lane == 0) {
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
-                for (int l = 0; l < 3 && ok; ++l)
-                    for (int c = 0; c < kChunks; ++c) {
-                        // the slot's previous chunk must have been consumed by its products
-                        if (issued[c] > 0 && !bar_wait(&wempty[c], (issued[c] - 1) & 1u, A.budget, abort_flag)) {
+            auto load_x = [&](int g, int64_t p) -> bool {
+                if (2 * p + g >= nj) return true;
+                uint32_t& n = g ? nx1 : nx0;  // == p
+                if (n > 0 && !bar_wait(&xempty[g], (n - 1) & 1u, A.budget, abort_flag)) return false;
+                bulk_load(base + kSmX + g * kXTileBytes, A.X + (size_t)tile_of(2 * p + g) * kXTileBytes,
+                          kXTileBytes, &xfull[g]);
+                ++n;
+                return true;
+            };
+            ok = load_x(0, 0) && load_x(1, 0);
+            for (int64_t p = 0; p < npairs && ok; ++p) {
+                for (int l = 1; l < 4 && ok; ++l) {
+                    for (int g = 0; g < 2 && ok; ++g) {
+                        if (2 * p + g >= nj) continue;
+                        for (int c = 0; c < kChunks; ++c) {
+                            const uint32_t slot = nw % kSlots, u = nw / kSlots;
+                            if (u > 0 && !bar_wait(&wempty[slot], (u - 1) & 1u, A.budget, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            bulk_load(base + kSmW + slot * kWChunkBytes,
+                                      A.w234img + (size_t)(l - 1) * kChunks * kWChunkBytes +
+                                          (size_t)c * kWChunkBytes,
+                                      kWChunkBytes, &wfull[slot]);
+                            ++nw;
+                        }
+                    }
+                    // the pair's first-layer products have read their inputs: fetch the next pair's
+                    if (l == 1 && ok) ok = load_x(0, p + 1) && load_x(1, p + 1);
+                }
+            }
+            if (!ok) *abort_flag = 1;
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer: layer by layer, alternating between the pair's tiles
+        if (lane == 0) {
+            bool ok = true;
+            uint32_t n = 0;  // weight chunks consumed
+            for (int64_t p = 0; p < npairs && ok; ++p) {
+                for (int l = 0; l < 4 && ok; ++l) {
+                    for (int g = 0; g < 2 && ok; ++g) {
+                        if (2 * p + g >= nj) continue;
+                        const uint32_t d = tmem + (uint32_t)g * 256;
+                        // the group's epilogue of the previous layer (for l = 0: of the last layer of its
+                        // previous tile) has drained this accumulator and, for l >= 1, written the input;
+                        // adone[g] completes 4 times per tile
+                        if ((p > 0 || l > 0) &&
+                            !bar_wait(&adone[g], (uint32_t)(l + 1) & 1u, A.budget, abort_flag)) {
                             ok = false;
                             break;
                         }
-                        bulk_load(base + kSmW + c * kWChunkBytes,
-                                  A.w234img + (size_t)l * kChunks * kWChunkBytes + (size_t)c * kWChunkBytes,
-                                  kWChunkBytes, &wfull[c]);
-                        ++issued[c];
+                        if (l == 0) {
+                            if (!bar_wait(&xfull[g], (uint32_t)p & 1u, A.budget, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            fence_after();
+                            mma_bf16_tc(d, smem_desc(base + kSmX + g * kXTileBytes, 128, 256),
+                                        smem_desc(base + kSmW1, 128, 256), idesc, 0u);
+                            mma_commit(&xempty[g]);
+                        } else {
+                            fence_after();
+                            const uint32_t abase = base + kSmA + g * kABytes;
+                            for (int c = 0; c < kChunks; ++c) {
+                                const uint32_t slot = n % kSlots;
+                                if (!bar_wait(&wfull[slot], (n / kSlots) & 1u, A.budget, abort_flag)) {
+                                    ok = false;
+                                    break;
+                                }
+                                fence_after();
+#pragma unroll
+                                for (int s2 = 0; s2 < 2; ++s2)
+                                    mma_bf16_tc(d, smem_desc(abase + c * kAChunkBytes + s2 * 256, 128, 512),
+                                                smem_desc(base + kSmW + slot * kWChunkBytes + s2 * 256, 128, 512),
+                                                idesc, (c | s2) ? 1u : 0u);
+                                mma_commit(&wempty[slot]);
+                                ++n;
+                            }
+                            if (!ok) break;
+                        }
+                        mma_commit(&accfull[g]);
                     }
+                }
+            }
             if (!ok) *abort_flag = 1;
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps (thread 0 also issues the products)
-        const int quarter = warp & 3, half = warp >> 2;
+        // ---------------- epilogue group g = warp / 4: tiles j = g, g + 2, ...
+        const int g = warp / kGroupWarps, quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const bool issuer = tid == 0;
-        uint32_t use = 0;  // weight-slot uses consumed (3 per tile)
+        const uint32_t acc = tmem + (uint32_t)g * 256 + ((uint32_t)(quarter * 32) << 16);
+        unsigned char* abuf = sm + kSmA + g * kABytes;
         bool ok = true;
-
-        auto load_x = [&](int64_t t) {  // 128 rows x 2 k groups, rows past M read as zeros
-            const int64_t m0 = t * kTileM;
-            const int r = tid >> 1, kg = tid & 1;
-            const bool in = m0 + r < A.M;
-            cp16(base + kSmX + k16_offset(r, kg * 8), A.X + (in ? (m0 + r) * kInPad + kg * 8 : 0), in);
-        };
-        auto issue_first = [&]() {  // layer 1 (K = 16) into accumulator 0
-            fence_after();
-            mma_bf16_tc(tmem, smem_desc(base + kSmX, 128, 256), smem_desc(base + kSmW1, 128, 256), idesc, 0u);
-            mma_commit(&accbar[0]);
-        };
-
-        int64_t t = blockIdx.x;
-        if (t < ntiles) {
-            load_x(t);
-            cp_wait_all();
-            fence_async_smem();
-            epi_sync();
-            if (issuer) issue_first();
-        }
-        for (; t < ntiles && ok; t += gridDim.x) {
-            const int64_t m0 = t * kTileM;
-            const int64_t tn = t + gridDim.x;
+        for (int64_t j = g; j < nj && ok; j += 2) {
+            const int64_t m0 = tile_of(j) * kTileM;
             for (int l = 0; l < 4; ++l) {
-                // layer l's accumulator is complete (layers alternate between the two)
-                const bool done = bar_wait(&accbar[l & 1], (uint32_t)(l >> 1) & 1u, A.budget, abort_flag);
-                if (epi_any(!done)) {
+                // accumulator g completes 4 times per tile: parity l & 1
+                const bool done = bar_wait(&accfull[g], (uint32_t)l & 1u, A.budget, abort_flag);
+                if (group_any(g, !done)) {
                     ok = false;
                     break;
                 }
                 fence_after();
-                if (l == 1 && tn < ntiles) load_x(tn);  // the first layer's products have read X
-                if (l == 3 && tn < ntiles) {            // next tile's first layer overlaps this epilogue
-                    cp_wait_all();
-                    fence_async_smem();
-                    fence_before();
-                    epi_sync();
-                    if (issuer) issue_first();
-                }
-                const uint32_t acc = tmem + (uint32_t)(l & 1) * 256 + lane_off;
-                const uint32_t nxt = tmem + (uint32_t)((l + 1) & 1) * 256;
                 const float* bias = sb + l * kH;
-                float ysum = 0.0f;
+                uint32_t ra[32], rb[32];
+                float2 ydot = make_float2(0.0f, 0.0f);
+                tmem_ld32(acc, ra);
+#pragma unroll
                 for (int c = 0; c < kChunks; ++c) {
-                    const int k0 = c * kChunkK + half * 16;
-                    float v[16];
-                    tmem_ld16(acc + (uint32_t)k0, v);
-                    float b[16];
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(b + j) =
-                                                        *reinterpret_cast<const float4*>(bias + k0 + j);
+                    uint32_t(&r)[32] = (c & 1) ? rb : ra;
+                    uint32_t(&rn)[32] = (c & 1) ? ra : rb;
+                    tmem_wait32(r);
+                    if (c + 1 < kChunks) tmem_ld32(acc + (uint32_t)((c + 1) * kChunkK), rn);
                     if (l < 3) {
-                        uint32_t pk[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(v[2 * e] + b[2 * e], 0.0f),
-                                                                      fmaxf(v[2 * e + 1] + b[2 * e + 1], 0.0f));
-                            pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+                        for (int q = 0; q < 4; ++q) {  // 8 columns: one 16-byte store
+                            const float4 b0 = *reinterpret_cast<const float4*>(bias + c * kChunkK + q * 8);
+                            const float4 b1 = *reinterpret_cast<const float4*>(bias + c * kChunkK + q * 8 + 4);
+                            const uint32_t* v = r + q * 8;
+                            *reinterpret_cast<uint4*>(abuf + chunk_offset(row, c * kChunkK + q * 8, kTileM)) =
+                                make_uint4(relu_bf16x2(add2(v[0], v[1], b0.x, b0.y)),
+                                           relu_bf16x2(add2(v[2], v[3], b0.z, b0.w)),
+                                           relu_bf16x2(add2(v[4], v[5], b1.x, b1.y)),
+                                           relu_bf16x2(add2(v[6], v[7], b1.z, b1.w)));
                         }
-                        unsigned char* dst = sm + kSmA + chunk_offset(row, k0, kTileM);
-                        *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                        fence_async_smem();
-                        fence_before();
-                        epi_sync();  // chunk c of the next layer's input is written
-                        if (issuer) {
-                            if (!bar_wait(&wfull[c], use & 1u, A.budget, abort_flag)) {
-                                *abort_flag = 1;
-                            } else {
-                                fence_after();
-#pragma unroll
-                                for (int s = 0; s < 2; ++s)
-                                    mma_bf16_tc(nxt,
-                                                smem_desc(base + kSmA + c * kAChunkBytes + s * 256, 128, 512),
-                                                smem_desc(base + kSmW + c * kWChunkBytes + s * 256, 128, 512),
-                                                idesc, (c | s) ? 1u : 0u);
-                                mma_commit(&wempty[c]);
-                                if (c == kChunks - 1) mma_commit(&accbar[(l + 1) & 1]);
-                            }
-                        }
-                        __syncwarp();
                     } else {
-                        float wv[16];
 #pragma unroll
-                        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(wv + j) =
-                                                            *reinterpret_cast<const float4*>(sw5 + k0 + j);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) ysum = fmaf(fmaxf(v[j] + b[j], 0.0f), wv[j], ysum);
+                        for (int q = 0; q < 32; q += 4) {
+                            const float4 bb = *reinterpret_cast<const float4*>(bias + c * kChunkK + q);
+                            const float4 ww = *reinterpret_cast<const float4*>(sw5 + c * kChunkK + q);
+                            ydot.x = fmaf(fmaxf(__uint_as_float(r[q]) + bb.x, 0.0f), ww.x, ydot.x);
+                            ydot.y = fmaf(fmaxf(__uint_as_float(r[q + 1]) + bb.y, 0.0f), ww.y, ydot.y);
+                            ydot.x = fmaf(fmaxf(__uint_as_float(r[q + 2]) + bb.z, 0.0f), ww.z, ydot.x);
+                            ydot.y = fmaf(fmaxf(__uint_as_float(r[q + 3]) + bb.w, 0.0f), ww.w, ydot.y);
+                        }
                     }
                 }
-                if (l < 3) {
-                    ++use;
-                } else {
-                    if (half == 1) yp[row] = ysum;
-                    fence_before();
-                    epi_sync();
-                    if (half == 0 && m0 + row < A.M) A.y[m0 + row] = ysum + yp[row] + b5;
-                }
+                if (l < 3) fence_async_smem();  // the next layer's input, for the tensor core
+                fence_before();                 // accumulator reads ordered before its next products
+                __syncwarp();
+                if (lane == 0) bar_arrive(&adone[g]);
+                if (l == 3 && m0 + row < A.M) A.y[m0 + row] = ydot.x + ydot.y + b5;
             }
         }
         if (!ok) *abort_flag = 1;
-        cp_wait_all();  // no input copy lands after the CTA has left
     }
     __syncthreads();
     if (*abort_flag) {
-        if (tid == 0) {  // products in flight finish before TMEM is freed
-            atomicExch(A.status, 1);
+        if (warp == kMmaWarp && lane == 0) {  // products in flight finish before TMEM is freed
             mma_commit(drain);
             bar_wait(drain, 0u, kDrainCycles, nullptr);
         }
-        if (warp == kEpiWarps && lane == 0)  // and the last weight copy of every slot lands
-            for (int c = 0; c < kChunks; ++c)
-                if (issued[c] > 0) bar_wait(&wfull[c], (issued[c] - 1) & 1u, kDrainCycles, nullptr);
+        if (warp == kProdWarp && lane == 0) {  // and the last copy of every slot lands
+            for (uint32_t sl = 0; sl < (uint32_t)kSlots; ++sl) {
+                const uint32_t u = nw / kSlots + (sl < nw % kSlots ? 1u : 0u);
+                if (u > 0) bar_wait(&wfull[sl], (u - 1) & 1u, kDrainCycles, nullptr);
+            }
+            if (nx0 > 0) bar_wait(&xfull[0], (nx0 - 1) & 1u, kDrainCycles, nullptr);
+            if (nx1 > 0) bar_wait(&xfull[1], (nx1 - 1) & 1u, kDrainCycles, nullptr);
+        }
+        if (tid == 0) atomicExch(A.status, 1);
     }
     fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
     }
@@ -406,6 +472,7 @@ lmosem_status weights_img(lmosem_ctx* c, const __nv_bfloat16* w234, unsigned cha
 
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
                          const unsigned char* w234img, const __nv_bfloat16* X, float* y, int64_t M) {
+    // X: tile-major inputs (x_tile_index), rows padded to a multiple of 128
     lmosem_status st;
     if ((st = ensure_status(c))) return st;
     int dev = 0, sms = 0;
@@ -413,7 +480,7 @@ lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* 
     LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LMOSEM_CK(c, cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBytes));
     TcArgs A;
-    A.X = X;
+    A.X = reinterpret_cast<const unsigned char*>(X);
     A.M = M;
     A.w1 = w1;
     A.w234img = w234img;
