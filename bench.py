@@ -177,6 +177,26 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(t_ms, world, dev):
+    """The slowest rank's timed total (all ranks receive it); weak scaling
+    reports the units all ranks processed divided by this time."""
+    if world <= 1:
+        return t_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: every rank processes units_per_rank per step."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, rank, world, local_rank):
@@ -251,13 +271,7 @@ def run_ours(args, rank, world, local_rank):
         launches += nl
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_total_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total_ms = float(t.item())
-        dist.barrier()
+    t_total_ms = max_over_ranks(sum(times), world, dev)
     ll_final = float(ll.item())
 
     # ---- end to end through host buffers (H2D of the events, D2H of image + LL)
@@ -335,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
     pass_bytes = model_bytes + ns * n_nz * 4          # model rows once + image reads
     pass_gbs = (pass_bytes / ns) / (pass_ms / max(1, pass_n) * 1e-3) / 1e9
     ms_step = t_total_ms / args.steps
-    value = world * evals / (ms_step * 1e-3)
+    value = aggregate_rate(evals, world, ms_step)
     e2e_ms = statistics.mean(e2e_times)
     out = {
         "metric": METRIC,
