@@ -48,6 +48,9 @@ WORKLOADS = {
                      "on exact scatter path sums of 32 jittered phantoms (~1M event-pixel pairs each); "
                      "one step = sensitivity, surrogate model build, 8 subsets x 10 iterations on "
                      "2,000,000 events of a held-out phantom"),
+    "windows64": ("energy-window variants (photopeak [143, 175], [120, 175], full [100, 175] keV) of the "
+                  "64 noise realisations of the 64x64 DaT phantom, each window reconstructed in one persistent "
+                  "launch, 8 subsets x 10 iterations; ROI-mean NRMSE over realisations"),
     "batch64": ("64 independent noise realisations of the 64x64 DaT phantom (120 angles, R = 150 mm), "
                 "event counts Poisson with means uniform in [50k, 400k], 8 subsets x 10 iterations, "
                 "all realisations in one persistent launch, FP32 model"),
@@ -175,6 +178,45 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ OS vs MLEM
+
+def os_vs_mlem(L, ph, g, a, u, e, ns, ni, stream, dev, T=1.0):
+    """Ordered subsets against plain LM-MLEM (N_s = 1) on the same events
+    (paper Sec. 4: similar images, about N_s times faster): seconds per
+    iteration of each (CUDA events, model cached, no log-likelihood pass),
+    and the MLEM iterations needed to reach the log-likelihood that `ni` OS
+    iterations reach."""
+    import torch
+    res = {}
+    for n_sub, iters in ((ns, ni), (1, 8 * ni)):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            L.lmosem_sensitivity(ctx, n_sub)
+            L.lmosem_build_model(ctx, a, u, e, n_sub, "fp32")
+            f = torch.empty(nsup, dtype=torch.float32, device=dev)
+            ll = torch.empty(iters, dtype=torch.float64, device=dev)
+            L.lmosem_init_image(ctx, T, f)
+            L.lmosem_iterate(ctx, iters, T, f, ll)
+            curve = ll.cpu().numpy()
+            L.lmosem_init_image(ctx, T, f)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.lmosem_iterate(ctx, iters, T, f)
+            e1.record(stream)
+            e1.synchronize()
+            res[n_sub] = (e0.elapsed_time(e1) / iters * 1e-3, curve)
+        finally:
+            L.lmosem_destroy(ctx)
+    t_os, ll_os = res[ns]
+    t_ml, ll_ml = res[1]
+    reached = np.nonzero(ll_ml >= ll_os[-1])[0]
+    need = int(reached[0]) + 1 if len(reached) else None
+    return {"subsets": ns, "os_iters": ni, "os_s_per_iter": t_os, "mlem_s_per_iter": t_ml,
+            "mlem_iters_to_match": need, "mlem_iters_run": 8 * ni,
+            "speedup_to_same_loglik": (need * t_ml) / (ni * t_os) if need else None}
 
 
 # ------------------------------------------------------------------ ranks
@@ -316,6 +358,7 @@ def run_ours(args, rank, world, local_rank):
         finally:
             L.lmosem_destroy(ctx)
 
+    osml = os_vs_mlem(L, ph, g, a_d, u_d, e_d, ns, ni, stream, dev) if rank == 0 else None
     terms, n_nz = strip_terms(ph, g, ev)
     evals = J * n_nz
     pk, pk_kind = peaks()
@@ -377,6 +420,7 @@ def run_ours(args, rank, world, local_rank):
         "kernel_share": {k: v[0] / tot_kernel_ms for k, v in agg.items() if v[1]},
         "model_build_evals_per_s": evals / (ps_launch_ms * ps_n / args.steps * 1e-3),
         "path_terms_per_step": terms,
+        "os_vs_mlem": osml,
         "loglik_final": ll_final,
         "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": UNIT,
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(J * 12),
@@ -850,6 +894,88 @@ def run_surrogate_bench(args):
     }
 
 
+# ------------------------------------------------------------------ energy windows
+
+WINDOWS = (("full", 100.0), ("e120", 120.0), ("photopeak", 143.0))
+
+
+def run_windows_bench(args):
+    """Energy-window variants (paper Sec. 3: photopeak only, E > 120 keV and
+    the whole spectrum, applied to the same acquisitions) over the 64 noise
+    realisations of the batching workload: each window's events are cut from
+    the full-spectrum data and reconstructed together in one persistent launch
+    (8 subsets x 10 iterations).  The true image of a realisation is the
+    phantom activity scaled so that the model's expected count T sum_n s_n f_n
+    equals that realisation's event count in the window; caudate and putamen
+    means of every image are compared with the true ones (NRMSE and mean bias
+    over realisations, per window)."""
+    import multiprocessing as mp
+
+    from paper_2002_12471_gb300 import synthetic as S
+    counts = S.realisation_counts(64, seed=4)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any CUDA call
+        parts = pool.map(_realisation_events, list(enumerate(counts)))
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g_full, _, ns, ni = S.workload("dat64")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    act = ph.activity.reshape(-1)
+    truth = {k: float(np.dot(w.reshape(-1), act) / w.sum()) for k, w in ph.rois.items()}
+    out = {}
+    times = []
+    for name, e_lo in WINDOWS:
+        g = dict(g_full, e_lo_kev=e_lo)
+        keep = [p[2] >= e_lo for p in parts]
+        n_r = np.array([int(k.sum()) for k in keep])
+        off = np.concatenate([[0], np.cumsum(n_r)]).astype(np.int64)
+        a = torch.from_numpy(np.concatenate([p[0][k] for p, k in zip(parts, keep)])).to(dev)
+        u = torch.from_numpy(np.concatenate([p[1][k] for p, k in zip(parts, keep)])).to(dev)
+        e = torch.from_numpy(np.concatenate([p[2][k] for p, k in zip(parts, keep)])).to(dev)
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            sup = L.lmosem_support(ctx)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sens = torch.zeros((ns, nsup), dtype=torch.float64, device=dev)
+            t0.record(stream)
+            L.lmosem_sensitivity(ctx, ns, sens)
+            L.lmosem_build_model_batch(ctx, a, u, e, off, ns)
+            f = torch.empty((len(counts), nsup), dtype=torch.float32, device=dev)
+            L.lmosem_init_image_batch(ctx, 1.0, f)
+            L.lmosem_iterate_batch(ctx, ni, 1.0, f)
+            t1.record(stream)
+            t1.synchronize()
+            times.append(t0.elapsed_time(t1))
+            fr = f.double().cpu().numpy()
+            s_tot = sens.sum(0).cpu().numpy()
+        finally:
+            L.lmosem_destroy(ctx)
+        expected_per_activity = float(np.dot(s_tot, act[sup]))   # T = 1
+        rel = {k: [] for k in truth}
+        for r in range(len(counts)):
+            scale = n_r[r] / expected_per_activity                 # true image = scale x activity
+            img = np.bincount(sup, weights=fr[r], minlength=act.size)
+            for k, w in ph.rois.items():
+                rel[k].append(float(np.dot(w.reshape(-1), img) / w.sum()) / (scale * truth[k]) - 1.0)
+        out[name] = {"e_lo_kev": e_lo, "events": int(off[-1]),
+                     "nrmse": {k: float(np.sqrt(np.mean(np.square(v)))) for k, v in rel.items()},
+                     "bias": {k: float(np.mean(v)) for k, v in rel.items()},
+                     "std": {k: float(np.std(v)) for k, v in rel.items()}}
+    J = int(sum(counts))
+    return {"metric": METRIC, "value": J * nsup / (times[0] * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": times[0], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events)",
+            "config": {"workload": WORKLOAD_DESC, "realisations": len(counts), "events": J},
+            "windows": out, "ms_per_window": dict(zip([w[0] for w in WINDOWS], times)),
+            "truth_roi_means": truth}
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -871,6 +997,8 @@ def main():
         out = run_batch_bench(args)
     elif WORKLOAD == "surrogate128":
         out = run_surrogate_bench(args)
+    elif WORKLOAD == "windows64":
+        out = run_windows_bench(args)
     else:
         out = run_ours(args, rank, world, local_rank)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
