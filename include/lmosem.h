@@ -226,6 +226,24 @@ lmosem_status lmosem_autotune_batch(lmosem_ctx* ctx, double acq_time, const floa
  * autotuning): chunk_rows in [8, 2^20], ctas_per_sm in [1, 16]. */
 lmosem_status lmosem_set_batch_tiles(lmosem_ctx* ctx, int32_t chunk_rows, int32_t ctas_per_sm);
 
+/* Support initialiser (paper Sec. 2.2, last paragraph: the cost grows with
+ * the non-zero voxels, so the object's boundary is first estimated from a
+ * crude OSEM reconstruction of the binned data).  Bins the events into the
+ * sinogram (angle x position bin, every energy of the window), reconstructs
+ * it over the whole grid with a crude projector (collimator response
+ * integrated over each bin; no attenuation, scatter or energy) by n_iters
+ * iterations of OSEM with n_subsets angle subsets (a mod n_subsets), and
+ * writes h_support[n] = 1 for the pixels within `dilate` pixels (square
+ * neighbourhood) of one with f_n >= threshold * max f, else 0 (host,
+ * nx * ny bytes, row-major; pass it to lmosem_create of the reconstruction).
+ * d_image (device, nx * ny FP32, may be NULL) receives the crude image.  The
+ * context's own support is not used.  Synchronises.  EINVAL for events out
+ * of range (as lmosem_build_model) or arguments outside 1 <= n_subsets <=
+ * n_angles, 1 <= n_iters <= 1000, 0 < threshold <= 1, 0 <= dilate <= 8. */
+lmosem_status lmosem_binned_support(lmosem_ctx* ctx, const int32_t* d_angle, const float* d_u_mm,
+                                    const float* d_e_kev, int64_t n_events, int32_t n_subsets, int32_t n_iters,
+                                    double threshold, int32_t dilate, uint8_t* h_support, float* d_image);
+
 /* Scatter surrogate (the learned form of the first-order scatter sum of paper
  * Eq. 2; the paper itself evaluates that sum exactly).
  *

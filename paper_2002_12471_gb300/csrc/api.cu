@@ -510,6 +510,23 @@ lmosem_status lmosem_model_rows(lmosem_ctx* c, const int64_t* d_ids, int64_t n, 
     return run_model_rows(c, d_ids, n, d_out);
 }
 
+lmosem_status lmosem_binned_support(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
+                                    const float* d_e_kev, int64_t n_events, int32_t n_subsets, int32_t n_iters,
+                                    double threshold, int32_t dilate, uint8_t* h_support, float* d_image) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_angle || !d_u_mm || !d_e_kev || !h_support) return fail(c, LMOSEM_EINVAL, "null argument");
+    if (n_events < 1 || n_events >= (int64_t(1) << 31))
+        return fail(c, LMOSEM_EINVAL, "n_events must be in [1, 2^31)");
+    if (n_subsets < 1 || n_subsets > c->n_angles || n_iters < 1 || n_iters > 1000 || !(threshold > 0.0) ||
+        !(threshold <= 1.0) || dilate < 0 || dilate > 8)
+        return fail(c, LMOSEM_EINVAL,
+                    "need 1 <= n_subsets <= n_angles, 1 <= n_iters <= 1000, 0 < threshold <= 1, 0 <= dilate <= 8");
+    lmosem_status st = validate_events(c, d_angle, d_u_mm, d_e_kev, n_events);
+    if (st) return st;
+    return run_binned_support(c, d_angle, d_u_mm, n_events, n_subsets, n_iters, threshold, dilate, h_support,
+                              d_image);
+}
+
 lmosem_status lmosem_surrogate_samples(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
                                        const float* d_e_kev, int64_t n_events, float* d_features,
                                        float* d_log_scatter) {

@@ -193,6 +193,13 @@ void dev_free(T** p) {
 // ---- host entry points implemented in the other translation units
 lmosem_status build_tables(lmosem_ctx* c);                      // siddon.cu
 // h_offsets: n_real + 1 event offsets of the realisations (nullptr: one)
+// EINVAL unless every event's angle, position and energy are in range (synchronises)
+lmosem_status validate_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u, const float* d_e,
+                              int64_t n);
+// support.cu: the binned-OSEM support initialiser
+lmosem_status run_binned_support(lmosem_ctx* c, const int32_t* d_angle, const float* d_u, int64_t n,
+                                 int n_subsets, int n_iters, double threshold, int dilate,
+                                 uint8_t* h_support, float* d_image);
 lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
                           const float* d_e, int64_t n, int n_subsets,
                           const int64_t* h_offsets, int n_real);  // sort.cu

@@ -199,9 +199,8 @@ lmosem_status counting_pass(lmosem_ctx* c, const Digit& dg, int ndig, const int3
 
 }  // namespace
 
-lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
-                          const float* d_e, int64_t n, int n_subsets, const int64_t* h_offsets,
-                          int n_real) {
+lmosem_status validate_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u, const float* d_e,
+                              int64_t n) {
     lmosem_status st;
     const float half = (float)(0.5 * c->n_bins * c->bin_mm);
     int32_t* d_bad = nullptr;
@@ -217,6 +216,15 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
     dev_free(&d_bad);
     if (bad) return fail(c, LMOSEM_EINVAL, std::to_string(bad) +
                                                " events have an angle, position or energy out of range");
+    return LMOSEM_OK;
+}
+
+lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
+                          const float* d_e, int64_t n, int n_subsets, const int64_t* h_offsets,
+                          int n_real) {
+    lmosem_status st;
+    if ((st = validate_events(c, d_angle, d_u, d_e, n))) return st;
+    const float half = (float)(0.5 * c->n_bins * c->bin_mm);
 
     const int group = (c->n_angles + n_subsets - 1) / n_subsets;
     const int ndig_a = n_subsets * group;

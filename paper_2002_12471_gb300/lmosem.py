@@ -69,6 +69,8 @@ _vp = ctypes.c_void_p
 _i32, _i64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 
 # name -> (restype, argtypes); mirrors include/lmosem.h
+_GRID = {}   # context -> (ny, nx) of its grid, for the host-side outputs sized by it
+
 SIGNATURES = {
     "lmosem_create": (ctypes.c_int, [ctypes.POINTER(Object), ctypes.POINTER(Geometry),
                                      ctypes.POINTER(Energy), ctypes.POINTER(Options), _vp,
@@ -94,6 +96,8 @@ SIGNATURES = {
     "lmosem_iterate_batch": (ctypes.c_int, [_vp, _i32, _dbl, _vp]),
     "lmosem_autotune_batch": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
     "lmosem_set_batch_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
+    "lmosem_binned_support": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_int32, _vp, _vp]),
     "lmosem_surrogate_samples": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "lmosem_surrogate_train": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(TrainOpts), _vp, _vp]),
     "lmosem_surrogate_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
@@ -173,10 +177,12 @@ def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                          s, ctypes.byref(h))
     if st != OK:
         raise LmosemError(st, "lmosem_create rejected the problem")
+    _GRID[h.value] = (ny, nx)
     return h.value
 
 
 def lmosem_destroy(ctx):
+    _GRID.pop(ctx, None)
     load().lmosem_destroy(ctx)
 
 
@@ -263,6 +269,21 @@ def lmosem_autotune_batch(ctx, acq_time, d_f):
 
 def lmosem_set_batch_tiles(ctx, chunk_rows, ctas_per_sm):
     _check(ctx, load().lmosem_set_batch_tiles(ctx, int(chunk_rows), int(ctas_per_sm)))
+
+
+def lmosem_binned_support(ctx, d_angle, d_u_mm, d_e_kev, n_subsets=4, n_iters=3, threshold=0.15, dilate=0,
+                          d_image=None):
+    """Support mask (ny * nx uint8, host) from the crude binned OSEM.  The
+    defaults cover every pixel of the DaT-like phantoms' activity (at 3, 6
+    and 10 iterations) and none of the air around them."""
+    n = int(d_angle.numel())
+    L = load()
+    ny, nx = _GRID[ctx]
+    mask = np.zeros(ny * nx, dtype=np.uint8)
+    _check(ctx, L.lmosem_binned_support(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev), n, int(n_subsets),
+                                        int(n_iters), float(threshold), int(dilate), mask.ctypes.data,
+                                        _ptr(d_image) if d_image is not None else None))
+    return mask
 
 
 def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_scatter):
