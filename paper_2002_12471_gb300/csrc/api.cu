@@ -67,23 +67,23 @@ void drop_graph(lmosem_ctx* c) {
 
 void free_model(lmosem_ctx* c) {
     drop_graph(c);
-    dev_free(&c->d_model);
-    dev_free(&c->d_scale);
-    dev_free(&c->d_stage);
-    dev_free(&c->d_perm);
-    dev_free(&c->d_rank);
-    dev_free(&c->d_u_s);
-    dev_free(&c->d_e_s);
-    dev_free(&c->d_a_s);
-    dev_free(&c->d_angle_row0);
-    dev_free(&c->d_angle_cnt);
-    dev_free(&c->d_tile_prefix);
-    dev_free(&c->d_wtab);
-    dev_free(&c->d_bsub_row0);
-    dev_free(&c->d_breal_row0);
-    dev_free(&c->d_bclaim);
-    dev_free(&c->d_bdone);
-    dev_free(&c->d_bpart_batch);
+    dev_free(c, &c->d_model);
+    dev_free(c, &c->d_scale);
+    dev_free(c, &c->d_stage);
+    dev_free(c, &c->d_perm);
+    dev_free(c, &c->d_rank);
+    dev_free(c, &c->d_u_s);
+    dev_free(c, &c->d_e_s);
+    dev_free(c, &c->d_a_s);
+    dev_free(c, &c->d_angle_row0);
+    dev_free(c, &c->d_angle_cnt);
+    dev_free(c, &c->d_tile_prefix);
+    dev_free(c, &c->d_wtab);
+    dev_free(c, &c->d_bsub_row0);
+    dev_free(c, &c->d_breal_row0);
+    dev_free(c, &c->d_bclaim);
+    dev_free(c, &c->d_bdone);
+    dev_free(c, &c->d_bpart_batch);
     c->bpart_batch_floats = 0;
     c->batch_model = false;
     c->use_surrogate = false;
@@ -126,7 +126,7 @@ lmosem_status build_model_common(lmosem_ctx* c, const int32_t* d_angle, const fl
     size_t elem = fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
     {
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, (size_t)n_events * c->ld_model * elem);
+        cudaError_t e = cudaMallocAsync(&p, (size_t)n_events * c->ld_model * elem, c->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             free_model(c);
@@ -195,23 +195,23 @@ void lmosem_destroy(lmosem_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     free_model(c);
-    dev_free(&c->d_mu);
-    dev_free(&c->d_sup);
-    dev_free(&c->d_scat);
-    dev_free(&c->d_trig);
-    dev_free(&c->d_l_edge);
-    dev_free(&c->d_l_pair);
-    dev_free(&c->d_compton);
-    dev_free(&c->d_mpar);
-    dev_free(&c->d_ppar);
-    dev_free(&c->d_du_m);
-    dev_free(&c->d_sens);
-    dev_free(&c->d_sens_angle);
-    dev_free(&c->d_bpart);
-    dev_free(&c->d_llpart);
-    dev_free(&c->d_scalar);
-    dev_free(&c->d_status);
-    dev_free(&c->d_surrogate);
+    dev_free(c, &c->d_mu);
+    dev_free(c, &c->d_sup);
+    dev_free(c, &c->d_scat);
+    dev_free(c, &c->d_trig);
+    dev_free(c, &c->d_l_edge);
+    dev_free(c, &c->d_l_pair);
+    dev_free(c, &c->d_compton);
+    dev_free(c, &c->d_mpar);
+    dev_free(c, &c->d_ppar);
+    dev_free(c, &c->d_du_m);
+    dev_free(c, &c->d_sens);
+    dev_free(c, &c->d_sens_angle);
+    dev_free(c, &c->d_bpart);
+    dev_free(c, &c->d_llpart);
+    dev_free(c, &c->d_scalar);
+    dev_free(c, &c->d_status);
+    dev_free(c, &c->d_surrogate);
     for (auto& r : c->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -242,6 +242,15 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     lmosem_ctx* c = new (std::nothrow) lmosem_ctx();
     if (!c) return LMOSEM_ENOMEM;
     c->stream = (cudaStream_t)stream;
+    {  // keep up to kPoolKeepBytes of freed device memory cached in the default pool
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = kPoolKeepBytes;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     c->nx = obj->nx;
     c->ny = obj->ny;
     c->npix = obj->nx * obj->ny;

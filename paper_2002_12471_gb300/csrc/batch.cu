@@ -444,9 +444,10 @@ lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int3
     c->profile = saved_profile;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    dev_free(&scratch);
+    dev_free(c, &scratch);
     int h = 0;
-    LMOSEM_CK(c, cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    LMOSEM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     if (h) return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait ran out during autotuning");
     c->batch_chunk_rows = best_ch;
     c->batch_ctas_per_sm = best_ct;

@@ -167,26 +167,33 @@ void prof_end(lmosem_ctx* c, int cls);
         if (e_ != cudaSuccess) return ::lmosem::cuda_fail(ctx, e_, "launch");  \
     } while (0)
 
+// Device memory of a context is stream-ordered on the context's stream
+// (cudaMallocAsync / cudaFreeAsync from the device's default pool, which keeps
+// up to kPoolKeepBytes cached between calls): a buffer may be freed right
+// after the launches that use it, and repeated builds reuse the pool's memory
+// instead of paying a device-wide synchronising allocation each time.
+constexpr uint64_t kPoolKeepBytes = uint64_t(16) << 30;
+
 template <typename T>
 lmosem_status dev_alloc(lmosem_ctx* c, T** p, size_t count) {
     if (*p) {
-        cudaFree(*p);
+        cudaFreeAsync(*p, c->stream);
         *p = nullptr;
     }
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        return fail(c, LMOSEM_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+        return fail(c, LMOSEM_ENOMEM, "allocation of " + std::to_string(count * sizeof(T)) +
                                           " bytes failed: " + cudaGetErrorString(e));
     }
     return LMOSEM_OK;
 }
 
 template <typename T>
-void dev_free(T** p) {
-    if (*p) cudaFree(*p);
+void dev_free(lmosem_ctx* c, T** p) {
+    if (*p) cudaFreeAsync(*p, c->stream);
     *p = nullptr;
 }
 

@@ -580,9 +580,9 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     LMOSEM_CK(c, cudaMemcpyAsync(&h, tb.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     if (h_loss) *h_loss = h;
-    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&tb.X); dev_free(&tb.XT);
-    dev_free(&tb.H); dev_free(&tb.HT); dev_free(&tb.dz); dev_free(&tb.dzT); dev_free(&tb.t);
-    dev_free(&tb.y); dev_free(&tb.dy); dev_free(&tb.gtmp); dev_free(&tb.loss);
+    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &tb.X); dev_free(c, &tb.XT);
+    dev_free(c, &tb.H); dev_free(c, &tb.HT); dev_free(c, &tb.dz); dev_free(c, &tb.dzT); dev_free(c, &tb.t);
+    dev_free(c, &tb.y); dev_free(c, &tb.dy); dev_free(c, &tb.gtmp); dev_free(c, &tb.loss);
     return LMOSEM_OK;
 }
 
@@ -632,11 +632,11 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
         LMOSEM_CK(c, cudaMemcpyAsync(h_loss_curve, d_curve, sizeof(double) * steps, cudaMemcpyDeviceToHost,
                                      c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&tb.X); dev_free(&tb.H);
-    dev_free(&tb.HT); dev_free(&tb.dz); dev_free(&tb.dzT); dev_free(&tb.t); dev_free(&tb.y);
-    dev_free(&tb.dy); dev_free(&tb.gtmp); dev_free(&tb.grad); dev_free(&tb.m); dev_free(&tb.v);
-    dev_free(&d_curve);
-    dev_free(&d_floor);
+    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &tb.X); dev_free(c, &tb.H);
+    dev_free(c, &tb.HT); dev_free(c, &tb.dz); dev_free(c, &tb.dzT); dev_free(c, &tb.t); dev_free(c, &tb.y);
+    dev_free(c, &tb.dy); dev_free(c, &tb.gtmp); dev_free(c, &tb.grad); dev_free(c, &tb.m); dev_free(c, &tb.v);
+    dev_free(c, &d_curve);
+    dev_free(c, &d_floor);
     return LMOSEM_OK;
 }
 
@@ -657,7 +657,7 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
     if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;
     st = take_status(c);   // synchronises
-    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&w.wimg); dev_free(&X); dev_free(&H);
+    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &w.wimg); dev_free(c, &X); dev_free(c, &H);
     return st;
 }
 
@@ -725,8 +725,8 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     }
     st = take_status(c);   // synchronises
-    dev_free(&w.w1); dev_free(&w.w234); dev_free(&w.w234t); dev_free(&w.wimg); dev_free(&X); dev_free(&H);
-    dev_free(&y);
+    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &w.wimg); dev_free(c, &X); dev_free(c, &H);
+    dev_free(c, &y);
     return st;
 }
 

@@ -552,9 +552,9 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         }
     }
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(&d_all);
-    dev_free(&c->d_wtab);
-    dev_free(&c->d_stage);
+    dev_free(c, &d_all);
+    dev_free(c, &c->d_wtab);
+    dev_free(c, &c->d_stage);
     return LMOSEM_OK;
 }
 

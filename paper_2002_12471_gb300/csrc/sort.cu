@@ -213,7 +213,7 @@ lmosem_status validate_events(lmosem_ctx* c, const int32_t* d_angle, const float
     int32_t bad = 0;
     LMOSEM_CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(&d_bad);
+    dev_free(c, &d_bad);
     if (bad) return fail(c, LMOSEM_EINVAL, std::to_string(bad) +
                                                " events have an angle, position or energy out of range");
     return LMOSEM_OK;
@@ -280,12 +280,12 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
     LMOSEM_CK(c, cudaMemcpyAsync(h_cnt.data(), cnt, h_cnt.size() * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(&H);
-    dev_free(&tot);
-    dev_free(&p1);
-    dev_free(&p2);
-    dev_free(&cnt);
-    dev_free(&d_off);
+    dev_free(c, &H);
+    dev_free(c, &tot);
+    dev_free(c, &p1);
+    dev_free(c, &p2);
+    dev_free(c, &cnt);
+    dev_free(c, &d_off);
 
     // rows of (realisation, angle) and of (realisation, subset), in sorted order
     c->n_real = n_real;

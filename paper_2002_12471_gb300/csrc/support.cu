@@ -215,12 +215,12 @@ lmosem_status run_binned_support(lmosem_ctx* c, const int32_t* d_angle, const fl
     LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
     LMOSEM_CK(c, cudaMemcpyAsync(h_support, mask, npix, cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(&geo);
-    dev_free(&sino);
-    dev_free(&sens);
-    dev_free(&y);
-    dev_free(&mask);
-    dev_free(&fown);
+    dev_free(c, &geo);
+    dev_free(c, &sino);
+    dev_free(c, &sens);
+    dev_free(c, &y);
+    dev_free(c, &mask);
+    dev_free(c, &fown);
     return LMOSEM_OK;
 }
 
