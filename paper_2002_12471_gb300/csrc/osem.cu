@@ -560,6 +560,15 @@ lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
     if (c->ring_rows > 0) G = std::min(kRingMaxG, c->ring_rows);
     int S = (int)std::max<int64_t>(2, std::min<int64_t>(kRingMaxStages, (96 << 10) / (G * rb)));
     if (c->ring_stages > 0) S = std::max(2, std::min(kRingMaxStages, c->ring_stages));
+    // a caller-chosen shape is cut to the shared memory a CTA may opt into:
+    // fewer stages first (at least two), then fewer rows per stage
+    int dev0 = 0, smem_max = 0;
+    LMOSEM_CK(c, cudaGetDevice(&dev0));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0));
+    while ((int64_t)S * G * rb > smem_max && S > 2) --S;
+    while ((int64_t)S * G * rb > smem_max && G > 1) --G;
+    if ((int64_t)S * G * rb > smem_max)  // two stages of one row do not fit: use the register pass
+        return launch_pass_reg_t<H, VPT, BACK>(c, A0, rows, nt);
     const size_t smem = (size_t)S * G * rb;
     LMOSEM_CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;

@@ -220,6 +220,17 @@ def test_ring_pass_variant_matches_oracle(rows_stages):
     np.testing.assert_allclose(out["loglik"], ll_ref, rtol=1e-6)
 
 
+def test_ring_pass_shape_is_cut_to_shared_memory():
+    """A caller-chosen ring shape larger than a CTA's shared memory (8 rows x
+    8 stages of 22.6 KB rows at 128 x 128) is cut to fit and reconstructs
+    what the register pass does."""
+    ph, g, J, ns, ni = S.workload("dat128")
+    ev = S.simulate_events(ph, g, 3000, seed=14)
+    ref = gpu_reconstruct(ph, g, ev, ns, 2)
+    out = gpu_reconstruct(ph, g, ev, ns, 2, pass_variant=2, ring_rows=8, ring_stages=8)
+    assert oracle.rel_l2(out["f"], ref["f"]) <= 1e-5
+
+
 def test_wait_timeout_reports_etimeout_and_context_survives():
     """A bounded device wait that runs out (a one-cycle budget injected through
     the options; the bulk copies still complete and are drained) makes
