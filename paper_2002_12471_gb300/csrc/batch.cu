@@ -410,8 +410,9 @@ lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int3
     const int ctas[] = {1, 2, 3, 4};
     if ((st = ensure_batch_buffers(c, chunks[0]))) return st;
     float* scratch = nullptr;
+    Scratch tmp(c);
     const size_t nimg = (size_t)c->n_real * c->n_sup;
-    if ((st = dev_alloc(c, &scratch, nimg))) return st;
+    if ((st = tmp.alloc(&scratch, nimg))) return st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     LMOSEM_CK(c, cudaEventCreate(&e0));
     LMOSEM_CK(c, cudaEventCreate(&e1));
@@ -444,7 +445,6 @@ lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int3
     c->profile = saved_profile;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    dev_free(c, &scratch);
     int h = 0;
     LMOSEM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));

@@ -197,6 +197,33 @@ void dev_free(lmosem_ctx* c, T** p) {
     *p = nullptr;
 }
 
+// Device buffers local to one call: allocated through the guard, freed
+// (stream-ordered) when the guard goes out of scope, on every return path.
+// Declare the guard after the pointers it owns.
+class Scratch {
+public:
+    explicit Scratch(lmosem_ctx* c) : c_(c) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    ~Scratch() {
+        for (void** p : owned_)
+            if (*p) {
+                cudaFreeAsync(*p, c_->stream);
+                *p = nullptr;
+            }
+    }
+    template <typename T>
+    lmosem_status alloc(T** p, size_t count) {
+        lmosem_status st = dev_alloc(c_, p, count);
+        if (st == LMOSEM_OK) owned_.push_back(reinterpret_cast<void**>(p));
+        return st;
+    }
+
+private:
+    lmosem_ctx* c_;
+    std::vector<void**> owned_;
+};
+
 // ---- host entry points implemented in the other translation units
 lmosem_status build_tables(lmosem_ctx* c);                      // siddon.cu
 // h_offsets: n_real + 1 event offsets of the realisations (nullptr: one)

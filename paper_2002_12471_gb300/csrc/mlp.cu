@@ -472,11 +472,11 @@ lmosem_status weights_bf16(lmosem_ctx* c, const float* blob, MlpBufs& w) {
 
 // BF16 weights for inference: the row-major copies and, for the tcgen05
 // kernel, the chunked operand image
-lmosem_status infer_weights(lmosem_ctx* c, const float* blob, MlpBufs& w) {
+lmosem_status infer_weights(lmosem_ctx* c, const float* blob, MlpBufs& w, Scratch& tmp) {
     lmosem_status st;
     if ((st = weights_bf16(c, blob, w))) return st;
     if (c->surrogate_kernel == 1) return LMOSEM_OK;
-    if ((st = dev_alloc(c, &w.wimg, (size_t)3 * kH * kH * 2))) return st;
+    if ((st = tmp.alloc(&w.wimg, (size_t)3 * kH * kH * 2))) return st;
     return weights_img(c, w.w234, w.wimg);
 }
 
@@ -560,13 +560,14 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     const int B = (int)n;
     MlpBufs w;
     TrainBufs tb;
-    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
-        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &tb.X, (size_t)B * kInPad)) ||
-        (st = dev_alloc(c, &tb.XT, (size_t)B * kInPad)) || (st = dev_alloc(c, &tb.H, (size_t)4 * B * kH)) ||
-        (st = dev_alloc(c, &tb.HT, (size_t)B * kH)) || (st = dev_alloc(c, &tb.dz, (size_t)2 * B * kH)) ||
-        (st = dev_alloc(c, &tb.dzT, (size_t)B * kH)) || (st = dev_alloc(c, &tb.t, B)) ||
-        (st = dev_alloc(c, &tb.y, B)) || (st = dev_alloc(c, &tb.dy, B)) ||
-        (st = dev_alloc(c, &tb.gtmp, (size_t)kH * kH)) || (st = dev_alloc(c, &tb.loss, 1)))
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
+        (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&tb.X, (size_t)B * kInPad)) ||
+        (st = tmp.alloc(&tb.XT, (size_t)B * kInPad)) || (st = tmp.alloc(&tb.H, (size_t)4 * B * kH)) ||
+        (st = tmp.alloc(&tb.HT, (size_t)B * kH)) || (st = tmp.alloc(&tb.dz, (size_t)2 * B * kH)) ||
+        (st = tmp.alloc(&tb.dzT, (size_t)B * kH)) || (st = tmp.alloc(&tb.t, B)) ||
+        (st = tmp.alloc(&tb.y, B)) || (st = tmp.alloc(&tb.dy, B)) ||
+        (st = tmp.alloc(&tb.gtmp, (size_t)kH * kH)) || (st = tmp.alloc(&tb.loss, 1)))
         return st;
     LMOSEM_CK(c, cudaMemsetAsync(grad_out, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(tb.loss, 0, sizeof(double), c->stream));
@@ -580,9 +581,6 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     LMOSEM_CK(c, cudaMemcpyAsync(&h, tb.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     if (h_loss) *h_loss = h;
-    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &tb.X); dev_free(c, &tb.XT);
-    dev_free(c, &tb.H); dev_free(c, &tb.HT); dev_free(c, &tb.dz); dev_free(c, &tb.dzT); dev_free(c, &tb.t);
-    dev_free(c, &tb.y); dev_free(c, &tb.dy); dev_free(c, &tb.gtmp); dev_free(c, &tb.loss);
     return LMOSEM_OK;
 }
 
@@ -594,14 +592,15 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
     TrainBufs tb;
     double* d_curve = nullptr;
     float* d_floor = nullptr;
-    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
-        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &tb.X, (size_t)B * kInPad)) ||
-        (st = dev_alloc(c, &tb.H, (size_t)4 * B * kH)) || (st = dev_alloc(c, &tb.HT, (size_t)B * kH)) ||
-        (st = dev_alloc(c, &tb.dz, (size_t)2 * B * kH)) || (st = dev_alloc(c, &tb.dzT, (size_t)B * kH)) ||
-        (st = dev_alloc(c, &tb.t, B)) || (st = dev_alloc(c, &tb.y, B)) || (st = dev_alloc(c, &tb.dy, B)) ||
-        (st = dev_alloc(c, &tb.gtmp, (size_t)kH * kH)) || (st = dev_alloc(c, &tb.grad, kParams)) ||
-        (st = dev_alloc(c, &tb.m, kParams)) || (st = dev_alloc(c, &tb.v, kParams)) ||
-        (st = dev_alloc(c, &d_curve, std::max(1, steps))) || (st = dev_alloc(c, &d_floor, 1)))
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
+        (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&tb.X, (size_t)B * kInPad)) ||
+        (st = tmp.alloc(&tb.H, (size_t)4 * B * kH)) || (st = tmp.alloc(&tb.HT, (size_t)B * kH)) ||
+        (st = tmp.alloc(&tb.dz, (size_t)2 * B * kH)) || (st = tmp.alloc(&tb.dzT, (size_t)B * kH)) ||
+        (st = tmp.alloc(&tb.t, B)) || (st = tmp.alloc(&tb.y, B)) || (st = tmp.alloc(&tb.dy, B)) ||
+        (st = tmp.alloc(&tb.gtmp, (size_t)kH * kH)) || (st = tmp.alloc(&tb.grad, kParams)) ||
+        (st = tmp.alloc(&tb.m, kParams)) || (st = tmp.alloc(&tb.v, kParams)) ||
+        (st = tmp.alloc(&d_curve, std::max(1, steps))) || (st = tmp.alloc(&d_floor, 1)))
         return st;
     LMOSEM_CK(c, cudaMemsetAsync(tb.m, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(tb.v, 0, sizeof(float) * kParams, c->stream));
@@ -632,11 +631,6 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
         LMOSEM_CK(c, cudaMemcpyAsync(h_loss_curve, d_curve, sizeof(double) * steps, cudaMemcpyDeviceToHost,
                                      c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &tb.X); dev_free(c, &tb.H);
-    dev_free(c, &tb.HT); dev_free(c, &tb.dz); dev_free(c, &tb.dzT); dev_free(c, &tb.t); dev_free(c, &tb.y);
-    dev_free(c, &tb.dy); dev_free(c, &tb.gtmp); dev_free(c, &tb.grad); dev_free(c, &tb.m); dev_free(c, &tb.v);
-    dev_free(c, &d_curve);
-    dev_free(c, &d_floor);
     return LMOSEM_OK;
 }
 
@@ -645,11 +639,12 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     lmosem_status st;
     MlpBufs w;
     __nv_bfloat16 *X = nullptr, *H = nullptr;
-    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
-        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)((n + 127) / 128 * 128) * kInPad)) ||
-        (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)4 * n * kH))))
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
+        (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&X, (size_t)((n + 127) / 128 * 128) * kInPad)) ||
+        (c->surrogate_kernel == 1 && (st = tmp.alloc(&H, (size_t)4 * n * kH))))
         return st;
-    if ((st = infer_weights(c, blob, w))) return st;
+    if ((st = infer_weights(c, blob, w, tmp))) return st;
     LMOSEM_PROF_BEGIN(c);
     k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, nullptr, X, out,
                                                                  c->surrogate_kernel != 1);
@@ -657,7 +652,6 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
     if ((st = forward_infer(c, blob, w, X, Hs, out, n))) return st;
     st = take_status(c);   // synchronises
-    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &w.wimg); dev_free(c, &X); dev_free(c, &H);
     return st;
 }
 
@@ -701,11 +695,12 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
     MlpBufs w;
     __nv_bfloat16 *X = nullptr, *H = nullptr;
     float* y = nullptr;
-    if ((st = dev_alloc(c, &w.w1, kH * kInPad)) || (st = dev_alloc(c, &w.w234, 3 * kH * kH)) ||
-        (st = dev_alloc(c, &w.w234t, 3 * kH * kH)) || (st = dev_alloc(c, &X, (size_t)((M + 127) / 128 * 128) * kInPad)) ||
-        (c->surrogate_kernel == 1 && (st = dev_alloc(c, &H, (size_t)2 * M * kH))) || (st = dev_alloc(c, &y, M)))
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
+        (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&X, (size_t)((M + 127) / 128 * 128) * kInPad)) ||
+        (c->surrogate_kernel == 1 && (st = tmp.alloc(&H, (size_t)2 * M * kH))) || (st = tmp.alloc(&y, M)))
         return st;
-    if ((st = infer_weights(c, c->d_surrogate, w))) return st;
+    if ((st = infer_weights(c, c->d_surrogate, w, tmp))) return st;
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double se0 = fw2s * c->fwhm_frac * c->e0;
     __nv_bfloat16* Hs[4] = {H, H + M * kH, H, H + M * kH};  // ping-pong
@@ -725,8 +720,6 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     }
     st = take_status(c);   // synchronises
-    dev_free(c, &w.w1); dev_free(c, &w.w234); dev_free(c, &w.w234t); dev_free(c, &w.wimg); dev_free(c, &X); dev_free(c, &H);
-    dev_free(c, &y);
     return st;
 }
 

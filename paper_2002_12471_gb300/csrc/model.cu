@@ -446,7 +446,8 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     host_all.insert(host_all.end(), e_prefix.begin(), e_prefix.end());
     host_all.insert(host_all.end(), slot_angle.begin(), slot_angle.end());
     int32_t* d_all = nullptr;
-    if ((st = dev_alloc(c, &d_all, host_all.size()))) return st;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&d_all, host_all.size()))) return st;
     LMOSEM_CK(c, cudaMemcpyAsync(d_all, host_all.data(), host_all.size() * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, c->stream));
     const int32_t* d_ent_angle = d_all;
@@ -552,7 +553,6 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         }
     }
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, &d_all);
     dev_free(c, &c->d_wtab);
     dev_free(c, &c->d_stage);
     return LMOSEM_OK;

@@ -204,7 +204,8 @@ lmosem_status validate_events(lmosem_ctx* c, const int32_t* d_angle, const float
     lmosem_status st;
     const float half = (float)(0.5 * c->n_bins * c->bin_mm);
     int32_t* d_bad = nullptr;
-    if ((st = dev_alloc(c, &d_bad, 1))) return st;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&d_bad, 1))) return st;
     LMOSEM_CK(c, cudaMemsetAsync(d_bad, 0, sizeof(int32_t), c->stream));
     LMOSEM_PROF_BEGIN(c);
     k_check_events<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(
@@ -213,7 +214,6 @@ lmosem_status validate_events(lmosem_ctx* c, const int32_t* d_angle, const float
     int32_t bad = 0;
     LMOSEM_CK(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, &d_bad);
     if (bad) return fail(c, LMOSEM_EINVAL, std::to_string(bad) +
                                                " events have an angle, position or energy out of range");
     return LMOSEM_OK;
@@ -238,18 +238,19 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
     const int sblk = (int)((hn + kScanBlock * 4 - 1) / (kScanBlock * 4));
     int32_t *H = nullptr, *tot = nullptr, *p1 = nullptr, *p2 = nullptr, *cnt = nullptr;
     int64_t* d_off = nullptr;
-    if ((st = dev_alloc(c, &H, hn))) return st;
-    if ((st = dev_alloc(c, &tot, sblk))) return st;
-    if ((st = dev_alloc(c, &p1, n))) return st;
-    if ((st = dev_alloc(c, &cnt, (size_t)n_real * c->n_angles))) return st;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&H, hn))) return st;
+    if ((st = tmp.alloc(&tot, sblk))) return st;
+    if ((st = tmp.alloc(&p1, n))) return st;
+    if ((st = tmp.alloc(&cnt, (size_t)n_real * c->n_angles))) return st;
     if ((st = dev_alloc(c, &c->d_perm, n))) return st;
     if ((st = dev_alloc(c, &c->d_rank, n))) return st;
     if ((st = dev_alloc(c, &c->d_a_s, n))) return st;
     if ((st = dev_alloc(c, &c->d_u_s, n))) return st;
     if ((st = dev_alloc(c, &c->d_e_s, n))) return st;
     if (n_real > 1) {
-        if ((st = dev_alloc(c, &p2, n))) return st;
-        if ((st = dev_alloc(c, &d_off, n_real + 1))) return st;
+        if ((st = tmp.alloc(&p2, n))) return st;
+        if ((st = tmp.alloc(&d_off, n_real + 1))) return st;
         LMOSEM_CK(c, cudaMemcpyAsync(d_off, h_offsets, (n_real + 1) * sizeof(int64_t),
                                      cudaMemcpyHostToDevice, c->stream));
     }
@@ -280,12 +281,6 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
     LMOSEM_CK(c, cudaMemcpyAsync(h_cnt.data(), cnt, h_cnt.size() * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, &H);
-    dev_free(c, &tot);
-    dev_free(c, &p1);
-    dev_free(c, &p2);
-    dev_free(c, &cnt);
-    dev_free(c, &d_off);
 
     // rows of (realisation, angle) and of (realisation, subset), in sorted order
     c->n_real = n_real;

@@ -177,9 +177,10 @@ lmosem_status run_binned_support(lmosem_ctx* c, const int32_t* d_angle, const fl
     unsigned int* sino = nullptr;
     float *sens = nullptr, *y = nullptr, *fown = nullptr;
     uint8_t* mask = nullptr;
-    if ((st = dev_alloc(c, &geo, (size_t)na * npix)) || (st = dev_alloc(c, &sino, (size_t)na * nb)) ||
-        (st = dev_alloc(c, &sens, (size_t)n_subsets * npix)) || (st = dev_alloc(c, &y, (size_t)na * nb)) ||
-        (st = dev_alloc(c, &mask, npix)) || (!d_image && (st = dev_alloc(c, &fown, npix))))
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&geo, (size_t)na * npix)) || (st = tmp.alloc(&sino, (size_t)na * nb)) ||
+        (st = tmp.alloc(&sens, (size_t)n_subsets * npix)) || (st = tmp.alloc(&y, (size_t)na * nb)) ||
+        (st = tmp.alloc(&mask, npix)) || (!d_image && (st = tmp.alloc(&fown, npix))))
         return st;
     float* f = d_image ? d_image : fown;
     LMOSEM_CK(c, cudaMemsetAsync(sino, 0, sizeof(unsigned int) * na * nb, c->stream));
@@ -215,12 +216,6 @@ lmosem_status run_binned_support(lmosem_ctx* c, const int32_t* d_angle, const fl
     LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
     LMOSEM_CK(c, cudaMemcpyAsync(h_support, mask, npix, cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, &geo);
-    dev_free(c, &sino);
-    dev_free(c, &sens);
-    dev_free(c, &y);
-    dev_free(c, &mask);
-    dev_free(c, &fown);
     return LMOSEM_OK;
 }
 
