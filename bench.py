@@ -732,7 +732,7 @@ def run_surrogate_bench(args):
     J = len(a_h)
     a_d, u_d, e_d = a_h.to(dev), u_h.to(dev), e_h.to(dev)
 
-    train_steps, train_batch, train_floor = 30000, 8192, 12.0
+    train_steps, train_batch, train_floor = 60000, 8192, 10.0
     blob = torch.from_numpy(L.surrogate_init(seed=3)).to(dev)
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
     try:
