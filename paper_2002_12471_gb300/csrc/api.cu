@@ -195,6 +195,7 @@ void lmosem_destroy(lmosem_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     free_model(c);
+    dev_free(c, &c->d_wtab_all);
     dev_free(c, &c->d_mu);
     dev_free(c, &c->d_sup);
     dev_free(c, &c->d_scat);

@@ -88,6 +88,9 @@ struct lmosem_ctx {
     int32_t* d_tile_prefix = nullptr;                // n_angles + 1 cumulative event tiles
     std::vector<int32_t> h_tile_prefix;
     float* d_wtab = nullptr;      // scatter-weight planes (s, b, -lw) of one angle group
+    float* d_wtab_all = nullptr;  // planes of every angle, indexed by angle: built with the
+                                  // sensitivity when they fit the table budget, consumed (and
+                                  // freed) by the next model build
     int64_t wtab_bytes = 0;
 
     // iteration scratch
@@ -239,6 +242,12 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
                           const int64_t* h_offsets, int n_real);  // sort.cu
 lmosem_status build_model_rows(lmosem_ctx* c);                  // model.cu
 lmosem_status compute_sensitivity(lmosem_ctx* c, int n_subsets);  // sens.cu
+// model.cu: every angle's scatter-weight planes into d_wtab_all and, in the
+// same pass, the per-angle sensitivities (arithmetic of the sensitivity
+// kernel: FP32 terms, FP64 every 32 terms); false from wtab_all_fits when
+// the planes of all angles exceed the table budget
+bool wtab_all_fits(const lmosem_ctx* c);
+lmosem_status wtab_all_with_sens(lmosem_ctx* c, double* sens_angle, float w_const_sens, float de0);
 lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll);
 lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out);
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f);

@@ -90,6 +90,73 @@ __global__ void k_wtable(WTabArgs A) {
     base[2 * plane] = nlw;
 }
 
+// Every angle's planes (s, b, -lw) (indexed by angle) and, in the same pass,
+// the per-angle subset-sensitivity sum of s_eff = w D_u D_E over the primary
+// and every scatter path of support pixel n (paper Eq. 7 denominator): the
+// terms are formed as in k_wtable and k_sens_angle (FP32 terms, added into
+// an FP64 accumulator every 32 scatter pixels), so both results are bitwise
+// those of the two separate kernels.
+struct WSensArgs {
+    WTabArgs w;
+    const float4* ppar;   // .w = D_u of the primary
+    const float* du_m;    // [a][m]
+    float w_const_sens;   // D^2 / (2 pi)
+    float de0;            // window mass of the photopeak
+    double* sens_angle;   // [a][n]
+};
+
+__global__ void k_wtable_sens(WSensArgs S) {
+    const WTabArgs& A = S.w;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.y;
+    if (n >= A.ld_w) return;
+    const size_t plane = (size_t)A.n_scat * A.ld_w;
+    float* base = A.wtab + (size_t)a * 3 * plane + n;
+    if (n >= A.n_sup) {  // padding columns: no path
+        for (int k = 0; k < A.n_scat; ++k) {
+            base[(size_t)k * A.ld_w] = 0.0f;
+            base[plane + (size_t)k * A.ld_w] = 0.0f;
+            base[2 * plane + (size_t)k * A.ld_w] = INFINITY;
+        }
+        return;
+    }
+    const int pn = A.sup[n];
+    const float2 trig = A.trig[a];
+    double acc = (double)(expf(-A.l_edge[(size_t)a * A.npix + pn]) * S.ppar[(size_t)a * A.ld_w + n].w * S.de0);
+    const float* lp = A.l_pair + n;
+    const float* le = A.l_edge + (size_t)a * A.npix;
+    const float* du = S.du_m + (size_t)a * A.n_scat;
+    float part = 0.0f;
+    for (int k = 0; k < A.n_scat; ++k) {
+        const int pm = __ldg(A.scat + k);
+        float s = 0.0f, b = 0.0f, nlw = INFINITY;
+        float cpsi, rinv;
+        if (path_geometry(pn, pm, A.nx, A.ny, A.dpx, trig, &cpsi, &rinv)) {
+            float P, kt;
+            compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
+            const float2 cr = compton_lookup(A.compton, cpsi);  // (mu ratio, window mass)
+            const float att = lp[(size_t)k * A.n_sup] + cr.x * __ldg(le + pm);
+            const float mu = __ldg(A.mu + pm);
+            const float e1 = A.e0 * P;
+            const float ri = rsqrtf(e1);
+            nlw = att * kLog2e - log2f(A.w_const * mu * kt * rinv * ri);
+            s = A.cE * ri;
+            b = -e1 * s;
+            const float w = S.w_const_sens * mu * kt * rinv * expf(-att);
+            part = fmaf(w, __ldg(du + k) * cr.y, part);
+        }
+        base[(size_t)k * A.ld_w] = s;
+        base[plane + (size_t)k * A.ld_w] = b;
+        base[2 * plane + (size_t)k * A.ld_w] = nlw;
+        if ((k & 31) == 31) {
+            acc += (double)part;
+            part = 0.0f;
+        }
+    }
+    acc += (double)part;
+    S.sens_angle[(size_t)a * A.n_sup + n] = acc;
+}
+
 struct PathSumArgs {
     const float* u_s;
     const float* e_s;
@@ -378,10 +445,65 @@ __global__ void k_quantize(const float* __restrict__ stage, int64_t ld_stage, in
     if (lane == 0) scale[row0 + r] = c;
 }
 
+// scatter-table arguments of the context (sigma_E^2 = kappa E)
+WTabArgs wtab_args(const lmosem_ctx* c, float* wtab, const int32_t* slot_angle, int s0) {
+    const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;
+    WTabArgs W;
+    W.nx = c->nx;
+    W.ny = c->ny;
+    W.npix = c->npix;
+    W.dpx = (float)c->dpx;
+    W.sup = c->d_sup;
+    W.n_sup = c->n_sup;
+    W.ld_w = c->ld_w;
+    W.scat = c->d_scat;
+    W.n_scat = c->n_scat;
+    W.mu = c->d_mu;
+    W.trig = c->d_trig;
+    W.l_edge = c->d_l_edge;
+    W.l_pair = c->d_l_pair;
+    W.compton = c->d_compton;
+    W.slot_angle = slot_angle;
+    W.s0 = s0;
+    W.eps0 = (float)(c->e0 / kMec2Kev);
+    W.inv_kbar = (float)(1.0 / c->kbar);
+    W.e0 = (float)c->e0;
+    W.w_const = (float)(c->dpx * c->dpx / (2.0 * kPi * sqrt(2.0 * kPi * kappa)));
+    W.cE = (float)sqrt(1.4426950408889634 / (2.0 * kappa));
+    W.wtab = wtab;
+    return W;
+}
+
+int64_t wtab_angle_floats(const lmosem_ctx* c) { return (int64_t)3 * c->n_scat * c->ld_w; }
+
 }  // namespace
 
+bool wtab_all_fits(const lmosem_ctx* c) {
+    return (int64_t)c->n_angles * wtab_angle_floats(c) * (int64_t)sizeof(float) <= c->table_budget;
+}
+
+lmosem_status wtab_all_with_sens(lmosem_ctx* c, double* sens_angle, float w_const_sens, float de0) {
+    lmosem_status st;
+    if ((st = dev_alloc(c, &c->d_wtab_all, (size_t)c->n_angles * wtab_angle_floats(c)))) return st;
+    WSensArgs S;
+    S.w = wtab_args(c, c->d_wtab_all, nullptr, 0);
+    S.ppar = c->d_ppar;
+    S.du_m = c->d_du_m;
+    S.w_const_sens = w_const_sens;
+    S.de0 = de0;
+    S.sens_angle = sens_angle;
+    LMOSEM_PROF_BEGIN(c);
+    k_wtable_sens<<<dim3((c->ld_w + 127) / 128, c->n_angles), 128, 0, c->stream>>>(S);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SENS);
+    return LMOSEM_OK;
+}
+
 lmosem_status build_model_rows(lmosem_ctx* c) {
-    if (c->use_surrogate) return build_model_surrogate(c);
+    if (c->use_surrogate) {
+        dev_free(c, &c->d_wtab_all);  // the surrogate form has no use for the tables
+        return build_model_surrogate(c);
+    }
     lmosem_status st;
     const int n_ptiles = c->ld_w / kTN;
     const int group = (c->n_angles + c->n_subsets - 1) / c->n_subsets;
@@ -395,9 +517,12 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     }
     const int ns = (int)slot_angle.size();
 
-    // angle groups bounded by the scatter-table budget (three FP32 planes)
-    const int64_t per_angle = (int64_t)3 * c->n_scat * c->ld_w * sizeof(float);
-    const int gsz = (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
+    // angle groups bounded by the scatter-table budget (three FP32 planes);
+    // one group indexed by angle when the sensitivity pass left every
+    // angle's planes behind
+    const bool pre = c->d_wtab_all != nullptr;
+    const int64_t per_angle = wtab_angle_floats(c) * (int64_t)sizeof(float);
+    const int gsz = pre ? ns : (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
     const int n_groups = (ns + gsz - 1) / gsz;
 
     // launch entries (realisation, angle) of every group, in sorted-row order
@@ -415,7 +540,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
                 if (cnt == 0) continue;
                 if (g_row0[gi] < 0) g_row0[gi] = c->h_angle_row0[k];
                 e_angle.push_back(a);
-                e_wpos.push_back(s - s0);
+                e_wpos.push_back(pre ? a : s - s0);
                 e_row0.push_back((int32_t)c->h_angle_row0[k]);
                 e_cnt.push_back((int32_t)cnt);
                 e_tiles.push_back((int32_t)((cnt + kTJ - 1) / kTJ));
@@ -457,7 +582,8 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const int32_t* d_prefix = d_all + 4 * n_ent;
     const int32_t* d_slot_angle = d_all + 4 * n_ent + e_prefix.size();
 
-    if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * 3 * c->n_scat * c->ld_w))) return st;
+    if (!pre && (st = dev_alloc(c, &c->d_wtab, (size_t)gsz * wtab_angle_floats(c)))) return st;
+    float* wtab = pre ? c->d_wtab_all : c->d_wtab;
     const bool scaled = c->fmt != LMOSEM_MODEL_FP32;
     if (scaled) {
         // scaled rows are staged per group: one realisation, contiguous rows
@@ -475,32 +601,12 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
 
     for (int gi = 0; gi < n_groups; ++gi) {
         const int s0 = gi * gsz, s1 = std::min(ns, s0 + gsz);
-        WTabArgs W;
-        W.nx = c->nx;
-        W.ny = c->ny;
-        W.npix = c->npix;
-        W.dpx = (float)c->dpx;
-        W.sup = c->d_sup;
-        W.n_sup = c->n_sup;
-        W.ld_w = c->ld_w;
-        W.scat = c->d_scat;
-        W.n_scat = c->n_scat;
-        W.mu = c->d_mu;
-        W.trig = c->d_trig;
-        W.l_edge = c->d_l_edge;
-        W.l_pair = c->d_l_pair;
-        W.compton = c->d_compton;
-        W.slot_angle = d_slot_angle;
-        W.s0 = s0;
-        W.eps0 = (float)(c->e0 / kMec2Kev);
-        W.inv_kbar = (float)(1.0 / c->kbar);
-        W.e0 = (float)c->e0;
-        W.w_const = (float)(c->dpx * c->dpx / (2.0 * kPi * sqrt(2.0 * kPi * kappa)));
-        W.cE = (float)sqrt(1.4426950408889634 / (2.0 * kappa));
-        W.wtab = c->d_wtab;
-        LMOSEM_PROF_BEGIN(c);
-        k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, s1 - s0), 256, 0, c->stream>>>(W);
-        LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
+        if (!pre) {
+            WTabArgs W = wtab_args(c, c->d_wtab, d_slot_angle, s0);
+            LMOSEM_PROF_BEGIN(c);
+            k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, s1 - s0), 256, 0, c->stream>>>(W);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
+        }
 
         const int tiles = g_tiles[gi];
         if (tiles == 0) continue;
@@ -515,7 +621,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.tile_prefix = d_prefix + e0 + gi;
         P.n_ent = g_first[gi + 1] - e0;
         P.n_ptiles = n_ptiles;
-        P.wtab = c->d_wtab;
+        P.wtab = wtab;
         P.ld_w = c->ld_w;
         P.n_scat = c->n_scat;
         P.mpar = c->d_mpar;
@@ -554,6 +660,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     }
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     dev_free(c, &c->d_wtab);
+    dev_free(c, &c->d_wtab_all);  // consumed
     dev_free(c, &c->d_stage);
     return LMOSEM_OK;
 }

@@ -110,9 +110,16 @@ lmosem_status compute_sensitivity(lmosem_ctx* c, int n_subsets) {
     A.w_const = (float)(c->dpx * c->dpx / (2.0 * kPi));
     A.de0 = (float)c->de0;
     A.sens_angle = c->d_sens_angle;
-    LMOSEM_PROF_BEGIN(c);
-    k_sens_angle<<<dim3((c->n_sup + 127) / 128, c->n_angles), 128, 0, c->stream>>>(A);
-    LMOSEM_LAUNCHED(c, LMOSEM_K_SENS);
+    if (wtab_all_fits(c)) {
+        // the scatter-weight planes of every angle fit the table budget: build
+        // them in the same pass (same terms) and keep them for the model build
+        if ((st = wtab_all_with_sens(c, c->d_sens_angle, A.w_const, A.de0))) return st;
+    } else {
+        dev_free(c, &c->d_wtab_all);
+        LMOSEM_PROF_BEGIN(c);
+        k_sens_angle<<<dim3((c->n_sup + 127) / 128, c->n_angles), 128, 0, c->stream>>>(A);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SENS);
+    }
     // rows 0..n_subsets-1: s^i; row n_subsets: s = sum_i s^i
     LMOSEM_PROF_BEGIN(c);
     k_sens_reduce<<<(c->n_sup + 255) / 256, 256, 0, c->stream>>>(
