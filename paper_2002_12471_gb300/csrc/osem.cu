@@ -68,6 +68,20 @@ struct Vec<__nv_bfloat16> {
     }
 };
 
+// (a.x b.x + c.x, a.y b.y + c.y) in one packed FP32x2 FMA
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 struct PassArgs {
     const void* model;
     int64_t ld_bytes;        // row stride in bytes
@@ -127,14 +141,16 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
         float d[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            float s = 0.0f;
+            float2 s2 = make_float2(0.0f, 0.0f);  // even and odd columns
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 float p[EPV];
                 Vec<H>::cvt(raw[i][v], p);
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) s = fmaf(p[e], fr[v][e], s);
+                for (int e = 0; e < EPV; e += 2)
+                    s2 = ffma2(make_float2(p[e], p[e + 1]), make_float2(fr[v][e], fr[v][e + 1]), s2);
             }
+            float s = s2.x + s2.y;
 #pragma unroll
             for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             d[i] = s;
@@ -151,12 +167,18 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
             const bool ok = r + i < re && y > 0.0f;
             if constexpr (BACK) {
                 const float inv = ok ? 1.0f / y : 0.0f;
+                const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     float p[EPV];
                     Vec<H>::cvt(raw[i][v], p);
 #pragma unroll
-                    for (int e = 0; e < EPV; ++e) br[v][e] = fmaf(p[e], inv, br[v][e]);
+                    for (int e = 0; e < EPV; e += 2) {
+                        const float2 b2 = ffma2(make_float2(p[e], p[e + 1]), inv2,
+                                                make_float2(br[v][e], br[v][e + 1]));
+                        br[v][e] = b2.x;
+                        br[v][e + 1] = b2.y;
+                    }
                 }
             } else {
                 if (ok && t == i) {
