@@ -99,8 +99,29 @@ struct PassArgs {
 // One pass over rows [r0, r1): thread t owns the 16-byte column vectors
 // t, t + NT, ... (VPT of them); groups of R rows are double-buffered in
 // registers.  BACK: accumulate b; otherwise accumulate the log-likelihood.
+// Rows per pipeline step (R) and minimum CTAs per SM of the register pass,
+// per instance, as measured on GB300 (ms per OSEM iteration, one box):
+//  * FP32, up to 4 vectors per thread: R = 4 or 2, no register cap (a cap
+//    of two CTAs shortens the schedule: 64x64 rows 0.25 vs 0.31 ms);
+//  * FP32, 6 or 8 vectors: R = 1 and two CTAs per SM (one CTA otherwise:
+//    128x128 rows 1.03 vs 1.29 ms);
+//  * 2-byte rows with 3 vectors per thread (twice the elements, and the
+//    registers, per vector): R = 1 and two CTAs per SM, so the conversion
+//    chains of one CTA overlap the other's (128x128 FP16 0.70 vs 0.76 ms);
+//  * other 2-byte shapes: as FP32.
+template <typename H, int VPT>
+constexpr bool pass_half3() { return !std::is_same<H, float>::value && VPT == 3; }
+template <typename H, int VPT>
+constexpr int pass_min_ctas() {
+    return pass_half3<H, VPT>() || (std::is_same<H, float>::value && VPT >= 6) ? 2 : 1;
+}
+template <typename H, int VPT>
+constexpr int pass_rows() {
+    return pass_half3<H, VPT>() ? 1 : (VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4));
+}
+
 template <typename H, int VPT, int R, bool BACK>
-__global__ void __launch_bounds__(kMaxPassThreads) k_pass(PassArgs A) {
+__global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass(PassArgs A) {
     constexpr int EPV = Vec<H>::N;
     __shared__ float red[2][R][kMaxPassThreads / 32];
     __shared__ double llred[kMaxPassThreads / 32];
@@ -552,7 +573,7 @@ PassShape pass_shape(const lmosem_ctx* c) {
 // register-pipelined pass (pass_variant 0 or 1)
 template <typename H, int VPT, bool BACK>
 lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
-    constexpr int R = VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4);
+    constexpr int R = pass_rows<H, VPT>();
     auto kern = k_pass<H, VPT, R, BACK>;
     int per_sm = 0, dev = 0, sms = 0;
     LMOSEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0));
