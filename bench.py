@@ -438,15 +438,24 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+def kernel_source_sha1():
+    """Hash of the path-sum kernel's source text (its argument block through
+    the end of the kernel), so that edits elsewhere in the file keep the
+    committed traffic figure valid."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2002_12471_gb300", "csrc", "model.cu"), "rb").read()
+    i = src.find(b"struct PathSumArgs {")
+    j = src.find(b"\n// Row scaling and rounding", i)
+    return hashlib.sha1(src[i:j] if i >= 0 and j > i else src).hexdigest()[:12]
+
+
 def read_traffic(kernel):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if
     the kernel's source has not changed since it was taken."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2002_12471_gb300", "csrc", "model.cu")
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    h = kernel_source_sha1()
     for ln in open(path):
         parts = dict(p.split("=", 1) for p in ln.split() if "=" in p)
         if parts.get("kernel") == kernel and parts.get("source_sha1") == h:

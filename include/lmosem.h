@@ -93,9 +93,11 @@ typedef struct {
      * their CUDA-graph replay on non-default streams and are not timed. */
     int32_t profile;
     /* Clock-cycle budget of every bounded device wait (the mbarrier waits of
-     * the streaming OSEM pass); 0 selects 2e9 (about one second).  A wait that
-     * runs out abandons the pass and the call returns LMOSEM_ETIMEOUT; the
-     * context stays usable.  Tests set a tiny budget to exercise that path. */
+     * the streaming OSEM pass, the path-sum stage ring, the tensor-core
+     * surrogate and the batch scheduler); 0 selects 2e9 (about one second).
+     * A wait that runs out abandons its kernel and the call returns
+     * LMOSEM_ETIMEOUT; the context stays usable.  Tests set a tiny budget
+     * (here or with lmosem_set_wait_budget) to exercise that path. */
     int64_t wait_budget_cycles;
     /* Streaming-pass implementation (tuning knobs; 0 = automatic):
      * 1 = rows double-buffered in registers, 2 = rows staged in a shared-
@@ -323,6 +325,12 @@ int64_t lmosem_model_bytes(const lmosem_ctx* ctx);
 
 /* Number of kernel launches this context has enqueued so far. */
 int64_t lmosem_launch_count(const lmosem_ctx* ctx);
+
+/* Change the clock-cycle budget of the bounded device waits (see
+ * lmosem_options.wait_budget_cycles; 0 restores 2e9) for the calls that
+ * follow, e.g. to let a test build the model and then make one pass time
+ * out.  EINVAL: negative budget. */
+lmosem_status lmosem_set_wait_budget(lmosem_ctx* ctx, int64_t cycles);
 
 /* Device time (ms) and launch count per kernel class since the last read,
  * from the CUDA events of a context created with opts->profile != 0.

@@ -4,6 +4,7 @@
 // allocates, and enqueues.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <new>
@@ -179,6 +180,13 @@ int32_t lmosem_n_support(const lmosem_ctx* ctx) { return ctx ? ctx->n_sup : 0; }
 int32_t lmosem_n_scatter(const lmosem_ctx* ctx) { return ctx ? ctx->n_scat : 0; }
 int64_t lmosem_launch_count(const lmosem_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+lmosem_status lmosem_set_wait_budget(lmosem_ctx* c, int64_t cycles) {
+    if (!c) return LMOSEM_EINVAL;
+    if (cycles < 0) return fail(c, LMOSEM_EINVAL, "negative wait budget");
+    c->wait_budget = cycles > 0 ? cycles : 2000000000LL;
+    return LMOSEM_OK;
+}
+
 int64_t lmosem_model_bytes(const lmosem_ctx* ctx) {
     if (!ctx || ctx->fmt < 0) return 0;
     int64_t elem = ctx->fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
@@ -199,6 +207,7 @@ void lmosem_destroy(lmosem_ctx* c) {
     dev_free(c, &c->d_mu);
     dev_free(c, &c->d_sup);
     dev_free(c, &c->d_scat);
+    dev_free(c, &c->d_scat_geo);
     dev_free(c, &c->d_trig);
     dev_free(c, &c->d_l_edge);
     dev_free(c, &c->d_l_pair);
@@ -328,7 +337,8 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
 
     lmosem_status st;
     if ((st = dev_alloc(c, &c->d_mu, c->npix)) || (st = dev_alloc(c, &c->d_sup, c->n_sup)) ||
-        (st = dev_alloc(c, &c->d_scat, std::max(1, c->n_scat)))) {
+        (st = dev_alloc(c, &c->d_scat, std::max(1, c->n_scat))) ||
+        (st = dev_alloc(c, &c->d_scat_geo, std::max(1, c->n_scat)))) {
         lmosem_destroy(c);
         return st;
     }
@@ -340,6 +350,22 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     if (e == cudaSuccess && c->n_scat)
         e = cudaMemcpyAsync(c->d_scat, c->h_scat.data(), c->n_scat * sizeof(int32_t),
                             cudaMemcpyHostToDevice, c->stream);
+    // scatter-pixel centres: (ix + 1/2 - nx/2) is exact in FP32, so the one
+    // rounding of the product by the pixel size gives the device's bits
+    std::vector<float4> geo(c->n_scat);
+    for (int k = 0; k < c->n_scat; ++k) {
+        const int pm = c->h_scat[k];
+        const float fx = (float)(pm % c->nx) + 0.5f - 0.5f * (float)c->nx;
+        const float fy = (float)(pm / c->nx) + 0.5f - 0.5f * (float)c->ny;
+        int32_t bits = pm;
+        float fbits;
+        memcpy(&fbits, &bits, sizeof(float));
+        geo[k] = make_float4(fx * (float)c->dpx, fy * (float)c->dpx, mu[pm], fbits);
+    }
+    if (e == cudaSuccess && c->n_scat)
+        e = cudaMemcpyAsync(c->d_scat_geo, geo.data(), c->n_scat * sizeof(float4),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // geo is a stack buffer
     if (e != cudaSuccess) {
         cuda_fail(c, e, "copy of the mu-map");
         lmosem_destroy(c);

@@ -52,6 +52,7 @@ struct lmosem_ctx {
     float* d_mu = nullptr;        // npix
     int32_t* d_sup = nullptr;     // n_sup
     int32_t* d_scat = nullptr;    // n_scat
+    float4* d_scat_geo = nullptr; // n_scat: (x_m, y_m, mu_m, pixel index as int bits)
     float2* d_trig = nullptr;     // n_angles: (cos, sin) theta_a
     float* d_l_edge = nullptr;    // n_angles x npix: mu(E0) integral pixel centre -> edge
     float* d_l_pair = nullptr;    // n_scat x n_sup: integral scatter centre <-> support centre
@@ -285,11 +286,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Pixel centres: the offset (i + 1/2 - n/2) is exact in FP32 and the scale
+// is one rounded product (never fused into a later add), which the host
+// reproduces for the scatter-pixel table.
 __device__ __forceinline__ float pixel_x(int pix, int nx, float dpx) {
-    return ((float)(pix % nx) + 0.5f - 0.5f * (float)nx) * dpx;
+    return __fmul_rn((float)(pix % nx) + 0.5f - 0.5f * (float)nx, dpx);
 }
 __device__ __forceinline__ float pixel_y(int pix, int nx, int ny, float dpx) {
-    return ((float)(pix / nx) + 0.5f - 0.5f * (float)ny) * dpx;
+    return __fmul_rn((float)(pix / nx) + 0.5f - 0.5f * (float)ny, dpx);
 }
 
 // Linear interpolation of the cos(psi) table.
@@ -302,15 +306,17 @@ __device__ __forceinline__ float2 compton_lookup(const float2* tab, float c) {
     return make_float2(fmaf(fr, b.x - a.x, a.x), fmaf(fr, b.y - a.y, a.y));
 }
 
-// Geometry of one scatter path (n -> m at angle a): cos of the deflection
-// angle and 1/|p_m - p_n|.  Returns false when m == n.
-__device__ __forceinline__ bool path_geometry(int pix_n, int pix_m, int nx, int ny, float dpx,
-                                              float2 trig, float* cpsi, float* rinv) {
-    if (pix_n == pix_m) return false;
-    float vx = pixel_x(pix_m, nx, dpx) - pixel_x(pix_n, nx, dpx);
-    float vy = pixel_y(pix_m, nx, ny, dpx) - pixel_y(pix_n, nx, ny, dpx);
+// Geometry of one scatter path (n -> m at angle a) from the two pixel
+// centres: cos of the deflection angle and 1/|p_m - p_n|.  Returns false
+// when m == n.  Every mul-add is written out, so each kernel that forms a
+// path gets the same bits whatever the compiler would have fused.
+__device__ __forceinline__ bool path_geometry_xy(float xn, float yn, float xm, float ym, bool same,
+                                                 float2 trig, float* cpsi, float* rinv) {
+    if (same) return false;
+    float vx = xm - xn;
+    float vy = ym - yn;
     float ri = rsqrtf(fmaf(vx, vx, vy * vy));
-    float c = (vx * trig.x + vy * trig.y) * ri;
+    float c = fmaf(vx, trig.x, vy * trig.y) * ri;  // one contraction, fixed in the source
     *cpsi = fminf(fmaxf(c, -1.0f), 1.0f);
     *rinv = ri;
     return true;

@@ -451,7 +451,7 @@ lmosem_status take_status(lmosem_ctx* c) {
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     if (!h) return LMOSEM_OK;
     LMOSEM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
-    return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait of the surrogate inference ran out");
+    return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait ran out");
 }
 
 // hidden weights (3 x 256 x 256, row-major [layer][out][in]) to the chunked

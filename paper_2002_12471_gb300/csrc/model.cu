@@ -25,6 +25,9 @@
 // (|u_j - u_m| <= k_sigma sigma_u(m)); terms outside that cut for a given
 // event are exactly zero.  The table slices of the next 16 scatter pixels are
 // copied into shared memory with cp.async while the current 16 are summed.
+// A warp (8 events) skips the staged scatter pixels outside the cut of all
+// of its events, and a last column tile with few live columns runs in a
+// narrow form (one event per thread); both leave every result bit unchanged.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -46,6 +49,7 @@ struct WTabArgs {
     const int32_t* sup;
     int n_sup, ld_w;
     const int32_t* scat;
+    const float4* scat_geo;     // (x_m, y_m, mu_m, pixel index bits)
     int n_scat;
     const float* mu;
     const float2* trig;
@@ -69,16 +73,19 @@ __global__ void k_wtable(WTabArgs A) {
     float s = 0.0f, b = 0.0f, nlw = INFINITY;
     if (n < A.n_sup) {
         int a = A.slot_angle[A.s0 + g];
-        int pn = A.sup[n], pm = A.scat[k];
+        int pn = A.sup[n];
+        const float4 gm = __ldg(A.scat_geo + k);
+        const int pm = __float_as_int(gm.w);
         float cpsi, rinv;
-        if (path_geometry(pn, pm, A.nx, A.ny, A.dpx, A.trig[a], &cpsi, &rinv)) {
+        if (path_geometry_xy(pixel_x(pn, A.nx, A.dpx), pixel_y(pn, A.nx, A.ny, A.dpx), gm.x, gm.y,
+                             pn == pm, A.trig[a], &cpsi, &rinv)) {
             float P, kt;
             compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
             float e1 = A.e0 * P;
             float ratio = compton_lookup(A.compton, cpsi).x;
-            float att = A.l_pair[(size_t)k * A.n_sup + n] + ratio * A.l_edge[(size_t)a * A.npix + pm];
+            float att = fmaf(ratio, A.l_edge[(size_t)a * A.npix + pm], A.l_pair[(size_t)k * A.n_sup + n]);
             float ri = rsqrtf(e1);
-            nlw = att * kLog2e - log2f(A.w_const * A.mu[pm] * kt * rinv * ri);
+            nlw = fmaf(att, kLog2e, -log2f(A.w_const * gm.z * kt * rinv * ri));
             s = A.cE * ri;
             b = -e1 * s;
         }
@@ -121,6 +128,7 @@ __global__ void k_wtable_sens(WSensArgs S) {
         return;
     }
     const int pn = A.sup[n];
+    const float xn = pixel_x(pn, A.nx, A.dpx), yn = pixel_y(pn, A.nx, A.ny, A.dpx);
     const float2 trig = A.trig[a];
     double acc = (double)(expf(-A.l_edge[(size_t)a * A.npix + pn]) * S.ppar[(size_t)a * A.ld_w + n].w * S.de0);
     const float* lp = A.l_pair + n;
@@ -128,18 +136,19 @@ __global__ void k_wtable_sens(WSensArgs S) {
     const float* du = S.du_m + (size_t)a * A.n_scat;
     float part = 0.0f;
     for (int k = 0; k < A.n_scat; ++k) {
-        const int pm = __ldg(A.scat + k);
+        const float4 gm = __ldg(A.scat_geo + k);
+        const int pm = __float_as_int(gm.w);
         float s = 0.0f, b = 0.0f, nlw = INFINITY;
         float cpsi, rinv;
-        if (path_geometry(pn, pm, A.nx, A.ny, A.dpx, trig, &cpsi, &rinv)) {
+        if (path_geometry_xy(xn, yn, gm.x, gm.y, pn == pm, trig, &cpsi, &rinv)) {
             float P, kt;
             compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
             const float2 cr = compton_lookup(A.compton, cpsi);  // (mu ratio, window mass)
-            const float att = lp[(size_t)k * A.n_sup] + cr.x * __ldg(le + pm);
-            const float mu = __ldg(A.mu + pm);
+            const float att = fmaf(cr.x, __ldg(le + pm), lp[(size_t)k * A.n_sup]);
+            const float mu = gm.z;
             const float e1 = A.e0 * P;
             const float ri = rsqrtf(e1);
-            nlw = att * kLog2e - log2f(A.w_const * mu * kt * rinv * ri);
+            nlw = fmaf(att, kLog2e, -log2f(A.w_const * mu * kt * rinv * ri));
             s = A.cE * ri;
             b = -e1 * s;
             const float w = S.w_const_sens * mu * kt * rinv * expf(-att);
@@ -167,7 +176,8 @@ struct PathSumArgs {
     const int32_t* ent_cnt;      // rows
     const int32_t* tile_prefix;  // cumulative event tiles, tile_prefix[0] = 0
     int n_ent;
-    int n_ptiles;
+    int pt0, n_pt;               // column tiles pt0 .. pt0 + n_pt - 1 in this launch
+    int nq_tail;                 // narrow form: live 4-column groups of its tile
     const float* wtab;
     int ld_w, n_scat;
     const float4* mpar;          // [a][m]
@@ -203,52 +213,40 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// shared-memory layout of k_pathsum, in floats
-constexpr int kPlaneF = kStage * kTN;                 // one plane of one stage
-constexpr int kOffPlanes = 0;                         // [2][3][kStage][kTN]
-constexpr int kOffU = kOffPlanes + 2 * 3 * kPlaneF;   // [kStage][kTJ] float2
-constexpr int kOffMp = kOffU + 2 * kStage * kTJ;      // [2][kStage] float4
-constexpr int kOffEv = kOffMp + 2 * kStage * 4;       // u[kTJ], e[kTJ]
-constexpr int kOffMisc = kOffEv + 2 * kTJ;            // 16 ints
-constexpr int kOffList = kOffMisc + 16;               // n_scat ints
+// ---- per-tile setup shared by both forms
 
-__global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
-    extern __shared__ float4 smem4[];
-    float* sm = reinterpret_cast<float*>(smem4);
-    float* planes = sm + kOffPlanes;
-    float2* sU = reinterpret_cast<float2*>(sm + kOffU);
-    float4* mp = reinterpret_cast<float4*>(sm + kOffMp);
-    float* ev_u = sm + kOffEv;
-    float* ev_e = ev_u + kTJ;
-    int* misc = reinterpret_cast<int*>(sm + kOffMisc);
-    int* mlist = reinterpret_cast<int*>(sm + kOffList);
-    float* red = reinterpret_cast<float*>(misc);
+// Where a CTA's event tile sits, and the scatter pixels whose cut interval
+// reaches any of its events (the strip union), compacted into mlist.
+struct TileInfo {
+    int ent, a, nr, n0, nm;
+    int64_t r0;
+};
 
+__device__ __forceinline__ TileInfo tile_setup(const PathSumArgs& A, int et, int pt, float* ev_u,
+                                               float* ev_e, int* misc, int* mlist) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int et = blockIdx.x / A.n_ptiles, pt = blockIdx.x % A.n_ptiles;
-
-    // entry (realisation, angle) of this event tile
-    int lo = 0, hi = A.n_ent - 1;
+    float* red = reinterpret_cast<float*>(misc);
+    TileInfo T;
+    int lo = 0, hi = A.n_ent - 1;  // entry (realisation, angle) of the event tile
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (A.tile_prefix[mid] <= et) lo = mid; else hi = mid - 1;
     }
-    const int ent = lo;
-    const int a = A.ent_angle[ent];
-    const int tile = et - A.tile_prefix[ent];
-    const int64_t r0 = (int64_t)A.ent_row0[ent] + (int64_t)tile * kTJ;
-    const int nr = min(kTJ, A.ent_cnt[ent] - tile * kTJ);
-    const int n0 = pt * kTN;
+    T.ent = lo;
+    T.a = A.ent_angle[lo];
+    const int tile = et - A.tile_prefix[lo];
+    T.r0 = (int64_t)A.ent_row0[lo] + (int64_t)tile * kTJ;
+    T.nr = min(kTJ, A.ent_cnt[lo] - tile * kTJ);
+    T.n0 = pt * kTN;
 
     if (tid < kTJ) {
-        ev_u[tid] = tid < nr ? A.u_s[r0 + tid] : 1e30f;
-        ev_e[tid] = tid < nr ? A.e_s[r0 + tid] : 0.0f;
+        ev_u[tid] = tid < T.nr ? A.u_s[T.r0 + tid] : 1e30f;
+        ev_e[tid] = tid < T.nr ? A.e_s[T.r0 + tid] : 0.0f;
     }
     __syncthreads();
-    // position range of the tile's events
-    if (warp == 0) {
+    if (warp == 0) {  // position range of the tile's events
         float mn = INFINITY, mx = -INFINITY;
-        for (int j = lane; j < nr; j += 32) {
+        for (int j = lane; j < T.nr; j += 32) {
             mn = fminf(mn, ev_u[j]);
             mx = fmaxf(mx, ev_u[j]);
         }
@@ -265,10 +263,9 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     const float umin = red[8], umax = red[9];
     __syncthreads();
 
-    // scatter pixels whose cut interval reaches the tile (block compaction)
-    const float4* mp_a = A.mpar + (size_t)a * A.n_scat;
+    const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
     int nm = 0;
-    for (int m0 = 0; m0 < A.n_scat; m0 += kBuildThreads) {
+    for (int m0 = 0; m0 < A.n_scat; m0 += kBuildThreads) {  // block compaction
         int m = m0 + tid;
         bool in = false;
         if (m < A.n_scat) {
@@ -288,86 +285,261 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         __syncthreads();
         nm += total;
     }
+    T.nm = nm;
+    return T;
+}
+
+// primary path of event (uj, ej) at 4 support pixels
+__device__ __forceinline__ void primary4(const PathSumArgs& A, const float4* pp, float uj, float ej,
+                                         float2& lo, float2& hi) {
+    const float te = (ej - A.e0) * A.sE0;
+    const float le = fmaf(-te, te, A.lE0);
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float t = (uj - pp[q].x) * pp[q].y;
+        v[q] = A.scatter_only ? 0.0f : ex2_approx(fmaf(-t, t, pp[q].z + le));
+    }
+    lo = make_float2(v[0], v[1]);
+    hi = make_float2(v[2], v[3]);
+}
+
+// U_jm of one event (position u) at scatter pixel parameters q
+__device__ __forceinline__ float strip_weight(float u, float4 q) {
+    const float d = u - q.x;
+    const float z = d * q.y;
+    return fabsf(d) <= q.w ? ex2_approx(fmaf(-z, z, q.z)) : 0.0f;
+}
+
+// Scatter terms of one event at 4 support pixels (two packed pairs):
+// acc += U 2^-((E s + b)^2 + w).  Both forms call this, so a column's bits do
+// not depend on the form that computed it.
+__device__ __forceinline__ void terms4(float2 E2, float2 U, float4 S, float4 B, float4 W, float2& lo,
+                                       float2& hi) {
+    const float2 t0 = ffma2(E2, make_float2(S.x, S.y), make_float2(B.x, B.y));
+    const float2 t1 = ffma2(E2, make_float2(S.z, S.w), make_float2(B.z, B.w));
+    const float2 z0 = ffma2(t0, t0, make_float2(W.x, W.y));
+    const float2 z1 = ffma2(t1, t1, make_float2(W.z, W.w));
+    const float2 e0 = make_float2(ex2_approx(-z0.x), ex2_approx(-z0.y));
+    const float2 e1 = make_float2(ex2_approx(-z1.x), ex2_approx(-z1.y));
+    lo = ffma2(U, e0, lo);
+    hi = ffma2(U, e1, hi);
+}
+
+__device__ __forceinline__ void store4(const PathSumArgs& A, float* row, int n, float2 lo, float2 hi) {
+    if (n + 3 < A.n_store) {
+        *reinterpret_cast<float4*>(row + n) = make_float4(lo.x, lo.y, hi.x, hi.y);
+    } else {
+        const float v[4] = {lo.x, lo.y, hi.x, hi.y};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (n + q < A.n_store) row[n + q] = v[q];
+    }
+}
+
+// ---- staging shared by both forms
+//
+// Shared-memory layout, in floats: the three table planes and the position
+// parameters of kStage scatter pixels per stage, double-buffered with
+// cp.async; U_jm of the stage; the tile's events; scratch; the strip union.
+constexpr int kPlaneF = kStage * kTN;                 // one plane of one stage
+constexpr int kOffPlanes = 0;                         // [2][3][kStage][kTN]
+constexpr int kOffU = kOffPlanes + 2 * 3 * kPlaneF;   // [kStage][kTJ] float2
+constexpr int kOffMp = kOffU + 2 * kStage * kTJ;      // [2][kStage] float4
+constexpr int kOffEv = kOffMp + 2 * kStage * 4;       // u[kTJ], e[kTJ]
+constexpr int kOffMisc = kOffEv + 2 * kTJ;            // 16 ints
+constexpr int kOffList = kOffMisc + 16;               // n_scat ints
+
+// stage c0 .. c0 + kStage - 1 of the strip union into buffer buf: the first
+// nq 4-column groups of each plane row (padded scatter pixels get s = b = 0,
+// w = inf and a negative cut, i.e. exact zeros), then commit the group
+__device__ __forceinline__ void stage_issue(const TileInfo& T, const int* mlist, const float* tab,
+                                            size_t plane, int ld_w, const float4* mp_a, float* planes,
+                                            float4* mp, int c0, int buf, int nq) {
+    const int tid = threadIdx.x;
+    for (int k = tid; k < 3 * kStage * nq; k += kBuildThreads) {
+        const int p = k / (kStage * nq);
+        const int r = k - p * (kStage * nq);
+        const int mc = r / nq, q = r - mc * nq;
+        float* dst = planes + ((buf * 3 + p) * kStage + mc) * kTN + 4 * q;
+        if (c0 + mc < T.nm) {
+            cp_async16(dst, tab + p * plane + (size_t)mlist[c0 + mc] * ld_w + 4 * q);
+        } else {
+            const float v = p == 2 ? INFINITY : 0.0f;
+            *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
+        }
+    }
+    if (tid < kStage) {
+        float4* dst = mp + buf * kStage + tid;
+        if (c0 + tid < T.nm) cp_async16(dst, mp_a + mlist[c0 + tid]);
+        else *dst = make_float4(0.0f, 0.0f, -INFINITY, -1.0f);  // cut < 0: U = 0
+    }
+    cp_async_commit();
+}
+
+// ---- narrow form: a last column tile of at most kNarrowQ x 4 live columns
+//
+// Each thread holds one event and up to kNarrowQ / 4 groups of 4 columns
+// (instead of 8 events x 4 columns of a 128-column tile with most lanes
+// idle).
+constexpr int kNarrowQ = 16;
+static_assert(kBuildThreads == 4 * kTJ, "narrow form: 64 events x 4 column groups per pass");
+
+__global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs A) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    float* planes = sm + kOffPlanes;
+    float2* sU = reinterpret_cast<float2*>(sm + kOffU);
+    float4* mp = reinterpret_cast<float4*>(sm + kOffMp);
+    float* ev_u = sm + kOffEv;
+    float* ev_e = ev_u + kTJ;
+    int* misc = reinterpret_cast<int*>(sm + kOffMisc);
+    int* mlist = reinterpret_cast<int*>(sm + kOffList);
+    const int tid = threadIdx.x;
+    const TileInfo T = tile_setup(A, blockIdx.x, A.pt0, ev_u, ev_e, misc, mlist);
+    const int nq = A.nq_tail;
+    constexpr int kQ = kNarrowQ / 4;
+    const int jn = tid & (kTJ - 1), qs = tid / kTJ;  // event, first column group
+    const float2 E2 = make_float2(ev_e[jn], ev_e[jn]);
+    float2 acc[kQ][2];
+#pragma unroll
+    for (int qi = 0; qi < kQ; ++qi) {
+        const int q = qs + 4 * qi;
+        acc[qi][0] = acc[qi][1] = make_float2(0.0f, 0.0f);
+        if (q < nq) {
+            const float4* pp_a = A.ppar + (size_t)T.a * A.ld_w + T.n0 + 4 * q;
+            float4 pp[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pp[c] = __ldg(pp_a + c);
+            primary4(A, pp, ev_u[jn], ev_e[jn], acc[qi][0], acc[qi][1]);
+        }
+    }
+
+    const size_t plane = (size_t)A.n_scat * A.ld_w;
+    const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
+    const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
+    const int nchunks = (T.nm + kStage - 1) / kStage;
+    if (nchunks > 0) stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, 0, 0, nq);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) {
+            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 1) * kStage, buf ^ 1, nq);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        for (int k = tid; k < kStage * kTJ; k += kBuildThreads) {
+            const int mc = k / kTJ, j = k - mc * kTJ;
+            const float U = strip_weight(ev_u[j], mp[buf * kStage + mc]);
+            sU[mc * kTJ + j] = make_float2(U, U);
+        }
+        __syncthreads();
+        const float* pS = planes + (buf * 3 + 0) * kPlaneF;
+        const float* pB = planes + (buf * 3 + 1) * kPlaneF;
+        const float* pW = planes + (buf * 3 + 2) * kPlaneF;
+#pragma unroll 2
+        for (int mc = 0; mc < kStage; ++mc) {
+            const float2 Uj = sU[mc * kTJ + jn];
+#pragma unroll
+            for (int qi = 0; qi < kQ; ++qi) {
+                const int q = qs + 4 * qi;
+                if (q >= nq) break;
+                const int o = mc * kTN + 4 * q;
+                terms4(E2, Uj, *reinterpret_cast<const float4*>(pS + o),
+                       *reinterpret_cast<const float4*>(pB + o), *reinterpret_cast<const float4*>(pW + o),
+                       acc[qi][0], acc[qi][1]);
+            }
+        }
+        __syncthreads();
+    }
+
+    if (jn >= T.nr) return;
+    float* row = A.out + (T.r0 + jn - A.row_base) * A.ld_out;
+#pragma unroll
+    for (int qi = 0; qi < kQ; ++qi) {
+        const int q = qs + 4 * qi;
+        if (q >= nq) break;
+        store4(A, row, T.n0 + 4 * q, acc[qi][0], acc[qi][1]);
+    }
+    const int ngs = (min(A.n_store - T.n0, kTN) + 3) / 4;  // stored groups of the tile
+    for (int q = qs; q < ngs; q += 4)
+        if (q >= nq) store4(A, row, T.n0 + 4 * q, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f));
+}
+
+// ---- wide form: 64 events x 128 columns, 8 events x 4 columns per thread
+//
+// Each stage's U_jm are formed by the whole CTA; bit mc of live[w] is set when
+// some event of warp w (events 8w .. 8w + 7) lies in the cut of the stage's
+// scatter pixel mc, and a warp skips the others, whose terms are exact zeros
+// for all of its events.
+static_assert(kStage * kTJ % kBuildThreads == 0 && kTJ == 64 && kStage <= 32,
+              "U staging: every warp covers 32 events of one scatter pixel per step");
+
+__global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    float* planes = sm + kOffPlanes;
+    float2* sU = reinterpret_cast<float2*>(sm + kOffU);
+    float4* mp = reinterpret_cast<float4*>(sm + kOffMp);
+    float* ev_u = sm + kOffEv;
+    float* ev_e = ev_u + kTJ;
+    int* misc = reinterpret_cast<int*>(sm + kOffMisc);
+    int* mlist = reinterpret_cast<int*>(sm + kOffList);
+    unsigned* live = reinterpret_cast<unsigned*>(misc) + 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TileInfo T = tile_setup(A, blockIdx.x / A.n_pt, A.pt0 + blockIdx.x % A.n_pt, ev_u, ev_e, misc,
+                                  mlist);
 
     // accumulators (pairs of adjacent support pixels), initialised with the
     // primary path
     float2 E2[8];
     float2 acc[8][2];
     {
-        const float4* pp_a = A.ppar + (size_t)a * A.ld_w + n0 + 4 * lane;
+        const float4* pp_a = A.ppar + (size_t)T.a * A.ld_w + T.n0 + 4 * lane;
         float4 pp[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) pp[q] = __ldg(pp_a + q);
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
-            float uj = ev_u[8 * warp + jj];
-            float ej = ev_e[8 * warp + jj];
+            const float uj = ev_u[8 * warp + jj], ej = ev_e[8 * warp + jj];
             E2[jj] = make_float2(ej, ej);
-            float te = (ej - A.e0) * A.sE0;
-            float le = fmaf(-te, te, A.lE0);
-            float v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float t = (uj - pp[q].x) * pp[q].y;
-                v[q] = A.scatter_only ? 0.0f : ex2_approx(fmaf(-t, t, pp[q].z + le));
-            }
-            acc[jj][0] = make_float2(v[0], v[1]);
-            acc[jj][1] = make_float2(v[2], v[3]);
+            primary4(A, pp, uj, ej, acc[jj][0], acc[jj][1]);
         }
     }
 
-    // strip staging: three table planes and the position parameters of
-    // kStage scatter pixels per stage, double-buffered with cp.async
     const size_t plane = (size_t)A.n_scat * A.ld_w;
-    const float* tab = A.wtab + (size_t)A.ent_wpos[ent] * 3 * plane + n0;
-    auto issue = [&](int c0, int buf) {
-        for (int k = tid; k < 3 * kStage * (kTN / 4); k += kBuildThreads) {
-            int p = k / (kStage * (kTN / 4));
-            int r = k - p * (kStage * (kTN / 4));
-            int mc = r / (kTN / 4), q = r - mc * (kTN / 4);
-            float* dst = planes + ((buf * 3 + p) * kStage + mc) * kTN + 4 * q;
-            if (c0 + mc < nm) {
-                cp_async16(dst, tab + p * plane + (size_t)mlist[c0 + mc] * A.ld_w + 4 * q);
-            } else {
-                float v = p == 2 ? INFINITY : 0.0f;
-                *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
-            }
-        }
-        if (tid < kStage) {
-            float4* dst = mp + buf * kStage + tid;
-            if (c0 + tid < nm) cp_async16(dst, mp_a + mlist[c0 + tid]);
-            else *dst = make_float4(0.0f, 0.0f, -INFINITY, -1.0f);  // cut < 0: U = 0
-        }
-        cp_async_commit();
-    };
-
-    const int nchunks = (nm + kStage - 1) / kStage;
-    if (nchunks > 0) issue(0, 0);
+    const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
+    const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
+    const int nchunks = (T.nm + kStage - 1) / kStage;
+    if (nchunks > 0) stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, 0, 0, kTN / 4);
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c & 1;
+        if (tid < kBuildThreads / 32) live[tid] = 0u;
         if (c + 1 < nchunks) {
-            issue((c + 1) * kStage, buf ^ 1);
+            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 1) * kStage, buf ^ 1, kTN / 4);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
-        // U_jm of this stage, duplicated into FP32 pairs
         for (int k = tid; k < kStage * kTJ; k += kBuildThreads) {
-            int mc = k / kTJ, j = k - mc * kTJ;
-            float4 q = mp[buf * kStage + mc];
-            float d = ev_u[j] - q.x;
-            float z = d * q.y;
-            float U = fabsf(d) <= q.w ? ex2_approx(fmaf(-z, z, q.z)) : 0.0f;
+            const int mc = k / kTJ, j = k - mc * kTJ;
+            const float U = strip_weight(ev_u[j], mp[buf * kStage + mc]);
             sU[mc * kTJ + j] = make_float2(U, U);
+            // lanes hold events j = 32 (warp & 1) + lane of one mc
+            const unsigned bal = __ballot_sync(0xffffffffu, U != 0.0f);
+            if (lane < 4 && ((bal >> (8 * lane)) & 0xffu)) atomicOr(live + 4 * (warp & 1) + lane, 1u << mc);
         }
         __syncthreads();
         const float* pS = planes + (buf * 3 + 0) * kPlaneF + 4 * lane;
         const float* pB = planes + (buf * 3 + 1) * kPlaneF + 4 * lane;
         const float* pW = planes + (buf * 3 + 2) * kPlaneF + 4 * lane;
         const float4* pU = reinterpret_cast<const float4*>(sU + 8 * warp);
+        const unsigned wlive = live[warp];
 #pragma unroll 2
         for (int mc = 0; mc < kStage; ++mc) {
+            if (!((wlive >> mc) & 1u)) continue;
             const float4 S = *reinterpret_cast<const float4*>(pS + mc * kTN);
             const float4 B = *reinterpret_cast<const float4*>(pB + mc * kTN);
             const float4 W = *reinterpret_cast<const float4*>(pW + mc * kTN);
@@ -375,43 +547,21 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
             float2 U[8];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                float4 v = up[k];
+                const float4 v = up[k];
                 U[2 * k] = make_float2(v.x, v.y);
                 U[2 * k + 1] = make_float2(v.z, v.w);
             }
-            const float2 S01 = make_float2(S.x, S.y), S23 = make_float2(S.z, S.w);
-            const float2 B01 = make_float2(B.x, B.y), B23 = make_float2(B.z, B.w);
-            const float2 W01 = make_float2(W.x, W.y), W23 = make_float2(W.z, W.w);
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                float2 t0 = ffma2(E2[jj], S01, B01);
-                float2 t1 = ffma2(E2[jj], S23, B23);
-                float2 z0 = ffma2(t0, t0, W01);
-                float2 z1 = ffma2(t1, t1, W23);
-                float2 e0 = make_float2(ex2_approx(-z0.x), ex2_approx(-z0.y));
-                float2 e1 = make_float2(ex2_approx(-z1.x), ex2_approx(-z1.y));
-                acc[jj][0] = ffma2(U[jj], e0, acc[jj][0]);
-                acc[jj][1] = ffma2(U[jj], e1, acc[jj][1]);
-            }
+            for (int jj = 0; jj < 8; ++jj) terms4(E2[jj], U[jj], S, B, W, acc[jj][0], acc[jj][1]);
         }
         __syncthreads();
     }
 
-    // store the tile (columns past the support are exact zeros)
-    const int n = n0 + 4 * lane;
+    const int n = T.n0 + 4 * lane;
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
-        int j = 8 * warp + jj;
-        if (j >= nr) continue;
-        float* row = A.out + (r0 + j - A.row_base) * A.ld_out;
-        float v[4] = {acc[jj][0].x, acc[jj][0].y, acc[jj][1].x, acc[jj][1].y};
-        if (n + 3 < A.n_store) {
-            *reinterpret_cast<float4*>(row + n) = make_float4(v[0], v[1], v[2], v[3]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (n + q < A.n_store) row[n + q] = v[q];
-        }
+        const int j = 8 * warp + jj;
+        if (j < T.nr) store4(A, A.out + (T.r0 + j - A.row_base) * A.ld_out, n, acc[jj][0], acc[jj][1]);
     }
 }
 
@@ -458,6 +608,7 @@ WTabArgs wtab_args(const lmosem_ctx* c, float* wtab, const int32_t* slot_angle, 
     W.n_sup = c->n_sup;
     W.ld_w = c->ld_w;
     W.scat = c->d_scat;
+    W.scat_geo = c->d_scat_geo;
     W.n_scat = c->n_scat;
     W.mu = c->d_mu;
     W.trig = c->d_trig;
@@ -494,7 +645,8 @@ lmosem_status wtab_all_with_sens(lmosem_ctx* c, double* sens_angle, float w_cons
     S.de0 = de0;
     S.sens_angle = sens_angle;
     LMOSEM_PROF_BEGIN(c);
-    k_wtable_sens<<<dim3((c->ld_w + 127) / 128, c->n_angles), 128, 0, c->stream>>>(S);
+    // 64-thread blocks: every (column block, angle) resident at once
+    k_wtable_sens<<<dim3((c->ld_w + 63) / 64, c->n_angles), 64, 0, c->stream>>>(S);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SENS);
     return LMOSEM_OK;
 }
@@ -596,8 +748,13 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;  // sigma_E^2 = kappa E
     const double se0 = sqrt(kappa * c->e0);
     const size_t smem = sizeof(float) * ((size_t)kOffList + c->n_scat);
-    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
+    // a last column tile with few live columns takes the narrow form
+    const int nq_tail = (c->n_sup - (n_ptiles - 1) * kTN + 3) / 4;
+    const bool narrow_tail = nq_tail <= kNarrowQ;
+    const int n_wide = narrow_tail ? n_ptiles - 1 : n_ptiles;
 
     for (int gi = 0; gi < n_groups; ++gi) {
         const int s0 = gi * gsz, s1 = std::min(ns, s0 + gsz);
@@ -620,7 +777,9 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.ent_cnt = d_ent_cnt + e0;
         P.tile_prefix = d_prefix + e0 + gi;
         P.n_ent = g_first[gi + 1] - e0;
-        P.n_ptiles = n_ptiles;
+        P.pt0 = 0;
+        P.n_pt = n_wide;
+        P.nq_tail = nq_tail;
         P.wtab = wtab;
         P.ld_w = c->ld_w;
         P.n_scat = c->n_scat;
@@ -640,9 +799,18 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
             P.out = reinterpret_cast<float*>(c->d_model);
             P.row_base = 0;
         }
-        LMOSEM_PROF_BEGIN(c);
-        k_pathsum<<<(unsigned)((int64_t)tiles * n_ptiles), kBuildThreads, smem, c->stream>>>(P);
-        LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
+        if (n_wide > 0) {
+            LMOSEM_PROF_BEGIN(c);
+            k_pathsum<<<(unsigned)((int64_t)tiles * n_wide), kBuildThreads, smem, c->stream>>>(P);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
+        }
+        if (narrow_tail) {
+            P.pt0 = n_ptiles - 1;
+            P.n_pt = 1;
+            LMOSEM_PROF_BEGIN(c);
+            k_pathsum_narrow<<<(unsigned)tiles, kBuildThreads, smem, c->stream>>>(P);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
+        }
         if (scaled) {
             const int qthreads = 256;
             unsigned qblocks = (unsigned)((grows + qthreads / 32 - 1) / (qthreads / 32));

@@ -22,6 +22,7 @@ struct SensArgs {
     const int32_t* sup;
     int n_sup, ld_w;
     const int32_t* scat;
+    const float4* scat_geo;  // (x_m, y_m, mu_m, pixel index bits)
     int n_scat;
     const float* mu;
     const float2* trig;
@@ -41,6 +42,7 @@ __global__ void k_sens_angle(SensArgs A) {
     int a = blockIdx.y;
     if (n >= A.n_sup) return;
     int pn = A.sup[n];
+    const float xn = pixel_x(pn, A.nx, A.dpx), yn = pixel_y(pn, A.nx, A.ny, A.dpx);
     float2 trig = A.trig[a];
     double acc = (double)(expf(-A.l_edge[(size_t)a * A.npix + pn]) *
                           A.ppar[(size_t)a * A.ld_w + n].w * A.de0);
@@ -49,14 +51,15 @@ __global__ void k_sens_angle(SensArgs A) {
     const float* du = A.du_m + (size_t)a * A.n_scat;
     float part = 0.0f;
     for (int k = 0; k < A.n_scat; ++k) {
-        int pm = __ldg(A.scat + k);
+        const float4 gm = __ldg(A.scat_geo + k);
+        const int pm = __float_as_int(gm.w);
         float cpsi, rinv;
-        if (path_geometry(pn, pm, A.nx, A.ny, A.dpx, trig, &cpsi, &rinv)) {
+        if (path_geometry_xy(xn, yn, gm.x, gm.y, pn == pm, trig, &cpsi, &rinv)) {
             float P, kt;
             compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
             float2 cr = compton_lookup(A.compton, cpsi);  // (mu ratio, window mass)
-            float att = lp[(size_t)k * A.n_sup] + cr.x * __ldg(le + pm);
-            float w = A.w_const * __ldg(A.mu + pm) * kt * rinv * expf(-att);
+            float att = fmaf(cr.x, __ldg(le + pm), lp[(size_t)k * A.n_sup]);
+            float w = A.w_const * gm.z * kt * rinv * expf(-att);
             part = fmaf(w, __ldg(du + k) * cr.y, part);
         }
         if ((k & 31) == 31) {
@@ -97,6 +100,7 @@ lmosem_status compute_sensitivity(lmosem_ctx* c, int n_subsets) {
     A.n_sup = c->n_sup;
     A.ld_w = c->ld_w;
     A.scat = c->d_scat;
+    A.scat_geo = c->d_scat_geo;
     A.n_scat = c->n_scat;
     A.mu = c->d_mu;
     A.trig = c->d_trig;

@@ -89,6 +89,7 @@ SIGNATURES = {
     "lmosem_model_rows": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
     "lmosem_model_bytes": (_i64, [_vp]),
     "lmosem_launch_count": (_i64, [_vp]),
+    "lmosem_set_wait_budget": (ctypes.c_int, [_vp, _i64]),
     "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "lmosem_osem_subiter_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i64, _vp, _vp, _dbl, _vp]),
     "lmosem_build_model_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int]),
@@ -235,6 +236,10 @@ def lmosem_model_bytes(ctx):
 
 def lmosem_launch_count(ctx):
     return int(load().lmosem_launch_count(ctx))
+
+
+def lmosem_set_wait_budget(ctx, cycles):
+    _check(ctx, load().lmosem_set_wait_budget(ctx, int(cycles)))
 
 
 def lmosem_profile_read(ctx):

@@ -20,7 +20,7 @@ def _events(ph, g, counts, seed0):
     return evs, off, cat("angle", np.int32), cat("u_mm", np.float32), cat("e_kev", np.float32)
 
 
-def _batch_run(ph, g, a, u, e, off, ns, ni, tiles=None, autotune=False, **opts):
+def _batch_run(ph, g, a, u, e, off, ns, ni, tiles=None, autotune=False, budget_after_build=0, **opts):
     import torch
 
     import paper_2002_12471_gb300.lmosem as L
@@ -38,6 +38,8 @@ def _batch_run(ph, g, a, u, e, off, ns, ni, tiles=None, autotune=False, **opts):
             choice = L.lmosem_autotune_batch(ctx, 1.0, f)
         if tiles:
             L.lmosem_set_batch_tiles(ctx, *tiles)
+        if budget_after_build:
+            L.lmosem_set_wait_budget(ctx, budget_after_build)
         L.lmosem_iterate_batch(ctx, ni, 1.0, f)
         torch.cuda.synchronize()
         return f.cpu().numpy().astype(np.float64), choice
@@ -100,7 +102,7 @@ def test_batch_wait_budget_runs_out_cleanly(batch32):
     d = batch32
     with pytest.raises(L.LmosemError) as ei:
         _batch_run(d["ph"], d["g"], d["a"], d["u"], d["e"], d["off"], d["ns"], 4, tiles=(64, 4),
-                   wait_budget_cycles=1)
+                   budget_after_build=1)
     assert ei.value.status == L.ETIMEOUT
     f, _ = _batch_run(d["ph"], d["g"], d["a"], d["u"], d["e"], d["off"], d["ns"], 1)
     assert np.all(np.isfinite(f))

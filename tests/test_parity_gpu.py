@@ -190,6 +190,22 @@ def test_bitwise_deterministic():
     assert oracle.rel_l2(c["f"], a["f"]) <= 1e-5
 
 
+@pytest.mark.parametrize("wl,J", [("tiny16", 2000), ("dat32", 6000)])
+def test_table_paths_bitwise(wl, J):
+    """The scatter tables and the sensitivity come out bitwise the same
+    whether every angle's tables are built in the sensitivity pass (one
+    fused kernel) or per angle group by the model build under a small table
+    budget (separate table and sensitivity kernels)."""
+    ph, g, _, ns, ni = S.workload(wl)
+    ev = S.simulate_events(ph, g, J, seed=21)
+    fused = gpu_reconstruct(ph, g, ev, ns, 2, rows=np.arange(J))
+    grouped = gpu_reconstruct(ph, g, ev, ns, 2, rows=np.arange(J), table_budget_bytes=1 << 20)
+    assert grouped["launches"] > fused["launches"]          # the grouped path did run
+    assert np.array_equal(fused["sens"], grouped["sens"])
+    assert np.array_equal(fused["rows"], grouped["rows"])
+    assert np.array_equal(fused["f"], grouped["f"])
+
+
 def test_graph_replay_matches_direct_launches():
     """On a non-default stream lmosem_iterate replays one captured iteration
     as a CUDA graph; the image is bitwise the one of direct launches."""
@@ -232,8 +248,8 @@ def test_ring_pass_shape_is_cut_to_shared_memory():
 
 
 def test_wait_timeout_reports_etimeout_and_context_survives():
-    """A bounded device wait that runs out (a one-cycle budget injected through
-    the options; the bulk copies still complete and are drained) makes
+    """A bounded device wait that runs out (a one-cycle budget set after the
+    model build; the bulk copies still complete and are drained) makes
     lmosem_iterate return LMOSEM_ETIMEOUT without touching the image, and the
     GPU stays usable."""
     import torch
@@ -242,7 +258,7 @@ def test_wait_timeout_reports_etimeout_and_context_survives():
     ph, g, J, ns, ni = S.workload("tiny16")
     ev = S.simulate_events(ph, g, 500, seed=12)
     dev = torch.device("cuda:0")
-    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, wait_budget_cycles=1, pass_variant=2)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, pass_variant=2)
     try:
         L.lmosem_sensitivity(ctx, 2)
         L.lmosem_build_model(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
@@ -250,6 +266,7 @@ def test_wait_timeout_reports_etimeout_and_context_survives():
         f = torch.zeros(L.lmosem_n_support(ctx), dtype=torch.float32, device=dev)
         L.lmosem_init_image(ctx, 1.0, f)
         f0 = f.clone()
+        L.lmosem_set_wait_budget(ctx, 1)
         for _ in range(2):
             with pytest.raises(L.LmosemError) as ei:
                 L.lmosem_iterate(ctx, 1, 1.0, f)
