@@ -68,7 +68,8 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 20 for the dat64 GPU arm, about 0.6 s; 5 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fmt", choices=["fp32", "fp16", "bf16"], default="fp32")
@@ -77,6 +78,8 @@ def parse():
                     help="override the event count (small cases for profiling)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dat64")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.workload == "dat64" and args.impl == "ours" else 5
     global WORKLOAD, WORKLOAD_DESC
     WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOADS[args.workload]
     return args
@@ -138,7 +141,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
