@@ -469,25 +469,34 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs
 
 // ---- wide form: 64 events x 128 columns, 8 events x 4 columns per thread
 //
-// Each stage's U_jm are formed by the whole CTA; bit mc of live[w] is set when
-// some event of warp w (events 8w .. 8w + 7) lies in the cut of the stage's
-// scatter pixel mc, and a warp skips the others, whose terms are exact zeros
-// for all of its events.
-static_assert(kStage * kTJ % kBuildThreads == 0 && kTJ == 64 && kStage <= 32,
-              "U staging: every warp covers 32 events of one scatter pixel per step");
+// Three stage buffers: at the top of stage c one CTA barrier both publishes
+// stage c (landed by cp.async) and retires stage c - 1, whose buffer then
+// takes stage c + 2.  Each warp forms the U_jm of its own 8 events (events
+// 8w .. 8w + 7) and a 16-bit mask of the stage's scatter pixels whose cut
+// reaches any of them; it skips the others, whose terms are exact zeros for
+// all of its events.  One barrier per stage, no shared atomics.
+constexpr int kWBuf = 3;
+constexpr int kWarps = kBuildThreads / 32;
+constexpr int kWOffPlanes = 0;                                   // [kWBuf][3][kStage][kTN]
+constexpr int kWOffMp = kWOffPlanes + kWBuf * 3 * kPlaneF;       // [kWBuf][kStage] float4
+constexpr int kWOffU = kWOffMp + kWBuf * kStage * 4;             // [warp][kStage][8] float2
+constexpr int kWOffEv = kWOffU + kWarps * kStage * 8 * 2;        // u[kTJ], e[kTJ]
+constexpr int kWOffMisc = kWOffEv + 2 * kTJ;                     // 16 ints
+constexpr int kWOffList = kWOffMisc + 16;                        // n_scat ints
+static_assert(kWOffMp % 4 == 0 && kWOffU % 4 == 0, "16-byte aligned stage buffers");
+static_assert(kTJ == 8 * kWarps && kStage == 16, "8 events per warp; 16-bit live masks; 4 U per lane");
 
 __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
-    float* planes = sm + kOffPlanes;
-    float2* sU = reinterpret_cast<float2*>(sm + kOffU);
-    float4* mp = reinterpret_cast<float4*>(sm + kOffMp);
-    float* ev_u = sm + kOffEv;
+    float* planes = sm + kWOffPlanes;
+    float4* mp = reinterpret_cast<float4*>(sm + kWOffMp);
+    float* ev_u = sm + kWOffEv;
     float* ev_e = ev_u + kTJ;
-    int* misc = reinterpret_cast<int*>(sm + kOffMisc);
-    int* mlist = reinterpret_cast<int*>(sm + kOffList);
-    unsigned* live = reinterpret_cast<unsigned*>(misc) + 8;
+    int* misc = reinterpret_cast<int*>(sm + kWOffMisc);
+    int* mlist = reinterpret_cast<int*>(sm + kWOffList);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2* sUw = reinterpret_cast<float2*>(sm + kWOffU) + warp * kStage * 8;
     const TileInfo T = tile_setup(A, blockIdx.x / A.n_pt, A.pt0 + blockIdx.x % A.n_pt, ev_u, ev_e, misc,
                                   mlist);
 
@@ -512,38 +521,41 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
     const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
     const int nchunks = (T.nm + kStage - 1) / kStage;
-    if (nchunks > 0) stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, 0, 0, kTN / 4);
+    for (int q = 0; q < min(2, nchunks); ++q)
+        stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, q * kStage, q, kTN / 4);
+    const float uw = ev_u[8 * warp + (lane & 7)];  // this lane's event in the U step
     for (int c = 0; c < nchunks; ++c) {
-        const int buf = c & 1;
-        if (tid < kBuildThreads / 32) live[tid] = 0u;
-        if (c + 1 < nchunks) {
-            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 1) * kStage, buf ^ 1, kTN / 4);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        for (int k = tid; k < kStage * kTJ; k += kBuildThreads) {
-            const int mc = k / kTJ, j = k - mc * kTJ;
-            const float U = strip_weight(ev_u[j], mp[buf * kStage + mc]);
-            sU[mc * kTJ + j] = make_float2(U, U);
-            // lanes hold events j = 32 (warp & 1) + lane of one mc
+        const int buf = c % kWBuf;
+        if (c + 1 < nchunks) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();  // stage c landed everywhere; every warp is done with stage c - 1
+        if (c + 2 < nchunks)
+            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 2) * kStage, (c + 2) % kWBuf,
+                        kTN / 4);
+        // U_jm of this warp's events: lane holds event lane % 8 at scatter
+        // pixels lane / 8 + 4 i
+        unsigned live = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int mc = (lane >> 3) + 4 * i;
+            const float U = strip_weight(uw, mp[buf * kStage + mc]);
+            sUw[mc * 8 + (lane & 7)] = make_float2(U, U);
             const unsigned bal = __ballot_sync(0xffffffffu, U != 0.0f);
-            if (lane < 4 && ((bal >> (8 * lane)) & 0xffu)) atomicOr(live + 4 * (warp & 1) + lane, 1u << mc);
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if ((bal >> (8 * g)) & 0xffu) live |= 1u << (g + 4 * i);
         }
-        __syncthreads();
+        __syncwarp();
         const float* pS = planes + (buf * 3 + 0) * kPlaneF + 4 * lane;
         const float* pB = planes + (buf * 3 + 1) * kPlaneF + 4 * lane;
         const float* pW = planes + (buf * 3 + 2) * kPlaneF + 4 * lane;
-        const float4* pU = reinterpret_cast<const float4*>(sU + 8 * warp);
-        const unsigned wlive = live[warp];
 #pragma unroll 2
         for (int mc = 0; mc < kStage; ++mc) {
-            if (!((wlive >> mc) & 1u)) continue;
+            if (!((live >> mc) & 1u)) continue;
             const float4 S = *reinterpret_cast<const float4*>(pS + mc * kTN);
             const float4 B = *reinterpret_cast<const float4*>(pB + mc * kTN);
             const float4 W = *reinterpret_cast<const float4*>(pW + mc * kTN);
-            const float4* up = pU + mc * (kTJ / 2);
+            const float4* up = reinterpret_cast<const float4*>(sUw + mc * 8);
             float2 U[8];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -554,7 +566,6 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) terms4(E2[jj], U[jj], S, B, W, acc[jj][0], acc[jj][1]);
         }
-        __syncthreads();
     }
 
     const int n = T.n0 + 4 * lane;
@@ -747,10 +758,11 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;  // sigma_E^2 = kappa E
     const double se0 = sqrt(kappa * c->e0);
-    const size_t smem = sizeof(float) * ((size_t)kOffList + c->n_scat);
-    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem_w = sizeof(float) * ((size_t)kWOffList + c->n_scat);
+    const size_t smem_n = sizeof(float) * ((size_t)kOffList + c->n_scat);
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
     LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+                                      (int)smem_n));
     // a last column tile with few live columns takes the narrow form
     const int nq_tail = (c->n_sup - (n_ptiles - 1) * kTN + 3) / 4;
     const bool narrow_tail = nq_tail <= kNarrowQ;
@@ -801,14 +813,14 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         }
         if (n_wide > 0) {
             LMOSEM_PROF_BEGIN(c);
-            k_pathsum<<<(unsigned)((int64_t)tiles * n_wide), kBuildThreads, smem, c->stream>>>(P);
+            k_pathsum<<<(unsigned)((int64_t)tiles * n_wide), kBuildThreads, smem_w, c->stream>>>(P);
             LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
         }
         if (narrow_tail) {
             P.pt0 = n_ptiles - 1;
             P.n_pt = 1;
             LMOSEM_PROF_BEGIN(c);
-            k_pathsum_narrow<<<(unsigned)tiles, kBuildThreads, smem, c->stream>>>(P);
+            k_pathsum_narrow<<<(unsigned)tiles, kBuildThreads, smem_n, c->stream>>>(P);
             LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
         }
         if (scaled) {
