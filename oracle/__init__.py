@@ -14,6 +14,11 @@ the log-likelihood are written here with numpy, one line per equation:
 * Eq. 3  (log-likelihood, without the constant log J!):
          l(f) = sum_j log(T y_j) - T sum_n s_n f_n
 
+Binned attributes (the paper's binning experiment, Section 4): a row is a
+bin (angle, position bin, energy bin) with a count n_i; its model is the
+event model integrated over the bin, and the EM update and the likelihood
+weight each row by its count (n_i identical events).
+
 Readings where the paper is silent are listed in the design doc and repeated in
 the docstrings below.
 """
@@ -97,6 +102,10 @@ def lib():
             L.orc_model.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
                                     ctypes.c_int, _dp, _dp, _ip, _dp, _dp, ctypes.c_int64, _dp,
                                     ctypes.c_int]
+            L.orc_model_binned.restype = None
+            L.orc_model_binned.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
+                                           ctypes.c_int, _dp, _dp, _ip, _ip, _ip, ctypes.c_int64,
+                                           _dp, _dp, ctypes.c_int]
             L.orc_sensitivity.restype = None
             L.orc_sensitivity.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
                                           ctypes.c_int, _dp, _dp, ctypes.c_int, _dp]
@@ -209,6 +218,25 @@ class Problem:
                         _i(angle), _d(u), _d(e), n, _d(p), int(primary) | (int(scatter) << 1))
         return p
 
+    def model_binned(self, angle, pos_bin, e_bin, e_edges, primary=True, scatter=True):
+        """p[r, q] for binned rows r = (angle, detector position bin, energy
+        bin): the probability that an emission in support pixel q is detected
+        at that angle with its position and energy in the bin, i.e. the event
+        model of ``model`` integrated over the bin.  Position bins are the
+        detector's (n_bins of bin_mm over the extent); energy bin k is
+        [e_edges[k], e_edges[k + 1]]."""
+        angle = np.ascontiguousarray(angle, dtype=np.int32)
+        pb = np.ascontiguousarray(pos_bin, dtype=np.int32)
+        eb = np.ascontiguousarray(e_bin, dtype=np.int32)
+        edges = np.ascontiguousarray(e_edges, dtype=np.float64)
+        n = len(angle)
+        p = np.zeros((n, self.n_sup), dtype=np.float64)
+        lib().orc_model_binned(ctypes.byref(self.geom), _d(self.mu), _i(self.support), self.n_sup,
+                               _i(self.scatter), len(self.scatter), _d(self.l_edge),
+                               _d(self.l_pair), _i(angle), _i(pb), _i(eb), n, _d(edges), _d(p),
+                               int(primary) | (int(scatter) << 1))
+        return p
+
     def sensitivity(self, n_subsets: int):
         """s[i, q]: sum of s_eff over the paths from pixel q that reach the
         detector at angles of subset i (denominator of Eq. 7).  Subset i holds
@@ -234,23 +262,26 @@ def initial_image(n_events, s_total, T=1.0):
     return np.full(s_total.shape, n_events / (T * s_total.sum()), dtype=np.float64)
 
 
-def osem_subiteration(p_sub, f, s_i, T=1.0):
+def osem_subiteration(p_sub, f, s_i, T=1.0, w=None):
     """One OS-LM-MLEM sub-iteration (Eqs. 7-8) on the rows of one subset.
 
     y_j = sum_n p_jn f_n; events with y_j = 0 contribute nothing;
-    f_q <- f_q sum_j p_jq / y_j / (T s^i_q), and f_q = 0 where s^i_q = 0."""
+    f_q <- f_q sum_j w_j p_jq / y_j / (T s^i_q), and f_q = 0 where s^i_q = 0.
+    w_j = 1 for list-mode events; a binned row counts its n_j events."""
     y = p_sub @ f
     ok = y > 0
-    b = p_sub[ok].T @ (1.0 / y[ok])
+    wv = 1.0 if w is None else np.asarray(w, dtype=np.float64)[ok]
+    b = p_sub[ok].T @ (wv / y[ok])
     out = np.zeros_like(f)
     pos = s_i > 0
     out[pos] = f[pos] * b[pos] / (T * s_i[pos])
     return out
 
 
-def osem(p, angle, s_sub, n_iters, f0, T=1.0):
+def osem(p, angle, s_sub, n_iters, f0, T=1.0, weights=None):
     """N_g global iterations over N_s subsets in index order, always from the
     latest sub-iterate (reading of the iteration state eta of Eq. 9).
+    ``weights``: per-row counts of binned rows (None: list-mode events).
     Returns the image after every global iteration."""
     n_subsets = s_sub.shape[0]
     sub = subset_of(angle, n_subsets)
@@ -259,15 +290,18 @@ def osem(p, angle, s_sub, n_iters, f0, T=1.0):
     hist = []
     for _ in range(n_iters):
         for i in range(n_subsets):
-            f = osem_subiteration(p[rows[i]], f, s_sub[i], T)
+            w = None if weights is None else np.asarray(weights)[rows[i]]
+            f = osem_subiteration(p[rows[i]], f, s_sub[i], T, w)
         hist.append(f.copy())
     return f, hist
 
 
-def loglik(p, f, s_total, T=1.0):
-    """Eq. 3 without the data-only constant: sum_j log(T y_j) - T sum s f."""
+def loglik(p, f, s_total, T=1.0, weights=None):
+    """Eq. 3 without the data-only constant: sum_j w_j log(T y_j) - T sum s f
+    (w_j = 1 for events, the count of a binned row)."""
     y = p @ f
-    return float(np.sum(np.log(T * y)) - T * np.dot(s_total, f))
+    w = 1.0 if weights is None else np.asarray(weights, dtype=np.float64)
+    return float(np.sum(w * np.log(T * y)) - T * np.dot(s_total, f))
 
 
 def rel_l2(x, ref):

@@ -22,6 +22,8 @@
  *   pr(A|P) s_eff(P) = w k,   s_eff(P) = w D_u D_E.
  * Only first-order, in-plane scatter is kept (paper Section 2.2, last
  * paragraph before the GPU description).
+ * For binned attributes (paper Section 4) orc_model_binned integrates k over
+ * the bin: each Gaussian density becomes its mass on the bin.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
  * (closed forms, brute-force path enumeration, quadrature, invariants of the
@@ -421,4 +423,100 @@ void orc_sensitivity(const orc_geom* g, const double* mu, const int32_t* sup, in
             s_out[(size_t)sub * n_sup + i] += acc;
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Binned attributes (paper Section 4: position binned into the        */
+/* detector's bins, energy into a few bins)                            */
+/* ------------------------------------------------------------------ */
+
+/* Mass of N(m, s^2) inside [lo, hi], written so that a bin far out in either
+ * tail keeps its relative accuracy (the erfc of the nearer edge minus that of
+ * the farther one); equal to orc_gauss_mass up to rounding. */
+static double orc_gauss_mass_tail(double lo, double hi, double m, double s)
+{
+    double zl = (lo - m) / (s * sqrt(2.0)), zh = (hi - m) / (s * sqrt(2.0));
+    if (zl >= 0.0) return 0.5 * (erfc(zl) - erfc(zh));
+    if (zh <= 0.0) return 0.5 * (erfc(-zh) - erfc(-zl));
+    return 1.0 - 0.5 * (erfc(-zl) + erfc(zh));
+}
+
+/* p_out[r*n_sup + i]: probability that an emission in sup[i] is detected at
+ * angle row_angle[r] with its position in detector bin row_pos[r]
+ * ([-U/2 + b bin_mm, -U/2 + (b+1) bin_mm]) and its energy in
+ * [e_edges[row_e[r]], e_edges[row_e[r] + 1]].  This is the event model of
+ * orc_model with each Gaussian density replaced by its mass on the bin:
+ *   primary   w mass_u(bin; u_a(p_n), s_u) mass_E(bin; E0, s_E(E0))
+ *   scatter   w mass_u(bin; u_a(p_m), s_u) mass_E(bin; E', s_E(E'))
+ * A scatter path is skipped when the whole position bin lies beyond the
+ * position cut of its kernel (the cut of orc_model, at the bin's nearest
+ * point). */
+void orc_model_binned(const orc_geom* g, const double* mu, const int32_t* sup, int n_sup,
+                      const int32_t* scat, int n_scat, const double* l_edge, const double* l_pair,
+                      const int32_t* row_angle, const int32_t* row_pos, const int32_t* row_e,
+                      int64_t n_rows, const double* e_edges, double* p_out, int parts)
+{
+    int npix = g->nx * g->ny;
+    double kbar = orc_kn_mean(g->e0_kev);
+    double sig0 = orc_sigma_kn(g->e0_kev);
+    double se0 = orc_sigma_e(g, g->e0_kev);
+    double half = 0.5 * g->n_bins * g->bin_mm;
+    size_t tab = (size_t)n_sup * n_scat;
+    double* w = (double*)malloc(sizeof(double) * tab);   /* [k][i] */
+    double* ep = (double*)malloc(sizeof(double) * tab);  /* [k][i] */
+    double* ucen = (double*)malloc(sizeof(double) * (size_t)n_scat);
+    double* usig = (double*)malloc(sizeof(double) * (size_t)n_scat);
+    memset(p_out, 0, sizeof(double) * (size_t)n_rows * n_sup);
+
+    for (int a = 0; a < g->n_angles; ++a) {
+        int64_t cnt = 0;
+        for (int64_t r = 0; r < n_rows; ++r) cnt += (row_angle[r] == a);
+        if (cnt == 0) continue;
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < n_scat; ++k) {
+            double xm, ym;
+            orc_pixel_centre(g, scat[k], &xm, &ym);
+            ucen[k] = orc_det_u(g, a, xm, ym);
+            usig[k] = orc_sigma_u(g, orc_det_depth(g, a, xm, ym));
+            for (int i = 0; i < n_sup; ++i) {
+                double wv = 0.0, e1 = g->e0_kev;
+                orc_scatter_path(g, mu, a, sup[i], scat[k], l_pair[(size_t)i * n_scat + k],
+                                 l_edge[(size_t)a * npix + scat[k]], kbar, sig0, &wv, &e1);
+                w[(size_t)k * n_sup + i] = wv;
+                ep[(size_t)k * n_sup + i] = e1;
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t r = 0; r < n_rows; ++r) {
+            if (row_angle[r] != a) continue;
+            double* row = p_out + (size_t)r * n_sup;
+            double u0 = -half + row_pos[r] * g->bin_mm, u1 = u0 + g->bin_mm;
+            double e0 = e_edges[row_e[r]], e1 = e_edges[row_e[r] + 1];
+            for (int i = 0; i < n_sup && (parts & 1); ++i) {
+                double xn, yn;
+                orc_pixel_centre(g, sup[i], &xn, &yn);
+                double su = orc_sigma_u(g, orc_det_depth(g, a, xn, yn));
+                row[i] = exp(-l_edge[(size_t)a * npix + sup[i]]) *
+                         orc_gauss_mass_tail(u0, u1, orc_det_u(g, a, xn, yn), su) *
+                         orc_gauss_mass_tail(e0, e1, g->e0_kev, se0);
+            }
+            if (!(parts & 2)) continue;
+            for (int k = 0; k < n_scat; ++k) {
+                double dn = ucen[k] < u0 ? u0 - ucen[k] : (ucen[k] > u1 ? ucen[k] - u1 : 0.0);
+                double z = dn / usig[k];
+                if (0.5 * z * z > g->pos_cut) continue;
+                double pu = orc_gauss_mass_tail(u0, u1, ucen[k], usig[k]);
+                const double* wk = w + (size_t)k * n_sup;
+                const double* ek = ep + (size_t)k * n_sup;
+                for (int i = 0; i < n_sup; ++i) {
+                    if (wk[i] == 0.0) continue;
+                    row[i] += wk[i] * pu * orc_gauss_mass_tail(e0, e1, ek[i], orc_sigma_e(g, ek[i]));
+                }
+            }
+        }
+    }
+    free(w);
+    free(ep);
+    free(ucen);
+    free(usig);
 }

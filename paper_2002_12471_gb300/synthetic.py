@@ -266,3 +266,26 @@ def realisation_counts(n_real=64, seed=4, lo=50_000, hi=400_000):
     rng = np.random.Generator(np.random.Philox(key=int(seed)))
     lam = lo + (hi - lo) * rng.uniform(0.0, 1.0, n_real)
     return rng.poisson(lam).astype(np.int64)
+
+
+def bin_events(ev: Events, g: dict, e_edges) -> np.ndarray:
+    """Binned data of a list of events (the paper's binning experiment,
+    Section 4): photon counts per (angle, detector position bin, energy bin)
+    as a float32 array [n_angles, n_bins, len(e_edges) - 1].  Position bins
+    are the detector's (n_bins of bin_mm centred on the axis); energy bin k
+    is [e_edges[k], e_edges[k + 1]) (the last bin closed).  Events outside
+    the extent or the edges are dropped.  A histogram: no model arithmetic."""
+    edges = np.asarray(e_edges, dtype=np.float64)
+    nb, K = int(g["n_bins"]), len(edges) - 1
+    half = 0.5 * nb * g["bin_mm"]
+    u = np.asarray(ev.u_mm, dtype=np.float64)
+    e = np.asarray(ev.e_kev, dtype=np.float64)
+    a = np.asarray(ev.angle, dtype=np.int64)
+    b = np.floor((u + half) / g["bin_mm"]).astype(np.int64)
+    b = np.where(u == half, nb - 1, b)
+    k = np.searchsorted(edges, e, side="right") - 1
+    k = np.where(e == edges[-1], K - 1, k)
+    ok = (b >= 0) & (b < nb) & (k >= 0) & (k < K) & (a >= 0) & (a < g["n_angles"])
+    counts = np.zeros((int(g["n_angles"]), nb, K), dtype=np.float64)
+    np.add.at(counts, (a[ok], b[ok], k[ok]), 1.0)
+    return counts.astype(np.float32)
