@@ -51,6 +51,10 @@ WORKLOADS = {
     "windows64": ("energy-window variants (photopeak [143, 175], [120, 175], full [100, 175] keV) of the "
                   "64 noise realisations of the 64x64 DaT phantom, each window reconstructed in one persistent "
                   "launch, 8 subsets x 10 iterations; ROI-mean NRMSE over realisations"),
+    "binned64": ("binned attributes (paper Sec. 4): the 64 noise realisations of the 64x64 DaT phantom "
+                 "binned into the detector's 64 position bins and 2 ([100, 143, 175] keV) or 3 "
+                 "([100, 120, 143, 175] keV) energy bins, reconstructed from the bin-integrated model with "
+                 "count-weighted EM, against list mode; 8 subsets x 10 iterations; ROI-mean NRMSE"),
     "batch64": ("64 independent noise realisations of the 64x64 DaT phantom (120 angles, R = 150 mm), "
                 "event counts Poisson with means uniform in [50k, 400k], 8 subsets x 10 iterations, "
                 "all realisations in one persistent launch, FP32 model"),
@@ -988,6 +992,110 @@ def run_windows_bench(args):
             "truth_roi_means": truth}
 
 
+BINNINGS = (("binned_2e", (100.0, 143.0, 175.0)), ("binned_3e", (100.0, 120.0, 143.0, 175.0)))
+
+
+def run_binned_bench(args):
+    """The paper's binning experiment (Sec. 4): the list-mode data of the 64
+    noise realisations are binned into the detector's 64 position bins and 2
+    or 3 energy bins and reconstructed from the bin-integrated model with
+    count-weighted EM (8 subsets x 10 iterations), beside the list-mode
+    reconstruction of the same events (one persistent launch).  ROI means are
+    scored against the scaled phantom as in the window workload (NRMSE and
+    bias over realisations).  Timing: the binned model build and one
+    iteration per realisation, CUDA events on the context stream."""
+    import multiprocessing as mp
+
+    from paper_2002_12471_gb300 import synthetic as S
+    counts = S.realisation_counts(64, seed=4)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any CUDA call
+        parts = pool.map(_realisation_events, list(enumerate(counts)))
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g, _, ns, ni = S.workload("dat64")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    act = ph.activity.reshape(-1)
+    truth = {k: float(np.dot(w.reshape(-1), act) / w.sum()) for k, w in ph.rois.items()}
+    n_r = np.array([len(p[0]) for p in parts])
+
+    def score(images, sup, s_tot):
+        expected_per_activity = float(np.dot(s_tot, act[sup]))   # T = 1
+        rel = {k: [] for k in truth}
+        for r in range(len(counts)):
+            scale = n_r[r] / expected_per_activity
+            img = np.bincount(sup, weights=images[r], minlength=act.size)
+            for k, w in ph.rois.items():
+                rel[k].append(float(np.dot(w.reshape(-1), img) / w.sum()) / (scale * truth[k]) - 1.0)
+        return {"nrmse": {k: float(np.sqrt(np.mean(np.square(v)))) for k, v in rel.items()},
+                "bias": {k: float(np.mean(v)) for k, v in rel.items()},
+                "std": {k: float(np.std(v)) for k, v in rel.items()}}
+
+    out = {}
+    # list mode: every realisation in one persistent launch
+    off = np.concatenate([[0], np.cumsum(n_r)]).astype(np.int64)
+    a = torch.from_numpy(np.concatenate([p[0] for p in parts])).to(dev)
+    u = torch.from_numpy(np.concatenate([p[1] for p in parts])).to(dev)
+    e = torch.from_numpy(np.concatenate([p[2] for p in parts])).to(dev)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        sup = L.lmosem_support(ctx)
+        sens = torch.zeros((ns, nsup), dtype=torch.float64, device=dev)
+        L.lmosem_sensitivity(ctx, ns, sens)
+        L.lmosem_build_model_batch(ctx, a, u, e, off, ns)
+        f = torch.empty((len(counts), nsup), dtype=torch.float32, device=dev)
+        L.lmosem_init_image_batch(ctx, 1.0, f)
+        L.lmosem_iterate_batch(ctx, ni, 1.0, f)
+        stream.synchronize()
+        s_tot = sens.sum(0).cpu().numpy()
+        out["list_mode"] = dict(score(f.double().cpu().numpy(), sup, s_tot), rows=int(off[-1]))
+    finally:
+        L.lmosem_destroy(ctx)
+    del a, u, e
+    timing = {}
+    for name, edges in BINNINGS:
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+        try:
+            L.lmosem_sensitivity(ctx, ns)
+            imgs, t_build, t_iter, rows = [], [], [], []
+            for r, p in enumerate(parts):
+                ev = S.Events(p[0], p[1], p[2], np.arange(len(p[0])))
+                cnt = torch.from_numpy(S.bin_events(ev, g, edges)).to(dev)
+                t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                t0.record(stream)
+                L.lmosem_build_model_binned(ctx, cnt, edges, ns)
+                t1.record(stream)
+                f = torch.empty(nsup, dtype=torch.float32, device=dev)
+                L.lmosem_init_image(ctx, 1.0, f)
+                L.lmosem_iterate(ctx, ni, 1.0, f)
+                t2.record(stream)
+                t2.synchronize()
+                t_build.append(t0.elapsed_time(t1))
+                t_iter.append(t1.elapsed_time(t2) / ni)
+                rows.append(int((cnt > 0).sum().item()))
+                imgs.append(f.double().cpu().numpy())
+        finally:
+            L.lmosem_destroy(ctx)
+        out[name] = dict(score(np.stack(imgs), sup, s_tot), e_edges_kev=list(edges),
+                         rows_per_realisation_mean=float(np.mean(rows)))
+        timing[name] = {"build_ms_median": float(np.median(t_build[1:])),
+                        "ms_per_iter_median": float(np.median(t_iter[1:]))}
+    mean_rows = out["binned_3e"]["rows_per_realisation_mean"]
+    t3 = timing["binned_3e"]["build_ms_median"]
+    return {"metric": METRIC, "value": mean_rows * nsup / (t3 * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": len(counts), "warmup": 1, "ms_per_step": t3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events, binned)",
+            "config": {"workload": WORKLOAD_DESC, "realisations": len(counts), "events": int(off[-1]),
+                       "value_is": "binned (3 energy bins) model build: rows x support pixels per second"},
+            "results": out, "timing": timing, "truth_roi_means": truth}
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -1011,6 +1119,8 @@ def main():
         out = run_surrogate_bench(args)
     elif WORKLOAD == "windows64":
         out = run_windows_bench(args)
+    elif WORKLOAD == "binned64":
+        out = run_binned_bench(args)
     else:
         out = run_ours(args, rank, world, local_rank)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

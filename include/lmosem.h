@@ -193,6 +193,29 @@ lmosem_status lmosem_build_model(lmosem_ctx* ctx, const int32_t* d_angle, const 
                                  const float* d_e_kev, int64_t n_events, int32_t n_subsets,
                                  lmosem_model_fmt fmt);
 
+/* Binned form (the paper's binning experiment, Section 4): the data are
+ * photon counts per (angle, detector position bin, energy bin) instead of a
+ * list of events.  Position bins are the detector's n_bins bins of bin_mm;
+ * energy bin k is [h_e_edges[k], h_e_edges[k + 1]].  A row of the model is a
+ * bin with a positive count, and its model is the event model integrated
+ * over the bin: p_iq = the probability that an emission in pixel q is
+ * detected at the bin's angle with position and energy inside the bin (each
+ * Gaussian density of lmosem_build_model replaced by its mass on the bin).
+ * lmosem_init_image, lmosem_iterate and lmosem_loglik then weight every row
+ * by its count (a bin holding n_i photons acts as n_i identical events), and
+ * lmosem_model_rows takes the ordinals of the positive bins in dense
+ * (angle, position bin, energy bin) order.  FP32 model only.
+ * d_counts: device float32 [n_angles][n_bins][n_ebins], finite, >= 0.
+ * h_e_edges: host, n_ebins + 1 increasing energies; the first must equal the
+ * window's e_lo and the last its e_hi (relative 1e-9), so that the bins tile
+ * the window the sensitivity integrates over.  Synchronises the stream.
+ * EINVAL: n_ebins not in 1..8, bad edges, a negative or non-finite count, no
+ * positive count, n_subsets not in [1, n_angles].  ENOTIMPL: fmt other than
+ * FP32.  Any earlier model is released first. */
+lmosem_status lmosem_build_model_binned(lmosem_ctx* ctx, const float* d_counts, int32_t n_ebins,
+                                        const double* h_e_edges, int32_t n_subsets,
+                                        lmosem_model_fmt fmt);
+
 /* Batching form: one model for n_real independent list-mode data sets (noise
  * realisations; the paper repeats its study over multiple noise realisations,
  * Section 3) of the same object and scanner.  The events of realisation r are
@@ -295,7 +318,8 @@ lmosem_status lmosem_surrogate_infer(lmosem_ctx* ctx, const float* d_weights, co
  * model builds. */
 lmosem_status lmosem_surrogate_load(lmosem_ctx* ctx, const float* d_weights);
 
-/* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz).
+/* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz);
+ * J is the number of events, or the sum of the counts of a binned model.
  * ESTATE: no model or sensitivity. */
 lmosem_status lmosem_init_image(lmosem_ctx* ctx, double acq_time, float* d_f);
 

@@ -3,6 +3,8 @@
 // kernels of the other translation units; this file only checks arguments,
 // allocates, and enqueues.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -85,6 +87,8 @@ void free_model(lmosem_ctx* c) {
     dev_free(c, &c->d_bclaim);
     dev_free(c, &c->d_bdone);
     dev_free(c, &c->d_bpart_batch);
+    dev_free(c, &c->d_weight);
+    c->n_counts = 0.0;
     c->bpart_batch_floats = 0;
     c->batch_model = false;
     c->use_surrogate = false;
@@ -400,6 +404,104 @@ lmosem_status lmosem_build_model(lmosem_ctx* c, const int32_t* d_angle, const fl
     lmosem_status st = check_events_args(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, fmt);
     if (st) return st;
     return build_model_common(c, d_angle, d_u_mm, d_e_kev, n_events, n_subsets, fmt, nullptr, 1);
+}
+
+lmosem_status lmosem_build_model_binned(lmosem_ctx* c, const float* d_counts, int32_t n_ebins,
+                                        const double* h_e_edges, int32_t n_subsets, lmosem_model_fmt fmt) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_counts || !h_e_edges) return fail(c, LMOSEM_EINVAL, "null counts or energy edges");
+    if (n_ebins < 1 || n_ebins > 8) return fail(c, LMOSEM_EINVAL, "n_ebins must be in 1..8");
+    if (n_subsets < 1 || n_subsets > c->n_angles)
+        return fail(c, LMOSEM_EINVAL, "n_subsets must be in [1, n_angles]");
+    if (fmt != LMOSEM_MODEL_FP32) return fail(c, LMOSEM_ENOTIMPL, "the binned model is cached as FP32 only");
+    for (int k = 0; k <= n_ebins; ++k)
+        if (!std::isfinite(h_e_edges[k]) || (k > 0 && !(h_e_edges[k] > h_e_edges[k - 1])))
+            return fail(c, LMOSEM_EINVAL, "energy edges must be finite and increasing");
+    const double tol = 1e-9 * c->e_hi;
+    if (fabs(h_e_edges[0] - c->e_lo) > tol || fabs(h_e_edges[n_ebins] - c->e_hi) > tol)
+        return fail(c, LMOSEM_EINVAL, "energy edges must span the window [e_lo, e_hi]");
+
+    // counts to the host, checked, and the positive bins in sorted-row order:
+    // subsets in index order, their angles increasing, then (position, energy) bin
+    const int K = n_ebins, NB = c->n_bins, NA = c->n_angles;
+    const size_t nbins = (size_t)NA * NB * K;
+    std::vector<float> h(nbins);
+    LMOSEM_CK(c, cudaMemcpyAsync(h.data(), d_counts, nbins * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    int64_t n_rows = 0;
+    double total = 0.0;
+    for (size_t i = 0; i < nbins; ++i) {
+        if (!std::isfinite(h[i]) || h[i] < 0.0f) return fail(c, LMOSEM_EINVAL, "counts must be finite and >= 0");
+        if (h[i] > 0.0f) {
+            ++n_rows;
+            total += h[i];
+        }
+    }
+    if (n_rows == 0) return fail(c, LMOSEM_EINVAL, "no positive count");
+    std::vector<int32_t> rowmap(nbins, -1);
+    std::vector<float> weight(n_rows);
+    std::vector<int64_t> angle_row0(NA, 0), angle_cnt(NA, 0), subset_row0(n_subsets + 1, 0);
+    int64_t r = 0;
+    for (int i = 0; i < n_subsets; ++i) {
+        subset_row0[i] = r;
+        for (int a = i; a < NA; a += n_subsets) {
+            angle_row0[a] = r;
+            for (size_t q = (size_t)a * NB * K; q < (size_t)(a + 1) * NB * K; ++q)
+                if (h[q] > 0.0f) {
+                    rowmap[q] = (int32_t)r;
+                    weight[r++] = h[q];
+                }
+            angle_cnt[a] = r - angle_row0[a];
+        }
+    }
+    subset_row0[n_subsets] = r;
+    std::vector<int64_t> rank;  // ordinal of a positive bin in dense order -> row
+    rank.reserve(n_rows);
+    for (size_t q = 0; q < nbins; ++q)
+        if (rowmap[q] >= 0) rank.push_back(rowmap[q]);
+
+    free_model(c);
+    c->fmt = LMOSEM_MODEL_FP32;
+    c->use_surrogate = false;
+    c->J = n_rows;
+    c->n_subsets = n_subsets;
+    c->ld_model = (c->n_sup + 31) / 32 * 32;
+    c->n_real = 1;
+    c->h_real_row0 = {0, n_rows};
+    c->h_angle_row0 = angle_row0;
+    c->h_angle_cnt = angle_cnt;
+    c->h_subset_row0 = subset_row0;
+    lmosem_status st;
+    {
+        void* p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, (size_t)n_rows * c->ld_model * sizeof(float), c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_model(c);
+            return fail(c, LMOSEM_ENOMEM, "binned model does not fit");
+        }
+        c->d_model = p;
+    }
+    Scratch tmp(c);
+    int32_t* d_rowmap = nullptr;
+    if ((st = dev_alloc(c, &c->d_weight, (size_t)n_rows)) || (st = dev_alloc(c, &c->d_rank, (size_t)n_rows)) ||
+        (st = tmp.alloc(&d_rowmap, nbins))) {
+        free_model(c);
+        return st;
+    }
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_weight, weight.data(), n_rows * sizeof(float), cudaMemcpyHostToDevice,
+                                 c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_rank, rank.data(), n_rows * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(d_rowmap, rowmap.data(), nbins * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 c->stream));
+    if ((st = build_binned_rows(c, d_rowmap, K, h_e_edges))) {
+        free_model(c);
+        return st;
+    }
+    c->n_counts = total;
+    if (!c->d_bpart && (st = setup_pass(c))) return st;
+    return LMOSEM_OK;
 }
 
 lmosem_status lmosem_build_model_batch(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,

@@ -88,6 +88,9 @@ struct lmosem_ctx {
     int32_t* d_angle_cnt = nullptr;
     int32_t* d_tile_prefix = nullptr;                // n_angles + 1 cumulative event tiles
     std::vector<int32_t> h_tile_prefix;
+    // binned rows (the paper's binning experiment): per-row photon counts
+    float* d_weight = nullptr;    // J counts (nullptr for list-mode events)
+    double n_counts = 0.0;        // sum of the counts
     float* d_wtab = nullptr;      // scatter-weight planes (s, b, -lw) of one angle group
     float* d_wtab_all = nullptr;  // planes of every angle, indexed by angle: built with the
                                   // sensitivity when they fit the table budget, consumed (and
@@ -241,7 +244,11 @@ lmosem_status run_binned_support(lmosem_ctx* c, const int32_t* d_angle, const fl
 lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_u,
                           const float* d_e, int64_t n, int n_subsets,
                           const int64_t* h_offsets, int n_real);  // sort.cu
-lmosem_status build_model_rows(lmosem_ctx* c);                  // model.cu
+lmosem_status build_model_rows(lmosem_ctx* c);
+// binned rows: model of every (angle, position bin, energy bin) row of the
+// row map ([a][b][k] -> sorted row or -1) with energy bin edges e_edges
+lmosem_status build_binned_rows(lmosem_ctx* c, const int32_t* d_rowmap, int n_ebins,
+                                const double* e_edges);                  // model.cu
 lmosem_status compute_sensitivity(lmosem_ctx* c, int n_subsets);  // sens.cu
 // model.cu: every angle's scatter-weight planes into d_wtab_all and, in the
 // same pass, the per-angle sensitivities (arithmetic of the sensitivity

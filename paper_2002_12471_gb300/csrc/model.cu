@@ -607,6 +607,223 @@ __global__ void k_quantize(const float* __restrict__ stage, int64_t ld_stage, in
 }
 
 // scatter-table arguments of the context (sigma_E^2 = kappa E)
+// ---- binned rows (the paper's binning experiment, Section 4)
+//
+// A row is a bin (angle a, detector position bin b, energy bin k).  Its model
+// is the event model integrated over the bin, each Gaussian density replaced
+// by its mass on the bin:
+//   p_(abk),n = w_0(n) M_u(b; u_n) M_E(k; E0)
+//             + sum_m M_u(b; u_m) W_a(n, m) M_E(k; E'_a(n, m)).
+// For one (a, k) the scatter part is a product over m of the position-bin
+// masses (bins x scatter pixels) with C_k = W M_E (scatter pixels x support
+// pixels).  A CTA owns 64 position bins x 128 support pixels of one (a, k).
+// For each stage of 16 scatter pixels it forms C_k from the (s, b, -lw)
+// planes (sigma_E sqrt(2 pi) = sqrt(pi log2 e) / s, E' = -b / s, and
+// (E - E') / (sigma_E sqrt 2) = (E s + b) sqrt(ln 2)) and the bin masses from
+// the position parameters, then accumulates 8 bins x 4 pixels per thread; a
+// warp skips the scatter pixels whose cut misses all 8 of its bins.
+constexpr int kMaxEBins = 8;
+constexpr float kSqrtLn2 = 0.83255461115769776f;     // q sqrt(ln 2) = 1 / (sigma sqrt 2)
+constexpr float kSqrtPiLog2e = 2.1289340388624524f;  // sigma sqrt(2 pi) = sqrt(pi log2 e) / q
+
+struct BinnedArgs {
+    const float* wtab;
+    int ld_w, n_scat;
+    int a0;                       // first angle of the launch
+    int wslot_by_angle;           // 1: planes indexed by angle, else by a - a0
+    const float4* mpar;           // [a][m] (u_m, q_m, lq_m, cut_m)
+    const float4* ppar;           // [a][n] (u_n, q_n, lp_n, D_u)
+    int n_bins;
+    float bin_mm, half;           // detector position bins
+    int n_ebins;
+    float e_edge[kMaxEBins + 1];  // energy bin edges
+    float pe_mass[kMaxEBins];     // photopeak mass of each energy bin
+    int n_btiles, n_ptiles;
+    const int32_t* rowmap;        // [a][b][k] -> sorted row, or -1
+    float* out;
+    int64_t ld_out;
+    int n_store;
+    int scatter_only;
+};
+
+// mass of a unit Gaussian on [zl, zh] in units of sigma sqrt 2, keeping its
+// relative accuracy far out in either tail
+__device__ __forceinline__ float bin_mass(float zl, float zh) {
+    if (zl >= 0.0f) return 0.5f * (erfcf(zl) - erfcf(zh));
+    if (zh <= 0.0f) return 0.5f * (erfcf(-zh) - erfcf(-zl));
+    return 1.0f - 0.5f * (erfcf(-zl) + erfcf(zh));
+}
+
+constexpr int kBOffPlanes = 0;                          // [2][3][kStage][kTN]
+constexpr int kBOffMp = kBOffPlanes + 2 * 3 * kPlaneF;  // [2][kStage] float4
+constexpr int kBOffC = kBOffMp + 2 * kStage * 4;        // [kStage][kTN]  C_k of the stage
+constexpr int kBOffM = kBOffC + kStage * kTN;           // [kStage][kTJ]  bin masses of the stage
+constexpr int kBOffMisc = kBOffM + kStage * kTJ;        // 16 ints
+constexpr int kBOffList = kBOffMisc + 16;               // n_scat ints
+
+__global__ void __launch_bounds__(kBuildThreads, 2) k_binned(BinnedArgs A) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    float* planes = sm + kBOffPlanes;
+    float4* mp = reinterpret_cast<float4*>(sm + kBOffMp);
+    float* Cm = sm + kBOffC;
+    float* Mb = sm + kBOffM;
+    int* misc = reinterpret_cast<int*>(sm + kBOffMisc);
+    unsigned* live = reinterpret_cast<unsigned*>(misc) + 8;
+    int* mlist = reinterpret_cast<int*>(sm + kBOffList);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int idx = blockIdx.x;
+    const int pt = idx % A.n_ptiles;
+    idx /= A.n_ptiles;
+    const int bt = idx % A.n_btiles;
+    idx /= A.n_btiles;
+    const int k = idx % A.n_ebins;
+    const int a = A.a0 + idx / A.n_ebins;
+    const int b0 = bt * kTJ, n0 = pt * kTN;
+    const int nb = min(kTJ, A.n_bins - b0);
+    const int32_t* rmap = A.rowmap + (size_t)a * A.n_bins * A.n_ebins + k;
+
+    // nothing to do unless one of the CTA's bins holds a row
+    bool has = false;
+    for (int bl = tid; bl < nb; bl += kBuildThreads) has |= rmap[(size_t)(b0 + bl) * A.n_ebins] >= 0;
+    if (!__syncthreads_or(has)) return;
+
+    // scatter pixels whose cut interval reaches the CTA's bins
+    const float umin = -A.half + b0 * A.bin_mm, umax = -A.half + (b0 + nb) * A.bin_mm;
+    const float4* mp_a = A.mpar + (size_t)a * A.n_scat;
+    int nm = 0;
+    for (int m0 = 0; m0 < A.n_scat; m0 += kBuildThreads) {
+        const int m = m0 + tid;
+        bool in = false;
+        if (m < A.n_scat) {
+            const float4 q = __ldg(mp_a + m);
+            in = (q.x + q.w >= umin) && (q.x - q.w <= umax);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) misc[warp] = __popc(bal);
+        __syncthreads();
+        int off = nm, total = 0;
+        for (int w = 0; w < kBuildThreads / 32; ++w) {
+            const int cw = misc[w];
+            if (w < warp) off += cw;
+            total += cw;
+        }
+        if (in) mlist[off + __popc(bal & ((1u << lane) - 1u))] = m;
+        __syncthreads();
+        nm += total;
+    }
+
+    // primary path: w_0 M_u(b; u_n) M_E(k; E0), 8 bins x 4 pixels per thread
+    float2 acc[8][2];
+    {
+        const float4* pp_a = A.ppar + (size_t)a * A.ld_w + n0 + 4 * lane;
+        float w0[4], s2[4], un[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 pp = __ldg(pp_a + q);
+            w0[q] = (pp.y > 0.0f && !A.scatter_only) ? ex2_approx(pp.z) * kSqrtPiLog2e / pp.y * A.pe_mass[k]
+                                                     : 0.0f;
+            s2[q] = pp.y * kSqrtLn2;
+            un[q] = pp.x;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int b = b0 + 8 * warp + jj;
+            const float ulo = -A.half + b * A.bin_mm, uhi = ulo + A.bin_mm;
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v[q] = (b < A.n_bins && w0[q] != 0.0f)
+                           ? w0[q] * bin_mass((ulo - un[q]) * s2[q], (uhi - un[q]) * s2[q])
+                           : 0.0f;
+            acc[jj][0] = make_float2(v[0], v[1]);
+            acc[jj][1] = make_float2(v[2], v[3]);
+        }
+    }
+
+    const size_t plane = (size_t)A.n_scat * A.ld_w;
+    const int slot = A.wslot_by_angle ? a : a - A.a0;
+    const float* tab = A.wtab + (size_t)slot * 3 * plane + n0;
+    TileInfo T;
+    T.nm = nm;
+    const float el = A.e_edge[k], eh = A.e_edge[k + 1];
+    const int nchunks = (nm + kStage - 1) / kStage;
+    if (nchunks > 0) stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, 0, 0, kTN / 4);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (tid < kBuildThreads / 32) live[tid] = 0u;
+        if (c + 1 < nchunks) {
+            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 1) * kStage, buf ^ 1, kTN / 4);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        // bin masses of the stage: lanes hold bins 32 (warp & 1) + lane of one mc
+        for (int kk = tid; kk < kStage * kTJ; kk += kBuildThreads) {
+            const int mc = kk / kTJ, bl = kk - mc * kTJ;
+            const float4 q = mp[buf * kStage + mc];
+            const float ulo = -A.half + (b0 + bl) * A.bin_mm, uhi = ulo + A.bin_mm;
+            const float dn = q.x < ulo ? ulo - q.x : (q.x > uhi ? q.x - uhi : 0.0f);
+            const float s2 = q.y * kSqrtLn2;
+            const float M = (bl < nb && dn <= q.w) ? bin_mass((ulo - q.x) * s2, (uhi - q.x) * s2) : 0.0f;
+            Mb[mc * kTJ + bl] = M;
+            const unsigned bal = __ballot_sync(0xffffffffu, M != 0.0f);
+            if (lane < 4 && ((bal >> (8 * lane)) & 0xffu)) atomicOr(live + 4 * (warp & 1) + lane, 1u << mc);
+        }
+        // C_k = W M_E(k; E') of the stage
+        const float* pS = planes + (buf * 3 + 0) * kPlaneF;
+        const float* pB = planes + (buf * 3 + 1) * kPlaneF;
+        const float* pW = planes + (buf * 3 + 2) * kPlaneF;
+        for (int kk = tid; kk < kStage * kTN; kk += kBuildThreads) {
+            const float sv = pS[kk], bv = pB[kk], nlw = pW[kk];
+            float Cv = 0.0f;
+            if (sv > 0.0f && nlw < INFINITY)
+                Cv = ex2_approx(-nlw) * kSqrtPiLog2e / sv *
+                     bin_mass(fmaf(el, sv, bv) * kSqrtLn2, fmaf(eh, sv, bv) * kSqrtLn2);
+            Cm[kk] = Cv;
+        }
+        __syncthreads();
+        const unsigned wlive = live[warp];
+        for (int mc = 0; mc < kStage; ++mc) {
+            if (!((wlive >> mc) & 1u)) continue;
+            const float4 C = *reinterpret_cast<const float4*>(Cm + mc * kTN + 4 * lane);
+            const float4 M0 = *reinterpret_cast<const float4*>(Mb + mc * kTJ + 8 * warp);
+            const float4 M1 = *reinterpret_cast<const float4*>(Mb + mc * kTJ + 8 * warp + 4);
+            const float Mv[8] = {M0.x, M0.y, M0.z, M0.w, M1.x, M1.y, M1.z, M1.w};
+            const float2 C01 = make_float2(C.x, C.y), C23 = make_float2(C.z, C.w);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const float2 m2 = make_float2(Mv[jj], Mv[jj]);
+                acc[jj][0] = ffma2(m2, C01, acc[jj][0]);
+                acc[jj][1] = ffma2(m2, C23, acc[jj][1]);
+            }
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        const int b = b0 + 8 * warp + jj;
+        if (b >= A.n_bins) continue;
+        const int32_t r = rmap[(size_t)b * A.n_ebins];
+        if (r >= 0) {
+            float* row = A.out + (int64_t)r * A.ld_out;
+            const int n = n0 + 4 * lane;
+            if (n + 3 < A.n_store) {
+                *reinterpret_cast<float4*>(row + n) =
+                    make_float4(acc[jj][0].x, acc[jj][0].y, acc[jj][1].x, acc[jj][1].y);
+            } else {
+                const float v[4] = {acc[jj][0].x, acc[jj][0].y, acc[jj][1].x, acc[jj][1].y};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (n + q < A.n_store) row[n + q] = v[q];
+            }
+        }
+    }
+}
+
 WTabArgs wtab_args(const lmosem_ctx* c, float* wtab, const int32_t* slot_angle, int s0) {
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;
@@ -842,6 +1059,75 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     dev_free(c, &c->d_wtab);
     dev_free(c, &c->d_wtab_all);  // consumed
     dev_free(c, &c->d_stage);
+    return LMOSEM_OK;
+}
+
+
+lmosem_status build_binned_rows(lmosem_ctx* c, const int32_t* d_rowmap, int n_ebins, const double* e_edges) {
+    if (n_ebins < 1 || n_ebins > kMaxEBins) return fail(c, LMOSEM_EINVAL, "1..8 energy bins");
+    lmosem_status st;
+    const int n_ptiles = c->ld_w / kTN;
+    const int n_btiles = (c->n_bins + kTJ - 1) / kTJ;
+    const bool pre = c->d_wtab_all != nullptr;
+    const int64_t per_angle = wtab_angle_floats(c) * (int64_t)sizeof(float);
+    const int gsz = pre ? c->n_angles
+                        : (int)std::max<int64_t>(1, std::min<int64_t>(c->n_angles, c->table_budget / per_angle));
+
+    BinnedArgs B;
+    B.ld_w = c->ld_w;
+    B.n_scat = c->n_scat;
+    B.wslot_by_angle = pre ? 1 : 0;
+    B.mpar = c->d_mpar;
+    B.ppar = c->d_ppar;
+    B.n_bins = c->n_bins;
+    B.bin_mm = (float)c->bin_mm;
+    B.half = (float)(0.5 * c->n_bins * c->bin_mm);
+    B.n_ebins = n_ebins;
+    const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;  // sigma_E^2 = kappa E
+    const double se0 = sqrt(kappa * c->e0);
+    for (int k = 0; k <= n_ebins; ++k) B.e_edge[k] = (float)e_edges[k];
+    for (int k = 0; k < n_ebins; ++k)
+        B.pe_mass[k] = (float)(0.5 * erfc(-(e_edges[k + 1] - c->e0) / (se0 * sqrt(2.0))) -
+                               0.5 * erfc(-(e_edges[k] - c->e0) / (se0 * sqrt(2.0))));
+    B.n_btiles = n_btiles;
+    B.n_ptiles = n_ptiles;
+    B.rowmap = d_rowmap;
+    B.out = reinterpret_cast<float*>(c->d_model);
+    B.ld_out = c->ld_model;
+    B.n_store = (int)c->ld_model;
+    B.scatter_only = c->scatter_only ? 1 : 0;
+
+    // identity slot -> angle map for the per-group table kernel
+    Scratch tmp(c);
+    int32_t* d_ang = nullptr;
+    if (!pre) {
+        if ((st = tmp.alloc(&d_ang, c->n_angles))) return st;
+        std::vector<int32_t> ident(c->n_angles);
+        for (int a = 0; a < c->n_angles; ++a) ident[a] = a;
+        LMOSEM_CK(c, cudaMemcpyAsync(d_ang, ident.data(), ident.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, c->stream));
+        if ((st = dev_alloc(c, &c->d_wtab, (size_t)gsz * wtab_angle_floats(c)))) return st;
+    }
+    const size_t smem = sizeof(float) * ((size_t)kBOffList + c->n_scat);
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_binned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int a0 = 0; a0 < c->n_angles; a0 += gsz) {
+        const int na = std::min(gsz, c->n_angles - a0);
+        if (!pre) {
+            WTabArgs W = wtab_args(c, c->d_wtab, d_ang, a0);
+            LMOSEM_PROF_BEGIN(c);
+            k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, na), 256, 0, c->stream>>>(W);
+            LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
+        }
+        B.wtab = pre ? c->d_wtab_all : c->d_wtab;
+        B.a0 = a0;
+        LMOSEM_PROF_BEGIN(c);
+        k_binned<<<(unsigned)((int64_t)na * n_ebins * n_btiles * n_ptiles), kBuildThreads, smem, c->stream>>>(B);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
+    }
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, &c->d_wtab);
+    dev_free(c, &c->d_wtab_all);  // consumed
     return LMOSEM_OK;
 }
 

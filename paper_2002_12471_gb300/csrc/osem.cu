@@ -90,6 +90,7 @@ struct PassArgs {
     int64_t rows_per_cta;
     const float* f;
     const float* scale;      // row scales (scaled forms) or nullptr
+    const float* weight;     // row counts (binned rows) or nullptr (events: 1)
     int n_sup;
     double log_T;
     float* bpart;            // [cta][n_sup]
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
     const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
     const int64_t re = min(A.r1, rb + A.rows_per_cta);
     double ll = 0.0;
-    int npos = 0;
+    double npos = 0.0;  // weight of the rows with y > 0
 
     auto load = [&](int64_t r, uint4 (&dst)[R][VPT]) {
 #pragma unroll
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
             for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
             const bool ok = r + i < re && y > 0.0f;
             if constexpr (BACK) {
-                const float inv = ok ? 1.0f / y : 0.0f;
+                const float inv = ok ? (A.weight ? A.weight[r + i] : 1.0f) / y : 0.0f;
                 const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
@@ -203,9 +204,10 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
                 }
             } else {
                 if (ok && t == i) {
-                    float c = A.scale ? A.scale[r + i] : 1.0f;
-                    ll += (double)logf(c * y);
-                    ++npos;
+                    const float c = A.scale ? A.scale[r + i] : 1.0f;
+                    const double w = A.weight ? (double)A.weight[r + i] : 1.0;
+                    ll += w * (double)logf(c * y);
+                    npos += w;
                 }
             }
         }
@@ -230,8 +232,8 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
                 if (col0 + e < A.n_sup) bp[col0 + e] = br[v][e];
         }
     } else {
-        // per-CTA partial: sum_j log(c_j y_j) + (number of rows) log T, fixed order
-        ll += (double)npos * A.log_T;
+        // per-CTA partial: sum_j w_j (log(c_j y_j) + log T), fixed order
+        ll += npos * A.log_T;
         for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
         if (lane == 0) llred[warp] = ll;
         __syncthreads();
@@ -355,6 +357,7 @@ struct RingArgs {
     int G, S;                // rows per stage, stages
     const float* f;
     const float* scale;      // row scales (scaled forms) or nullptr
+    const float* weight;     // row counts (binned rows) or nullptr
     int n_sup;
     double log_T;
     float* bpart;            // [cta][n_sup]
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
         for (int64_t g = 0; g < min((int64_t)S, ngroups); ++g) issue(g);
 
     double ll = 0.0;
-    int npos = 0;
+    double npos = 0.0;  // weight of the rows with y > 0
     bool aborted = false;
     int64_t g = 0;
     for (; g < ngroups; ++g) {
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
             float y = 0.0f;
             for (int w = 0; w < NW; ++w) y += red[i][w];
             if constexpr (BACK) {
-                const float inv = y > 0.0f ? 1.0f / y : 0.0f;
+                const float inv = y > 0.0f ? (A.weight ? A.weight[row + i] : 1.0f) / y : 0.0f;
                 const uint4* rp = reinterpret_cast<const uint4*>(st + i * A.ld_bytes);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
@@ -506,9 +509,10 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
                 }
             } else {
                 if (t == (i & (kMaxPassThreads - 1)) && y > 0.0f) {
-                    float c = A.scale ? A.scale[row + i] : 1.0f;
-                    ll += (double)logf(c * y);
-                    ++npos;
+                    const float c = A.scale ? A.scale[row + i] : 1.0f;
+                    const double w = A.weight ? (double)A.weight[row + i] : 1.0;
+                    ll += w * (double)logf(c * y);
+                    npos += w;
                 }
             }
         }
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
                 if (col0 + e < A.n_sup) bp[col0 + e] = br[v][e];
         }
     } else {
-        ll += (double)npos * A.log_T;
+        ll += npos * A.log_T;
         for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
         if (lane == 0) llred[warp] = ll;
         __syncthreads();
@@ -634,6 +638,7 @@ lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
     A.S = S;
     A.f = A0.f;
     A.scale = A0.scale;
+    A.weight = A0.weight;
     A.n_sup = A0.n_sup;
     A.log_T = A0.log_T;
     A.bpart = A0.bpart;
@@ -676,6 +681,7 @@ lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f,
     A.rows_per_cta = 0;
     A.f = f;
     A.scale = c->fmt == LMOSEM_MODEL_FP32 ? nullptr : c->d_scale;
+    A.weight = c->d_weight;
     A.n_sup = c->n_sup;
     A.log_T = log(T);
     A.bpart = c->d_bpart;
@@ -806,7 +812,7 @@ lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_ou
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f) {
     LMOSEM_PROF_BEGIN(c);
     k_init_image<<<1, 256, 0, c->stream>>>(c->d_sens + (size_t)c->sens_subsets * c->n_sup,
-                                           c->n_sup, (double)c->J, T, d_f);
+                                           c->n_sup, c->d_weight ? c->n_counts : (double)c->J, T, d_f);
     LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
     return LMOSEM_OK;
 }
@@ -924,6 +930,7 @@ extern "C" lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_
     A.rows_per_cta = 0;
     A.f = d_f;
     A.scale = nullptr;
+    A.weight = nullptr;
     A.n_sup = n_support;
     A.log_T = 0.0;
     A.bpart = scratch;

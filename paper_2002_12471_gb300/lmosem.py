@@ -93,6 +93,7 @@ SIGNATURES = {
     "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "lmosem_osem_subiter_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i64, _vp, _vp, _dbl, _vp]),
     "lmosem_build_model_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int]),
+    "lmosem_build_model_binned": (ctypes.c_int, [_vp, _vp, _i32, _vp, _i32, ctypes.c_int]),
     "lmosem_init_image_batch": (ctypes.c_int, [_vp, _dbl, _vp]),
     "lmosem_iterate_batch": (ctypes.c_int, [_vp, _i32, _dbl, _vp]),
     "lmosem_autotune_batch": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
@@ -248,6 +249,15 @@ def lmosem_profile_read(ctx):
     n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
     _check(ctx, load().lmosem_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def lmosem_build_model_binned(ctx, d_counts, e_edges, n_subsets, fmt="fp32"):
+    """Binned form: d_counts is a device float32 tensor [n_angles, n_bins,
+    n_ebins] of photon counts, e_edges the n_ebins + 1 energy bin edges."""
+    edges = np.ascontiguousarray(e_edges, dtype=np.float64)
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    _check(ctx, load().lmosem_build_model_binned(ctx, _ptr(d_counts), len(edges) - 1, edges.ctypes.data,
+                                                 int(n_subsets), f))
 
 
 def lmosem_build_model_batch(ctx, d_angle, d_u_mm, d_e_kev, event_offsets, n_subsets, fmt="fp32"):
