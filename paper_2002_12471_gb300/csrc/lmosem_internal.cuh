@@ -333,7 +333,7 @@ __device__ __forceinline__ bool path_geometry_xy(float xn, float yn, float xm, f
 // Klein-Nishina weight K(psi)/Kbar.
 __device__ __forceinline__ void compton(float cpsi, float eps0, float inv_kbar, float* P, float* kt) {
     float inv_p = fmaf(eps0, 1.0f - cpsi, 1.0f);
-    float p = 1.0f / inv_p;
+    float p = __fdividef(1.0f, inv_p);  // inv_p in [1, 1 + 2 E0 / mc^2]
     float sin2 = fmaf(-cpsi, cpsi, 1.0f);
     *P = p;
     *kt = 0.5f * p * p * (p + inv_p - sin2) * inv_kbar;

@@ -85,7 +85,7 @@ __global__ void k_wtable(WTabArgs A) {
             float ratio = compton_lookup(A.compton, cpsi).x;
             float att = fmaf(ratio, A.l_edge[(size_t)a * A.npix + pm], A.l_pair[(size_t)k * A.n_sup + n]);
             float ri = rsqrtf(e1);
-            nlw = fmaf(att, kLog2e, -log2f(A.w_const * gm.z * kt * rinv * ri));
+            nlw = fmaf(att, kLog2e, -__log2f(A.w_const * gm.z * kt * rinv * ri));
             s = A.cE * ri;
             b = -e1 * s;
         }
@@ -148,10 +148,10 @@ __global__ void k_wtable_sens(WSensArgs S) {
             const float mu = gm.z;
             const float e1 = A.e0 * P;
             const float ri = rsqrtf(e1);
-            nlw = fmaf(att, kLog2e, -log2f(A.w_const * mu * kt * rinv * ri));
+            nlw = fmaf(att, kLog2e, -__log2f(A.w_const * mu * kt * rinv * ri));
             s = A.cE * ri;
             b = -e1 * s;
-            const float w = S.w_const_sens * mu * kt * rinv * expf(-att);
+            const float w = S.w_const_sens * mu * kt * rinv * __expf(-att);
             part = fmaf(w, __ldg(du + k) * cr.y, part);
         }
         base[(size_t)k * A.ld_w] = s;

@@ -59,7 +59,7 @@ __global__ void k_sens_angle(SensArgs A) {
             compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
             float2 cr = compton_lookup(A.compton, cpsi);  // (mu ratio, window mass)
             float att = fmaf(cr.x, __ldg(le + pm), lp[(size_t)k * A.n_sup]);
-            float w = A.w_const * gm.z * kt * rinv * expf(-att);
+            float w = A.w_const * gm.z * kt * rinv * __expf(-att);
             part = fmaf(w, __ldg(du + k) * cr.y, part);
         }
         if ((k & 31) == 31) {
