@@ -121,7 +121,9 @@ constexpr int pass_rows() {
     return pass_half3<H, VPT>() ? 1 : (VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4));
 }
 
-template <typename H, int VPT, int R, bool BACK>
+// W: rows carry counts (binned rows; A.weight), compiled apart so that the
+// list-mode pass keeps its exact instruction stream.
+template <typename H, int VPT, int R, bool BACK, bool W>
 __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass(PassArgs A) {
     constexpr int EPV = Vec<H>::N;
     __shared__ float red[2][R][kMaxPassThreads / 32];
@@ -188,7 +190,8 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
             for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
             const bool ok = r + i < re && y > 0.0f;
             if constexpr (BACK) {
-                const float inv = ok ? (A.weight ? A.weight[r + i] : 1.0f) / y : 0.0f;
+                float inv = ok ? 1.0f / y : 0.0f;
+                if constexpr (W) inv *= A.weight[r + i];  // a binned row counts its photons
                 const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
@@ -205,9 +208,14 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
             } else {
                 if (ok && t == i) {
                     const float c = A.scale ? A.scale[r + i] : 1.0f;
-                    const double w = A.weight ? (double)A.weight[r + i] : 1.0;
-                    ll += w * (double)logf(c * y);
-                    npos += w;
+                    if constexpr (W) {
+                        const double w = (double)A.weight[r + i];
+                        ll += w * (double)logf(c * y);
+                        npos += w;
+                    } else {
+                        ll += (double)logf(c * y);
+                        npos += 1.0;
+                    }
                 }
             }
         }
@@ -495,7 +503,8 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
             float y = 0.0f;
             for (int w = 0; w < NW; ++w) y += red[i][w];
             if constexpr (BACK) {
-                const float inv = y > 0.0f ? (A.weight ? A.weight[row + i] : 1.0f) / y : 0.0f;
+                float inv = y > 0.0f ? 1.0f / y : 0.0f;
+                if (A.weight) inv *= A.weight[row + i];  // a binned row counts its photons
                 const uint4* rp = reinterpret_cast<const uint4*>(st + i * A.ld_bytes);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
@@ -575,10 +584,10 @@ PassShape pass_shape(const lmosem_ctx* c) {
 }
 
 // register-pipelined pass (pass_variant 0 or 1)
-template <typename H, int VPT, bool BACK>
+template <typename H, int VPT, bool BACK, bool W>
 lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
     constexpr int R = pass_rows<H, VPT>();
-    auto kern = k_pass<H, VPT, R, BACK>;
+    auto kern = k_pass<H, VPT, R, BACK, W>;
     int per_sm = 0, dev = 0, sms = 0;
     LMOSEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0));
     LMOSEM_CK(c, cudaGetDevice(&dev));
@@ -597,9 +606,9 @@ lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt)
 }
 
 // bulk-copy ring pass (pass_variant 2)
-template <typename H, int VPT, bool BACK>
+template <typename H, int VPT, bool BACK, bool W>
 lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
-    if (c->pass_variant != 2) return launch_pass_reg_t<H, VPT, BACK>(c, A0, rows, nt);
+    if (c->pass_variant != 2) return launch_pass_reg_t<H, VPT, BACK, W>(c, A0, rows, nt);
     auto kern = k_pass_ring<H, VPT, BACK>;
     // ring shape: stages of G rows (~24 KB), ~96 KB of stages per CTA unless set
     const int64_t rb = A0.ld_bytes;
@@ -615,7 +624,7 @@ lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
     while ((int64_t)S * G * rb > smem_max && S > 2) --S;
     while ((int64_t)S * G * rb > smem_max && G > 1) --G;
     if ((int64_t)S * G * rb > smem_max)  // two stages of one row do not fit: use the register pass
-        return launch_pass_reg_t<H, VPT, BACK>(c, A0, rows, nt);
+        return launch_pass_reg_t<H, VPT, BACK, W>(c, A0, rows, nt);
     const size_t smem = (size_t)S * G * rb;
     LMOSEM_CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
@@ -652,15 +661,15 @@ lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
     return LMOSEM_OK;
 }
 
-template <typename H, bool BACK>
+template <typename H, bool BACK, bool W = false>
 lmosem_status launch_pass_h(lmosem_ctx* c, const PassArgs& A, int64_t rows, PassShape s) {
     switch (s.vpt) {
-        case 1: return launch_pass_t<H, 1, BACK>(c, A, rows, s.nt);
-        case 2: return launch_pass_t<H, 2, BACK>(c, A, rows, s.nt);
-        case 3: return launch_pass_t<H, 3, BACK>(c, A, rows, s.nt);
-        case 4: return launch_pass_t<H, 4, BACK>(c, A, rows, s.nt);
-        case 6: return launch_pass_t<H, 6, BACK>(c, A, rows, s.nt);
-        default: return launch_pass_t<H, 8, BACK>(c, A, rows, s.nt);
+        case 1: return launch_pass_t<H, 1, BACK, W>(c, A, rows, s.nt);
+        case 2: return launch_pass_t<H, 2, BACK, W>(c, A, rows, s.nt);
+        case 3: return launch_pass_t<H, 3, BACK, W>(c, A, rows, s.nt);
+        case 4: return launch_pass_t<H, 4, BACK, W>(c, A, rows, s.nt);
+        case 6: return launch_pass_t<H, 6, BACK, W>(c, A, rows, s.nt);
+        default: return launch_pass_t<H, 8, BACK, W>(c, A, rows, s.nt);
     }
 }
 
@@ -686,6 +695,10 @@ lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f,
     A.log_T = log(T);
     A.bpart = c->d_bpart;
     A.llpart = c->d_llpart;
+    if (c->d_weight) {  // binned rows: FP32 only
+        if (c->fmt != LMOSEM_MODEL_FP32) return fail(c, LMOSEM_ESTATE, "binned rows are FP32");
+        return launch_pass_h<float, BACK, true>(c, A, rows, s);
+    }
     if (c->fmt == LMOSEM_MODEL_FP32) return launch_pass_h<float, BACK>(c, A, rows, s);
     if (c->fmt == LMOSEM_MODEL_FP16_SCALED) return launch_pass_h<__half, BACK>(c, A, rows, s);
     return launch_pass_h<__nv_bfloat16, BACK>(c, A, rows, s);
@@ -856,7 +869,7 @@ cudaError_t noalloc_scratch(float** out) {
 template <int VPT>
 cudaError_t noalloc_pass(const PassArgs& A0, int64_t rows, int nt, cudaStream_t s, int* grid_out) {
     constexpr int R = VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4);
-    auto kern = k_pass<float, VPT, R, true>;
+    auto kern = k_pass<float, VPT, R, true, false>;
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
