@@ -290,6 +290,41 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const float* __restri
     }
 }
 
+// b_q over the per-CTA partials with every SM busy: a CTA owns 8 support
+// pixels, its 32 groups of 8 threads sum the partials g, g + 32, ... (one
+// 32-byte sector per load), then group 0 adds the 32 group sums in order.
+constexpr int kUpdPix = 8, kUpdGroups = 32;
+__global__ void __launch_bounds__(kUpdPix * kUpdGroups) k_update_px(const float* __restrict__ bpart, int nparts,
+                                                                  int n_sup, float* __restrict__ f,
+                                                                  const double* __restrict__ sens_i, double T,
+                                                                  const int* __restrict__ status) {
+    if (status && *status) return;
+    __shared__ float sh[kUpdGroups][kUpdPix + 1];
+    const int p = threadIdx.x % kUpdPix, g = threadIdx.x / kUpdPix;
+    const int n = blockIdx.x * kUpdPix + p;
+    float b = 0.0f;
+    if (n < n_sup) {
+        int c = g;
+        for (; c + 7 * kUpdGroups < nparts; c += 8 * kUpdGroups) {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = bpart[(size_t)(c + k * kUpdGroups) * n_sup + n];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b += v[k];
+        }
+        for (; c < nparts; c += kUpdGroups) b += bpart[(size_t)c * n_sup + n];
+    }
+    sh[g][p] = b;
+    __syncthreads();
+    if (g == 0 && n < n_sup) {
+        float s = 0.0f;
+        for (int k = 0; k < kUpdGroups; ++k) s += sh[k][p];
+        const double sd = sens_i[n];
+        const float ts = (float)(T * sd);
+        f[n] = sd > 0.0 ? f[n] * s / ts : 0.0f;
+    }
+}
+
 // loglik = sum of the per-CTA partials - T sum_q s_q f_q (FP64, one block)
 __global__ void k_ll_final(const double* __restrict__ llpart, int nparts,
                            const double* __restrict__ s_total, const float* __restrict__ f,
@@ -744,7 +779,7 @@ lmosem_status enqueue_iteration(lmosem_ctx* c, double T, float* d_f) {
         if ((st = launch_pass<true>(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T)))
             return st;
         LMOSEM_PROF_BEGIN(c);
-        k_update<<<(c->n_sup + 31) / 32, kUpdWarps * 32, 0, c->stream>>>(
+        k_update_px<<<(c->n_sup + kUpdPix - 1) / kUpdPix, kUpdPix * kUpdGroups, 0, c->stream>>>(
             c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T,
             c->d_status);
         LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
