@@ -362,6 +362,11 @@ def run_ours(args, rank, world, local_rank):
                     e1.record(stream)
                     e1.synchronize()
                     it_times.append(e0.elapsed_time(e1))
+                # count conservation of the last sub-iteration (Eq. 7), FP64
+                tot = torch.zeros(ns, dtype=torch.float64, device=dev)
+                L.lmosem_subset_totals(ctx, T, f, tot)
+                n_last = int(np.sum(ev.angle % ns == ns - 1))
+                count_resid = abs(float(tot[ns - 1].item()) - n_last) / max(1, n_last)
         finally:
             L.lmosem_destroy(ctx)
 
@@ -442,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
                          (model_bytes / 1e9)},
         "s_per_iter": statistics.mean(it_times) * 1e-3,
         "s_per_iter_on_the_fly": statistics.median(otf_times) * 1e-3,
+        "count_conservation_rel_residual": count_resid,
         "s_per_iter_detail": {"pass_ms_per_launch": pass_ms / max(1, pass_n),
                               "pass_gbs": pass_gbs, "hbm_peak_gbs": pk["hbm_gbs"],
                               "pass_frac_of_%s_hbm" % pk_kind: pass_gbs / pk["hbm_gbs"],

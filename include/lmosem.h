@@ -334,6 +334,14 @@ lmosem_status lmosem_init_image(lmosem_ctx* ctx, double acq_time, float* d_f);
 lmosem_status lmosem_iterate(lmosem_ctx* ctx, int32_t n_iters, double acq_time, float* d_f,
                              double* d_loglik);
 
+/* The expected count of every subset for the image d_f: d_out[i] =
+ * T sum_q s^i_q f_q (FP64, fixed-order reduction), n_subsets values.  Right
+ * after the sub-iteration of subset i this equals the number of its events
+ * (or the sum of its counts) with y_j > 0: the count conservation of the EM
+ * update (paper Eq. 7), a cheap check of a reconstruction.
+ * ESTATE: no sensitivity for the model's subset count. */
+lmosem_status lmosem_subset_totals(lmosem_ctx* ctx, double acq_time, const float* d_f, double* d_out);
+
 /* Log-likelihood of paper Eq. 3 (without log J!) of the image d_f:
  * sum_j log(T y_j) - T sum_q s_q f_q, FP64 reduction, into d_out[0]. */
 lmosem_status lmosem_loglik(lmosem_ctx* ctx, double acq_time, const float* d_f, double* d_out);

@@ -605,6 +605,14 @@ lmosem_status lmosem_iterate(lmosem_ctx* c, int32_t n_iters, double T, float* d_
     return LMOSEM_OK;
 }
 
+lmosem_status lmosem_subset_totals(lmosem_ctx* c, double T, const float* d_f, double* d_out) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!d_f || !d_out || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad arguments");
+    if (c->sens_subsets < 1 || (c->fmt >= 0 && c->sens_subsets != c->n_subsets))
+        return fail(c, LMOSEM_ESTATE, "needs a sensitivity for the model's subset count");
+    return run_subset_totals(c, T, d_f, d_out);
+}
+
 lmosem_status lmosem_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out) {
     if (!c) return LMOSEM_EINVAL;
     if (!d_f || !d_out || !finite_pos(T)) return fail(c, LMOSEM_EINVAL, "bad arguments");

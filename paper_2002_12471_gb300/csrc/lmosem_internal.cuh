@@ -259,6 +259,7 @@ lmosem_status wtab_all_with_sens(lmosem_ctx* c, double* sens_angle, float w_cons
 lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll);
 lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_out);
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f);
+lmosem_status run_subset_totals(lmosem_ctx* c, double T, const float* d_f, double* d_out);
 lmosem_status run_model_rows(lmosem_ctx* c, const int64_t* ids, int64_t n, float* out);
 lmosem_status setup_pass(lmosem_ctx* c);
 // the device status word (bounded waits that ran out), allocated once and zeroed

@@ -325,6 +325,22 @@ __global__ void __launch_bounds__(kUpdPix * kUpdGroups) k_update_px(const float*
     }
 }
 
+// T sum_q s^i_q f_q for every subset i (FP64; one CTA per subset, fixed order)
+__global__ void k_subset_totals(const double* __restrict__ sens, int n_sup, const float* __restrict__ f,
+                                double T, double* __restrict__ out) {
+    __shared__ double sh[256];
+    const double* s = sens + (size_t)blockIdx.x * n_sup;
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < n_sup; n += blockDim.x) acc += s[n] * (double)f[n];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) t += sh[k];
+        out[blockIdx.x] = T * t;
+    }
+}
+
 // loglik = sum of the per-CTA partials - T sum_q s_q f_q (FP64, one block)
 __global__ void k_ll_final(const double* __restrict__ llpart, int nparts,
                            const double* __restrict__ s_total, const float* __restrict__ f,
@@ -855,6 +871,13 @@ lmosem_status run_loglik(lmosem_ctx* c, double T, const float* d_f, double* d_ou
     lmosem_status st;
     if ((st = launch_pass<false>(c, 0, c->J, d_f, T))) return st;
     return ll_final(c, T, d_f, d_out);
+}
+
+lmosem_status run_subset_totals(lmosem_ctx* c, double T, const float* d_f, double* d_out) {
+    LMOSEM_PROF_BEGIN(c);
+    k_subset_totals<<<c->sens_subsets, 256, 0, c->stream>>>(c->d_sens, c->n_sup, d_f, T, d_out);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
+    return LMOSEM_OK;
 }
 
 lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f) {

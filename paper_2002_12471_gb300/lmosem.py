@@ -90,6 +90,7 @@ SIGNATURES = {
     "lmosem_model_bytes": (_i64, [_vp]),
     "lmosem_launch_count": (_i64, [_vp]),
     "lmosem_set_wait_budget": (ctypes.c_int, [_vp, _i64]),
+    "lmosem_subset_totals": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
     "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "lmosem_osem_subiter_noalloc": (ctypes.c_int, [_vp, _i64, _i32, _i64, _vp, _vp, _dbl, _vp]),
     "lmosem_build_model_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_int]),
@@ -220,6 +221,10 @@ def lmosem_init_image(ctx, acq_time, d_f):
 def lmosem_iterate(ctx, n_iters, acq_time, d_f, d_loglik=None):
     _check(ctx, load().lmosem_iterate(ctx, int(n_iters), float(acq_time), _ptr(d_f),
                                       _ptr(d_loglik)))
+
+
+def lmosem_subset_totals(ctx, acq_time, d_f, d_out):
+    _check(ctx, load().lmosem_subset_totals(ctx, float(acq_time), _ptr(d_f), _ptr(d_out)))
 
 
 def lmosem_loglik(ctx, acq_time, d_f, d_out):

@@ -84,6 +84,40 @@ def test_dat64_full_size_sampled_rows_and_invariants():
     assert np.dot(out["sens"][ns - 1], out["f"]) == pytest.approx(last, rel=1e-4)
 
 
+@pytest.mark.parametrize("wl,J", [("tiny16", 2000), ("dat32", 9000)])
+def test_subset_totals_count_conservation(wl, J):
+    """lmosem_subset_totals after an iteration: the last subset's expected
+    count T s^i . f equals its number of events (Eq. 7 conserves counts),
+    and every subset's total is the FP64 dot product of the returned
+    sensitivity and image."""
+    import torch
+
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g, _, ns, ni = S.workload(wl)
+    ev = S.simulate_events(ph, g, J, seed=17)
+    dev = torch.device("cuda:0")
+    T = 2.5
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream())
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        sens = torch.zeros((ns, nsup), dtype=torch.float64, device=dev)
+        L.lmosem_sensitivity(ctx, ns, sens)
+        L.lmosem_build_model(ctx, *(torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev)), ns)
+        f = torch.zeros(nsup, dtype=torch.float32, device=dev)
+        L.lmosem_init_image(ctx, T, f)
+        L.lmosem_iterate(ctx, 2, T, f)
+        tot = torch.zeros(ns, dtype=torch.float64, device=dev)
+        L.lmosem_subset_totals(ctx, T, f, tot)
+        torch.cuda.synchronize()
+        tot = tot.cpu().numpy()
+        ref = T * sens.cpu().numpy() @ f.double().cpu().numpy()
+        np.testing.assert_allclose(tot, ref, rtol=1e-12)
+        n_last = int(np.sum(ev.angle % ns == ns - 1))
+        assert tot[ns - 1] == pytest.approx(n_last, rel=1e-5)
+    finally:
+        L.lmosem_destroy(ctx)
+
+
 def test_mlem_loglik_monotone_on_gpu():
     ph, g, J, ns, ni = S.workload("tiny16")
     ev = S.simulate_events(ph, g, 3000, seed=9)
