@@ -129,11 +129,25 @@ __global__ void k_angle_params(int nx, int ny, float dpx, const float2* __restri
 
 // Total Klein-Nishina cross section (textbook closed form; units of
 // 2 pi r_e^2, only ratios are used).
-double sigma_kn_host(double e_kev) {
+__host__ __device__ double sigma_kn_total(double e_kev) {
     double k = e_kev / kMec2Kev;
     double l = log1p(2.0 * k);
     return (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / (1.0 + 2.0 * k) - l / k) + l / (2.0 * k) -
            (1.0 + 3.0 * k) / ((1.0 + 2.0 * k) * (1.0 + 2.0 * k));
+}
+
+// cos(psi) table: (sigma_KN(E') / sigma_KN(E0), window mass of the energy
+// blur at E') at kComptonNodes nodes on [-1, 1], in FP64
+__global__ void k_compton_table(double e0, double fwhm_frac, double e_lo, double e_hi, double sig0,
+                                float2* __restrict__ comp) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kComptonNodes) return;
+    const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    const double cp = -1.0 + 2.0 * k / (kComptonNodes - 1);
+    const double e1 = e0 / (1.0 + e0 / kMec2Kev * (1.0 - cp));
+    const double se = fwhm_frac * sqrt(e0 * e1) * fw2s;
+    const double de = 0.5 * (erfc((e_lo - e1) / (sqrt(2.0) * se)) - erfc((e_hi - e1) / (sqrt(2.0) * se)));
+    comp[k] = make_float2((float)(sigma_kn_total(e1) / sig0), (float)de);
 }
 
 double kn_shape_host(double e0, double c) {
@@ -167,16 +181,7 @@ lmosem_status build_tables(lmosem_ctx* c) {
         c->de0 = 0.5 * (erfc((c->e_lo - c->e0) / (sqrt(2.0) * s0)) -
                         erfc((c->e_hi - c->e0) / (sqrt(2.0) * s0)));
     }
-    std::vector<float2> comp(kComptonNodes);
-    const double sig0 = sigma_kn_host(c->e0);
-    for (int k = 0; k < kComptonNodes; ++k) {
-        double cp = -1.0 + 2.0 * k / (kComptonNodes - 1);
-        double e1 = c->e0 / (1.0 + c->e0 / kMec2Kev * (1.0 - cp));
-        double se = c->fwhm_frac * sqrt(c->e0 * e1) * fw2s;
-        double de = 0.5 * (erfc((c->e_lo - e1) / (sqrt(2.0) * se)) -
-                           erfc((c->e_hi - e1) / (sqrt(2.0) * se)));
-        comp[k] = make_float2((float)(sigma_kn_host(e1) / sig0), (float)de);
-    }
+    const double sig0 = sigma_kn_total(c->e0);
 
     if ((st = dev_alloc(c, &c->d_trig, c->n_angles))) return st;
     if ((st = dev_alloc(c, &c->d_compton, kComptonNodes))) return st;
@@ -187,8 +192,11 @@ lmosem_status build_tables(lmosem_ctx* c) {
     if ((st = dev_alloc(c, &c->d_ppar, (size_t)c->n_angles * c->ld_w))) return st;
     LMOSEM_CK(c, cudaMemcpyAsync(c->d_trig, trig.data(), trig.size() * sizeof(float2),
                                  cudaMemcpyHostToDevice, c->stream));
-    LMOSEM_CK(c, cudaMemcpyAsync(c->d_compton, comp.data(), comp.size() * sizeof(float2),
-                                 cudaMemcpyHostToDevice, c->stream));
+    // the cos(psi) table on the device (FP64; 16k nodes would cost the host ~1 ms)
+    LMOSEM_PROF_BEGIN(c);
+    k_compton_table<<<(kComptonNodes + 255) / 256, 256, 0, c->stream>>>(c->e0, c->fwhm_frac, c->e_lo, c->e_hi,
+                                                                         sig0, c->d_compton);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_TABLES);
 
     float dpx = (float)c->dpx;
     LMOSEM_PROF_BEGIN(c);
