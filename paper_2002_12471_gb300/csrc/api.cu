@@ -369,7 +369,6 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     if (e == cudaSuccess && c->n_scat)
         e = cudaMemcpyAsync(c->d_scat_geo, geo.data(), c->n_scat * sizeof(float4),
                             cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // geo is a stack buffer
     if (e != cudaSuccess) {
         cuda_fail(c, e, "copy of the mu-map");
         lmosem_destroy(c);

@@ -1055,7 +1055,8 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
             LMOSEM_LAUNCHED(c, LMOSEM_K_QUANTIZE);
         }
     }
-    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    // stream-ordered frees: no host wait (the caller's events were consumed
+    // before the sort's last synchronisation)
     dev_free(c, &c->d_wtab);
     dev_free(c, &c->d_wtab_all);  // consumed
     dev_free(c, &c->d_stage);
@@ -1125,8 +1126,7 @@ lmosem_status build_binned_rows(lmosem_ctx* c, const int32_t* d_rowmap, int n_eb
         k_binned<<<(unsigned)((int64_t)na * n_ebins * n_btiles * n_ptiles), kBuildThreads, smem, c->stream>>>(B);
         LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
     }
-    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, &c->d_wtab);
+    dev_free(c, &c->d_wtab);      // stream-ordered frees: no host wait
     dev_free(c, &c->d_wtab_all);  // consumed
     return LMOSEM_OK;
 }

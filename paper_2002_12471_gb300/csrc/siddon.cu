@@ -214,8 +214,8 @@ lmosem_status build_tables(lmosem_ctx* c) {
         c->d_l_edge, (float)c->radius, (float)c->fwhm0, (float)c->fwhm_slope, c->k_sigma,
         (float)(0.5 * c->n_bins * c->bin_mm), c->d_mpar, c->d_du_m, c->d_ppar);
     LMOSEM_LAUNCHED(c, LMOSEM_K_TABLES);
-    // the host vectors above must outlive the copies
-    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    // no host wait: a copy from pageable memory returns once its source has
+    // been staged, so the host vectors above may go
     return LMOSEM_OK;
 }
 
