@@ -329,3 +329,37 @@ def test_scaled_model_forms(fmt):
     for name, roi in ph.rois.items():
         w = roi.reshape(-1)
         assert np.dot(w, img) == pytest.approx(np.dot(w, ref), rel=1e-2), name
+
+
+def test_largest_scatter_set():
+    """The largest scatter-pixel set a context accepts (32,768 pixels with
+    mu > 0, the shared-memory bound of the path-sum kernels): model rows and
+    sensitivities against the oracle, with a small explicit support; one
+    more scatter pixel is rejected at creation."""
+    import torch
+
+    import paper_2002_12471_gb300.lmosem as L
+    n = 182                                  # 33,124 pixels
+    mu = np.full((n, n), 0.0146)
+    mu.reshape(-1)[: n * n - 32768] = 0.0    # leaves exactly 32,768 scatter pixels
+    yy, xx = np.mgrid[0:n, 0:n]
+    support = (xx - 100.5) ** 2 + (yy - 90.5) ** 2 <= 9.7 ** 2
+    g = S.geometry(8, 96, 3.0, 150.0)
+    pixel_mm = 1.0
+    rng = np.random.default_rng(23)
+    J = 120
+    angle = rng.integers(0, 8, J).astype(np.int32)
+    u = rng.uniform(-30.0, 30.0, J).astype(np.float32)
+    e = rng.uniform(100.0, 175.0, J).astype(np.float32)
+    ev = S.Events(angle, u, e, np.zeros(J, dtype=np.int8))
+    ph = S.Phantom(mu=mu, activity=np.zeros_like(mu), pixel_mm=pixel_mm, rois={})
+    out = gpu_reconstruct(ph, g, ev, 4, 1, support=support, rows=np.arange(J))
+    P = oracle_problem(ph, g, support=support)
+    assert P.n_sup == int(support.sum()) and len(P.scatter) == 32768
+    assert row_close(out["rows"], P.model(angle, u, e)) <= 1.0
+    np.testing.assert_allclose(out["sens"], P.sensitivity(4), rtol=1e-5)
+    mu2 = mu.copy()
+    mu2.reshape(-1)[0] = 0.0146              # 32,769 scatter pixels
+    with pytest.raises(L.LmosemError) as ei:
+        L.lmosem_create(mu2, pixel_mm, g, support=support)
+    assert ei.value.status == L.EINVAL
