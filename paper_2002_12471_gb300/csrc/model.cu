@@ -222,6 +222,7 @@ struct TileInfo {
     int64_t r0;
 };
 
+template <int NT = kBuildThreads>
 __device__ __forceinline__ TileInfo tile_setup(const PathSumArgs& A, int et, int pt, float* ev_u,
                                                float* ev_e, int* misc, int* mlist) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -264,8 +265,10 @@ __device__ __forceinline__ TileInfo tile_setup(const PathSumArgs& A, int et, int
     __syncthreads();
 
     const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
+    static_assert(NT >= kTJ && NT % 32 == 0 && NT <= 256, "64 to 256 threads");
+    constexpr int nwarps = NT / 32;
     int nm = 0;
-    for (int m0 = 0; m0 < A.n_scat; m0 += kBuildThreads) {  // block compaction
+    for (int m0 = 0; m0 < A.n_scat; m0 += NT) {  // block compaction
         int m = m0 + tid;
         bool in = false;
         if (m < A.n_scat) {
@@ -276,7 +279,7 @@ __device__ __forceinline__ TileInfo tile_setup(const PathSumArgs& A, int et, int
         if (lane == 0) misc[warp] = __popc(bal);
         __syncthreads();
         int off = nm, total = 0;
-        for (int w = 0; w < kBuildThreads / 32; ++w) {
+        for (int w = 0; w < nwarps; ++w) {
             int cw = misc[w];
             if (w < warp) off += cw;
             total += cw;
@@ -351,17 +354,19 @@ constexpr int kOffMisc = kOffEv + 2 * kTJ;            // 16 ints
 constexpr int kOffList = kOffMisc + 16;               // n_scat ints
 
 // stage c0 .. c0 + kStage - 1 of the strip union into buffer buf: the first
-// nq 4-column groups of each plane row (padded scatter pixels get s = b = 0,
-// w = inf and a negative cut, i.e. exact zeros), then commit the group
+// nq 4-column groups of each plane row, rows `row` floats apart (padded
+// scatter pixels get s = b = 0, w = inf and a negative cut, i.e. exact
+// zeros), then commit the group
+template <int NT = kBuildThreads>
 __device__ __forceinline__ void stage_issue(const TileInfo& T, const int* mlist, const float* tab,
                                             size_t plane, int ld_w, const float4* mp_a, float* planes,
-                                            float4* mp, int c0, int buf, int nq) {
+                                            float4* mp, int c0, int buf, int nq, int row = kTN) {
     const int tid = threadIdx.x;
-    for (int k = tid; k < 3 * kStage * nq; k += kBuildThreads) {
+    for (int k = tid; k < 3 * kStage * nq; k += NT) {
         const int p = k / (kStage * nq);
         const int r = k - p * (kStage * nq);
         const int mc = r / nq, q = r - mc * nq;
-        float* dst = planes + ((buf * 3 + p) * kStage + mc) * kTN + 4 * q;
+        float* dst = planes + ((buf * 3 + p) * kStage + mc) * row + 4 * q;
         if (c0 + mc < T.nm) {
             cp_async16(dst, tab + p * plane + (size_t)mlist[c0 + mc] * ld_w + 4 * q);
         } else {
@@ -465,6 +470,89 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs
     const int ngs = (min(A.n_store - T.n0, kTN) + 3) / 4;  // stored groups of the tile
     for (int q = qs; q < ngs; q += 4)
         if (q >= nq) store4(A, row, T.n0 + 4 * q, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f));
+}
+
+// ---- tail form: a last column tile of at most kTailQ x 4 live columns
+//
+// One event per thread and 64 threads per CTA: the thread forms its event's
+// U_jm itself (one ex2 per scatter pixel, skipped pixels are exact zeros)
+// and its nq <= kTailQ groups of 4 columns; three compact stage buffers and
+// one barrier per stage.  Same term operations as the other forms.
+constexpr int kTailQ = 4;
+constexpr int kTRow = 4 * kTailQ;                                 // floats per staged plane row
+constexpr int kTOffPlanes = 0;                                    // [3][3][kStage][kTRow]
+constexpr int kTOffMp = kTOffPlanes + 3 * 3 * kStage * kTRow;     // [3][kStage] float4
+constexpr int kTOffEv = kTOffMp + 3 * kStage * 4;                 // u[kTJ], e[kTJ]
+constexpr int kTOffMisc = kTOffEv + 2 * kTJ;                      // 16 ints
+constexpr int kTOffList = kTOffMisc + 16;                         // n_scat ints
+
+__global__ void __launch_bounds__(kTJ) k_pathsum_tail(PathSumArgs A) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    float* planes = sm + kTOffPlanes;
+    float4* mp = reinterpret_cast<float4*>(sm + kTOffMp);
+    float* ev_u = sm + kTOffEv;
+    float* ev_e = ev_u + kTJ;
+    int* misc = reinterpret_cast<int*>(sm + kTOffMisc);
+    int* mlist = reinterpret_cast<int*>(sm + kTOffList);
+    const int j = threadIdx.x;
+    const TileInfo T = tile_setup<kTJ>(A, blockIdx.x, A.pt0, ev_u, ev_e, misc, mlist);
+    const int nq = A.nq_tail;
+    const float uj = ev_u[j], ej = ev_e[j];
+    const float2 E2 = make_float2(ej, ej);
+    float2 acc[kTailQ][2];
+#pragma unroll
+    for (int q = 0; q < kTailQ; ++q) {
+        acc[q][0] = acc[q][1] = make_float2(0.0f, 0.0f);
+        if (q < nq) {
+            const float4* pp_a = A.ppar + (size_t)T.a * A.ld_w + T.n0 + 4 * q;
+            float4 pp[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pp[c] = __ldg(pp_a + c);
+            primary4(A, pp, uj, ej, acc[q][0], acc[q][1]);
+        }
+    }
+
+    const size_t plane = (size_t)A.n_scat * A.ld_w;
+    const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
+    const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
+    const int nchunks = (T.nm + kStage - 1) / kStage;
+    for (int q = 0; q < min(2, nchunks); ++q)
+        stage_issue<kTJ>(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, q * kStage, q, nq, kTRow);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c % 3;
+        if (c + 1 < nchunks) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();  // stage c landed everywhere; every thread is done with stage c - 1
+        if (c + 2 < nchunks)
+            stage_issue<kTJ>(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 2) * kStage, (c + 2) % 3, nq,
+                             kTRow);
+        const float* pS = planes + (buf * 3 + 0) * kStage * kTRow;
+        const float* pB = planes + (buf * 3 + 1) * kStage * kTRow;
+        const float* pW = planes + (buf * 3 + 2) * kStage * kTRow;
+        for (int mc = 0; mc < kStage; ++mc) {
+            const float U = strip_weight(uj, mp[buf * kStage + mc]);
+            if (U == 0.0f) continue;
+            const float2 U2 = make_float2(U, U);
+#pragma unroll
+            for (int q = 0; q < kTailQ; ++q) {
+                if (q >= nq) break;
+                const int o = mc * kTRow + 4 * q;
+                terms4(E2, U2, *reinterpret_cast<const float4*>(pS + o), *reinterpret_cast<const float4*>(pB + o),
+                       *reinterpret_cast<const float4*>(pW + o), acc[q][0], acc[q][1]);
+            }
+        }
+    }
+
+    if (j >= T.nr) return;
+    float* row = A.out + (T.r0 + j - A.row_base) * A.ld_out;
+#pragma unroll
+    for (int q = 0; q < kTailQ; ++q) {
+        if (q >= nq) break;
+        store4(A, row, T.n0 + 4 * q, acc[q][0], acc[q][1]);
+    }
+    const int ngs = (min(A.n_store - T.n0, kTN) + 3) / 4;  // stored groups of the tile
+    for (int q = nq; q < ngs; ++q) store4(A, row, T.n0 + 4 * q, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f));
 }
 
 // ---- wide form: 64 events x 128 columns, 8 events x 4 columns per thread
@@ -977,6 +1065,8 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const double se0 = sqrt(kappa * c->e0);
     const size_t smem_w = sizeof(float) * ((size_t)kWOffList + c->n_scat);
     const size_t smem_n = sizeof(float) * ((size_t)kOffList + c->n_scat);
+    const size_t smem_t = sizeof(float) * ((size_t)kTOffList + c->n_scat);
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
     LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
     LMOSEM_CK(c, cudaFuncSetAttribute(k_pathsum_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_n));
@@ -1037,7 +1127,10 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
             P.pt0 = n_ptiles - 1;
             P.n_pt = 1;
             LMOSEM_PROF_BEGIN(c);
-            k_pathsum_narrow<<<(unsigned)tiles, kBuildThreads, smem_n, c->stream>>>(P);
+            if (nq_tail <= kTailQ)
+                k_pathsum_tail<<<(unsigned)tiles, kTJ, smem_t, c->stream>>>(P);
+            else
+                k_pathsum_narrow<<<(unsigned)tiles, kBuildThreads, smem_n, c->stream>>>(P);
             LMOSEM_LAUNCHED(c, LMOSEM_K_PATHSUM);
         }
         if (scaled) {

@@ -363,3 +363,21 @@ def test_largest_scatter_set():
     with pytest.raises(L.LmosemError) as ei:
         L.lmosem_create(mu2, pixel_mm, g, support=support)
     assert ei.value.status == L.EINVAL
+
+
+@pytest.mark.parametrize("extra", [1, 6, 15])
+def test_short_last_column_tile(extra):
+    """Supports of 128 + extra pixels: the last column tile holds 1, 2 or 4
+    groups of 4 live columns and runs in the one-event-per-thread tail form;
+    rows against the oracle and a reconstruction."""
+    ph, g, J, ns, ni = S.workload("tiny16")
+    flat = np.nonzero(ph.mu.reshape(-1) > 0)[0][: 128 + extra]
+    supp = np.zeros(ph.mu.size, dtype=bool)
+    supp[flat] = True
+    supp = supp.reshape(ph.mu.shape)
+    ev = S.simulate_events(ph, g, 1500, seed=40 + extra)
+    P = oracle_problem(ph, g, support=supp)
+    p, s, f_ref, _ = _oracle_recon(P, ev, ns, 3)
+    out = gpu_reconstruct(ph, g, ev, ns, 3, support=supp, rows=np.arange(300))
+    assert row_close(out["rows"], p[:300]) <= 1.0
+    assert oracle.rel_l2(out["f"], f_ref) <= 1e-4
