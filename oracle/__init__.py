@@ -19,8 +19,8 @@ bin (angle, position bin, energy bin) with a count n_i; its model is the
 event model integrated over the bin, and the EM update and the likelihood
 weight each row by its count (n_i identical events).
 
-Readings where the paper is silent are listed in the design doc and repeated in
-the docstrings below.
+Where the paper is silent, the reading taken is stated in the docstring of
+the function that uses it.
 """
 from __future__ import annotations
 

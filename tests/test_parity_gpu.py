@@ -1,7 +1,7 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs.
 
-Tolerances (derived in the design doc):
+Tolerances (derived from the arithmetic of each step):
 * model entries: |p_gpu - p_orc| <= 2e-4 |p_orc| + 2e-6 max_n p_orc  (FP32
   terms with MUFU ex2, ~10^3-term FP32 sums, FP32 line integrals, and the
   6-sigma strip of the kernel, which moves entries by < 3e-7 of the row max);
