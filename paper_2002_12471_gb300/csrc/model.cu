@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         const float* pS = planes + (buf * 3 + 0) * kPlaneF + 4 * lane;
         const float* pB = planes + (buf * 3 + 1) * kPlaneF + 4 * lane;
         const float* pW = planes + (buf * 3 + 2) * kPlaneF + 4 * lane;
-#pragma unroll 2
+#pragma unroll 1  // measured: 1% faster than unrolling by 2 (the body is 32 MUFU + 48 FFMA2 already)
         for (int mc = 0; mc < kStage; ++mc) {
             if (!((live >> mc) & 1u)) continue;
             const float4 S = *reinterpret_cast<const float4*>(pS + mc * kTN);
