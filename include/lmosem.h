@@ -102,7 +102,9 @@ typedef struct {
     /* Streaming-pass implementation (tuning knobs; 0 = automatic):
      * 1 = rows double-buffered in registers, 2 = rows staged in a shared-
      * memory ring by bulk (TMA) copies, ring_rows rows per stage (1..8) and
-     * ring_stages stages (2..8). */
+     * ring_stages stages (2..8), 3 = each thread's row vectors staged in its
+     * own slots of a shared-memory ring by cp.async (several row groups in
+     * flight, the arithmetic of 1). */
     int32_t pass_variant;
     int32_t ring_rows;
     int32_t ring_stages;

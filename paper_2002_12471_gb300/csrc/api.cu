@@ -289,7 +289,7 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     }
     if (opts && opts->wait_budget_cycles > 0) c->wait_budget = opts->wait_budget_cycles;
     if (opts) {
-        if (opts->pass_variant < 0 || opts->pass_variant > 2 || opts->ring_rows < 0 ||
+        if (opts->pass_variant < 0 || opts->pass_variant > 3 || opts->ring_rows < 0 ||
             opts->ring_stages < 0) {
             delete c;
             return LMOSEM_EINVAL;

@@ -253,6 +253,173 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
     }
 }
 
+// The same pass with the rows staged through shared memory by cp.async:
+// thread t copies, and later reads, only its own 16-byte vectors of each row,
+// so its slots of the S-stage ring are private (no barrier guards them) and
+// S - 1 row groups stay in flight per thread instead of the one the
+// register double buffer allows.  The arithmetic is that of k_pass, in the
+// same order.
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most n of this thread's newest copy groups are pending (n < 8)
+__device__ __forceinline__ void cpa_wait(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+    }
+}
+constexpr int kCpaMaxStages = 8;
+
+template <typename H, int VPT, int R, bool BACK, bool W>
+__global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass_cpa(PassArgs A, int S) {
+    constexpr int EPV = Vec<H>::N;
+    extern __shared__ __align__(128) unsigned char cring[];
+    __shared__ float red[2][R][kMaxPassThreads / 32];
+    __shared__ double llred[kMaxPassThreads / 32];
+    const int NT = blockDim.x, NW = NT >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const char* model = reinterpret_cast<const char*>(A.model);
+
+    float fr[VPT][EPV], br[VPT][EPV];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        int col0 = EPV * (t + NT * v);
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) {
+            int col = col0 + e;
+            fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
+            br[v][e] = 0.0f;
+        }
+    }
+    const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
+    const int64_t re = min(A.r1, rb + A.rows_per_cta);
+    const int64_t ngroups = re > rb ? (re - rb + R - 1) / R : 0;
+    const size_t gbytes = (size_t)R * A.ld_bytes;
+    double ll = 0.0;
+    double npos = 0.0;
+
+    auto issue = [&](int64_t g) {
+        unsigned char* dst = cring + (size_t)(g % S) * gbytes;
+        const int64_t r0 = rb + g * R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int64_t vec = t + (int64_t)NT * v;
+                if (r0 + i < re && vec < A.nvec)
+                    cpa16(dst + i * A.ld_bytes + vec * 16, model + (r0 + i) * A.ld_bytes + vec * 16);
+            }
+        }
+        cpa_commit();
+    };
+    for (int64_t g = 0; g < min((int64_t)S - 1, ngroups); ++g) issue(g);
+    for (int64_t g = 0; g < ngroups; ++g) {
+        const int64_t issued = min(ngroups, g + S - 1);
+        cpa_wait((int)(issued - 1 - g));  // this thread's copies of group g have landed
+        if (g + S - 1 < ngroups) issue(g + S - 1);  // into the slots of group g - 1, read by this thread only
+        const unsigned char* st = cring + (size_t)(g % S) * gbytes;
+        const int64_t r = rb + g * R;
+        const int rb_ = (int)(g & 1);
+        uint4 raw[R][VPT];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int64_t vec = t + (int64_t)NT * v;
+                raw[i][v] = (r + i < re && vec < A.nvec)
+                                ? *reinterpret_cast<const uint4*>(st + i * A.ld_bytes + vec * 16)
+                                : make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        float d[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            float2 s2 = make_float2(0.0f, 0.0f);  // even and odd columns
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                float p[EPV];
+                Vec<H>::cvt(raw[i][v], p);
+#pragma unroll
+                for (int e = 0; e < EPV; e += 2)
+                    s2 = ffma2(make_float2(p[e], p[e + 1]), make_float2(fr[v][e], fr[v][e + 1]), s2);
+            }
+            float sum = s2.x + s2.y;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            d[i] = sum;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) red[rb_][i][warp] = d[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            float y = 0.0f;
+            for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
+            const bool ok = r + i < re && y > 0.0f;
+            if constexpr (BACK) {
+                float inv = ok ? 1.0f / y : 0.0f;
+                if constexpr (W) inv *= A.weight[r + i];
+                const float2 inv2 = make_float2(inv, inv);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    float p[EPV];
+                    Vec<H>::cvt(raw[i][v], p);
+#pragma unroll
+                    for (int e = 0; e < EPV; e += 2) {
+                        const float2 b2 = ffma2(make_float2(p[e], p[e + 1]), inv2,
+                                                make_float2(br[v][e], br[v][e + 1]));
+                        br[v][e] = b2.x;
+                        br[v][e + 1] = b2.y;
+                    }
+                }
+            } else {
+                if (ok && t == i) {
+                    const float c = A.scale ? A.scale[r + i] : 1.0f;
+                    if constexpr (W) {
+                        const double w = (double)A.weight[r + i];
+                        ll += w * (double)logf(c * y);
+                        npos += w;
+                    } else {
+                        ll += (double)logf(c * y);
+                        npos += 1.0;
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (BACK) {
+        float* bp = A.bpart + (size_t)blockIdx.x * A.n_sup;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            int col0 = EPV * (t + NT * v);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e)
+                if (col0 + e < A.n_sup) bp[col0 + e] = br[v][e];
+        }
+    } else {
+        ll += npos * A.log_T;
+        for (int o = 16; o; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if (lane == 0) llred[warp] = ll;
+        __syncthreads();
+        if (t == 0) {
+            double sm = 0.0;
+            for (int w = 0; w < NW; ++w) sm += llred[w];
+            A.llpart[blockIdx.x] = sm;
+        }
+    }
+}
+
 // b_q = sum of the per-CTA partials, then f_q <- f_q b_q / (T s^i_q).  One
 // CTA of kUpdWarps warps per 32 support pixels; warp w sums the partials
 // w, w + kUpdWarps, ... with eight loads in flight, then warp 0 adds the warp
@@ -656,9 +823,47 @@ lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt)
     return LMOSEM_OK;
 }
 
+// cp.async ring pass (pass_variant 3): stages of R rows, S stages per CTA
+template <typename H, int VPT, bool BACK, bool W>
+lmosem_status launch_pass_cpa_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt) {
+    constexpr int R = pass_rows<H, VPT>();
+    auto kern = k_pass_cpa<H, VPT, R, BACK, W>;
+    const size_t gbytes = (size_t)R * A.ld_bytes;
+    // about 104 KB of ring per CTA (two CTAs per SM), 3 to kCpaMaxStages stages
+    int S = (int)std::max<int64_t>(3, std::min<int64_t>(kCpaMaxStages, (int64_t)(104 << 10) / (int64_t)gbytes));
+    int dev = 0, sms = 0, smem_max = 0;
+    LMOSEM_CK(c, cudaGetDevice(&dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    while (S > 2 && (size_t)S * gbytes > (size_t)smem_max) --S;
+    if ((size_t)S * gbytes > (size_t)smem_max) return launch_pass_reg_t<H, VPT, BACK, W>(c, A, rows, nt);
+    const size_t smem = (size_t)S * gbytes;
+    LMOSEM_CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LMOSEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+    int64_t grid = std::max(1, per_sm) * (int64_t)sms;
+    grid = std::min<int64_t>(grid, c->pass_ctas);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, (rows + R - 1) / R));
+    A.rows_per_cta = (rows + grid - 1) / grid;
+    A.rows_per_cta = (A.rows_per_cta + R - 1) / R * R;
+    grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
+    c->pass_grid = (int)grid;
+    LMOSEM_PROF_BEGIN(c);
+    kern<<<(unsigned)grid, nt, smem, c->stream>>>(A, S);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
+    return LMOSEM_OK;
+}
+
 // bulk-copy ring pass (pass_variant 2)
 template <typename H, int VPT, bool BACK, bool W>
 lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
+    // automatic: wide FP32 rows (6 or 8 vectors per thread) stream faster
+    // through the cp.async ring (128x128 FP32: 0.98 vs 1.03 ms per iteration,
+    // 90% of HBM); the register pass is faster for every other shape measured
+    // (64x64 FP32 0.25 vs 0.34 ms, 2-byte rows 0.70 vs 0.92 ms at 128x128)
+    constexpr bool kWideF32 = std::is_same<H, float>::value && VPT >= 6;
+    if (c->pass_variant == 3 || (c->pass_variant == 0 && kWideF32))
+        return launch_pass_cpa_t<H, VPT, BACK, W>(c, A0, rows, nt);
     if (c->pass_variant != 2) return launch_pass_reg_t<H, VPT, BACK, W>(c, A0, rows, nt);
     auto kern = k_pass_ring<H, VPT, BACK>;
     // ring shape: stages of G rows (~24 KB), ~96 KB of stages per CTA unless set

@@ -381,3 +381,15 @@ def test_short_last_column_tile(extra):
     out = gpu_reconstruct(ph, g, ev, ns, 3, support=supp, rows=np.arange(300))
     assert row_close(out["rows"], p[:300]) <= 1.0
     assert oracle.rel_l2(out["f"], f_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("fmt", ["fp32", "fp16"])
+def test_cpasync_ring_pass_bitwise(fmt):
+    """The cp.async ring pass (pass_variant 3) does the register pass's
+    arithmetic in the same order: images and log-likelihoods bitwise equal."""
+    ph, g, J, ns, ni = S.workload("dat32")
+    ev = S.simulate_events(ph, g, 9001, seed=33)
+    reg = gpu_reconstruct(ph, g, ev, ns, 3, fmt=fmt, loglik=True, pass_variant=1)
+    cpa = gpu_reconstruct(ph, g, ev, ns, 3, fmt=fmt, loglik=True, pass_variant=3)
+    assert np.array_equal(reg["f"], cpa["f"])
+    assert np.array_equal(reg["loglik"], cpa["loglik"])
