@@ -393,3 +393,14 @@ def test_cpasync_ring_pass_bitwise(fmt):
     cpa = gpu_reconstruct(ph, g, ev, ns, 3, fmt=fmt, loglik=True, pass_variant=3)
     assert np.array_equal(reg["f"], cpa["f"])
     assert np.array_equal(reg["loglik"], cpa["loglik"])
+
+
+def test_wide_fp32_rows_take_the_cpasync_pass_bitwise():
+    """128 x 128 FP32 rows (6 vectors per thread) take the cp.async ring pass
+    automatically; it matches the register pass bit for bit."""
+    ph, g, J, ns, ni = S.workload("dat128")
+    ev = S.simulate_events(ph, g, 3000, seed=35)
+    auto = gpu_reconstruct(ph, g, ev, ns, 2, loglik=True)
+    reg = gpu_reconstruct(ph, g, ev, ns, 2, loglik=True, pass_variant=1)
+    assert np.array_equal(auto["f"], reg["f"])
+    assert np.array_equal(auto["loglik"], reg["loglik"])
