@@ -23,11 +23,15 @@
 // A CTA owns 64 events of one angle (consecutive in position) x 128 support
 // pixels and walks the scatter pixels whose kernel reaches any of its events
 // (|u_j - u_m| <= k_sigma sigma_u(m)); terms outside that cut for a given
-// event are exactly zero.  The table slices of the next 16 scatter pixels are
-// copied into shared memory with cp.async while the current 16 are summed.
-// A warp (8 events) skips the staged scatter pixels outside the cut of all
-// of its events, and a last column tile with few live columns runs in a
-// narrow form (one event per thread); both leave every result bit unchanged.
+// event are exactly zero.  The table slices of 16 scatter pixels at a time
+// are copied into shared memory with cp.async, two stages ahead of the one
+// being summed (three buffers, one CTA barrier per stage).  A warp (8 events)
+// skips the staged scatter pixels outside the cut of all of its events, and a
+// last column tile with few live columns runs in a tail form (one event per
+// thread); both leave every result bit unchanged.
+//
+// The binned form (paper Section 4) integrates the same model over position
+// and energy bins; it reads the same planes (k_binned, below).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
