@@ -6,10 +6,13 @@
 //     b_q = sum_{j in S_i, y_j > 0} p_jq / y_j.
 // Each sub-iteration is one streaming pass over the subset's model rows:
 // every row is loaded once from HBM into registers (the next rows are
-// already in flight while the current ones are reduced), y_j is formed by a
-// CTA reduction, and the same registers are back-projected into the CTA's
-// private b (registers, FP32).  A second kernel reduces the per-CTA b in CTA
-// order (deterministic) and applies the update with T s^i_q formed in FP64.
+// already in flight while the current ones are reduced; for wide FP32 rows
+// they are staged through a cp.async ring instead), y_j is formed by a CTA
+// reduction, and the same registers are back-projected into the CTA's
+// private b (registers, FP32).  A second kernel reduces the per-CTA b in a
+// fixed order (deterministic) and applies the update with T s^i_q formed in
+// FP64.  Binned rows carry a count that weights their back-projection and
+// log-likelihood terms.
 // The log-likelihood of Eq. 3 (without log J!) has its own pass: log(y_j) in
 // FP32, reduced in FP64.
 #include <cuda_bf16.h>
