@@ -404,3 +404,23 @@ def test_wide_fp32_rows_take_the_cpasync_pass_bitwise():
     reg = gpu_reconstruct(ph, g, ev, ns, 2, loglik=True, pass_variant=1)
     assert np.array_equal(auto["f"], reg["f"])
     assert np.array_equal(auto["loglik"], reg["loglik"])
+
+
+def test_introspection_and_error_messages():
+    """lmosem_n_scatter counts the mu > 0 pixels; a rejected call leaves its
+    reason in lmosem_last_error, which the binding puts in the exception."""
+    import torch
+
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g, J, ns, ni = S.workload("tiny16")
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream())
+    try:
+        assert L.lmosem_n_scatter(ctx) == int(np.sum(ph.mu > 0))
+        assert L.lmosem_n_support(ctx) == int(np.sum(ph.mu > 0))
+        with pytest.raises(L.LmosemError) as ei:
+            L.lmosem_sensitivity(ctx, g["n_angles"] + 1)
+        assert ei.value.status == L.EINVAL
+        msg = L.load().lmosem_last_error(ctx).decode()
+        assert "n_subsets" in msg and msg in str(ei.value)
+    finally:
+        L.lmosem_destroy(ctx)
