@@ -93,8 +93,9 @@ typedef struct {
      * their CUDA-graph replay on non-default streams and are not timed. */
     int32_t profile;
     /* Clock-cycle budget of every bounded device wait (the mbarrier waits of
-     * the streaming OSEM pass, the path-sum stage ring, the tensor-core
-     * surrogate and the batch scheduler); 0 selects 2e9 (about one second).
+     * the TMA-ring OSEM pass, the tensor-core surrogate and the batch
+     * scheduler's work queue; the path sum and the other passes wait only at
+     * CTA barriers); 0 selects 2e9 (about one second).
      * A wait that runs out abandons its kernel and the call returns
      * LMOSEM_ETIMEOUT; the context stays usable.  Tests set a tiny budget
      * (here or with lmosem_set_wait_budget) to exercise that path. */
