@@ -1,0 +1,138 @@
+"""The EM pins have teeth: plausible mistakes planted in copies of the
+oracle's update and log-likelihood (Eqs. 3, 7 and 8), on the CPU, each fail
+at least one of the checks that the unmodified oracle passes.  The checks
+are the ones that pin the oracle elsewhere: count conservation at every
+sub-iteration, the single-pixel closed form, and the likelihood maximum at
+the MLEM fixed point."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_12471_gb300 import synthetic as S
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    ph, g, J, _, _ = S.workload("tiny16")
+    g = dict(g, pixel_mm=ph.pixel_mm)
+    ev = S.simulate_events(ph, g, J, seed=1)
+    P = oracle.Problem(g, ph.mu)
+    p = P.model(ev.angle, ev.u_mm, ev.e_kev)
+    s4 = P.sensitivity(4)
+    supp = np.zeros_like(ph.mu)
+    supp[8, 7] = 1
+    P1 = oracle.Problem(g, ph.mu, support=supp)
+    ev1 = S.simulate_events(ph, g, 400, seed=2)
+    return dict(p=p, ev=ev, s4=s4, s1=P.sensitivity(1)[0], J=J,
+                p1=P1.model(ev1.angle, ev1.u_mm, ev1.e_kev), ev1=ev1, s1pix=P1.sensitivity(4))
+
+
+# ------------------------------------------------------------------ checks
+
+def conserves_counts(update, d, T=2.5):
+    p, s, ev = d["p"], d["s4"], d["ev"]
+    f = oracle.initial_image(d["J"], s.sum(0), T)
+    sub = oracle.subset_of(ev.angle, 4)
+    for _ in range(2):
+        for i in range(4):
+            rows = p[sub == i]
+            n_pos = int(np.sum(rows @ f > 0))
+            f = update(rows, f, s[i], T, s.sum(0))
+            if abs(T * np.dot(s[i], f) - n_pos) > 1e-10 * n_pos:
+                return False
+    return True
+
+
+def single_pixel_closed_form(update, d, T=0.7):
+    p, s, ev = d["p1"], d["s1pix"], d["ev1"]
+    sub = oracle.subset_of(ev.angle, 4)
+    f = np.array([5.0])
+    for i in range(4):
+        f = update(p[sub == i], f, s[i], T, s.sum(0))
+        if abs(f[0] - np.sum(sub == i) / (T * s[i, 0])) > 1e-11 * f[0]:
+            return False
+    return True
+
+
+def fixed_point_is_a_likelihood_maximum(loglik, d, n_iters=400, seed=3):
+    """After MLEM iterations the image is close to the maximiser, so small
+    non-negative perturbations along the support lower the likelihood."""
+    p, s = d["p"], d["s1"]
+    f = oracle.initial_image(d["J"], s)
+    for _ in range(n_iters):
+        f = oracle.osem_subiteration(p, f, s)
+    base = loglik(p, f, s)
+    rng = np.random.default_rng(seed)
+    for _ in range(8):
+        df = rng.normal(size=f.shape) * 0.05 * f
+        if loglik(p, f + df, s) > base + 1e-9 * abs(base):
+            return False
+    return True
+
+
+def oracle_update(p_sub, f, s_i, T, s_total):
+    return oracle.osem_subiteration(p_sub, f, s_i, T)
+
+
+# ------------------------------------------------------------------ mutants
+
+def m_total_sensitivity(p_sub, f, s_i, T, s_total):
+    """Normalises by the total sensitivity instead of the subset's."""
+    return oracle.osem_subiteration(p_sub, f, s_total, T)
+
+
+def m_dropped_T(p_sub, f, s_i, T, s_total):
+    """Forgets the acquisition time in the normalisation."""
+    return oracle.osem_subiteration(p_sub, f, s_i, 1.0)
+
+
+def m_squared_denominator(p_sub, f, s_i, T, s_total):
+    """Back-projects 1 / y_j^2 instead of 1 / y_j."""
+    y = p_sub @ f
+    b = p_sub.T @ (1.0 / y ** 2)
+    return f * b / (T * s_i)
+
+
+def m_damped(p_sub, f, s_i, T, s_total):
+    """A square-root (damped) multiplicative step: same fixed point, but not
+    the EM update."""
+    y = p_sub @ f
+    b = p_sub.T @ (1.0 / y)
+    return f * np.sqrt(b / (T * s_i))
+
+
+def m_forward_with_ones(p_sub, f, s_i, T, s_total):
+    """Forward-projects a uniform image instead of the current one."""
+    y = p_sub @ np.ones_like(f)
+    b = p_sub.T @ (1.0 / y)
+    return f * b / (T * s_i)
+
+
+def ll_flipped_sensitivity(p, f, s_total, T=1.0):
+    return float(np.sum(np.log(T * (p @ f))) + T * np.dot(s_total, f))
+
+
+def ll_no_log(p, f, s_total, T=1.0):
+    return float(np.sum(T * (p @ f)) - T * np.dot(s_total, f))
+
+
+# ------------------------------------------------------------------ tests
+
+def test_the_oracle_passes_every_check(tiny):
+    assert conserves_counts(oracle_update, tiny)
+    assert single_pixel_closed_form(oracle_update, tiny)
+    assert fixed_point_is_a_likelihood_maximum(oracle.loglik, tiny)
+
+
+@pytest.mark.parametrize("mutant", [m_total_sensitivity, m_dropped_T, m_squared_denominator,
+                                    m_damped, m_forward_with_ones],
+                         ids=lambda m: m.__name__)
+def test_planted_update_mistakes_fail_a_pin(tiny, mutant):
+    results = {"count conservation": conserves_counts(mutant, tiny),
+               "single-pixel closed form": single_pixel_closed_form(mutant, tiny)}
+    assert not all(results.values()), results
+
+
+@pytest.mark.parametrize("mutant", [ll_flipped_sensitivity, ll_no_log], ids=lambda m: m.__name__)
+def test_planted_likelihood_mistakes_fail_the_maximum_check(tiny, mutant):
+    assert not fixed_point_is_a_likelihood_maximum(mutant, tiny)
