@@ -349,6 +349,23 @@ lmosem_status lmosem_subset_totals(lmosem_ctx* ctx, double acq_time, const float
  * sum_j log(T y_j) - T sum_q s_q f_q, FP64 reduction, into d_out[0]. */
 lmosem_status lmosem_loglik(lmosem_ctx* ctx, double acq_time, const float* d_f, double* d_out);
 
+/* One whole reconstruction from host buffers, the end-to-end call of the
+ * library: copies the n_events events (host arrays as for lmosem_build_model;
+ * pinned memory makes the copies asynchronous, pageable memory also works) to
+ * the device on the context stream, computes the subset sensitivities, builds
+ * and caches the model in format fmt, starts from the uniform image, runs
+ * n_iters OS-LM-MLEM iterations (paper Eqs. 7-9) and copies the image
+ * (N_nz FP32) to h_f and, when h_loglik != NULL, the log-likelihood of paper
+ * Eq. 3 (without log J!) of that image to h_loglik[0].  The model and the
+ * sensitivity stay in the context; the device copies of the events and the
+ * image are released.  Synchronises.  Errors as lmosem_sensitivity,
+ * lmosem_build_model, lmosem_iterate and lmosem_loglik; h_f is written only
+ * on success. */
+lmosem_status lmosem_reconstruct(lmosem_ctx* ctx, const int32_t* h_angle, const float* h_u_mm,
+                                 const float* h_e_kev, int64_t n_events, int32_t n_subsets,
+                                 lmosem_model_fmt fmt, int32_t n_iters, double acq_time, float* h_f,
+                                 double* h_loglik);
+
 /* Copy model rows back as FP32 (dequantised for the scaled forms):
  * d_out[k * N_nz + q] = p_{j_k, q} for the caller's original event indices
  * j_k = d_event_ids[k] (device int64, each in [0, J)).  For tests and tools. */

@@ -628,6 +628,48 @@ lmosem_status lmosem_loglik(lmosem_ctx* c, double T, const float* d_f, double* d
     return LMOSEM_OK;
 }
 
+lmosem_status lmosem_reconstruct(lmosem_ctx* c, const int32_t* h_angle, const float* h_u_mm,
+                                 const float* h_e_kev, int64_t n_events, int32_t n_subsets,
+                                 lmosem_model_fmt fmt, int32_t n_iters, double T, float* h_f,
+                                 double* h_loglik) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!h_angle || !h_u_mm || !h_e_kev || !h_f) return fail(c, LMOSEM_EINVAL, "null host buffer");
+    if (n_events < 1 || n_events >= (int64_t(1) << 31))
+        return fail(c, LMOSEM_EINVAL, "n_events must be in [1, 2^31)");
+    if (n_iters < 0 || !finite_pos(T))
+        return fail(c, LMOSEM_EINVAL, "bad iteration count or acquisition time");
+    int32_t* d_a = nullptr;
+    float* d_u = nullptr;
+    float* d_e = nullptr;
+    float* d_f = nullptr;
+    double* d_ll = nullptr;
+    Scratch tmp(c);
+    lmosem_status st;
+    if ((st = tmp.alloc(&d_a, (size_t)n_events)) || (st = tmp.alloc(&d_u, (size_t)n_events)) ||
+        (st = tmp.alloc(&d_e, (size_t)n_events)) || (st = tmp.alloc(&d_f, (size_t)c->n_sup)) ||
+        (st = tmp.alloc(&d_ll, 1)))
+        return st;
+    const size_t n = (size_t)n_events;
+    LMOSEM_CK(c, cudaMemcpyAsync(d_a, h_angle, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(d_u, h_u_mm, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_CK(c, cudaMemcpyAsync(d_e, h_e_kev, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    if ((st = lmosem_sensitivity(c, n_subsets, nullptr)) ||
+        (st = lmosem_build_model(c, d_a, d_u, d_e, n_events, n_subsets, fmt)) ||
+        (st = lmosem_init_image(c, T, d_f)) || (st = lmosem_iterate(c, n_iters, T, d_f, nullptr)) ||
+        (h_loglik && (st = lmosem_loglik(c, T, d_f, d_ll)))) {
+        drop_graph(c);
+        return st;
+    }
+    // the captured iteration graph refers to d_f, which is released on return
+    drop_graph(c);
+    LMOSEM_CK(c, cudaMemcpyAsync(h_f, d_f, sizeof(float) * (size_t)c->n_sup, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    if (h_loglik)
+        LMOSEM_CK(c, cudaMemcpyAsync(h_loglik, d_ll, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    return LMOSEM_OK;
+}
+
 lmosem_status lmosem_profile_read(lmosem_ctx* c, double* h_ms, int64_t* h_launches) {
     if (!c || !h_ms || !h_launches) return LMOSEM_EINVAL;
     if (!c->profile) return fail(c, LMOSEM_ESTATE, "profiling is off");

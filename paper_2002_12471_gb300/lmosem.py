@@ -86,6 +86,8 @@ SIGNATURES = {
     "lmosem_init_image": (ctypes.c_int, [_vp, _dbl, _vp]),
     "lmosem_iterate": (ctypes.c_int, [_vp, _i32, _dbl, _vp, _vp]),
     "lmosem_loglik": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
+    "lmosem_reconstruct": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, ctypes.c_int, _i32, _dbl,
+                                          _vp, _vp]),
     "lmosem_model_rows": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
     "lmosem_model_bytes": (_i64, [_vp]),
     "lmosem_launch_count": (_i64, [_vp]),
@@ -229,6 +231,41 @@ def lmosem_subset_totals(ctx, acq_time, d_f, d_out):
 
 def lmosem_loglik(ctx, acq_time, d_f, d_out):
     _check(ctx, load().lmosem_loglik(ctx, float(acq_time), _ptr(d_f), _ptr(d_out)))
+
+
+def _host(x, dtype):
+    """Host address of a contiguous CPU torch tensor or numpy array of the
+    given numpy dtype (pinned torch tensors make the library's copies
+    asynchronous)."""
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda or not x.is_contiguous() or x.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError("expected a contiguous host tensor of %s" % np.dtype(dtype).name)
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+def lmosem_reconstruct(ctx, h_angle, h_u_mm, h_e_kev, n_subsets, n_iters, acq_time=1.0, fmt="fp32",
+                       h_f=None, h_loglik=None):
+    """Whole reconstruction from host event arrays; returns (image, loglik).
+    ``h_f`` / ``h_loglik``: optional host outputs (N_nz float32, 1 float64),
+    e.g. pinned torch tensors; numpy arrays are allocated otherwise."""
+    a, ka = _host(h_angle, np.int32)
+    u, ku = _host(h_u_mm, np.float32)
+    e, ke = _host(h_e_kev, np.float32)
+    n = int(len(ka))
+    if h_f is None:
+        h_f = np.empty(lmosem_n_support(ctx), dtype=np.float32)
+    if h_loglik is None:
+        h_loglik = np.empty(1, dtype=np.float64)
+    pf, kf = _host(h_f, np.float32)
+    pl, kl = _host(h_loglik, np.float64)
+    if len(kf) < lmosem_n_support(ctx) or len(kl) < 1:
+        raise ValueError("output buffers too small")
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    _check(ctx, load().lmosem_reconstruct(ctx, a, u, e, n, int(n_subsets), f, int(n_iters),
+                                          float(acq_time), pf, pl))
+    return kf, kl
 
 
 def lmosem_model_rows(ctx, d_event_ids, d_out):

@@ -63,6 +63,43 @@ def test_dat32_several_tiles_and_ragged_tails():
     assert oracle.rel_l2(out["f"], f_ref) <= 1e-4
 
 
+def test_reconstruct_from_host_buffers_matches_device_path():
+    """lmosem_reconstruct (host events in, host image and log-likelihood out)
+    runs the device-pointer calls' kernels in the same order, so its image is
+    bitwise theirs; pinned and pageable inputs give the same bits, and an
+    argument error leaves the context usable."""
+    import torch
+
+    import paper_2002_12471_gb300.lmosem as L
+
+    ph, g, _, ns, ni = S.workload("dat32")
+    ev = S.simulate_events(ph, g, 4000, seed=9)
+    ref = gpu_reconstruct(ph, g, ev, ns, ni)
+    P = oracle_problem(ph, g)
+    p, s, f_orc, _ = _oracle_recon(P, ev, ns, ni)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream())
+    try:
+        a = torch.from_numpy(np.ascontiguousarray(ev.angle)).pin_memory()
+        u = torch.from_numpy(np.ascontiguousarray(ev.u_mm)).pin_memory()
+        e = torch.from_numpy(np.ascontiguousarray(ev.e_kev)).pin_memory()
+        f_h = torch.empty(L.lmosem_n_support(ctx), dtype=torch.float32).pin_memory()
+        ll_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        f, ll = L.lmosem_reconstruct(ctx, a, u, e, ns, ni, 1.0, "fp32", f_h, ll_h)
+        f = f.numpy().astype(np.float64)
+        assert np.array_equal(f, ref["f"])
+        assert oracle.rel_l2(f, f_orc) <= 1e-4
+        assert float(ll[0]) == pytest.approx(oracle.loglik(p, f, s.sum(0)), rel=1e-6)
+        with pytest.raises(L.LmosemError):
+            L.lmosem_reconstruct(ctx, ev.angle[:0], ev.u_mm[:0], ev.e_kev[:0], ns, ni)
+        with pytest.raises(L.LmosemError):
+            L.lmosem_reconstruct(ctx, ev.angle, ev.u_mm, ev.e_kev, ns, ni, acq_time=0.0)
+        f2, ll2 = L.lmosem_reconstruct(ctx, ev.angle, ev.u_mm, ev.e_kev, ns, ni)
+        assert np.array_equal(f2.astype(np.float64), f)
+        assert float(ll2[0]) == float(ll[0])
+    finally:
+        L.lmosem_destroy(ctx)
+
+
 def test_dat64_full_size_sampled_rows_and_invariants():
     """The 64 x 64 DaT workload at full size (200k events, 120 angles, 8
     subsets), in the launch configuration the benchmark times: sampled model
