@@ -81,3 +81,26 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lmosem_n_support(None) == 0
     assert lib.lmosem_model_bytes(None) == 0
     lib.lmosem_destroy(None)
+
+
+def test_every_context_call_rejects_a_null_context(lib):
+    """Every status-returning entry point that takes a context returns
+    EINVAL for a null one, before touching the device."""
+    import ctypes
+    skip = {"lmosem_create", "lmosem_status_string", "lmosem_osem_subiter_noalloc",
+            "lmosem_n_support", "lmosem_n_scatter"}   # counts, 0 for a null context
+    seen = 0
+    for name, (res, args) in L.SIGNATURES.items():
+        if name in skip or res is not ctypes.c_int or not args or args[0] is not ctypes.c_void_p:
+            continue
+        vals = [None]
+        for t in args[1:]:
+            if t in (ctypes.c_double, ctypes.c_float):
+                vals.append(0.0)
+            elif t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64):
+                vals.append(0)
+            else:
+                vals.append(None)
+        assert getattr(lib, name)(*vals) == L.EINVAL, name
+        seen += 1
+    assert seen >= 20
