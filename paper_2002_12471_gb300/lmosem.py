@@ -238,7 +238,8 @@ def _host(x, dtype):
     given numpy dtype (pinned torch tensors make the library's copies
     asynchronous)."""
     if hasattr(x, "data_ptr"):
-        if x.is_cuda or not x.is_contiguous() or x.element_size() != np.dtype(dtype).itemsize:
+        if (x.is_cuda or not x.is_contiguous()
+                or str(x.dtype).replace("torch.", "") != np.dtype(dtype).name):
             raise ValueError("expected a contiguous host tensor of %s" % np.dtype(dtype).name)
         return x.data_ptr(), x
     a = np.ascontiguousarray(x, dtype=dtype)

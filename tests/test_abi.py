@@ -104,3 +104,16 @@ def test_every_context_call_rejects_a_null_context(lib):
         assert getattr(lib, name)(*vals) == L.EINVAL, name
         seen += 1
     assert seen >= 20
+
+
+def test_host_buffer_marshalling_checks_dtype_and_device():
+    """The host-buffer call's marshalling passes contiguous CPU tensors and
+    numpy arrays of the declared type and refuses anything else."""
+    import torch
+    p, keep = L._host(torch.arange(4, dtype=torch.int32), np.int32)
+    assert p == keep.data_ptr()
+    p, keep = L._host(np.arange(4, dtype=np.int64), np.int32)     # converted copy, kept alive
+    assert keep.dtype == np.int32 and p == keep.ctypes.data
+    for bad in (torch.zeros(4, dtype=torch.float32), torch.zeros(8, dtype=torch.int32)[::2]):
+        with pytest.raises(ValueError):
+            L._host(bad, np.int32)
