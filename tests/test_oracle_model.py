@@ -1,7 +1,8 @@
 """Pins of the oracle's event model p_jn and sensitivity s^i_n (CPU only):
 brute-force path enumeration with independent line integrals, the mu = 0
-closed form, quadrature of the model density against the sensitivity, and
-the 90-degree symmetry of a symmetric phantom."""
+closed form, the closed-form primary attenuation of a uniform medium,
+quadrature of the model density against the sensitivity, and the 90-degree
+symmetry of a symmetric phantom."""
 import math
 
 import numpy as np
@@ -205,3 +206,37 @@ def test_model_parts_add_up():
     scat = P.model(ev.angle, ev.u_mm, ev.e_kev, primary=False)
     np.testing.assert_allclose(prim + scat, full, rtol=1e-13, atol=1e-300)
     assert np.all(scat > 0) and np.all(prim >= 0)
+
+
+def test_uniform_medium_primary_closed_form():
+    """Closed-form attenuation: with mu uniform over the whole square grid,
+    the primary path of pixel n at angle a crosses mu over the exact distance
+    from its centre to the square's edge along omega_a, so its model entry is
+    exp(-mu l) phi(u; p.t, sigma_u(R - p.omega)) phi(E; E0, sigma_E(E0)).
+    No line-integral code is involved on this side."""
+    n, dpx, mu0 = 7, 4.0, 0.015
+    g = tiny_geom(n_angles=12, n_bins=16, bin_mm=4.0, radius_mm=60.0, angle0_rad=0.1)
+    mu = np.full((n, n), mu0)
+    P = oracle.Problem(dict(g, pixel_mm=dpx), mu)
+    assert P.n_sup == n * n
+    rng = np.random.default_rng(5)
+    J = 40
+    a = rng.integers(0, g["n_angles"], J).astype(np.int32)
+    u = rng.uniform(-12.0, 12.0, J).astype(np.float32)
+    e = rng.uniform(140.0, 175.0, J).astype(np.float32)
+    p = P.model(a, u, e, primary=True, scatter=False)
+    half = 0.5 * n * dpx
+    e0 = g["e0_kev"]
+    se0 = g["fwhm_frac_e0"] * e0 * F2S
+    want = np.zeros((J, n * n))
+    for j in range(J):
+        th = g["angle0_rad"] + 2 * math.pi * a[j] / g["n_angles"]
+        om = np.array([math.cos(th), math.sin(th)])
+        tv = np.array([-math.sin(th), math.cos(th)])
+        for q in range(n * n):
+            pc = np.array([(q % n + 0.5 - 0.5 * n) * dpx, (q // n + 0.5 - 0.5 * n) * dpx])
+            ell = min((math.copysign(half, om[k]) - pc[k]) / om[k] for k in range(2) if om[k] != 0.0)
+            su = (g["coll_fwhm0_mm"] + g["coll_fwhm_slope"] * (g["radius_mm"] - pc @ om)) * F2S
+            want[j, q] = (math.exp(-mu0 * ell) * gauss(float(u[j]), pc @ tv, su)
+                          * gauss(float(e[j]), e0, se0))
+    np.testing.assert_allclose(p, want, rtol=1e-11, atol=1e-15 * want.max())
