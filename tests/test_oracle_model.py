@@ -24,9 +24,15 @@ def gauss(x, m, s):
     return math.exp(-0.5 * ((x - m) / s) ** 2) / (s * math.sqrt(2 * math.pi))
 
 
-def brute_force_row(g, mu, dpx, support, a, u, e):
+def brute_force_row(g, mu, dpx, support, a, u, e, mistake=None):
     """Every path from every support pixel, each with its own line integrals
-    (pixel clipping, no tables), following the frozen model reading."""
+    (pixel clipping, no tables), following the frozen model reading.
+    ``mistake`` plants one plausible error (tests of the pin's power only):
+    'response_at_n' centres the scatter path's collimator response on the
+    emission pixel, 'no_inv_2pi_r' drops the 1/(2 pi r) factor,
+    'flipped_angle' uses -cos(psi) in the Compton and Klein-Nishina laws,
+    'det_from_n' attenuates the scattered photon from the emission pixel,
+    'mu_at_n' takes the interaction probability at the emission pixel."""
     ny, nx = mu.shape
     th = g["angle0_rad"] + 2 * math.pi * a / g["n_angles"]
     om = np.array([math.cos(th), math.sin(th)])
@@ -51,13 +57,18 @@ def brute_force_row(g, mu, dpx, support, a, u, e):
             v = pm - pn
             r = math.hypot(*v)
             c = (v @ om) / r
+            if mistake == "flipped_angle":
+                c = -c
             e1 = oracle.compton_energy(e0, c)
             kt = oracle.kn_shape(e0, c) / kbar
             ratio = oracle.sigma_kn(e1) / oracle.sigma_kn(e0)
-            w = (dpx * dpx * mu.reshape(-1)[m] * kt * math.exp(-clip_line_integral(mu, dpx, pn, pm))
-                 * math.exp(-ratio * clip_line_integral(mu, dpx, pm, pm + far * om))
-                 / (2 * math.pi * r))
-            val += w * gauss(u, pm @ tv, su(pm)) * gauss(e, e1, se(e1))
+            pd = pn if mistake == "det_from_n" else pm
+            mu_i = mu.reshape(-1)[n if mistake == "mu_at_n" else m]
+            w = (dpx * dpx * mu_i * kt * math.exp(-clip_line_integral(mu, dpx, pn, pm))
+                 * math.exp(-ratio * clip_line_integral(mu, dpx, pd, pd + far * om))
+                 / (1.0 if mistake == "no_inv_2pi_r" else 2 * math.pi * r))
+            pr = pn if mistake == "response_at_n" else pm
+            val += w * gauss(u, pr @ tv, su(pr)) * gauss(e, e1, se(e1))
         row.append(val)
     return np.array(row)
 

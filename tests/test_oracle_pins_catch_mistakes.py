@@ -1,9 +1,13 @@
-"""The EM pins have teeth: plausible mistakes planted in copies of the
-oracle's update and log-likelihood (Eqs. 3, 7 and 8), on the CPU, each fail
-at least one of the checks that the unmodified oracle passes.  The checks
-are the ones that pin the oracle elsewhere: count conservation at every
-sub-iteration, the single-pixel closed form, and the likelihood maximum at
-the MLEM fixed point."""
+"""The pins have teeth: plausible mistakes planted on the CPU each fail a
+check that the unmodified oracle passes.
+
+* EM (Eqs. 3, 7 and 8): mistakes in copies of the update and the
+  log-likelihood break count conservation at every sub-iteration, the
+  single-pixel closed form, or the likelihood maximum at the MLEM fixed
+  point.
+* Event model (Eqs. 2 and 4): each mistake planted in the brute-force path
+  enumeration makes it disagree with the oracle far beyond the 1e-12 bound of
+  the enumeration pin, so the same mistake in the oracle would fail it."""
 import numpy as np
 import pytest
 
@@ -136,3 +140,26 @@ def test_planted_update_mistakes_fail_a_pin(tiny, mutant):
 @pytest.mark.parametrize("mutant", [ll_flipped_sensitivity, ll_no_log], ids=lambda m: m.__name__)
 def test_planted_likelihood_mistakes_fail_the_maximum_check(tiny, mutant):
     assert not fixed_point_is_a_likelihood_maximum(mutant, tiny)
+
+
+@pytest.mark.parametrize("mistake", ["response_at_n", "no_inv_2pi_r", "flipped_angle", "det_from_n",
+                                     "mu_at_n"])
+def test_planted_model_mistakes_break_the_enumeration_pin(mistake):
+    from tests.test_oracle_model import brute_force_row, tiny_geom
+    rng = np.random.default_rng(1)
+    n, dpx = 5, 7.0
+    mu = rng.uniform(0.005, 0.03, (n, n)) * (rng.uniform(0, 1, (n, n)) > 0.25)
+    g = tiny_geom(n_angles=4, angle0_rad=0.37, radius_mm=45.0)
+    g["pixel_mm"] = dpx
+    P = oracle.Problem(g, mu, support=np.ones((n, n), dtype=bool))
+    a = rng.integers(0, 4, 6).astype(np.int32)
+    u = rng.uniform(-15, 15, 6)
+    e = rng.uniform(100, 175, 6)
+    p = P.model(a, u, e)
+    worst = 0.0
+    for j in range(6):
+        good = brute_force_row(g, mu, dpx, P.support, int(a[j]), u[j], e[j])
+        bad = brute_force_row(g, mu, dpx, P.support, int(a[j]), u[j], e[j], mistake=mistake)
+        np.testing.assert_allclose(p[j], good, rtol=1e-12, atol=1e-16 * good.max())
+        worst = max(worst, float(np.max(np.abs(p[j] - bad) / (1e-12 * np.abs(good) + 1e-16 * good.max()))))
+    assert worst > 1e3, worst
