@@ -255,6 +255,8 @@ def lmosem_reconstruct(ctx, h_angle, h_u_mm, h_e_kev, n_subsets, n_iters, acq_ti
     u, ku = _host(h_u_mm, np.float32)
     e, ke = _host(h_e_kev, np.float32)
     n = int(len(ka))
+    if len(ku) != n or len(ke) != n:
+        raise ValueError("angle, position and energy arrays differ in length")
     if h_f is None:
         h_f = np.empty(lmosem_n_support(ctx), dtype=np.float32)
     if h_loglik is None:

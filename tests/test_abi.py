@@ -117,3 +117,11 @@ def test_host_buffer_marshalling_checks_dtype_and_device():
     for bad in (torch.zeros(4, dtype=torch.float32), torch.zeros(8, dtype=torch.int32)[::2]):
         with pytest.raises(ValueError):
             L._host(bad, np.int32)
+
+
+def test_host_call_rejects_mismatched_event_arrays():
+    """The host-buffer call checks the three event arrays' lengths before the
+    library reads them (no context is needed to reach that check)."""
+    with pytest.raises(ValueError):
+        L.lmosem_reconstruct(None, np.zeros(4, np.int32), np.zeros(3, np.float32),
+                             np.zeros(4, np.float32), 1, 1)
