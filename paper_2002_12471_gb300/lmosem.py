@@ -209,8 +209,17 @@ def lmosem_sensitivity(ctx, n_subsets, d_sens=None):
     _check(ctx, load().lmosem_sensitivity(ctx, int(n_subsets), _ptr(d_sens)))
 
 
+def _n_events(d_angle, d_u_mm, d_e_kev):
+    """Common length of the three event arrays: the library reads that many
+    entries of each, so a shorter one is refused here."""
+    ns = [int(x.numel()) if hasattr(x, "numel") else int(len(x)) for x in (d_angle, d_u_mm, d_e_kev)]
+    if ns[1] != ns[0] or ns[2] != ns[0]:
+        raise ValueError("angle, position and energy arrays differ in length")
+    return ns[0]
+
+
 def lmosem_build_model(ctx, d_angle, d_u_mm, d_e_kev, n_subsets, fmt="fp32"):
-    n = int(d_angle.numel()) if hasattr(d_angle, "numel") else int(len(d_angle))
+    n = _n_events(d_angle, d_u_mm, d_e_kev)
     f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
     _check(ctx, load().lmosem_build_model(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev), n,
                                           int(n_subsets), f))
@@ -254,9 +263,7 @@ def lmosem_reconstruct(ctx, h_angle, h_u_mm, h_e_kev, n_subsets, n_iters, acq_ti
     a, ka = _host(h_angle, np.int32)
     u, ku = _host(h_u_mm, np.float32)
     e, ke = _host(h_e_kev, np.float32)
-    n = int(len(ka))
-    if len(ku) != n or len(ke) != n:
-        raise ValueError("angle, position and energy arrays differ in length")
+    n = _n_events(ka, ku, ke)
     if h_f is None:
         h_f = np.empty(lmosem_n_support(ctx), dtype=np.float32)
     if h_loglik is None:
@@ -307,6 +314,8 @@ def lmosem_build_model_binned(ctx, d_counts, e_edges, n_subsets, fmt="fp32"):
 
 def lmosem_build_model_batch(ctx, d_angle, d_u_mm, d_e_kev, event_offsets, n_subsets, fmt="fp32"):
     off = np.ascontiguousarray(event_offsets, dtype=np.int64)
+    if len(off) and off[-1] > _n_events(d_angle, d_u_mm, d_e_kev):
+        raise ValueError("the last event offset lies beyond the event arrays")
     f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
     _check(ctx, load().lmosem_build_model_batch(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev),
                                                 off.ctypes.data, len(off) - 1, int(n_subsets), f))
@@ -336,7 +345,7 @@ def lmosem_binned_support(ctx, d_angle, d_u_mm, d_e_kev, n_subsets=4, n_iters=3,
     """Support mask (ny * nx uint8, host) from the crude binned OSEM.  The
     defaults cover every pixel of the DaT-like phantoms' activity (at 3, 6
     and 10 iterations) and none of the air around them."""
-    n = int(d_angle.numel())
+    n = _n_events(d_angle, d_u_mm, d_e_kev)
     L = load()
     ny, nx = _GRID[ctx]
     mask = np.zeros(ny * nx, dtype=np.uint8)
@@ -347,7 +356,7 @@ def lmosem_binned_support(ctx, d_angle, d_u_mm, d_e_kev, n_subsets=4, n_iters=3,
 
 
 def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_scatter):
-    n = int(d_angle.numel())
+    n = _n_events(d_angle, d_u_mm, d_e_kev)
     _check(ctx, load().lmosem_surrogate_samples(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev), n,
                                                 _ptr(d_features), _ptr(d_log_scatter)))
 

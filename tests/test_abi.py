@@ -125,3 +125,15 @@ def test_host_call_rejects_mismatched_event_arrays():
     with pytest.raises(ValueError):
         L.lmosem_reconstruct(None, np.zeros(4, np.int32), np.zeros(3, np.float32),
                              np.zeros(4, np.float32), 1, 1)
+
+
+def test_device_calls_reject_mismatched_event_arrays():
+    """Every wrapper that passes event arrays checks their common length (and
+    the batch's last offset against it) before the library reads them."""
+    a, u, e = np.zeros(5, np.int32), np.zeros(4, np.float32), np.zeros(5, np.float32)
+    for call in (lambda: L.lmosem_build_model(None, a, u, e, 1),
+                 lambda: L.lmosem_surrogate_samples(None, a, u, e, None, None),
+                 lambda: L.lmosem_build_model_batch(None, a, u, e, [0, 5], 1),
+                 lambda: L.lmosem_build_model_batch(None, a, e, e, [0, 6], 1)):
+        with pytest.raises(ValueError):
+            call()
