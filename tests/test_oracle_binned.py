@@ -1,6 +1,6 @@
-"""Pins of the support initialiser's FP64 reference (CPU only): the bin-
-integrated projector against numerical quadrature of the collimator
-response, the sinogram against a brute-force count, the EM count identity of
+"""Pins of the support initialiser's FP64 reference (CPU only): its detector
+geometry against closed forms at the axis angles, the bin-integrated
+projector against numerical quadrature of the collimator response, the sinogram against a brute-force count, the EM count identity of
 every sub-iteration, likelihood ascent and point-source recovery on noiseless
 data, and the threshold/dilation on hand-made images."""
 import math
@@ -105,3 +105,20 @@ def test_support_mask_threshold_and_dilation():
     # the threshold keeps only the hot pixel
     m3 = binned.support_mask(f, nx, ny, 0.5, 0)
     assert m3.sum() == 1 and m3[4 * nx + 4]
+
+
+def test_geometry_at_the_axis_angles():
+    """u_a(p) and sigma_u(d_a(p)) against their closed forms at theta = 0,
+    pi/2, pi, 3 pi/2, where the lateral axis and the depth are read off the
+    pixel coordinates: u = y, -x, -y, x and d = R - x, R - y, R + x, R + y."""
+    g = S.geometry(4, 12, 6.0, 60.0, coll_fwhm0_mm=2.0, coll_fwhm_slope=0.1)
+    nx, ny, dpx = 5, 4, 7.0
+    u, sig = binned.geometry_arrays(g, nx, ny, dpx)
+    f2s = 1.0 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    R = g["radius_mm"]
+    for n in range(nx * ny):
+        x = (n % nx + 0.5 - 0.5 * nx) * dpx
+        y = (n // nx + 0.5 - 0.5 * ny) * dpx
+        for a, (uu, d) in enumerate(((y, R - x), (-x, R - y), (-y, R + x), (x, R + y))):
+            assert u[a, n] == pytest.approx(uu, abs=1e-12)
+            assert sig[a, n] == pytest.approx((2.0 + 0.1 * d) * f2s, rel=1e-13)
