@@ -7,7 +7,9 @@ check that the unmodified oracle passes.
   point.
 * Event model (Eqs. 2 and 4): each mistake planted in the brute-force path
   enumeration makes it disagree with the oracle far beyond the 1e-12 bound of
-  the enumeration pin, so the same mistake in the oracle would fail it."""
+  the enumeration pin, so the same mistake in the oracle would fail it.
+* Surrogate MLP: mistakes planted in the backward pass fail the central-
+  difference check of the gradients."""
 import numpy as np
 import pytest
 
@@ -163,3 +165,82 @@ def test_planted_model_mistakes_break_the_enumeration_pin(mistake):
         np.testing.assert_allclose(p[j], good, rtol=1e-12, atol=1e-16 * good.max())
         worst = max(worst, float(np.max(np.abs(p[j] - bad) / (1e-12 * np.abs(good) + 1e-16 * good.max()))))
     assert worst > 1e3, worst
+
+
+# ------------------------------------------------------------------ MLP oracle
+
+def _fd_agrees(seed=1):
+    """The central-difference check of the MLP oracle's gradients, as a
+    predicate (the loss comes from the forward pass alone)."""
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    params = mlp.init_params(3, (6, 16, 12, 8, 1))
+    for W, b in params:
+        b += rng.normal(0, 0.3, b.shape)
+    X = rng.normal(0, 1, (40, 6))
+    t = rng.normal(0, 1, 40)
+    _, grads = mlp.mse_loss_and_grad(params, X, t)
+    h = 1e-6
+    for l, (W, b) in enumerate(params):
+        for arr, g in ((W, grads[l][0]), (b, grads[l][1])):
+            for ix in list(zip(*[rng.integers(0, s, 4) for s in arr.shape])):
+                old = arr[ix]
+                arr[ix] = old + h
+                lp = float(np.mean((mlp.forward(params, X)[0] - t) ** 2))
+                arr[ix] = old - h
+                lm = float(np.mean((mlp.forward(params, X)[0] - t) ** 2))
+                arr[ix] = old
+                if abs(g[ix] - (lp - lm) / (2 * h)) > 1e-6 * abs(g[ix]) + 1e-9:
+                    return False
+    return True
+
+
+def _backward_no_relu_mask(params, cache, dy):
+    g = np.asarray(dy, dtype=np.float64)[:, None]
+    grads = [None] * len(params)
+    for k in range(len(params) - 1, -1, -1):
+        h, z = cache[k]
+        W, _ = params[k]
+        grads[k] = [g.T @ h, g.sum(axis=0)]
+        g = g @ W
+    return grads
+
+
+def _backward_mean_bias(params, cache, dy):
+    g = np.asarray(dy, dtype=np.float64)[:, None]
+    grads = [None] * len(params)
+    for k in range(len(params) - 1, -1, -1):
+        h, z = cache[k]
+        if k < len(params) - 1:
+            g = g * (z > 0.0)
+        W, _ = params[k]
+        grads[k] = [g.T @ h, g.mean(axis=0)]
+        g = g @ W
+    return grads
+
+
+def _backward_relu_value_as_slope(params, cache, dy):
+    """Multiplies by the ReLU's value instead of its slope."""
+    g = np.asarray(dy, dtype=np.float64)[:, None]
+    grads = [None] * len(params)
+    for k in range(len(params) - 1, -1, -1):
+        h, z = cache[k]
+        if k < len(params) - 1:
+            g = g * np.maximum(z, 0.0)
+        W, _ = params[k]
+        grads[k] = [g.T @ h, g.sum(axis=0)]
+        g = g @ W
+    return grads
+
+
+def test_mlp_oracle_passes_the_difference_check():
+    assert _fd_agrees()
+
+
+@pytest.mark.parametrize("mutant", [_backward_no_relu_mask, _backward_mean_bias,
+                                    _backward_relu_value_as_slope],
+                         ids=lambda m: m.__name__)
+def test_planted_backward_mistakes_fail_the_difference_check(monkeypatch, mutant):
+    from oracle import mlp
+    monkeypatch.setattr(mlp, "backward", mutant)
+    assert not _fd_agrees()
