@@ -9,7 +9,9 @@ check that the unmodified oracle passes.
   enumeration makes it disagree with the oracle far beyond the 1e-12 bound of
   the enumeration pin, so the same mistake in the oracle would fail it.
 * Surrogate MLP: mistakes planted in the backward pass fail the central-
-  difference check of the gradients."""
+  difference check of the gradients.
+* Support initialiser: mistakes planted in copies of its bin-integrated
+  projector fail the quadrature check."""
 import numpy as np
 import pytest
 
@@ -244,3 +246,59 @@ def test_planted_backward_mistakes_fail_the_difference_check(monkeypatch, mutant
     from oracle import mlp
     monkeypatch.setattr(mlp, "backward", mutant)
     assert not _fd_agrees()
+
+
+# ------------------------------------------------------------------ support initialiser
+
+def _projector_agrees_with_quadrature(projector):
+    """The quadrature check of the support initialiser's projector, as a
+    predicate: bin masses of the Gaussian collimator response."""
+    import math
+
+    from scipy import integrate
+
+    from oracle import binned
+    g = S.geometry(8, 12, 6.0, 60.0)
+    nx = ny = 8
+    dpx = 7.0
+    A = projector(g, nx, ny, dpx)
+    u, sig = binned.geometry_arrays(g, nx, ny, dpx)
+    rng = np.random.default_rng(0)
+    w = g["bin_mm"]
+    for _ in range(25):
+        a, k, n = rng.integers(0, g["n_angles"]), rng.integers(0, g["n_bins"]), rng.integers(0, nx * ny)
+        lo = -0.5 * g["n_bins"] * w + k * w
+        dens = lambda x: math.exp(-0.5 * ((x - u[a, n]) / sig[a, n]) ** 2) / (sig[a, n] * math.sqrt(2 * math.pi))
+        ref, _ = integrate.quad(dens, lo, lo + w, epsabs=1e-14, epsrel=1e-12)
+        if abs(A[a, k, n] - ref) > 1e-9 * ref + 1e-14:
+            return False
+    return True
+
+
+def _projector_without_sqrt2(g, nx, ny, pixel_mm):
+    """erf of (edge - u) / sigma, missing the 1/sqrt(2)."""
+    from oracle import binned
+    u, sigma = binned.geometry_arrays(g, nx, ny, pixel_mm)
+    w = g["bin_mm"]
+    edges = -0.5 * g["n_bins"] * w + w * np.arange(g["n_bins"] + 1)
+    E = binned._erf((edges[None, :, None] - u[:, None, :]) / sigma[:, None, :])
+    return 0.5 * (E[:, 1:, :] - E[:, :-1, :])
+
+
+def _projector_edges_from_zero(g, nx, ny, pixel_mm):
+    """Bin edges counted from the detector centre instead of its edge."""
+    import math
+
+    from oracle import binned
+    u, sigma = binned.geometry_arrays(g, nx, ny, pixel_mm)
+    w = g["bin_mm"]
+    edges = w * np.arange(g["n_bins"] + 1)
+    E = binned._erf((edges[None, :, None] - u[:, None, :]) / (math.sqrt(2.0) * sigma[:, None, :]))
+    return 0.5 * (E[:, 1:, :] - E[:, :-1, :])
+
+
+def test_support_projector_passes_and_planted_mistakes_fail_quadrature():
+    from oracle import binned
+    assert _projector_agrees_with_quadrature(binned.projector)
+    assert not _projector_agrees_with_quadrature(_projector_without_sqrt2)
+    assert not _projector_agrees_with_quadrature(_projector_edges_from_zero)
