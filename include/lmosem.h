@@ -401,8 +401,9 @@ lmosem_status lmosem_profile_read(lmosem_ctx* ctx, double* h_ms, int64_t* h_laun
  * the library reserves on every GPU that loads it, until the process exits.
  *
  *   d_rows     device, n_rows x ld FP32 model rows p_jq of the subset's
- *              events (row-major, 16-byte aligned, ld a multiple of 4,
- *              columns n_support..ld-1 ignored if they hold zeros)
+ *              events (row-major, 16-byte aligned, ld a multiple of 4 and at
+ *              most 8192); columns n_support..ld-1 are read and multiplied by
+ *              zero, so they must hold finite values (zeros recommended)
  *   d_f        device, n_support FP32 image, updated in place:
  *              f_q <- f_q sum_j p_jq / y_j / (T s_q), y_j = sum_q p_jq f_q;
  *              rows with y_j = 0 add nothing; f_q = 0 where s_q = 0
@@ -410,14 +411,21 @@ lmosem_status lmosem_profile_read(lmosem_ctx* ctx, double* h_ms, int64_t* h_laun
  *   acq_time   T > 0
  *   stream     cudaStream_t the work is enqueued on (NULL: legacy stream)
  *
- * EINVAL: null pointers, n_rows < 1, n_support < 1 or above 16384 (the
- * static array holds at least 64 per-CTA partials of that length), ld out of
- * range or misaligned rows.  ECUDA: a launch or the scratch lookup failed.
- * The first call on each device looks up the address of the static array
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array and each call overwrites what
- * it needs, so calls whose work overlaps on the GPU (different streams or
- * threads) race and must be serialised by the caller. */
+ * EINVAL: null pointers, n_rows < 1, n_support < 1 or above 8192 (the
+ * widest row the register pass holds: 256 threads x 8 vectors of 4 floats;
+ * the static array then holds 128 per-CTA partials), ld out of range or
+ * misaligned rows.  ECUDA: a CUDA error from earlier work was still pending
+ * when the call began (nothing runs and the error is left for the caller to
+ * read), or the set-up or one of this call's launches failed.
+ * The first call on each device, with that device current, looks up the
+ * address of the static array (cudaGetSymbolAddress), caches it and loads
+ * every kernel the entry point can launch, so later calls load nothing; make
+ * that first call before any stream capture.  The cached address belongs to
+ * the device's primary context: after cudaDeviceReset on that device this
+ * entry point must not be called again in the same process.  All calls share
+ * the array and each call overwrites what it needs, so calls whose work
+ * overlaps on the GPU (different streams or threads) race and must be
+ * serialised by the caller. */
 lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_t n_rows, int32_t n_support,
                                           int64_t ld, float* d_f, const double* d_sens_i,
                                           double acq_time, void* stream);

@@ -1108,7 +1108,13 @@ lmosem_status run_init_image(lmosem_ctx* c, double T, float* d_f) {
 namespace {
 
 constexpr int64_t kNoAllocScratchFloats = int64_t(1) << 20;  // 4 MiB
-constexpr int kNoAllocMaxSupport = 16384;                    // >= 64 partial slots
+// The register pass holds at most 8 four-float vectors per thread in
+// kMaxPassThreads threads, so rows (and the support) are at most 8192 wide;
+// the array then still holds 128 per-CTA partials.
+constexpr int kNoAllocMaxVpt = 8;
+constexpr int64_t kNoAllocMaxLd = int64_t(kMaxPassThreads) * kNoAllocMaxVpt * 4;
+constexpr int kNoAllocMaxSupport = (int)kNoAllocMaxLd;
+static_assert(kNoAllocScratchFloats / kNoAllocMaxSupport >= 64, "too few partial slots");
 constexpr int kNoAllocMaxDevices = 64;
 
 __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
@@ -1116,18 +1122,38 @@ __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
+template <int VPT>
+inline auto noalloc_kernel() {
+    return k_pass<float, VPT, VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4), true, false>;
+}
+
+// First call on a device: the array's address, and every kernel this entry
+// point can launch loaded now (module loading is lazy by default), so that
+// later calls with another row width load nothing.
+cudaError_t noalloc_setup() {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    const void* kerns[] = {(const void*)noalloc_kernel<1>(), (const void*)noalloc_kernel<2>(),
+                           (const void*)noalloc_kernel<3>(), (const void*)noalloc_kernel<4>(),
+                           (const void*)noalloc_kernel<6>(), (const void*)noalloc_kernel<8>(),
+                           (const void*)k_update};
+    for (const void* k : kerns)
+        if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+    return cudaSuccess;
+}
+
 cudaError_t noalloc_scratch(float** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<float*>(p);
-    }
+    if (!g_noalloc_ptr[dev] && (e = noalloc_setup()) != cudaSuccess) return e;
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
 }
@@ -1135,7 +1161,7 @@ cudaError_t noalloc_scratch(float** out) {
 template <int VPT>
 cudaError_t noalloc_pass(const PassArgs& A0, int64_t rows, int nt, cudaStream_t s, int* grid_out) {
     constexpr int R = VPT >= 6 ? 1 : (VPT >= 3 ? 2 : 4);
-    auto kern = k_pass<float, VPT, R, true, false>;
+    auto kern = noalloc_kernel<VPT>();
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -1150,7 +1176,10 @@ cudaError_t noalloc_pass(const PassArgs& A0, int64_t rows, int nt, cudaStream_t 
     grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
     kern<<<(unsigned)grid, nt, 0, s>>>(A);
     *grid_out = (int)grid;
-    return cudaGetLastError();
+    // no error was pending before the call, so one seen here is this launch's
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) (void)cudaGetLastError();
+    return e;
 }
 
 }  // namespace
@@ -1182,23 +1211,25 @@ extern "C" lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_
     using namespace lmosem;
     if (!d_rows || !d_f || !d_sens_i) return LMOSEM_EINVAL;
     if (n_rows < 1 || n_support < 1 || n_support > kNoAllocMaxSupport) return LMOSEM_EINVAL;
-    if (ld < n_support || ld % 4 != 0 || (reinterpret_cast<uintptr_t>(d_rows) & 15u) != 0)
+    if (ld < n_support || ld > kNoAllocMaxLd || ld % 4 != 0 ||
+        (reinterpret_cast<uintptr_t>(d_rows) & 15u) != 0)
         return LMOSEM_EINVAL;
     if (!(acq_time > 0.0) || !isfinite(acq_time)) return LMOSEM_EINVAL;
+    // an error left by earlier work stays the caller's to read: run nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return LMOSEM_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return LMOSEM_ECUDA;
 
     // same column-vector shape as the context path (FP32 rows, 4 per vector)
     const int64_t nvec = ld / 4;
-    const int opts[] = {1, 2, 3, 4, 6, 8};
-    int vpt = 8;
+    const int opts[] = {1, 2, 3, 4, 6, kNoAllocMaxVpt};
+    int vpt = kNoAllocMaxVpt;
     for (int v : opts)
         if ((nvec + v - 1) / v <= kMaxPassThreads) {
             vpt = v;
             break;
         }
-    if ((nvec + vpt - 1) / vpt > kMaxPassThreads) return LMOSEM_EINVAL;
     const int nt = (int)(((nvec + vpt - 1) / vpt + 31) / 32 * 32);
     PassArgs A;
     A.model = d_rows;
@@ -1222,10 +1253,14 @@ extern "C" lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_
         case 3: e = noalloc_pass<3>(A, n_rows, nt, s, &grid); break;
         case 4: e = noalloc_pass<4>(A, n_rows, nt, s, &grid); break;
         case 6: e = noalloc_pass<6>(A, n_rows, nt, s, &grid); break;
-        default: e = noalloc_pass<8>(A, n_rows, nt, s, &grid); break;
+        default: e = noalloc_pass<kNoAllocMaxVpt>(A, n_rows, nt, s, &grid); break;
     }
     if (e != cudaSuccess) return LMOSEM_ECUDA;
     k_update<<<(n_support + 31) / 32, 256, 0, s>>>(scratch, grid, n_support, d_f, d_sens_i, acq_time,
                                                    nullptr);
-    return cudaGetLastError() == cudaSuccess ? LMOSEM_OK : LMOSEM_ECUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LMOSEM_ECUDA;
+    }
+    return LMOSEM_OK;
 }

@@ -2,7 +2,8 @@
 cudaMalloc (their own allocator owns the device memory, or their loop must
 not make calls that can synchronise the device).  It must give the same image
 as the context path's lmosem_iterate on the same model rows, two calls in a
-row.  This file is collected last on purpose."""
+row, and leave the device's free memory unchanged after its first call.  This
+file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -11,13 +12,19 @@ from paper_2002_12471_gb300 import synthetic as S
 
 pytestmark = pytest.mark.gpu
 
+MAX_WIDTH = 8192   # 256 threads x 8 vectors x 4 floats of the register pass
 
-def test_noalloc_subiteration_matches_iterate_twice():
-    import torch
 
+def _lib():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2002_12471_gb300.lmosem as L
+    return L
+
+
+def test_noalloc_subiteration_matches_iterate_twice():
+    import torch
+    L = _lib()
 
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream()
@@ -48,12 +55,49 @@ def test_noalloc_subiteration_matches_iterate_twice():
             got, want = f_na.cpu().numpy(), f_ref.cpu().numpy()
             assert np.all(np.isfinite(got))
             assert oracle.rel_l2(got, want) <= 1e-5, (call, oracle.rel_l2(got, want))
-        # sizes beyond the static scratch array are rejected before any launch
-        big = torch.zeros((4, 16388), dtype=torch.float32, device=dev)
-        fb = torch.ones(16388, dtype=torch.float32, device=dev)
-        sb = torch.ones(16388, dtype=torch.float64, device=dev)
-        with pytest.raises(L.LmosemError) as ei:
-            L.lmosem_osem_subiter_noalloc(big, 16388, fb, sb, 1.0, stream=stream)
-        assert ei.value.status == L.EINVAL
     finally:
         L.lmosem_destroy(ctx)
+
+
+def test_noalloc_widest_rows_and_free_memory():
+    """Rows of the widest accepted width (8192) against the FP64 oracle's
+    sub-iteration on the same rows; free device memory unchanged across
+    calls after the first; one column more is rejected before any launch."""
+    import torch
+    L = _lib()
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(5)
+    n_rows = 300
+    p = rng.uniform(0.0, 1.0, (n_rows, MAX_WIDTH)) * (rng.uniform(0, 1, (n_rows, MAX_WIDTH)) < 0.3)
+    f0 = rng.uniform(0.5, 1.5, MAX_WIDTH)
+    s = rng.uniform(0.5, 2.0, MAX_WIDTH)
+    s[::97] = 0.0                               # pixels without sensitivity go to zero
+    p32 = p.astype(np.float32)
+    rows = torch.from_numpy(p32).to(dev)
+    f = torch.from_numpy(f0.astype(np.float32)).to(dev)
+    sd = torch.from_numpy(s).to(dev)
+    small = torch.from_numpy(p32[:, :64].copy()).to(dev)
+    fs = f[:64].clone()
+    torch.cuda.synchronize()
+    L.lmosem_osem_subiter_noalloc(small, 64, fs, sd[:64], 1.0, stream=stream)   # first call: set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    want = f0.astype(np.float32).astype(np.float64)
+    for call in range(2):
+        L.lmosem_osem_subiter_noalloc(rows, MAX_WIDTH, f, sd, 2.0, stream=stream)
+        torch.cuda.synchronize()
+        want = oracle.osem_subiteration(p32.astype(np.float64), want, s, T=2.0)
+        got = f.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(got))
+        assert oracle.rel_l2(got, want) <= 1e-5, (call, oracle.rel_l2(got, want))
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    # one column beyond the widest row is rejected (support and row stride)
+    wide = torch.zeros((4, MAX_WIDTH + 4), dtype=torch.float32, device=dev)
+    fw = torch.ones(MAX_WIDTH + 1, dtype=torch.float32, device=dev)
+    sw = torch.ones(MAX_WIDTH + 1, dtype=torch.float64, device=dev)
+    for nsup in (MAX_WIDTH + 1, MAX_WIDTH):   # support too wide; stride too wide
+        with pytest.raises(L.LmosemError) as ei:
+            L.lmosem_osem_subiter_noalloc(wide, nsup, fw, sw, 1.0, stream=stream)
+        assert ei.value.status == L.EINVAL
