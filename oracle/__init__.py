@@ -47,10 +47,17 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                           "-o", tmp, _SRC, "-lm"])
+    compile_source(_SRC, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def compile_source(src, out):
+    """gcc a copy of the C oracle into a shared library (same flags as
+    ``build``); the tests use it for copies with a planted mistake."""
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-o", out, src, "-lm"])
+    return out
 
 
 class Geom(ctypes.Structure):
@@ -75,42 +82,49 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            L.orc_compton_energy.restype = ctypes.c_double
-            L.orc_compton_energy.argtypes = [ctypes.c_double, ctypes.c_double]
-            L.orc_kn_shape.restype = ctypes.c_double
-            L.orc_kn_shape.argtypes = [ctypes.c_double, ctypes.c_double]
-            L.orc_kn_mean.restype = ctypes.c_double
-            L.orc_kn_mean.argtypes = [ctypes.c_double]
-            L.orc_sigma_kn.restype = ctypes.c_double
-            L.orc_sigma_kn.argtypes = [ctypes.c_double]
-            L.orc_line_integral.restype = ctypes.c_double
-            L.orc_line_integral.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                            ctypes.c_double, ctypes.c_double,
-                                            ctypes.c_double, ctypes.c_double]
-            L.orc_ray_to_edge.restype = ctypes.c_double
-            L.orc_ray_to_edge.argtypes = L.orc_line_integral.argtypes
-            L.orc_det_u.restype = ctypes.c_double
-            L.orc_det_u.argtypes = [ctypes.POINTER(Geom), ctypes.c_int,
-                                    ctypes.c_double, ctypes.c_double]
-            L.orc_det_depth.restype = ctypes.c_double
-            L.orc_det_depth.argtypes = L.orc_det_u.argtypes
-            L.orc_build_tables.restype = None
-            L.orc_build_tables.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int,
-                                           _ip, ctypes.c_int, _dp, _dp]
-            L.orc_model.restype = None
-            L.orc_model.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
-                                    ctypes.c_int, _dp, _dp, _ip, _dp, _dp, ctypes.c_int64, _dp,
-                                    ctypes.c_int]
-            L.orc_model_binned.restype = None
-            L.orc_model_binned.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
-                                           ctypes.c_int, _dp, _dp, _ip, _ip, _ip, ctypes.c_int64,
-                                           _dp, _dp, ctypes.c_int]
-            L.orc_sensitivity.restype = None
-            L.orc_sensitivity.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
-                                          ctypes.c_int, _dp, _dp, ctypes.c_int, _dp]
-            _lib = L
+            _lib = load(build())
     return _lib
+
+
+def load(path):
+    """Load a compiled copy of ``lmosem_oracle.c`` and declare its functions
+    (``lib()`` loads the one ``build()`` makes)."""
+    L = ctypes.CDLL(path)
+    L.orc_compton_energy.restype = ctypes.c_double
+    L.orc_compton_energy.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.orc_kn_shape.restype = ctypes.c_double
+    L.orc_kn_shape.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.orc_kn_mean.restype = ctypes.c_double
+    L.orc_kn_mean.argtypes = [ctypes.c_double]
+    L.orc_sigma_kn.restype = ctypes.c_double
+    L.orc_sigma_kn.argtypes = [ctypes.c_double]
+    L.orc_line_integral.restype = ctypes.c_double
+    L.orc_line_integral.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double]
+    L.orc_ray_to_edge.restype = ctypes.c_double
+    L.orc_ray_to_edge.argtypes = L.orc_line_integral.argtypes
+    L.orc_det_u.restype = ctypes.c_double
+    L.orc_det_u.argtypes = [ctypes.POINTER(Geom), ctypes.c_int,
+                            ctypes.c_double, ctypes.c_double]
+    L.orc_det_depth.restype = ctypes.c_double
+    L.orc_det_depth.argtypes = L.orc_det_u.argtypes
+    L.orc_build_tables.restype = None
+    L.orc_build_tables.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int,
+                                   _ip, ctypes.c_int, _dp, _dp]
+    L.orc_model.restype = None
+    L.orc_model.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
+                            ctypes.c_int, _dp, _dp, _ip, _dp, _dp, ctypes.c_int64, _dp,
+                            ctypes.c_int]
+    L.orc_model_binned.restype = None
+    L.orc_model_binned.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
+                                   ctypes.c_int, _dp, _dp, _ip, _ip, _ip, ctypes.c_int64,
+                                   _dp, _dp, ctypes.c_int]
+    L.orc_sensitivity.restype = None
+    L.orc_sensitivity.argtypes = [ctypes.POINTER(Geom), _dp, _ip, ctypes.c_int, _ip,
+                                  ctypes.c_int, _dp, _dp, ctypes.c_int, _dp,
+                                  ctypes.c_int]
+    return L
 
 
 def _d(a):
@@ -237,15 +251,17 @@ class Problem:
                                int(primary) | (int(scatter) << 1))
         return p
 
-    def sensitivity(self, n_subsets: int):
+    def sensitivity(self, n_subsets: int, primary=True, scatter=True):
         """s[i, q]: sum of s_eff over the paths from pixel q that reach the
         detector at angles of subset i (denominator of Eq. 7).  Subset i holds
         the angles a with a mod n_subsets == i (reading of 'based on the
-        detector angle')."""
+        detector angle').  The flags restrict the sum to the primary path or
+        to the first-order scatter paths."""
         s = np.zeros((n_subsets, self.n_sup), dtype=np.float64)
         lib().orc_sensitivity(ctypes.byref(self.geom), _d(self.mu), _i(self.support),
                               self.n_sup, _i(self.scatter), len(self.scatter),
-                              _d(self.l_edge), _d(self.l_pair), int(n_subsets), _d(s))
+                              _d(self.l_edge), _d(self.l_pair), int(n_subsets), _d(s),
+                              int(primary) | (int(scatter) << 1))
         return s
 
 

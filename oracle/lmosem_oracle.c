@@ -27,8 +27,10 @@
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
  * (closed forms, brute-force path enumeration, quadrature, invariants of the
- * EM update).  The full reconstruction is pinned only through those
- * invariants.
+ * EM update).  The absolute path weights are pinned against physics: photon
+ * counts per scatter order from an independent Monte-Carlo converge to the
+ * sensitivities restricted to each path type as the pixel shrinks.  The
+ * full reconstruction is pinned only through those invariants.
  */
 #include <math.h>
 #include <stdint.h>
@@ -386,10 +388,11 @@ void orc_model(const orc_geom* g, const double* mu, const int32_t* sup, int n_su
 
 /* s_out[i*n_sup + q] = sum over angles a with a mod n_subsets == i of the
  * detection probability of every path from sup[q]:
- *   exp(-L_det) D_u D_E(E0)  +  sum_m w(n,m) D_u(m) D_E(E'). */
+ *   exp(-L_det) D_u D_E(E0)  +  sum_m w(n,m) D_u(m) D_E(E').
+ * parts: bit 0 keeps the primary path, bit 1 the scatter paths (3: both). */
 void orc_sensitivity(const orc_geom* g, const double* mu, const int32_t* sup, int n_sup,
                      const int32_t* scat, int n_scat, const double* l_edge, const double* l_pair,
-                     int n_subsets, double* s_out)
+                     int n_subsets, double* s_out, int parts)
 {
     int npix = g->nx * g->ny;
     double kbar = orc_kn_mean(g->e0_kev);
@@ -404,11 +407,13 @@ void orc_sensitivity(const orc_geom* g, const double* mu, const int32_t* sup, in
         for (int i = 0; i < n_sup; ++i) {
             double xn, yn;
             orc_pixel_centre(g, sup[i], &xn, &yn);
-            double acc = exp(-l_edge[(size_t)a * npix + sup[i]]) *
-                         orc_gauss_mass(-half, half, orc_det_u(g, a, xn, yn),
-                                        orc_sigma_u(g, orc_det_depth(g, a, xn, yn))) *
-                         de0;
-            for (int k = 0; k < n_scat; ++k) {
+            double acc = 0.0;
+            if (parts & 1)
+                acc = exp(-l_edge[(size_t)a * npix + sup[i]]) *
+                      orc_gauss_mass(-half, half, orc_det_u(g, a, xn, yn),
+                                     orc_sigma_u(g, orc_det_depth(g, a, xn, yn))) *
+                      de0;
+            for (int k = 0; k < n_scat && (parts & 2); ++k) {
                 double wv, e1;
                 if (!orc_scatter_path(g, mu, a, sup[i], scat[k], l_pair[(size_t)i * n_scat + k],
                                       l_edge[(size_t)a * npix + scat[k]], kbar, sig0, &wv, &e1))

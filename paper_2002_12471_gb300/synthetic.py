@@ -183,11 +183,9 @@ def _sample_deflection(rng, e_kev):
     return psi
 
 
-def simulate_events(ph: Phantom, g: dict, n_events: int, seed: int, *, max_order=6,
-                    batch=1 << 20) -> Events:
-    """Exactly ``n_events`` detected events from a seeded photon Monte-Carlo
-    (Philox bit generator keyed by ``seed``)."""
-    rng = np.random.Generator(np.random.Philox(key=int(seed)))
+def _photon_batch(rng, ph: Phantom, g: dict, n: int, max_order: int):
+    """Track ``n`` emitted photons; return (angle, u, E, order) of those
+    detected inside the extent and the window."""
     ny, nx = ph.mu.shape
     dpx = ph.pixel_mm
     xmin, ymin = -0.5 * nx * dpx, -0.5 * ny * dpx
@@ -200,64 +198,84 @@ def simulate_events(ph: Phantom, g: dict, n_events: int, seed: int, *, max_order
     half = 0.5 * g["n_bins"] * g["bin_mm"]
     dth = 2 * np.pi / g["n_angles"]
     fw2s = 1.0 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
-    out_a, out_u, out_e, out_o = [], [], [], []
+    pix = np.searchsorted(cdf, rng.uniform(0.0, 1.0, n), side="right")
+    pix = np.minimum(pix, nx * ny - 1)
+    x = xmin + (pix % nx + rng.uniform(0, 1, n)) * dpx
+    y = ymin + (pix // nx + rng.uniform(0, 1, n)) * dpx
+    phi = rng.uniform(0.0, 2 * np.pi, n)
+    e = np.full(n, e0)
+    order = np.zeros(n, dtype=np.int8)
+    lx, ly = x.copy(), y.copy()            # last emission / interaction point
+    alive = np.ones(n, dtype=bool)
+    escaped = np.zeros(n, dtype=bool)
+    while True:
+        idx = np.nonzero(alive & ~escaped)[0]
+        if len(idx) == 0:
+            break
+        mu_max = mu_max0 * _kn_sim_total(e[idx]) / s0
+        step = -np.log(rng.uniform(0.0, 1.0, len(idx)) + 1e-300) / mu_max
+        x[idx] += step * np.cos(phi[idx])
+        y[idx] += step * np.sin(phi[idx])
+        ix = np.floor((x[idx] - xmin) / dpx).astype(np.int64)
+        iy = np.floor((y[idx] - ymin) / dpx).astype(np.int64)
+        inside = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny)
+        escaped[idx[~inside]] = True
+        idx, ix, iy = idx[inside], ix[inside], iy[inside]
+        real = rng.uniform(0.0, 1.0, len(idx)) * mu_max0 < mu0[iy * nx + ix]
+        hit = idx[real]
+        if len(hit):
+            psi = _sample_deflection(rng, e[hit])
+            e[hit] = e[hit] / (1.0 + e[hit] / MEC2_KEV * (1.0 - np.cos(psi)))
+            phi[hit] = np.mod(phi[hit] + psi, 2 * np.pi)
+            order[hit] += 1
+            lx[hit], ly[hit] = x[hit], y[hit]
+            alive[hit[order[hit] > max_order]] = False
+    det = np.nonzero(escaped & alive)[0]
+    a = np.mod(np.rint((phi[det] - g["angle0_rad"]) / dth).astype(np.int64), g["n_angles"])
+    th = g["angle0_rad"] + a * dth
+    px, py = lx[det], ly[det]
+    depth = g["radius_mm"] - (px * np.cos(th) + py * np.sin(th))
+    su = (g["coll_fwhm0_mm"] + g["coll_fwhm_slope"] * depth) * fw2s
+    u = -px * np.sin(th) + py * np.cos(th) + su * rng.standard_normal(len(det))
+    se = g["fwhm_frac_e0"] * np.sqrt(e0 * e[det]) * fw2s
+    em = e[det] + se * rng.standard_normal(len(det))
+    keep = (np.abs(u) <= half) & (em >= g["e_lo_kev"]) & (em <= g["e_hi_kev"])
+    u32 = u[keep].astype(np.float32)
+    e32 = em[keep].astype(np.float32)
+    # float32 rounding must not push a value out of the acceptance region
+    u32 = np.clip(u32, np.float32(-half), np.float32(half))
+    e32 = np.clip(e32, np.float32(g["e_lo_kev"]), np.float32(g["e_hi_kev"]))
+    return a[keep].astype(np.int32), u32, e32, order[det][keep]
+
+
+def simulate_events(ph: Phantom, g: dict, n_events: int, seed: int, *, max_order=6,
+                    batch=1 << 20) -> Events:
+    """Exactly ``n_events`` detected events from a seeded photon Monte-Carlo
+    (Philox bit generator keyed by ``seed``)."""
+    rng = np.random.Generator(np.random.Philox(key=int(seed)))
+    out = []
     got = 0
     while got < n_events:
-        pix = np.searchsorted(cdf, rng.uniform(0.0, 1.0, batch), side="right")
-        pix = np.minimum(pix, nx * ny - 1)
-        x = xmin + (pix % nx + rng.uniform(0, 1, batch)) * dpx
-        y = ymin + (pix // nx + rng.uniform(0, 1, batch)) * dpx
-        phi = rng.uniform(0.0, 2 * np.pi, batch)
-        e = np.full(batch, e0)
-        order = np.zeros(batch, dtype=np.int8)
-        lx, ly = x.copy(), y.copy()            # last emission / interaction point
-        alive = np.ones(batch, dtype=bool)
-        escaped = np.zeros(batch, dtype=bool)
-        while True:
-            idx = np.nonzero(alive & ~escaped)[0]
-            if len(idx) == 0:
-                break
-            mu_max = mu_max0 * _kn_sim_total(e[idx]) / s0
-            step = -np.log(rng.uniform(0.0, 1.0, len(idx)) + 1e-300) / mu_max
-            x[idx] += step * np.cos(phi[idx])
-            y[idx] += step * np.sin(phi[idx])
-            ix = np.floor((x[idx] - xmin) / dpx).astype(np.int64)
-            iy = np.floor((y[idx] - ymin) / dpx).astype(np.int64)
-            inside = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny)
-            escaped[idx[~inside]] = True
-            idx, ix, iy = idx[inside], ix[inside], iy[inside]
-            real = rng.uniform(0.0, 1.0, len(idx)) * mu_max0 < mu0[iy * nx + ix]
-            hit = idx[real]
-            if len(hit):
-                psi = _sample_deflection(rng, e[hit])
-                e[hit] = e[hit] / (1.0 + e[hit] / MEC2_KEV * (1.0 - np.cos(psi)))
-                phi[hit] = np.mod(phi[hit] + psi, 2 * np.pi)
-                order[hit] += 1
-                lx[hit], ly[hit] = x[hit], y[hit]
-                alive[hit[order[hit] > max_order]] = False
-        det = np.nonzero(escaped & alive)[0]
-        a = np.mod(np.rint((phi[det] - g["angle0_rad"]) / dth).astype(np.int64), g["n_angles"])
-        th = g["angle0_rad"] + a * dth
-        px, py = lx[det], ly[det]
-        depth = g["radius_mm"] - (px * np.cos(th) + py * np.sin(th))
-        su = (g["coll_fwhm0_mm"] + g["coll_fwhm_slope"] * depth) * fw2s
-        u = -px * np.sin(th) + py * np.cos(th) + su * rng.standard_normal(len(det))
-        se = g["fwhm_frac_e0"] * np.sqrt(e0 * e[det]) * fw2s
-        em = e[det] + se * rng.standard_normal(len(det))
-        keep = (np.abs(u) <= half) & (em >= g["e_lo_kev"]) & (em <= g["e_hi_kev"])
-        u32 = u[keep].astype(np.float32)
-        e32 = em[keep].astype(np.float32)
-        # float32 rounding must not push a value out of the acceptance region
-        u32 = np.clip(u32, np.float32(-half), np.float32(half))
-        e32 = np.clip(e32, np.float32(g["e_lo_kev"]), np.float32(g["e_hi_kev"]))
-        out_a.append(a[keep].astype(np.int32))
-        out_u.append(u32)
-        out_e.append(e32)
-        out_o.append(order[det][keep])
-        got += int(keep.sum())
-    A = np.concatenate(out_a)[:n_events]
-    return Events(angle=A, u_mm=np.concatenate(out_u)[:n_events],
-                  e_kev=np.concatenate(out_e)[:n_events], order=np.concatenate(out_o)[:n_events])
+        out.append(_photon_batch(rng, ph, g, batch, max_order))
+        got += len(out[-1][0])
+    A, U, E, O = (np.concatenate(c)[:n_events] for c in zip(*out))
+    return Events(angle=A, u_mm=U, e_kev=E, order=O)
+
+
+def simulate_emissions(ph: Phantom, g: dict, n_emitted: int, seed: int, *, max_order=6,
+                       batch=1 << 20) -> Events:
+    """Every detected event of exactly ``n_emitted`` emitted photons (same
+    Monte-Carlo as ``simulate_events``), so that counts per scatter order can
+    be compared with their expectation per emitted photon."""
+    rng = np.random.Generator(np.random.Philox(key=int(seed)))
+    out = []
+    left = int(n_emitted)
+    while left > 0:
+        n = min(batch, left)
+        out.append(_photon_batch(rng, ph, g, n, max_order))
+        left -= n
+    A, U, E, O = (np.concatenate(c) for c in zip(*out))
+    return Events(angle=A, u_mm=U, e_kev=E, order=O)
 
 
 def realisation_counts(n_real=64, seed=4, lo=50_000, hi=400_000):
