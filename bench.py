@@ -2,20 +2,28 @@
 """Benchmark of the list-mode OS-LM-MLEM attenuation-and-scatter-compensated
 reconstruction on one GB300.
 
-One step is one pass of the whole hot path on the 64 x 64 DaT-like brain
-workload (200k events, 120 angles, 8 subsets x 10 iterations, FP32 model):
+One step is one pass of the whole hot path on the 128 x 128 DaT-like brain
+workload (1,000,000 events, 120 angles, 8 subsets x 10 iterations):
 attenuation tables, subset sensitivities, the per-event path-sum model
-build, the initial image, ten OSEM iterations and the FP64 log-likelihood of
-the result, all through the C ABI with the events resident on the device.
+build, the model cache in the chosen format, the initial image, ten OSEM
+iterations and the FP64 log-likelihood of the result, all through the C ABI
+with the events resident on the device.  The chosen form caches the model
+as FP16 with per-event FP32 scales; the exact form (FP32 model) is timed
+beside it on the same events.
 
 Printed (rank 0, one JSON line): the event-pixel model evals/s of the whole
-step (J * N_nz per step / step time), seconds per OSEM iteration with the
-model cached, the end-to-end rate through host buffers, the roofline of the
-dominant kernel (timed live with CUDA events on the library's stream), the
-CPU oracle baseline, SM clocks sampled during the timed region and the
+step (J * N_nz per step / step time) for the chosen form and, under
+"exact", for the FP32 form; seconds per OSEM iteration with the model cached;
+each form's error against the FP64 oracle on a frozen 20,000-event subset of
+the same events and the chosen form's error against the exact form on all
+events; the end-to-end rate through host buffers; the roofline of the
+dominant kernel (timed live with CUDA events on the library's stream); the
+CPU oracle baseline; SM clocks sampled during the timed region and the
 number of kernel launches.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload dat128|dat64|batch64|surrogate128|windows64|binned64]
+                  [--fmt fp16|bf16|fp32]
 
 Under torchrun every rank reconstructs its own noise realisation (weak
 scaling, no collective on the data path); rank 0 prints the aggregate.
@@ -55,12 +63,21 @@ WORKLOADS = {
                  "binned into the detector's 64 position bins and 2 ([100, 143, 175] keV) or 3 "
                  "([100, 120, 143, 175] keV) energy bins, reconstructed from the bin-integrated model with "
                  "count-weighted EM, against list mode; 8 subsets x 10 iterations; ROI-mean NRMSE"),
+    "mlp_infer": ("scatter-surrogate inference alone: MLP 6 -> 4 x 256 -> 1, BF16 operands, FP32 accumulation, "
+                  "2,000,000 rows of standard-normal inputs (He-initialised weights; the kernel's work does not "
+                  "depend on their values), one lmosem_surrogate_infer call per step"),
     "batch64": ("64 independent noise realisations of the 64x64 DaT phantom (120 angles, R = 150 mm), "
                 "event counts Poisson with means uniform in [50k, 400k], 8 subsets x 10 iterations, "
                 "all realisations in one persistent launch, FP32 model"),
 }
-WORKLOAD = "dat64"
+WORKLOAD = "dat128"
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
+# event seeds of the single-set workloads (rank r adds r): the same event sets
+# the parity tests and the frozen oracle subset are drawn from
+SEEDS = {"dat64": 2, "dat128": 3}
+# the chosen model format of each single-set workload; the exact FP32 form is
+# timed beside any other
+CHOSEN_FMT = {"dat64": "fp32", "dat128": "fp16"}
 # MUFU ex2 throughput of a GB300 SM, measured with independent ex2.approx.ftz.f32
 # chains (4 CTAs x 512 threads per SM): 31.8 per clock, i.e. 32 (twice the 16 of
 # compute capability 10.0).  Each path term needs one ex2 and three FP32 FMAs,
@@ -76,12 +93,18 @@ def parse():
                     help="timed steps (default: 20 for the dat64 GPU arm, about 0.6 s; 5 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--fmt", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--fmt", choices=["fp32", "fp16", "bf16"], default=None,
+                    help="chosen model format (default: fp16 at 128x128, fp32 at 64x64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=0,
                     help="override the event count (small cases for profiling)")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dat64")
+    ap.add_argument("--table-budget-mb", type=int, default=0,
+                    help="device budget of the scatter-weight tables (0: the library's 4 GiB); "
+                         "small profiling captures keep one angle group resident")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dat128")
     args = ap.parse_args()
+    if args.fmt is None:
+        args.fmt = CHOSEN_FMT.get(args.workload, "fp32")
     if args.steps is None:
         args.steps = 20 if args.workload == "dat64" and args.impl == "ours" else 5
     global WORKLOAD, WORKLOAD_DESC
@@ -253,6 +276,67 @@ def aggregate_rate(units_per_rank, world, ms_per_step):
 
 # ------------------------------------------------------------------ our arm
 
+EXACT_FMT = "fp32"
+GOLDEN_128 = os.path.join(ROOT, "tests", "golden", "dat128_subset_oracle.npz")
+
+
+def workload_config(J, n_nz, chosen, world):
+    """The config block both arms print (same keys, same values)."""
+    cfg = {"workload": WORKLOAD_DESC, "events": J, "support_pixels": n_nz,
+           "model_format": chosen, "parallelism": "replicas" if world > 1 else "1 GPU",
+           "l2": "model larger than L2 (129 MB); 256 MB L2 flush before every step"}
+    if chosen != EXACT_FMT:
+        cfg["exact_format"] = EXACT_FMT
+    return cfg
+
+
+def roi_means(img_full, rois):
+    return {k: float(np.dot(w.reshape(-1), img_full) / w.sum()) for k, w in rois.items()}
+
+
+def oracle_subset_errors(L, stream, dev, fmts=("fp32", "fp16", "bf16"), T=1.0):
+    """Every model format reconstructs the frozen 20,000-event subset of the
+    128 x 128 workload (tests/golden, written by the FP64 oracle alone);
+    returns each image's rel-L2 and striatal ROI-mean errors against the
+    oracle's image, and the FP32 form's log-likelihood error."""
+    import torch
+    G = np.load(GOLDEN_128)
+    g = {k: float(v) for k, v in zip(G["geometry_keys"], G["geometry_values"])}
+    g["n_angles"], g["n_bins"] = int(g["n_angles"]), int(g["n_bins"])
+    ns, ni = int(G["n_subsets"]), int(G["n_iters"])
+    mu, sup = G["mu"], G["support"]
+    rois = {"caudate": G["roi_caudate"].astype(np.float64), "putamen": G["roi_putamen"].astype(np.float64)}
+    ref = np.zeros(mu.size)
+    ref[sup] = G["image"]
+    ref_roi = roi_means(ref, rois)
+    a = torch.from_numpy(G["angle"].astype(np.int32)).to(dev)
+    u = torch.from_numpy(G["u_mm"]).to(dev)
+    e = torch.from_numpy(G["e_kev"]).to(dev)
+    out = {"subset": "%d of the 1,000,000 events (seeded pick), 8 subsets x 10 iterations; "
+                     "the FP64 oracle's image from tests/golden" % len(G["angle"])}
+    for fmt in fmts:
+        ctx = L.lmosem_create(mu, float(G["pixel_mm"]), g, stream=stream)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            if not np.array_equal(L.lmosem_support(ctx), sup):
+                raise RuntimeError("support differs from the oracle's")
+            L.lmosem_sensitivity(ctx, ns)
+            L.lmosem_build_model(ctx, a, u, e, ns, fmt)
+            f = torch.empty(nsup, dtype=torch.float32, device=dev)
+            ll = torch.empty(ni, dtype=torch.float64, device=dev)
+            L.lmosem_init_image(ctx, T, f)
+            L.lmosem_iterate(ctx, ni, T, f, ll)
+            img = np.zeros(mu.size)
+            img[sup] = f.cpu().numpy()
+            r = roi_means(img, rois)
+            out[fmt] = {"rel_l2": float(np.linalg.norm(img - ref) / np.linalg.norm(ref)),
+                        "roi_rel": {k: r[k] / ref_roi[k] - 1.0 for k in r},
+                        "loglik_rel": abs(float(ll[-1].item()) / float(G["loglik"][-1]) - 1.0)}
+        finally:
+            L.lmosem_destroy(ctx)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -266,8 +350,10 @@ def run_ours(args, rank, world, local_rank):
     # CUDA graphs on it
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-    ph, g, ev, ns, ni = make_inputs(seed=2 + rank, events=args.events)
+    ph, g, ev, ns, ni = make_inputs(seed=SEEDS[WORKLOAD] + rank, events=args.events)
     J = len(ev)
+    chosen = args.fmt
+    forms = [chosen] + ([EXACT_FMT] if chosen != EXACT_FMT else [])
     a_h = torch.from_numpy(ev.angle).pin_memory()
     u_h = torch.from_numpy(ev.u_mm).pin_memory()
     e_h = torch.from_numpy(ev.e_kev).pin_memory()
@@ -275,12 +361,15 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB of L2
     T = 1.0
 
-    def step(a, u, e, profile=0):
-        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile)
+    budget = args.table_budget_mb << 20
+
+    def step(fmt, a, u, e, profile=0):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile,
+                              table_budget_bytes=budget)
         try:
             nsup = L.lmosem_n_support(ctx)
             L.lmosem_sensitivity(ctx, ns)
-            L.lmosem_build_model(ctx, a, u, e, ns, args.fmt)
+            L.lmosem_build_model(ctx, a, u, e, ns, fmt)
             f = torch.empty(nsup, dtype=torch.float32, device=dev)
             ll = torch.empty(1, dtype=torch.float64, device=dev)
             L.lmosem_init_image(ctx, T, f)
@@ -292,11 +381,12 @@ def run_ours(args, rank, world, local_rank):
         finally:
             L.lmosem_destroy(ctx)
 
-    for _ in range(args.warmup):
-        step(a_d, u_d, e_d)
+    for fmt in forms:
+        for _ in range(args.warmup):
+            step(fmt, a_d, u_d, e_d)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region
+    # ---- device-resident timed region, one block of steps per model format
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -308,22 +398,27 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    times, profs, launches = [], [], 0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        # kernel timing of everything but the graph-replayed OSEM iterations
-        nsup, prof, nl, f, ll = step(a_d, u_d, e_d, profile=2)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        profs.append(prof)
-        launches += nl
+    runs = {}
+    for fmt in forms:
+        times, profs, launches = [], [], 0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            # kernel timing of everything but the graph-replayed OSEM iterations
+            nsup, prof, nl, f, ll = step(fmt, a_d, u_d, e_d, profile=2)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            profs.append(prof)
+            launches += nl
+        runs[fmt] = dict(times=times, profs=profs, launches=launches,
+                         f=f.cpu().numpy().astype(np.float64), ll=float(ll.item()))
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_total_ms = max_over_ranks(sum(times), world, dev)
-    ll_final = float(ll.item())
+    for fmt in forms:
+        runs[fmt]["t_total_ms"] = max_over_ranks(sum(runs[fmt]["times"]), world, dev)
+    ll_final = runs[chosen]["ll"]
 
     # ---- end to end through the host-buffer call: lmosem_create, then
     # lmosem_reconstruct copies the pinned events in and the image and the
@@ -338,7 +433,7 @@ def run_ours(args, rank, world, local_rank):
         e0.record(stream)
         ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
         try:
-            L.lmosem_reconstruct(ctx, a_h, u_h, e_h, ns, ni, T, args.fmt, f_h, ll_h)
+            L.lmosem_reconstruct(ctx, a_h, u_h, e_h, ns, ni, T, chosen, f_h, ll_h)
         finally:
             L.lmosem_destroy(ctx)
         e1.record(stream)
@@ -349,51 +444,53 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- seconds per OSEM iteration with the model cached (graph replay), and
     # the per-kernel times of the pass and the update from a profiled context
-    it_times = []
-    for prof_level in (0, 1):
-        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=prof_level)
-        try:
-            L.lmosem_sensitivity(ctx, ns)
-            L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, args.fmt)
-            f = torch.empty(nsup, dtype=torch.float32, device=dev)
-            L.lmosem_init_image(ctx, T, f)
-            L.lmosem_iterate(ctx, 2, T, f)
-            if prof_level:
-                L.lmosem_profile_read(ctx)
-                L.lmosem_iterate(ctx, 10, T, f)
-                it_prof = L.lmosem_profile_read(ctx)
-            else:
-                model_bytes = L.lmosem_model_bytes(ctx)
-                for _ in range(10):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    L.lmosem_iterate(ctx, 1, T, f)
-                    e1.record(stream)
-                    e1.synchronize()
-                    it_times.append(e0.elapsed_time(e1))
-                # count conservation of the last sub-iteration (Eq. 7), FP64
-                tot = torch.zeros(ns, dtype=torch.float64, device=dev)
-                L.lmosem_subset_totals(ctx, T, f, tot)
-                n_last = int(np.sum(ev.angle % ns == ns - 1))
-                count_resid = abs(float(tot[ns - 1].item()) - n_last) / max(1, n_last)
-        finally:
-            L.lmosem_destroy(ctx)
+    for fmt in forms:
+        it_times = []
+        for prof_level in (0, 1):
+            ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=prof_level)
+            try:
+                L.lmosem_sensitivity(ctx, ns)
+                L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, fmt)
+                f = torch.empty(nsup, dtype=torch.float32, device=dev)
+                L.lmosem_init_image(ctx, T, f)
+                L.lmosem_iterate(ctx, 2, T, f)
+                if prof_level:
+                    L.lmosem_profile_read(ctx)
+                    L.lmosem_iterate(ctx, 10, T, f)
+                    runs[fmt]["it_prof"] = L.lmosem_profile_read(ctx)
+                else:
+                    runs[fmt]["model_bytes"] = L.lmosem_model_bytes(ctx)
+                    for _ in range(10):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        L.lmosem_iterate(ctx, 1, T, f)
+                        e1.record(stream)
+                        e1.synchronize()
+                        it_times.append(e0.elapsed_time(e1))
+                    # count conservation of the last sub-iteration (Eq. 7), FP64
+                    tot = torch.zeros(ns, dtype=torch.float64, device=dev)
+                    L.lmosem_subset_totals(ctx, T, f, tot)
+                    n_last = int(np.sum(ev.angle % ns == ns - 1))
+                    runs[fmt]["count_resid"] = abs(float(tot[ns - 1].item()) - n_last) / max(1, n_last)
+            finally:
+                L.lmosem_destroy(ctx)
+        runs[fmt]["s_per_iter"] = statistics.mean(it_times) * 1e-3
 
     # ---- the paper's structure: the model recomputed for every iteration (no
     # cache).  One iteration = scatter tables + path sums (lmosem_build_model
     # without a preceding sensitivity pass builds the tables itself) + the
-    # 8 subset passes and updates.
+    # subset passes and updates.
     otf_times = []
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
     try:
         L.lmosem_sensitivity(ctx, ns)
-        L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, args.fmt)
+        L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, chosen)
         f_otf = torch.empty(nsup, dtype=torch.float32, device=dev)
         L.lmosem_init_image(ctx, T, f_otf)
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, args.fmt)
+            L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, chosen)
             L.lmosem_iterate(ctx, 1, T, f_otf)
             e1.record(stream)
             e1.synchronize()
@@ -401,7 +498,10 @@ def run_ours(args, rank, world, local_rank):
     finally:
         L.lmosem_destroy(ctx)
 
-    osml = os_vs_mlem(L, ph, g, a_d, u_d, e_d, ns, ni, stream, dev) if rank == 0 else None
+    osml = (os_vs_mlem(L, ph, g, a_d, u_d, e_d, ns, ni, stream, dev)
+            if rank == 0 and WORKLOAD == "dat64" else None)
+    errors = (oracle_subset_errors(L, stream, dev)
+              if rank == 0 and WORKLOAD == "dat128" and os.path.exists(GOLDEN_128) else None)
     terms, n_nz = strip_terms(ph, g, ev)
     evals = J * n_nz
     pk, pk_kind = peaks()
@@ -409,34 +509,44 @@ def run_ours(args, rank, world, local_rank):
     sms = props.multi_processor_count
     sm_max = (clk or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK)
 
-    agg = {}
-    for p in profs:
-        for k, (ms, n) in p.items():
-            a = agg.setdefault(k, [0.0, 0])
-            a[0] += ms
-            a[1] += n
-    # the timed steps replay the OSEM iterations as CUDA graphs, untimed per
-    # kernel; their pass and update kernels enter the breakdown from the
-    # profiled context (10 iterations), scaled to the step's iterations
-    for k in ("pass", "update"):
-        ms, n = it_prof[k]
-        a = agg.setdefault(k, [0.0, 0])
-        a[0] += ms * ni / 10 * args.steps
-        a[1] += int(round(n * ni / 10 * args.steps))
+    def summary(fmt):
+        R = runs[fmt]
+        agg = {}
+        for p in R["profs"]:
+            for k, (ms, n) in p.items():
+                a = agg.setdefault(k, [0.0, 0])
+                a[0] += ms
+                a[1] += n
+        # when the timed steps replayed the OSEM iterations as CUDA graphs
+        # (untimed per kernel), their pass and update kernels enter the
+        # breakdown from the profiled context (10 iterations), scaled to the
+        # step's iterations; the persistent launch is timed in the steps
+        coop = R["it_prof"]["pass"][1] < 10   # one launch for the 10 profiled iterations
+        if not coop:
+            for k in ("pass", "update"):
+                ms, n = R["it_prof"][k]
+                a = agg.setdefault(k, [0.0, 0])
+                a[0] += ms * ni / 10 * args.steps
+                a[1] += int(round(n * ni / 10 * args.steps))
+        # the profiled 10 iterations: one persistent launch (passes and updates of
+        # every subset), or one pass kernel per subset with its update apart
+        pass_ms, pass_n = R["it_prof"]["pass"]
+        iter_bytes = R["model_bytes"] + ns * n_nz * 4          # model rows once + image reads
+        pass_gbs = 10 * iter_bytes / (pass_ms * 1e-3) / 1e9
+        ms_step = R["t_total_ms"] / args.steps
+        return agg, pass_ms, pass_n, pass_gbs, ms_step
+
+    agg, pass_ms, pass_n, pass_gbs, ms_step = summary(chosen)
     tot_kernel_ms = sum(v[0] for v in agg.values())
     ps_ms, ps_n = agg["pathsum"]
     ps_launch_ms = ps_ms / max(1, ps_n)
     terms_per_launch = terms / max(1, ps_n / args.steps)
     achieved = terms_per_launch / (ps_launch_ms * 1e-3) / 1e9          # Gterm/s
     peak = MUFU_EX2_PER_CLK_SM * sms * sm_max * 1e6 / 1e9             # Gterm/s (1 ex2 / term)
-    traffic = read_traffic("k_pathsum")
-
-    pass_ms, pass_n = it_prof["pass"]
-    pass_bytes = model_bytes + ns * n_nz * 4          # model rows once + image reads
-    pass_gbs = (pass_bytes / ns) / (pass_ms / max(1, pass_n) * 1e-3) / 1e9
-    ms_step = t_total_ms / args.steps
+    traffic = read_traffic("k_pathsum", WORKLOAD)
     value = aggregate_rate(evals, world, ms_step)
     e2e_ms = statistics.mean(e2e_times)
+    R = runs[chosen]
     out = {
         "metric": METRIC,
         "value": value,
@@ -448,19 +558,16 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.fmt == "fp32" else args.fmt + "+f32",
+        "dtype": "f32" if chosen == "fp32" else chosen + "+f32",
         "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events)",
-        "config": {"workload": WORKLOAD_DESC, "events": J, "support_pixels": n_nz,
-                   "model_format": args.fmt, "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "model (%.2f GB) larger than L2; 256 MB L2 flush before every step" %
-                         (model_bytes / 1e9)},
-        "s_per_iter": statistics.mean(it_times) * 1e-3,
+        "config": workload_config(J, n_nz, chosen, world),
+        "s_per_iter": R["s_per_iter"],
         "s_per_iter_on_the_fly": statistics.median(otf_times) * 1e-3,
-        "count_conservation_rel_residual": count_resid,
-        "s_per_iter_detail": {"pass_ms_per_launch": pass_ms / max(1, pass_n),
+        "count_conservation_rel_residual": R["count_resid"],
+        "s_per_iter_detail": {"pass_class_ms_per_iteration": pass_ms / 10, "pass_class_launches_per_10_iterations": pass_n,
                               "pass_gbs": pass_gbs, "hbm_peak_gbs": pk["hbm_gbs"],
                               "pass_frac_of_%s_hbm" % pk_kind: pass_gbs / pk["hbm_gbs"],
-                              "model_bytes": model_bytes},
+                              "model_bytes": R["model_bytes"]},
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in agg.items() if v[1]},
         "kernel_share": {k: v[0] / tot_kernel_ms for k, v in agg.items() if v[1]},
         "model_build_evals_per_s": evals / (ps_launch_ms * ps_n / args.steps * 1e-3),
@@ -474,12 +581,32 @@ def run_ours(args, rank, world, local_rank):
                      "unit": "Gterm/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "%d MUFU ex2 per clock per SM x %d SMs x %.0f MHz; one ex2 and "
                                    "three FP32 FMAs per path term" % (MUFU_EX2_PER_CLK_SM, sms, sm_max)},
-        "roofline_pass": {"bound": "hbm", "kernel": "k_pass", "achieved": pass_gbs,
+        "roofline_pass": {"bound": "hbm", "kernel": "k_osem_coop" if pass_n < 10 else "k_pass",
+                          "units": "model rows once per iteration plus the image once per subset",
+                          "achieved": pass_gbs,
                           "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": pass_gbs / pk["hbm_gbs"],
                           "peak_kind": pk_kind},
         "clocks": clk,
-        "gpu_launches": launches,
+        "gpu_launches": sum(runs[f]["launches"] for f in forms),
     }
+    if chosen != EXACT_FMT:
+        _, x_pass_ms, x_pass_n, x_pass_gbs, x_ms_step = summary(EXACT_FMT)
+        X = runs[EXACT_FMT]
+        out["exact"] = {"model_format": EXACT_FMT, "value": aggregate_rate(evals, world, x_ms_step),
+                        "unit": UNIT, "ms_per_step": x_ms_step, "s_per_iter": X["s_per_iter"],
+                        "pass_gbs": x_pass_gbs, "pass_frac_of_%s_hbm" % pk_kind: x_pass_gbs / pk["hbm_gbs"],
+                        "model_bytes": X["model_bytes"], "loglik_final": X["ll"]}
+        fc, fx = np.zeros(ph.mu.size), np.zeros(ph.mu.size)
+        sup = np.nonzero(ph.mu.reshape(-1) > 0)[0]
+        fc[sup], fx[sup] = R["f"], X["f"]
+        rc, rx = roi_means(fc, ph.rois), roi_means(fx, ph.rois)
+        out["chosen_vs_exact"] = {
+            "what": "the chosen form's image against the exact FP32 form's, all %d events" % J,
+            "rel_l2": float(np.linalg.norm(fc - fx) / np.linalg.norm(fx)),
+            "roi_rel": {k: rc[k] / rx[k] - 1.0 for k in rc},
+            "s_per_iter_ratio": R["s_per_iter"] / X["s_per_iter"]}
+    if errors is not None:
+        out["error_vs_fp64_oracle"] = errors
     return out
 
 
@@ -494,16 +621,17 @@ def kernel_source_sha1():
     return hashlib.sha1(src[i:j] if i >= 0 and j > i else src).hexdigest()[:12]
 
 
-def read_traffic(kernel):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if
-    the kernel's source has not changed since it was taken."""
+def read_traffic(kernel, workload):
+    """DRAM bytes per launch of a kernel on a workload from the committed ncu
+    summary, if the kernel's source has not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     h = kernel_source_sha1()
     for ln in open(path):
         parts = dict(p.split("=", 1) for p in ln.split() if "=" in p)
-        if parts.get("kernel") == kernel and parts.get("source_sha1") == h:
+        if (parts.get("kernel") == kernel and parts.get("source_sha1") == h
+                and parts.get("workload", "").split("_")[0] == workload):
             try:
                 return float(parts["dram_bytes_per_launch"])
             except (KeyError, ValueError):
@@ -513,47 +641,67 @@ def read_traffic(kernel):
 
 # ------------------------------------------------------------------ oracle arm
 
-def oracle_sample_run(ph, g, ev, ns, ni, per_angle):
-    """The FP64 oracle on a bounded sample: full attenuation tables and
-    sensitivity, model rows and OSEM for `per_angle` events of every angle.
-    Returns phase times in seconds."""
+# Angles in the oracle sample: all of them at 64 x 64; every 15th at 128 x 128
+# (8 of 120, one per subset), where the full tables and sensitivity alone take
+# minutes of CPU.
+ORACLE_ANGLE_STRIDE = {"dat64": 1, "dat128": 15}
+
+
+def oracle_sample_run(ph, g, ev, ns, ni, per_angle, stride=1, P=None):
+    """The FP64 oracle on a bounded sample: attenuation tables, subset
+    sensitivity, then model rows and OSEM for `per_angle` events of every
+    `stride`-th angle.  With stride > 1 the sample runs on a scanner with
+    only those angles (the same physical angles, a -> a / stride), so its
+    sensitivity and per-angle table cost are 1/stride of the workload's.
+    Returns phase times in seconds (tables 0 when a built problem P is
+    passed in) and the problem."""
     import oracle
+    gs = dict(g, n_angles=g["n_angles"] // stride, pixel_mm=ph.pixel_mm)
     rng = np.random.default_rng(per_angle)
     idx = np.concatenate([rng.choice(np.nonzero(ev.angle == a)[0],
                                      min(per_angle, int(np.sum(ev.angle == a))), replace=False)
-                          for a in range(g["n_angles"]) if np.any(ev.angle == a)])
+                          for a in range(0, g["n_angles"], stride) if np.any(ev.angle == a)])
+    a_s = (ev.angle[idx] // stride).astype(np.int32)
     t0 = time.perf_counter()
-    P = oracle.Problem(dict(g, pixel_mm=ph.pixel_mm), ph.mu)
+    tables = 0.0
+    if P is None:
+        P = oracle.Problem(gs, ph.mu)
+        tables = time.perf_counter() - t0
     t1 = time.perf_counter()
-    s = P.sensitivity(ns)
+    s = P.sensitivity(min(ns, gs["n_angles"]))
     t2 = time.perf_counter()
-    p = P.model(ev.angle[idx], ev.u_mm[idx], ev.e_kev[idx])
+    p = P.model(a_s, ev.u_mm[idx], ev.e_kev[idx])
     t3 = time.perf_counter()
-    f, _ = oracle.osem(p, ev.angle[idx], s, ni, oracle.initial_image(len(idx), s.sum(0)))
+    f, _ = oracle.osem(p, a_s, s, ni, oracle.initial_image(len(idx), s.sum(0)))
     oracle.loglik(p, f, s.sum(0))
     t4 = time.perf_counter()
-    return dict(tables=t1 - t0, sens=t2 - t1, model=t3 - t2, osem=t4 - t3, n=len(idx), n_nz=P.n_sup)
+    return dict(tables=tables, sens=t2 - t1, model=t3 - t2, osem=t4 - t3, n=len(idx), n_nz=P.n_sup,
+                stride=stride, P=P)
 
 
 def oracle_rate(ph, g, ev, ns, ni, fit=None):
-    """Oracle evals/s extrapolated to the full event count.  The model time is
-    fitted as per-angle table cost + per-event cost from two sample sizes."""
+    """Oracle evals/s extrapolated to the whole workload: tables + sensitivity
+    x stride + per-angle model tables x stride + (model + OSEM per event) x J.
+    The model time is fitted as a per-angle table cost plus a per-event cost
+    from two sample sizes; a given fit (with its problem) is reused and only
+    the larger sample is run again."""
     J = len(ev)
+    stride = ORACLE_ANGLE_STRIDE.get(WORKLOAD, 1)
+    small, large = (3, 6) if stride == 1 else (2, 10)
     if fit is None:
-        r1 = oracle_sample_run(ph, g, ev, ns, ni, 3)
-        r2 = oracle_sample_run(ph, g, ev, ns, ni, 6)
+        r1 = oracle_sample_run(ph, g, ev, ns, ni, small, stride)
+        r2 = oracle_sample_run(ph, g, ev, ns, ni, large, stride, P=r1["P"])
         b = max(0.0, (r2["model"] - r1["model"]) / (r2["n"] - r1["n"]))
         a = max(0.0, r2["model"] - b * r2["n"])
-        c = r2["osem"] / r2["n"]
-        fit = dict(model_fixed=a, model_per_event=b, osem_per_event=c)
+        fit = dict(model_fixed=a, model_per_event=b, tables=r1["tables"], P=r1["P"])
+        wall = sum(r[k] for r in (r1, r2) for k in ("tables", "sens", "model", "osem"))
         run = r2
     else:
-        run = oracle_sample_run(ph, g, ev, ns, ni, 6)
-        fit = dict(fit, osem_per_event=run["osem"] / run["n"])
-    t_full = (run["tables"] + run["sens"] + fit["model_fixed"] + fit["model_per_event"] * J
-              + fit["osem_per_event"] * J)
+        run = oracle_sample_run(ph, g, ev, ns, ni, large, stride, P=fit["P"])
+        wall = run["sens"] + run["model"] + run["osem"]
+    t_full = (fit["tables"] + stride * (run["sens"] + fit["model_fixed"])
+              + (fit["model_per_event"] + run["osem"] / run["n"]) * J)
     value = J * run["n_nz"] / t_full
-    wall = run["tables"] + run["sens"] + run["model"] + run["osem"]
     return value, fit, run, wall
 
 
@@ -562,36 +710,48 @@ def cores_used():
     return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
 
 
-def cpu_baseline_block(value, run, wall):
+def cpu_baseline_block(value, run, wall, J):
+    st, na = run["stride"], run["P"].geom.n_angles
+    where = ("every angle" if st == 1 else
+             "every %d-th angle (%d of %d, on a scanner with only those angles; sensitivity and "
+             "per-angle table time x %d)" % (st, na, na * st, st))
     return {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
-            "sample": ("FP64 C/OpenMP oracle: full attenuation tables and 8-subset sensitivity, model "
-                       "rows and 10 OSEM iterations for %d of the %s events (6 per angle); model and "
-                       "OSEM time extrapolated linearly in J (per-angle table cost fitted from a 3-per-"
-                       "angle run); %.1f s of CPU wall time" % (run["n"], "200,000", wall))}
+            "sample": ("FP64 C/OpenMP oracle on %s: attenuation tables, subset sensitivity, model rows "
+                       "and 10 OSEM iterations for %d of the %d events; the whole workload's time "
+                       "extrapolated linearly in J and in the angle count (model time fitted as a "
+                       "per-angle table cost plus a per-event cost from two sample sizes); %.1f s of "
+                       "CPU wall time measured" % (where, run["n"], J, wall))}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    ph, g, ev, ns, ni = make_inputs(seed=2)
+    ph, g, ev, ns, ni = make_inputs(seed=SEEDS[WORKLOAD])
     J = len(ev)
+    stride = ORACLE_ANGLE_STRIDE.get(WORKLOAD, 1)
+    P = None
     for _ in range(args.warmup):
-        oracle_sample_run(ph, g, ev, ns, ni, 1)
-    _, fit, _, _ = oracle_rate(ph, g, ev, ns, ni)
+        P = oracle_sample_run(ph, g, ev, ns, ni, 1, stride, P=P)["P"]
+    v0, fit, run0, wall0 = oracle_rate(ph, g, ev, ns, ni)
     vals, walls = [], []
-    run = None
+    run = run0
     for _ in range(args.steps):
         v, _, run, wall = oracle_rate(ph, g, ev, ns, ni, fit)
         vals.append(v)
         walls.append(wall)
     value = statistics.mean(vals)
     ms = J * run["n_nz"] / value * 1e3
+    cpu = cpu_baseline_block(value, run, statistics.mean(walls), J)
+    cpu["sample"] += ("; each timed step reran the larger sample on the problem the fit built "
+                      "(its %.1f s of tables counted once in every extrapolation)" % fit["tables"])
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "ms_per_step_kind": "extrapolated to the whole workload from the measured sample",
+            "sample_wall_ms_per_step": statistics.mean(walls) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded ellipse phantom, photon Monte-Carlo list-mode events)",
-            "config": {"workload": WORKLOAD_DESC, "events": J, "support_pixels": run["n_nz"]},
-            "cpu_baseline": cpu_baseline_block(value, run, statistics.mean(walls)),
+            "config": workload_config(J, run["n_nz"], args.fmt, world),
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -726,6 +886,63 @@ def surrogate_jobs(eval_events):
             + [(SURR_EVAL_SEED, n, SURR_EVAL_SEED * 100 + k) for k, n in enumerate(sizes) if n > 0])
 
 
+def run_mlp_bench(args):
+    """The tcgen05 inference kernel alone (the tensor roofline of form 4):
+    each step is one lmosem_surrogate_infer call on `--events` rows (default
+    2M); the network's own time comes from the library's per-kernel profile."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    from paper_2002_12471_gb300 import synthetic as S
+    rows = args.events or 2_000_000
+    ph, g, *_ = S.workload("tiny16")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    rng = np.random.default_rng(1)
+    blob = torch.from_numpy(L.surrogate_init(seed=2)).to(dev)
+    X = torch.from_numpy(rng.standard_normal((rows, 6)).astype(np.float32)).to(dev)
+    y = torch.empty(rows, dtype=torch.float32, device=dev)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=1)
+    try:
+        for _ in range(args.warmup):
+            L.lmosem_surrogate_infer(ctx, blob, X, y)
+        L.lmosem_profile_read(ctx)
+        clocks = ClockSampler(None)
+        clocks.start()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.lmosem_surrogate_infer(ctx, blob, X, y)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        clk = clocks.stop()
+        prof = L.lmosem_profile_read(ctx)
+        launches = L.lmosem_launch_count(ctx)
+    finally:
+        L.lmosem_destroy(ctx)
+    if not bool(torch.isfinite(y).all()):
+        raise RuntimeError("non-finite network output")
+    mlp_ms = prof["mlp"][0] / args.steps
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    achieved = rows * MLP_FLOPS_PER_PAIR / (mlp_ms * 1e-3) / 1e12
+    return {"metric": METRIC, "value": rows / (statistics.mean(ms) * 1e-3), "unit": "rows/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+            "data": "synthetic (standard-normal inputs, He-initialised weights)",
+            "config": {"workload": WORKLOAD_DESC, "rows": rows},
+            "network_ms_per_step": mlp_ms,
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_tc", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": pk_kind + " sustained BF16"},
+            "clocks": clk, "gpu_launches": launches}
+
+
 def run_surrogate_bench(args):
     """Form (4): the scatter term of the model from the MLP surrogate.  The
     network is trained (untimed) on exact scatter path sums of 32 jittered
@@ -815,6 +1032,7 @@ def run_surrogate_bench(args):
     torch.cuda.empty_cache()
 
     support = None
+    last_check = [None]
     rows_ids = torch.arange(0, J, max(1, J // 2000), dtype=torch.int64, device=dev)
 
     def step(surrogate, a, u, e, profile=0, rows=None, host_out=None):
@@ -828,6 +1046,8 @@ def run_surrogate_bench(args):
                 L.lmosem_surrogate_load(ctx, blob)
             L.lmosem_sensitivity(ctx, ns)
             L.lmosem_build_model(ctx, a, u, e, ns, "surrogate" if surrogate else "fp32")
+            if surrogate:
+                last_check[0] = L.lmosem_surrogate_check(ctx)
             f = torch.empty(nsup, dtype=torch.float32, device=dev)
             ll = torch.empty(1, dtype=torch.float64, device=dev)
             L.lmosem_init_image(ctx, T, f)
@@ -925,6 +1145,10 @@ def run_surrogate_bench(args):
                                     "exact": pairs / (ex_build_ms * 1e-3),
                                     "exact_path_terms": terms},
         "exact_step_ms": ex_ms,
+        "exact_check": {"what": "the library's exact judge of every surrogate build: 512 evenly spaced rows "
+                                "recomputed with the exact path sum; above the tolerance the build falls back "
+                                "to the exact model", "tol": 1e-2, "rows_rel_l2": last_check[0][0],
+                        "worst_row_rel_l2": last_check[0][1], "fell_back_to_exact": last_check[0][2]},
         "error_vs_exact": {"model_rows_rel_l2": row_err, "image_rel_l2": img_err,
                            "roi_mean_rel": roi, "rows_sampled": int(rows_ids.numel()),
                            "held_out_scatter_rel_l2": ho_lin,
@@ -1155,6 +1379,8 @@ def main():
         out = run_batch_bench(args)
     elif WORKLOAD == "surrogate128":
         out = run_surrogate_bench(args)
+    elif WORKLOAD == "mlp_infer":
+        out = run_mlp_bench(args)
     elif WORKLOAD == "windows64":
         out = run_windows_bench(args)
     elif WORKLOAD == "binned64":
@@ -1162,9 +1388,9 @@ def main():
     else:
         out = run_ours(args, rank, world, local_rank)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            ph, g, ev, ns, ni = make_inputs(seed=2)
+            ph, g, ev, ns, ni = make_inputs(seed=SEEDS[WORKLOAD])
             v, _, run, wall = oracle_rate(ph, g, ev, ns, ni)
-            out["cpu_baseline"] = cpu_baseline_block(v, run, wall)
+            out["cpu_baseline"] = cpu_baseline_block(v, run, wall, len(ev))
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:

@@ -100,12 +100,17 @@ typedef struct {
      * LMOSEM_ETIMEOUT; the context stays usable.  Tests set a tiny budget
      * (here or with lmosem_set_wait_budget) to exercise that path. */
     int64_t wait_budget_cycles;
-    /* Streaming-pass implementation (tuning knobs; 0 = automatic):
-     * 1 = rows double-buffered in registers, 2 = rows staged in a shared-
-     * memory ring by bulk (TMA) copies, ring_rows rows per stage (1..8) and
-     * ring_stages stages (2..8), 3 = each thread's row vectors staged in its
-     * own slots of a shared-memory ring by cp.async (several row groups in
-     * flight, the arithmetic of 1). */
+    /* Streaming-pass implementation (tuning knobs; 0 = automatic, which is
+     * 4 for lmosem_iterate without per-iteration log-likelihoods and 1 or 3
+     * otherwise): 1 = rows double-buffered in registers, 2 = rows staged in a
+     * shared-memory ring by bulk (TMA) copies, ring_rows rows per stage
+     * (1..8) and ring_stages stages (2..8), 3 = each thread's row vectors
+     * staged in its own slots of a shared-memory ring by cp.async (several
+     * row groups in flight, the arithmetic of 1), 4 = every sub-iteration of
+     * the call in one persistent cooperative launch: the ring of 3, a
+     * bounded grid barrier, the update of each CTA's slice of the support,
+     * a second barrier, and the copies of the next subset's rows in flight
+     * across both barriers. */
     int32_t pass_variant;
     int32_t ring_rows;
     int32_t ring_stages;
@@ -321,6 +326,29 @@ lmosem_status lmosem_surrogate_infer(lmosem_ctx* ctx, const float* d_weights, co
  * model builds. */
 lmosem_status lmosem_surrogate_load(lmosem_ctx* ctx, const float* d_weights);
 
+/* The exact path sum as the judge and the fallback of the surrogate form.
+ * The surrogate replaces the first-order scatter sum of paper Eq. 2 (with
+ * Eq. 4; Section 2.2), so every LMOSEM_MODEL_SURROGATE_FP32 build is checked
+ * against that sum: n_check_rows sorted rows, evenly spaced over the model
+ * (row (k + 1/2) J / K of K, so every subset and angle group is sampled),
+ * are rebuilt with the exact path sum and compared with the surrogate's
+ * rows.  When the relative L2 error over those rows exceeds tol, the build
+ * replaces the whole model with the exact path sum.  tol = 0: measure only,
+ * never rebuild.  Defaults: tol 1e-2, 512 rows (0 selects 512).  Applies to
+ * the builds that follow.  EINVAL: tol negative or not finite, n_check_rows
+ * not in [0, 65536]. */
+lmosem_status lmosem_set_surrogate_check(lmosem_ctx* ctx, double tol, int32_t n_check_rows);
+
+/* Result of the check of the current model (see lmosem_set_surrogate_check):
+ * *h_rel_err = relative L2 error of the sampled surrogate rows against the
+ * exact ones, *h_row_max = the largest per-row relative L2 error, *h_exact =
+ * 1 when the check rebuilt the model with the exact path sum (the model then
+ * holds exact FP32 rows), 0 when it holds the surrogate's rows.  Any pointer
+ * may be NULL.  ESTATE: the current model was not built in the surrogate
+ * form. */
+lmosem_status lmosem_surrogate_check(const lmosem_ctx* ctx, double* h_rel_err, double* h_row_max,
+                                     int32_t* h_exact);
+
 /* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz);
  * J is the number of events, or the sum of the counts of a binned model.
  * ESTATE: no model or sensitivity. */
@@ -383,6 +411,17 @@ int64_t lmosem_launch_count(const lmosem_ctx* ctx);
  * follow, e.g. to let a test build the model and then make one pass time
  * out.  EINVAL: negative budget. */
 lmosem_status lmosem_set_wait_budget(lmosem_ctx* ctx, int64_t cycles);
+
+/* Measured throughput of the exponential unit (ex2.approx.ftz.f32 per
+ * second on the current device): grid = SMs x ctas_per_sm CTAs of `threads`
+ * threads, each running 8 independent chains of `iters` steps (one ex2 and
+ * one FP32 add per step), timed with CUDA events after one warm-up launch on
+ * `stream`.  The paper has no counterpart; the path sum of Eq. 2 costs one
+ * ex2 per term, so this rate bounds it.  Synchronises.  EINVAL: ctas_per_sm
+ * not in 1..32, threads not a multiple of 32 in 32..1024, iters not in
+ * 1..2^32, NULL output.  ECUDA: a launch or the timing failed. */
+lmosem_status lmosem_measure_ex2_rate(void* stream, int32_t ctas_per_sm, int32_t threads, int64_t iters,
+                                      double* h_per_second);
 
 /* Device time (ms) and launch count per kernel class since the last read,
  * from the CUDA events of a context created with opts->profile != 0.

@@ -92,6 +92,8 @@ void free_model(lmosem_ctx* c) {
     c->bpart_batch_floats = 0;
     c->batch_model = false;
     c->use_surrogate = false;
+    c->sur_checked = false;
+    c->sur_exact = false;
     c->n_real = 1;
     c->fmt = -1;
     c->J = 0;
@@ -111,6 +113,24 @@ lmosem_status check_events_args(lmosem_ctx* c, const int32_t* d_angle, const flo
         return fail(c, LMOSEM_EINVAL, "unknown model format");
     if (fmt == LMOSEM_MODEL_SURROGATE_FP32 && !c->d_surrogate)
         return fail(c, LMOSEM_ESTATE, "no surrogate loaded (lmosem_surrogate_load)");
+    return LMOSEM_OK;
+}
+
+// The surrogate rows against the exact path sum on a sample of rows; above
+// the tolerance the whole model is rebuilt exactly.
+lmosem_status check_surrogate(lmosem_ctx* c) {
+    double err = 0.0, mx = 0.0;
+    lmosem_status st = judge_surrogate(c, &err, &mx);
+    if (st) return st;
+    c->sur_checked = true;
+    c->sur_err = err;
+    c->sur_row_max = mx;
+    c->sur_exact = false;
+    if (c->sur_tol > 0.0 && !(err <= c->sur_tol)) {  // a NaN error rebuilds too
+        c->use_surrogate = false;
+        if ((st = build_model_rows(c))) return st;
+        c->sur_exact = true;
+    }
     return LMOSEM_OK;
 }
 
@@ -149,7 +169,7 @@ lmosem_status build_model_common(lmosem_ctx* c, const int32_t* d_angle, const fl
         free_model(c);
         return st;
     }
-    if ((st = build_model_rows(c))) {
+    if ((st = build_model_rows(c)) || (sur && (st = check_surrogate(c)))) {
         free_model(c);
         return st;
     }
@@ -222,6 +242,8 @@ void lmosem_destroy(lmosem_ctx* c) {
     dev_free(c, &c->d_sens);
     dev_free(c, &c->d_sens_angle);
     dev_free(c, &c->d_bpart);
+    dev_free(c, &c->d_coop);
+    c->coop_words = 0;
     dev_free(c, &c->d_llpart);
     dev_free(c, &c->d_scalar);
     dev_free(c, &c->d_status);
@@ -289,7 +311,7 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     }
     if (opts && opts->wait_budget_cycles > 0) c->wait_budget = opts->wait_budget_cycles;
     if (opts) {
-        if (opts->pass_variant < 0 || opts->pass_variant > 3 || opts->ring_rows < 0 ||
+        if (opts->pass_variant < 0 || opts->pass_variant > 4 || opts->ring_rows < 0 ||
             opts->ring_stages < 0) {
             delete c;
             return LMOSEM_EINVAL;
@@ -599,7 +621,9 @@ lmosem_status lmosem_iterate(lmosem_ctx* c, int32_t n_iters, double T, float* d_
     int h[2] = {0, 0};
     LMOSEM_CK(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    if (h[0]) return fail(c, LMOSEM_ETIMEOUT, "a bounded device wait ran out; the image is not updated");
+    if (h[0])
+        return fail(c, LMOSEM_ETIMEOUT,
+                    "a bounded device wait ran out; the image may hold the sub-iterations finished before it");
     if (h[1]) return fail(c, LMOSEM_ENUMERIC, std::to_string(h[1]) + " non-finite image values");
     return LMOSEM_OK;
 }
@@ -760,6 +784,25 @@ lmosem_status lmosem_surrogate_infer(lmosem_ctx* c, const float* d_weights, cons
     if (!d_weights || !d_features || !d_out || n < 1 || n > (int64_t(1) << 26))
         return fail(c, LMOSEM_EINVAL, "bad inference arguments (1 <= n <= 2^26)");
     return run_surrogate_infer(c, d_weights, d_features, n, d_out);
+}
+
+lmosem_status lmosem_set_surrogate_check(lmosem_ctx* c, double tol, int32_t n_check_rows) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!(tol >= 0.0) || !isfinite(tol) || n_check_rows < 0 || n_check_rows > 65536)
+        return fail(c, LMOSEM_EINVAL, "need tol >= 0 (finite) and 0 <= n_check_rows <= 65536");
+    c->sur_tol = tol;
+    c->sur_check_rows = n_check_rows ? n_check_rows : 512;
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_surrogate_check(const lmosem_ctx* c, double* h_rel_err, double* h_row_max,
+                                     int32_t* h_exact) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!c->sur_checked) return LMOSEM_ESTATE;
+    if (h_rel_err) *h_rel_err = c->sur_err;
+    if (h_row_max) *h_row_max = c->sur_row_max;
+    if (h_exact) *h_exact = c->sur_exact ? 1 : 0;
+    return LMOSEM_OK;
 }
 
 lmosem_status lmosem_surrogate_load(lmosem_ctx* c, const float* d_weights) {

@@ -105,12 +105,21 @@ struct lmosem_ctx {
     double* d_scalar = nullptr;   // small FP64 scratch
     int* d_status = nullptr;      // [0] = 1 after a bounded device wait ran out
     long long wait_budget = 2000000000LL;  // clock cycles per bounded wait
-    int pass_variant = 0;         // 0 auto, 1 register pipeline, 2 bulk-copy ring
+    int pass_variant = 0;         // 0 auto, 1 register pipeline, 2 bulk-copy ring, 3 cp.async ring,
+                                  // 4 persistent cooperative launch (the automatic choice)
+    int64_t* d_coop = nullptr;    // persistent form: subset offsets and two barrier words
+    size_t coop_words = 0;
     // scatter surrogate
     float* d_surrogate = nullptr;             // LMOSEM_SURROGATE_PARAMS FP32 parameters
     bool scatter_only = false;                // model build leaves the primary path out
     bool use_surrogate = false;               // model build takes the scatter part from the MLP
     int surrogate_kernel = 0;                 // inference: 0 auto (tcgen05), 1 mma.sync, 2 tcgen05
+    // exact check of a surrogate build: rows recomputed by the path sum
+    double sur_tol = 1e-2;                    // rel-L2 above which the model is rebuilt exactly (0: never)
+    int sur_check_rows = 512;                 // sampled rows
+    bool sur_checked = false;                 // a surrogate build has been checked
+    double sur_err = 0.0, sur_row_max = 0.0;  // rel-L2 of the sampled rows; largest per-row rel-L2
+    bool sur_exact = false;                   // the check rebuilt the model with the exact path sum
     // batching form: per-realisation work words, partial slots, tiles, graph
     bool batch_model = false;
     int64_t* d_bsub_row0 = nullptr;           // n_real * (n_subsets + 1)
@@ -280,6 +289,10 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
                                   float* out);
 lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ);
 lmosem_status build_model_surrogate(lmosem_ctx* c);
+// model.cu: exact rows of an evenly spaced sample of the model's events
+// against the rows the surrogate built (relative L2 over the sampled rows,
+// and the largest per-row value); synchronises
+lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max);
 // mlp_tc.cu: fused tcgen05 inference of M rows of BF16 inputs (M x 16)
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
                          const unsigned char* w234img, const __nv_bfloat16* X, float* y, int64_t M);

@@ -1160,6 +1160,142 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     return LMOSEM_OK;
 }
 
+namespace {
+
+__global__ void k_gather_events(const int32_t* __restrict__ a_s, const float* __restrict__ u_s,
+                                const float* __restrict__ e_s, const int64_t* __restrict__ rows, int64_t K,
+                                int32_t* __restrict__ a_o, float* __restrict__ u_o, float* __restrict__ e_o) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int64_t r = rows[k];
+    a_o[k] = a_s[r];
+    u_o[k] = u_s[r];
+    e_o[k] = e_s[r];
+}
+
+// sampled row k: sum over the support of (surrogate - exact)^2 and exact^2,
+// FP64, in a fixed order (one CTA per row)
+__global__ void __launch_bounds__(256) k_judge_rows(const float* __restrict__ model, int64_t ld,
+                                                    const int64_t* __restrict__ rows,
+                                                    const float* __restrict__ exact, int n_sup,
+                                                    double* __restrict__ out) {
+    __shared__ double sh[2][8];
+    const int64_t k = blockIdx.x;
+    const float* ps = model + rows[k] * ld;
+    const float* pe = exact + k * ld;
+    double d2 = 0.0, e2 = 0.0;
+    for (int n = threadIdx.x; n < n_sup; n += blockDim.x) {
+        const double e = pe[n], d = (double)ps[n] - e;
+        d2 += d * d;
+        e2 += e * e;
+    }
+    for (int o = 16; o; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][warp] = d2;
+        sh[1][warp] = e2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        out[2 * k] = a;
+        out[2 * k + 1] = b;
+    }
+}
+
+}  // namespace
+
+// The exact judge of a surrogate build: K sorted rows evenly spaced over the
+// model ((k + 1/2) J / K, so every subset and angle group is sampled) are
+// rebuilt with the exact path sum into scratch rows, by running the exact
+// row build on the sample in place of the model's events, and compared with
+// the surrogate's rows.
+lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max) {
+    const int64_t J = c->J;
+    const int64_t K = std::min<int64_t>(J, c->sur_check_rows);
+    std::vector<int64_t> rows(K);
+    for (int64_t k = 0; k < K; ++k) rows[k] = (int64_t)(((double)k + 0.5) * (double)J / (double)K);
+    lmosem_status st;
+    int64_t* d_rows = nullptr;
+    int32_t* d_a = nullptr;
+    float *d_u = nullptr, *d_e = nullptr, *d_ex = nullptr;
+    double* d_sums = nullptr;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&d_rows, K)) || (st = tmp.alloc(&d_a, K)) || (st = tmp.alloc(&d_u, K)) ||
+        (st = tmp.alloc(&d_e, K)) || (st = tmp.alloc(&d_ex, (size_t)K * c->ld_model)) ||
+        (st = tmp.alloc(&d_sums, 2 * K)))
+        return st;
+    LMOSEM_CK(c, cudaMemcpyAsync(d_rows, rows.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_PROF_BEGIN(c);
+    k_gather_events<<<(unsigned)((K + 255) / 256), 256, 0, c->stream>>>(c->d_a_s, c->d_u_s, c->d_e_s, d_rows, K,
+                                                                        d_a, d_u, d_e);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
+    std::vector<int32_t> h_a(K);
+    LMOSEM_CK(c, cudaMemcpyAsync(h_a.data(), d_a, K * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    // rows of every (realisation, angle) of the sample: contiguous, since the
+    // sample keeps the model's sorted order
+    std::vector<int64_t> s_row0((size_t)c->n_real * c->n_angles, 0), s_cnt((size_t)c->n_real * c->n_angles, 0);
+    for (int64_t k = 0; k < K; ++k) {
+        int r = 0;
+        while (r + 1 < c->n_real && rows[k] >= c->h_real_row0[r + 1]) ++r;
+        const size_t i = (size_t)r * c->n_angles + h_a[k];
+        if (s_cnt[i]++ == 0) s_row0[i] = k;
+    }
+    // the exact build on the sample, with the model's event state put back after
+    const int64_t J0 = c->J;
+    int32_t* a0 = c->d_a_s;
+    float *u0 = c->d_u_s, *e0 = c->d_e_s;
+    void* m0 = c->d_model;
+    const int fmt0 = c->fmt;
+    std::vector<int64_t> row0_0, cnt0;
+    row0_0.swap(c->h_angle_row0);
+    cnt0.swap(c->h_angle_cnt);
+    c->h_angle_row0 = s_row0;
+    c->h_angle_cnt = s_cnt;
+    c->J = K;
+    c->d_a_s = d_a;
+    c->d_u_s = d_u;
+    c->d_e_s = d_e;
+    c->d_model = d_ex;
+    c->fmt = LMOSEM_MODEL_FP32;
+    c->use_surrogate = false;
+    st = build_model_rows(c);
+    c->use_surrogate = true;
+    c->fmt = fmt0;
+    c->d_model = m0;
+    c->d_e_s = e0;
+    c->d_u_s = u0;
+    c->d_a_s = a0;
+    c->J = J0;
+    c->h_angle_row0.swap(row0_0);
+    c->h_angle_cnt.swap(cnt0);
+    if (st) return st;
+    LMOSEM_PROF_BEGIN(c);
+    k_judge_rows<<<(unsigned)K, 256, 0, c->stream>>>(reinterpret_cast<const float*>(c->d_model), c->ld_model,
+                                                      d_rows, d_ex, c->n_sup, d_sums);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
+    std::vector<double> sums(2 * K);
+    LMOSEM_CK(c, cudaMemcpyAsync(sums.data(), d_sums, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    double d2 = 0.0, e2 = 0.0, mx = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        d2 += sums[2 * k];
+        e2 += sums[2 * k + 1];
+        if (sums[2 * k + 1] > 0.0) mx = std::max(mx, sqrt(sums[2 * k] / sums[2 * k + 1]));
+        else if (sums[2 * k] > 0.0) mx = INFINITY;
+    }
+    *rel_err = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
+    *row_max = mx;
+    return LMOSEM_OK;
+}
 
 lmosem_status build_binned_rows(lmosem_ctx* c, const int32_t* d_rowmap, int n_ebins, const double* e_edges) {
     if (n_ebins < 1 || n_ebins > kMaxEBins) return fail(c, LMOSEM_EINVAL, "1..8 energy bins");

@@ -85,6 +85,14 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+// Programmatic dependent launch: a sub-iteration's pass and update are
+// launched with programmatic stream serialisation, so a kernel can start
+// while its predecessor finishes.  pdl_wait() blocks until the preceding
+// kernel of the stream has completed and its writes are visible (a no-op
+// without such a launch); pdl_trigger() lets the next kernel be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 struct PassArgs {
     const void* model;
     int64_t ld_bytes;        // row stride in bytes
@@ -137,15 +145,23 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
 
     float fr[VPT][EPV], br[VPT][EPV];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        int col0 = EPV * (t + NT * v);
+    for (int v = 0; v < VPT; ++v)
 #pragma unroll
-        for (int e = 0; e < EPV; ++e) {
-            int col = col0 + e;
-            fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
-            br[v][e] = 0.0f;
+        for (int e = 0; e < EPV; ++e) br[v][e] = 0.0f;
+    // the image, once the kernel that wrote it has finished (the first rows
+    // are already in flight: they do not depend on it)
+    auto load_f = [&]() {
+        pdl_wait();
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            int col0 = EPV * (t + NT * v);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+                int col = col0 + e;
+                fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
+            }
         }
-    }
+    };
     const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
     const int64_t re = min(A.r1, rb + A.rows_per_cta);
     double ll = 0.0;
@@ -226,6 +242,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
 
     uint4 P0[R][VPT], P1[R][VPT];
     if (rb < re) load(rb, P0);
+    load_f();
     for (int64_t r = rb; r < re; r += 2 * R) {
         if (r + R < re) load(r + R, P1);
         process(r, P0, 0);
@@ -233,6 +250,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
         if (r + 2 * R < re) load(r + 2 * R, P0);
         process(r + R, P1, 1);
     }
+    pdl_trigger();
     if constexpr (BACK) {
         float* bp = A.bpart + (size_t)blockIdx.x * A.n_sup;
 #pragma unroll
@@ -294,15 +312,9 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
 
     float fr[VPT][EPV], br[VPT][EPV];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        int col0 = EPV * (t + NT * v);
+    for (int v = 0; v < VPT; ++v)
 #pragma unroll
-        for (int e = 0; e < EPV; ++e) {
-            int col = col0 + e;
-            fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
-            br[v][e] = 0.0f;
-        }
-    }
+        for (int e = 0; e < EPV; ++e) br[v][e] = 0.0f;
     const int64_t rb = A.r0 + (int64_t)blockIdx.x * A.rows_per_cta;
     const int64_t re = min(A.r1, rb + A.rows_per_cta);
     const int64_t ngroups = re > rb ? (re - rb + R - 1) / R : 0;
@@ -325,6 +337,18 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
         cpa_commit();
     };
     for (int64_t g = 0; g < min((int64_t)S - 1, ngroups); ++g) issue(g);
+    // the image, once the kernel that wrote it has finished (the first row
+    // groups are already in flight)
+    pdl_wait();
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        int col0 = EPV * (t + NT * v);
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) {
+            int col = col0 + e;
+            fr[v][e] = col < A.n_sup ? A.f[col] : 0.0f;
+        }
+    }
     for (int64_t g = 0; g < ngroups; ++g) {
         const int64_t issued = min(ngroups, g + S - 1);
         cpa_wait((int)(issued - 1 - g));  // this thread's copies of group g have landed
@@ -401,6 +425,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
             }
         }
     }
+    pdl_trigger();
     if constexpr (BACK) {
         float* bp = A.bpart + (size_t)blockIdx.x * A.n_sup;
 #pragma unroll
@@ -468,6 +493,8 @@ __global__ void __launch_bounds__(kUpdPix * kUpdGroups) k_update_px(const float*
                                                                   int n_sup, float* __restrict__ f,
                                                                   const double* __restrict__ sens_i, double T,
                                                                   const int* __restrict__ status) {
+    pdl_trigger();  // the next pass may start loading its rows (they do not depend on f)
+    pdl_wait();     // the pass that wrote the partials has finished
     if (status && *status) return;
     __shared__ float sh[kUpdGroups][kUpdPix + 1];
     const int p = threadIdx.x % kUpdPix, g = threadIdx.x / kUpdPix;
@@ -785,6 +812,269 @@ __global__ void __launch_bounds__(kMaxPassThreads) k_pass_ring(RingArgs A) {
     }
 }
 
+// ---- persistent OS-EM: the sub-iterations of n_iters iterations in one
+// cooperative launch.
+//
+// Every CTA streams its share of each subset's rows through the thread-
+// private cp.async ring of k_pass_cpa (same arithmetic per row), writes its
+// partial b, and meets the other CTAs at a grid barrier.  CTA c then sums
+// the partials of its slice of the support in CTA order (fixed, so the image
+// is reproducible) and applies f_q <- f_q b_q / (T s^i_q); a second barrier
+// publishes the new image.  The ring is not drained at subset boundaries:
+// copies of the next subset's first rows (which do not depend on f) are in
+// flight while the CTAs wait at the barriers and reduce.  Both barriers are
+// bounded: a wait that runs out sets the status word, and every CTA leaves.
+struct CoopArgs {
+    const void* model;
+    int64_t ld_bytes;
+    int64_t nvec;
+    const int64_t* sub_row0;  // n_subsets + 1 sorted-row offsets of the subsets
+    int n_subsets, n_iters;
+    float* f;                 // image, updated in place
+    const double* sens;       // [n_subsets][n_sup] subset sensitivities (without T)
+    double T;
+    const float* weight;      // row counts (binned rows) or nullptr
+    int n_sup;
+    float* bpart;             // [grid][n_sup] partial back-projections
+    unsigned* bar;            // arrivals, completed barriers (zero at launch)
+    int* status;
+    long long budget;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier number `target` (1, 2, ...) of the launch.  Returns false when
+// this CTA's wait ran out (status set) or another CTA has given up.
+__device__ __forceinline__ bool coop_barrier(const CoopArgs& A, unsigned target, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        __threadfence();  // this CTA's partials and image writes before the arrival
+        const unsigned arrived = atomicAdd(&A.bar[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&A.bar[0], 0u);
+            __threadfence();
+            atomicAdd(&A.bar[1], 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&A.bar[1]) < target) {
+                if (*reinterpret_cast<volatile int*>(A.status)) {
+                    good = 0;
+                    break;
+                }
+                if (clock64() - t0 > A.budget) {
+                    atomicExch(A.status, 1);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_ok = good;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <typename H, int VPT>
+constexpr int coop_rows() {
+    // rows per ring stage, about 12 to 25 KB of row data
+    return std::is_same<H, float>::value ? (VPT <= 2 ? 4 : (VPT <= 4 ? 2 : 1)) : (VPT <= 1 ? 4 : (VPT <= 3 ? 2 : 1));
+}
+
+template <typename H, int VPT>
+constexpr int coop_min_ctas() {
+    // two CTAs per SM, except 2-byte rows of 6 or 8 vectors per thread (over
+    // 8192 columns), whose image and partial registers need the whole file
+    return !std::is_same<H, float>::value && VPT >= 6 ? 1 : 2;
+}
+
+template <typename H, int VPT, int R, bool W>
+__global__ void __launch_bounds__(kMaxPassThreads, coop_min_ctas<H, VPT>()) k_osem_coop(CoopArgs A, int S) {
+    constexpr int EPV = Vec<H>::N;
+    extern __shared__ __align__(128) unsigned char cring[];
+    __shared__ float red[2][R][kMaxPassThreads / 32];
+    __shared__ int s_ok;
+    const int NT = blockDim.x, NW = NT >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const char* model = reinterpret_cast<const char*>(A.model);
+    const size_t gbytes = (size_t)R * A.ld_bytes;
+    const int K = A.n_iters * A.n_subsets;
+    if (*reinterpret_cast<volatile int*>(A.status)) return;  // an earlier wait ran out
+
+    // this CTA's rows of sub-iteration k (the subsets split in R-row chunks)
+    auto rows_of = [&](int k, int64_t& rb, int64_t& re) {
+        const int i = k % A.n_subsets;
+        const int64_t r0 = A.sub_row0[i], r1 = A.sub_row0[i + 1];
+        int64_t chunk = (r1 - r0 + G - 1) / G;
+        chunk = (chunk + R - 1) / R * R;
+        rb = min(r1, r0 + (int64_t)cta * chunk);
+        re = min(r1, rb + chunk);
+    };
+    // issue cursor: the next row group to copy, across sub-iterations
+    int ki = 0;
+    int64_t rbi, rei;
+    rows_of(0, rbi, rei);
+    int64_t ri = rbi;
+    int64_t issued = 0;
+    auto issue_next = [&]() {
+        while (ki < K && ri >= rei) {
+            if (++ki < K) {
+                rows_of(ki, rbi, rei);
+                ri = rbi;
+            }
+        }
+        if (ki >= K) return;
+        unsigned char* dst = cring + (size_t)(issued % S) * gbytes;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int64_t vec = t + (int64_t)NT * v;
+                if (ri + i < rei && vec < A.nvec)
+                    cpa16(dst + i * A.ld_bytes + vec * 16, model + (ri + i) * A.ld_bytes + vec * 16);
+            }
+        }
+        cpa_commit();
+        ri += R;
+        ++issued;
+    };
+    for (int s = 0; s < S - 1; ++s) issue_next();
+
+    int64_t consumed = 0;
+    unsigned barriers = 0;
+    const int P = (A.n_sup + G - 1) / G;  // support pixels reduced by each CTA
+    const int q0 = min(A.n_sup, cta * P), q1 = min(A.n_sup, q0 + P);
+    for (int k = 0; k < K; ++k) {
+        const int isub = k % A.n_subsets;
+        float fr[VPT][EPV], br[VPT][EPV];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int col0 = EPV * (t + NT * v);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+                const int col = col0 + e;
+                fr[v][e] = col < A.n_sup ? __ldcg(A.f + col) : 0.0f;  // written by other CTAs
+                br[v][e] = 0.0f;
+            }
+        }
+        int64_t rb, re;
+        rows_of(k, rb, re);
+        for (int64_t r = rb; r < re; r += R, ++consumed) {
+            cpa_wait((int)min((int64_t)7, issued - 1 - consumed));  // this group has landed
+            issue_next();  // into the slots of the previous group, read by this thread only
+            const unsigned char* st = cring + (size_t)(consumed % S) * gbytes;
+            const int rb_ = (int)(consumed & 1);
+            uint4 raw[R][VPT];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int64_t vec = t + (int64_t)NT * v;
+                    raw[i][v] = (r + i < re && vec < A.nvec)
+                                    ? *reinterpret_cast<const uint4*>(st + i * A.ld_bytes + vec * 16)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            float d[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                float2 s2 = make_float2(0.0f, 0.0f);  // even and odd columns
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    float p[EPV];
+                    Vec<H>::cvt(raw[i][v], p);
+#pragma unroll
+                    for (int e = 0; e < EPV; e += 2)
+                        s2 = ffma2(make_float2(p[e], p[e + 1]), make_float2(fr[v][e], fr[v][e + 1]), s2);
+                }
+                float sum = s2.x + s2.y;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                d[i] = sum;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) red[rb_][i][warp] = d[i];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                float y = 0.0f;
+                for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
+                const bool ok = r + i < re && y > 0.0f;
+                float inv = ok ? 1.0f / y : 0.0f;
+                if constexpr (W) inv *= ok ? A.weight[r + i] : 0.0f;
+                const float2 inv2 = make_float2(inv, inv);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    float p[EPV];
+                    Vec<H>::cvt(raw[i][v], p);
+#pragma unroll
+                    for (int e = 0; e < EPV; e += 2) {
+                        const float2 b2 = ffma2(make_float2(p[e], p[e + 1]), inv2,
+                                                make_float2(br[v][e], br[v][e + 1]));
+                        br[v][e] = b2.x;
+                        br[v][e + 1] = b2.y;
+                    }
+                }
+            }
+        }
+        {
+            float* bp = A.bpart + (size_t)cta * A.n_sup;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col0 = EPV * (t + NT * v);
+#pragma unroll
+                for (int e = 0; e < EPV; ++e)
+                    if (col0 + e < A.n_sup) __stcg(bp + col0 + e, br[v][e]);
+            }
+        }
+        if (!coop_barrier(A, ++barriers, &s_ok)) break;
+        // b_q of this CTA's slice: warp w takes the pixels q0 + w, q0 + w + NW,
+        // ...; lane l sums the partials l, l + 32, ... in order and the lanes
+        // are added in a fixed pattern (deterministic); T s^i_q in FP64
+        const double* si = A.sens + (size_t)isub * A.n_sup;
+        for (int q = q0 + warp; q < q1; q += NW) {
+            float acc = 0.0f;
+#pragma unroll 4
+            for (int g = lane; g < G; g += 32) acc += __ldcg(A.bpart + (size_t)g * A.n_sup + q);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                const double sd = si[q];
+                const float ts = (float)(A.T * sd);
+                __stcg(A.f + q, sd > 0.0 ? __ldcg(A.f + q) * acc / ts : 0.0f);
+            }
+        }
+        if (!coop_barrier(A, ++barriers, &s_ok)) break;
+    }
+    cpa_wait(0);  // no copy outlives the CTA (an abandoned launch included)
+}
+
+// launch with programmatic stream serialisation (see pdl_wait)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct PassShape {
     int vpt, nt;
     int64_t nvec;
@@ -821,7 +1111,7 @@ lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt)
     grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
     c->pass_grid = (int)grid;
     LMOSEM_PROF_BEGIN(c);
-    kern<<<(unsigned)grid, nt, 0, c->stream>>>(A);
+    LMOSEM_CK(c, launch_pdl(kern, dim3((unsigned)grid), dim3(nt), 0, c->stream, A));
     LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
     return LMOSEM_OK;
 }
@@ -852,7 +1142,7 @@ lmosem_status launch_pass_cpa_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt)
     grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
     c->pass_grid = (int)grid;
     LMOSEM_PROF_BEGIN(c);
-    kern<<<(unsigned)grid, nt, smem, c->stream>>>(A, S);
+    LMOSEM_CK(c, launch_pdl(kern, dim3((unsigned)grid), dim3(nt), smem, c->stream, A, S));
     LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
     return LMOSEM_OK;
 }
@@ -963,6 +1253,84 @@ lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f,
     return launch_pass_h<__nv_bfloat16, BACK>(c, A, rows, s);
 }
 
+// the persistent cooperative form of n_iters iterations (one launch)
+template <typename H, int VPT, bool W>
+lmosem_status launch_coop_t(lmosem_ctx* c, CoopArgs A, int nt) {
+    constexpr int R = coop_rows<H, VPT>();
+    auto kern = k_osem_coop<H, VPT, R, W>;
+    const size_t gbytes = (size_t)R * A.ld_bytes;
+    // about 100 KB of ring per CTA (two CTAs per SM), 2 to kCpaMaxStages stages
+    int S = (int)std::max<int64_t>(2, std::min<int64_t>(kCpaMaxStages, (int64_t)(100 << 10) / (int64_t)gbytes));
+    int dev = 0, sms = 0, smem_max = 0;
+    LMOSEM_CK(c, cudaGetDevice(&dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LMOSEM_CK(c, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    while (S > 2 && (size_t)S * gbytes > (size_t)smem_max) --S;
+    if ((size_t)S * gbytes > (size_t)smem_max) return fail(c, LMOSEM_ENOTIMPL, "rows too wide for the ring");
+    const size_t smem = (size_t)S * gbytes;
+    LMOSEM_CK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LMOSEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+    if (per_sm < 1) return fail(c, LMOSEM_ENOTIMPL, "the persistent pass does not fit an SM");
+    const int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, c->pass_ctas);
+    LMOSEM_CK(c, cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), c->stream));
+    void* args[] = {&A, &S};
+    c->pass_grid = grid;
+    LMOSEM_PROF_BEGIN(c);
+    LMOSEM_CK(c, cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3((unsigned)nt), args,
+                                             smem, c->stream));
+    LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
+    return LMOSEM_OK;
+}
+
+template <typename H, bool W = false>
+lmosem_status launch_coop_h(lmosem_ctx* c, const CoopArgs& A, PassShape s) {
+    switch (s.vpt) {
+        case 1: return launch_coop_t<H, 1, W>(c, A, s.nt);
+        case 2: return launch_coop_t<H, 2, W>(c, A, s.nt);
+        case 3: return launch_coop_t<H, 3, W>(c, A, s.nt);
+        case 4: return launch_coop_t<H, 4, W>(c, A, s.nt);
+        case 6: return launch_coop_t<H, 6, W>(c, A, s.nt);
+        default: return launch_coop_t<H, 8, W>(c, A, s.nt);
+    }
+}
+
+lmosem_status run_coop(lmosem_ctx* c, int n_iters, double T, float* d_f) {
+    if (n_iters < 1) return LMOSEM_OK;
+    lmosem_status st;
+    const size_t words = (size_t)c->n_subsets + 2;  // subset offsets, then the barrier words
+    if (c->coop_words < words) {
+        if ((st = dev_alloc(c, &c->d_coop, words))) return st;
+        c->coop_words = words;
+    }
+    LMOSEM_CK(c, cudaMemcpyAsync(c->d_coop, c->h_subset_row0.data(), ((size_t)c->n_subsets + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    PassShape s = pass_shape(c);
+    CoopArgs A;
+    A.model = c->d_model;
+    A.ld_bytes = c->ld_model * (c->fmt == LMOSEM_MODEL_FP32 ? 4 : 2);
+    A.nvec = s.nvec;
+    A.sub_row0 = c->d_coop;
+    A.n_subsets = c->n_subsets;
+    A.n_iters = n_iters;
+    A.f = d_f;
+    A.sens = c->d_sens;
+    A.T = T;
+    A.weight = c->d_weight;
+    A.n_sup = c->n_sup;
+    A.bpart = c->d_bpart;
+    A.bar = reinterpret_cast<unsigned*>(c->d_coop + c->n_subsets + 1);
+    A.status = c->d_status;
+    A.budget = c->wait_budget;
+    if (c->d_weight) {  // binned rows: FP32 only
+        if (c->fmt != LMOSEM_MODEL_FP32) return fail(c, LMOSEM_ESTATE, "binned rows are FP32");
+        return launch_coop_h<float, true>(c, A, s);
+    }
+    if (c->fmt == LMOSEM_MODEL_FP32) return launch_coop_h<float>(c, A, s);
+    if (c->fmt == LMOSEM_MODEL_FP16_SCALED) return launch_coop_h<__half>(c, A, s);
+    return launch_coop_h<__nv_bfloat16>(c, A, s);
+}
+
 lmosem_status ll_final(lmosem_ctx* c, double T, const float* d_f, double* out) {
     LMOSEM_PROF_BEGIN(c);
     k_ll_final<<<1, 256, 0, c->stream>>>(c->d_llpart, c->pass_grid,
@@ -1003,9 +1371,9 @@ lmosem_status enqueue_iteration(lmosem_ctx* c, double T, float* d_f) {
         if ((st = launch_pass<true>(c, c->h_subset_row0[i], c->h_subset_row0[i + 1], d_f, T)))
             return st;
         LMOSEM_PROF_BEGIN(c);
-        k_update_px<<<(c->n_sup + kUpdPix - 1) / kUpdPix, kUpdPix * kUpdGroups, 0, c->stream>>>(
-            c->d_bpart, c->pass_grid, c->n_sup, d_f, c->d_sens + (size_t)i * c->n_sup, T,
-            c->d_status);
+        LMOSEM_CK(c, launch_pdl(k_update_px, dim3((c->n_sup + kUpdPix - 1) / kUpdPix), dim3(kUpdPix * kUpdGroups),
+                                0, c->stream, (const float*)c->d_bpart, c->pass_grid, c->n_sup, d_f,
+                                (const double*)(c->d_sens + (size_t)i * c->n_sup), T, (const int*)c->d_status));
         LMOSEM_LAUNCHED(c, LMOSEM_K_UPDATE);
     }
     return LMOSEM_OK;
@@ -1060,6 +1428,9 @@ lmosem_status iterate_graph(lmosem_ctx* c, int n_iters, double T, float* d_f, bo
 
 lmosem_status run_iterations(lmosem_ctx* c, int n_iters, double T, float* d_f, double* d_ll) {
     lmosem_status st;
+    // the persistent form when asked for (pass_variant 4), unless a
+    // log-likelihood is taken after every iteration
+    if (!d_ll && !c->batch_model && c->pass_variant == 4) return run_coop(c, n_iters, T, d_f);
     if (!d_ll) {
         bool done = false;
         if ((st = iterate_graph(c, n_iters, T, d_f, &done))) return st;

@@ -108,6 +108,9 @@ SIGNATURES = {
     "lmosem_surrogate_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "lmosem_surrogate_infer": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
     "lmosem_surrogate_load": (ctypes.c_int, [_vp, _vp]),
+    "lmosem_set_surrogate_check": (ctypes.c_int, [_vp, _dbl, _i32]),
+    "lmosem_measure_ex2_rate": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp]),
+    "lmosem_surrogate_check": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -389,6 +392,22 @@ def lmosem_surrogate_load(ctx, d_weights):
     _check(ctx, load().lmosem_surrogate_load(ctx, _ptr(d_weights)))
 
 
+def lmosem_set_surrogate_check(ctx, tol=1e-2, n_check_rows=0):
+    """Tolerance (relative L2 of sampled rows) above which a surrogate build
+    is replaced by the exact path sum (0: measure only), and the sampled row
+    count (0: 512)."""
+    _check(ctx, load().lmosem_set_surrogate_check(ctx, float(tol), int(n_check_rows)))
+
+
+def lmosem_surrogate_check(ctx):
+    """(rel_err, row_max, exact) of the exact check of the current surrogate
+    model: relative L2 error of the sampled rows, largest per-row error, and
+    whether the model was rebuilt with the exact path sum."""
+    err, mx, ex = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(ctx, load().lmosem_surrogate_check(ctx, ctypes.byref(err), ctypes.byref(mx), ctypes.byref(ex)))
+    return err.value, mx.value, bool(ex.value)
+
+
 def surrogate_init(seed=0, layers=(6, 256, 256, 256, 256, 1)):
     """Initial surrogate weights as a blob: He-normal weights (standard
     deviation sqrt(2 / fan_in)), zero biases, output standardisation (0, 1);
@@ -438,3 +457,13 @@ def header_functions(header_path=None):
         header_path = os.path.join(os.path.dirname(_HERE), "include", "lmosem.h")
     txt = open(header_path).read()
     return sorted(set(re.findall(r"\b(lmosem_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lmosem_measure_ex2_rate(stream=None, ctas_per_sm=4, threads=512, iters=1 << 16):
+    """ex2.approx.ftz.f32 evaluations per second on the current device."""
+    out = ctypes.c_double()
+    s = getattr(stream, "cuda_stream", stream)
+    st = load().lmosem_measure_ex2_rate(s, int(ctas_per_sm), int(threads), int(iters), ctypes.byref(out))
+    if st != OK:
+        raise LmosemError(st, "lmosem_measure_ex2_rate failed")
+    return out.value

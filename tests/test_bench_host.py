@@ -118,16 +118,20 @@ def test_clock_summary_takes_median_and_active_reasons():
 
 def test_traffic_figure_is_gated_on_the_path_sum_source():
     """The committed DRAM-bytes figure is used only while the path-sum
-    kernel's source hash matches the one recorded beside it."""
+    kernel's source hash matches the one recorded beside it, and only for
+    the workload it was taken on."""
     h = bench.kernel_source_sha1()
     assert len(h) == 12
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     rec = [dict(p.split("=", 1) for p in ln.split() if "=" in p) for ln in open(path)]
     mine = [r for r in rec if r.get("kernel") == "k_pathsum"]
     assert mine, "no k_pathsum traffic line"
-    t = bench.read_traffic("k_pathsum")
-    if any(r["source_sha1"] == h for r in mine):
-        assert t == float([r for r in mine if r["source_sha1"] == h][0]["dram_bytes_per_launch"])
-    else:
-        assert t is None
-    assert bench.read_traffic("no_such_kernel") is None
+    for wl in ("dat64", "dat128"):
+        t = bench.read_traffic("k_pathsum", wl)
+        match = [r for r in mine if r["source_sha1"] == h and r.get("workload", "").split("_")[0] == wl]
+        if match:
+            assert t == float(match[0]["dram_bytes_per_launch"])
+        else:
+            assert t is None
+    assert bench.read_traffic("no_such_kernel", "dat64") is None
+    assert bench.read_traffic("k_pathsum", "no_such_workload") is None

@@ -32,3 +32,27 @@ def test_oracle_matches_frozen_fixture():
     f, hist = oracle.osem(p, a, s, len(G["loglik"]), f0)
     np.testing.assert_allclose(f, G["image"], rtol=1e-9)
     np.testing.assert_allclose([oracle.loglik(p, h, s.sum(0)) for h in hist], G["loglik"], rtol=1e-12)
+
+
+def test_dat128_subset_fixture_is_the_workloads_case():
+    """The frozen 128 x 128 subset (tests/golden/make_dat128_subset.py) holds
+    the precision workload's phantom, scanner and ROI weights, events inside
+    the detector's extent and energy window, and an oracle image and
+    sensitivity of the support's size."""
+    from paper_2002_12471_gb300 import synthetic as S
+    G = np.load(os.path.join(HERE, "golden", "dat128_subset_oracle.npz"))
+    ph, g, J, ns, ni = S.workload("dat128")
+    np.testing.assert_allclose(G["mu"], ph.mu, rtol=0, atol=1e-15)
+    for name in ("caudate", "putamen"):
+        np.testing.assert_allclose(G["roi_" + name], ph.rois[name], rtol=0, atol=1e-6)
+    gd = dict(zip(G["geometry_keys"].tolist(), G["geometry_values"].tolist()))
+    assert gd == {k: float(v) for k, v in g.items()}
+    assert (int(G["n_subsets"]), int(G["n_iters"]), float(G["pixel_mm"])) == (ns, ni, ph.pixel_mm)
+    half = 0.5 * g["n_bins"] * g["bin_mm"]
+    assert np.all(np.abs(G["u_mm"]) <= half)
+    assert np.all((G["e_kev"] >= g["e_lo_kev"]) & (G["e_kev"] <= g["e_hi_kev"]))
+    assert np.all((G["angle"] >= 0) & (G["angle"] < g["n_angles"]))
+    assert np.array_equal(G["support"], np.nonzero(ph.mu.reshape(-1) > 0)[0])
+    n_sup = len(G["support"])
+    assert G["image"].shape == (n_sup,) and G["sens"].shape == (ns, n_sup)
+    assert np.all(G["image"] >= 0) and np.all(np.isfinite(G["loglik"]))

@@ -351,6 +351,49 @@ def test_wait_timeout_reports_etimeout_and_context_survives():
     assert oracle.rel_l2(out["f"], f_ref) <= 1e-4
 
 
+def test_persistent_pass_barrier_timeout_and_variants_agree():
+    """The persistent cooperative form (every sub-iteration in one launch,
+    bounded grid barriers): a one-cycle wait budget makes lmosem_iterate
+    return LMOSEM_ETIMEOUT and the context stays usable; with the default
+    budget its images match those of the register pass (other reduction
+    order, 1e-5) and of the FP64 oracle (1e-4), and two runs are bitwise
+    equal."""
+    import torch
+
+    import paper_2002_12471_gb300.lmosem as L
+    ph, g, J, ns, ni = S.workload("dat32")
+    ev = S.simulate_events(ph, g, 4000, seed=13)
+    dev = torch.device("cuda:0")
+    a, u, e = (torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev))
+    images = {}
+    for variant in (4, 1):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, pass_variant=variant)
+        try:
+            L.lmosem_sensitivity(ctx, ns)
+            L.lmosem_build_model(ctx, a, u, e, ns)
+            f = torch.zeros(L.lmosem_n_support(ctx), dtype=torch.float32, device=dev)
+            if variant == 4:
+                L.lmosem_init_image(ctx, 1.0, f)
+                L.lmosem_set_wait_budget(ctx, 1)
+                with pytest.raises(L.LmosemError) as ei:
+                    L.lmosem_iterate(ctx, 2, 1.0, f)
+                assert ei.value.status == L.ETIMEOUT
+                L.lmosem_set_wait_budget(ctx, 0)
+            runs = []
+            for _ in range(2):
+                L.lmosem_init_image(ctx, 1.0, f)
+                L.lmosem_iterate(ctx, ni, 1.0, f)
+                runs.append(f.cpu().numpy().astype(np.float64))
+            assert np.array_equal(runs[0], runs[1])
+            images[variant] = runs[0]
+        finally:
+            L.lmosem_destroy(ctx)
+    assert oracle.rel_l2(images[4], images[1]) <= 1e-5
+    P = oracle_problem(ph, g)
+    p, s, f_ref, _ = _oracle_recon(P, ev, ns, ni)
+    assert oracle.rel_l2(images[4], f_ref) <= 1e-4
+
+
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 def test_scaled_model_forms(fmt):
     ph, g, J, ns, ni = S.workload("dat32")

@@ -274,6 +274,7 @@ def test_surrogate_model_rows_agree_across_kernels(L, trained):
     for kern in (1, 2):
         ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream(), surrogate_kernel=kern)
         try:
+            L.lmosem_set_surrogate_check(ctx, 0.0)    # measure only: keep the surrogate's rows
             L.lmosem_surrogate_load(ctx, trained["blob"])
             nsup = L.lmosem_n_support(ctx)
             L.lmosem_build_model(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
@@ -301,6 +302,7 @@ def test_surrogate_model_gains_over_no_scatter_compensation(L, trained):
         dev = torch.device("cuda:0")
         ctx = Lm.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream())
         try:
+            Lm.lmosem_set_surrogate_check(ctx, 0.0)   # measure only: keep the surrogate's rows
             Lm.lmosem_surrogate_load(ctx, blob)
             nsup = Lm.lmosem_n_support(ctx)
             Lm.lmosem_sensitivity(ctx, ns)
@@ -326,3 +328,82 @@ def test_surrogate_model_gains_over_no_scatter_compensation(L, trained):
         e_none = abs(np.dot(w, img(f_none)) - ref) / ref
         assert e_sur < 0.5 * e_none, (name, e_sur, e_none)
     assert oracle.rel_l2(f_sur, exact["f"]) < 0.5 * oracle.rel_l2(f_none, exact["f"])
+
+
+def _model_rows(L, ctx, n_events, nsup, step=1):
+    import torch
+    dev = torch.device("cuda:0")
+    ids = torch.arange(0, n_events, step, dtype=torch.int64, device=dev)
+    out = torch.zeros((ids.numel(), nsup), dtype=torch.float32, device=dev)
+    L.lmosem_model_rows(ctx, ids, out)
+    return out.cpu().numpy()
+
+
+def test_surrogate_check_measures_the_row_error(L, trained):
+    """The exact judge of a surrogate build (measure only): its error over
+    512 sampled rows estimates the error of all rows against the exact path
+    sum, and a tolerance below it replaces the model by the exact rows."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, ns = trained["ph"], trained["g"], trained["ns"]
+    ev = S.simulate_events(ph, g, 6000, seed=54)
+    a, u, e = (torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev))
+    rows = {}
+    for name, fmt, tol in (("exact", "fp32", None), ("sur", "surrogate", 0.0), ("fallback", "surrogate", "below")):
+        ctx = _ctx(L, ph, g)
+        try:
+            nsup = L.lmosem_n_support(ctx)
+            L.lmosem_surrogate_load(ctx, trained["blob"])
+            if tol == "below":
+                L.lmosem_set_surrogate_check(ctx, 0.5 * rows["check"][0])
+            elif tol is not None:
+                L.lmosem_set_surrogate_check(ctx, tol)
+            L.lmosem_build_model(ctx, a, u, e, ns, fmt)
+            if fmt == "fp32":
+                with pytest.raises(L.LmosemError) as ei:
+                    L.lmosem_surrogate_check(ctx)
+                assert ei.value.status == L.ESTATE
+            elif tol == 0.0:
+                rows["check"] = L.lmosem_surrogate_check(ctx)
+            else:
+                rows["check_fb"] = L.lmosem_surrogate_check(ctx)
+            rows[name] = _model_rows(L, ctx, len(ev), nsup)
+        finally:
+            L.lmosem_destroy(ctx)
+    err, row_max, exact = rows["check"]
+    full = oracle.rel_l2(rows["sur"].astype(np.float64), rows["exact"].astype(np.float64))
+    assert not exact and err > 0.0 and row_max >= err
+    assert 0.5 * full <= err <= 2.0 * full, (err, full)
+    err_fb, _, exact_fb = rows["check_fb"]
+    assert exact_fb and err_fb == pytest.approx(err, rel=1e-9)
+    assert np.array_equal(rows["fallback"], rows["exact"])
+
+
+def test_untrained_surrogate_falls_back_to_the_exact_model(L):
+    """An untrained network fails the exact check at the default tolerance;
+    the build then holds the exact rows, and the reconstruction matches the
+    FP64 oracle (16 x 16 disk, 2,000 events, 4 subsets x 5 iterations)."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, J, ns, ni = S.workload("tiny16")
+    ev = S.simulate_events(ph, g, J, seed=1)
+    a, u, e = (torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev))
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        L.lmosem_surrogate_load(ctx, torch.from_numpy(L.surrogate_init(seed=4)).to(dev))
+        L.lmosem_sensitivity(ctx, ns)
+        L.lmosem_build_model(ctx, a, u, e, ns, "surrogate")
+        err, row_max, exact = L.lmosem_surrogate_check(ctx)
+        f = torch.zeros(nsup, dtype=torch.float32, device=dev)
+        L.lmosem_init_image(ctx, 1.0, f)
+        L.lmosem_iterate(ctx, ni, 1.0, f)
+        f_gpu = f.cpu().numpy().astype(np.float64)
+    finally:
+        L.lmosem_destroy(ctx)
+    assert exact and err > 1e-2
+    P = oracle_problem(ph, g)
+    p = P.model(ev.angle, ev.u_mm, ev.e_kev)
+    s = P.sensitivity(ns)
+    f_ref, _ = oracle.osem(p, ev.angle, s, ni, oracle.initial_image(J, s.sum(0)))
+    assert oracle.rel_l2(f_gpu, f_ref) <= 1e-4
