@@ -63,9 +63,15 @@ WORKLOADS = {
                  "binned into the detector's 64 position bins and 2 ([100, 143, 175] keV) or 3 "
                  "([100, 120, 143, 175] keV) energy bins, reconstructed from the bin-integrated model with "
                  "count-weighted EM, against list mode; 8 subsets x 10 iterations; ROI-mean NRMSE"),
+    "ex2_peak": ("throughput of the exponential unit (ex2.approx.ftz.f32), the bound of the path sum: every SM "
+                 "runs 4 CTAs x 512 threads of 8 independent chains (one ex2 and one FP32 add per step)"),
     "mlp_infer": ("scatter-surrogate inference alone: MLP 6 -> 4 x 256 -> 1, BF16 operands, FP32 accumulation, "
                   "2,000,000 rows of standard-normal inputs (He-initialised weights; the kernel's work does not "
                   "depend on their values), one lmosem_surrogate_infer call per step"),
+    "mlp_train": ("scatter-surrogate training alone: MLP 6 -> 4 x 256 -> 1, BF16 products on the tcgen05 "
+                  "tensor cores with FP32 accumulation, Adam on FP32 parameters; minibatches of 8,192 rows "
+                  "drawn from 4,000,000 standard-normal samples; one step = one Adam step (the whole "
+                  "lmosem_surrogate_train call of --steps steps is timed)"),
     "batch64": ("64 independent noise realisations of the 64x64 DaT phantom (120 angles, R = 150 mm), "
                 "event counts Poisson with means uniform in [50k, 400k], 8 subsets x 10 iterations, "
                 "all realisations in one persistent launch, FP32 model"),
@@ -886,6 +892,38 @@ def surrogate_jobs(eval_events):
             + [(SURR_EVAL_SEED, n, SURR_EVAL_SEED * 100 + k) for k, n in enumerate(sizes) if n > 0])
 
 
+def run_ex2_bench(args):
+    """The MUFU ex2 rate that the path sum's ALU roofline divides by, measured
+    by the library (lmosem_measure_ex2_rate) under the clock sampler; also
+    the rate with other launch shapes, to show where it saturates."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    for _ in range(args.warmup):
+        L.lmosem_measure_ex2_rate(None, 4, 512, 1 << 14)
+    clocks = ClockSampler(None)
+    clocks.start()
+    rates = [L.lmosem_measure_ex2_rate(None, 4, 512, 1 << 16) for _ in range(args.steps)]
+    clk = clocks.stop()
+    shapes = {}
+    for cps, nt in ((1, 128), (1, 512), (2, 512), (4, 256), (4, 512), (8, 256)):
+        shapes["%dx%d" % (cps, nt)] = L.lmosem_measure_ex2_rate(None, cps, nt, 1 << 15)
+    mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ_FALLBACK
+    rate = statistics.median(rates)
+    per_clk = lambda r: r / (sms * mhz * 1e6)
+    return {"metric": "ex2.approx.ftz.f32 per second", "value": rate, "unit": "ex2/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "config": {"workload": WORKLOAD_DESC, "sms": sms},
+            "per_clock_per_sm": per_clk(rate), "clock_mhz_used": mhz,
+            "per_clock_per_sm_by_launch_shape": {k: per_clk(v) for k, v in shapes.items()},
+            "clocks": clk}
+
+
 def run_mlp_bench(args):
     """The tcgen05 inference kernel alone (the tensor roofline of form 4):
     each step is one lmosem_surrogate_infer call on `--events` rows (default
@@ -941,6 +979,76 @@ def run_mlp_bench(args):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_kind": pk_kind + " sustained BF16"},
             "clocks": clk, "gpu_launches": launches}
+
+
+# flops of one training step per minibatch row: the forward products
+# (16 -> 256, 3 x 256 -> 256), the input-gradient products of the three hidden
+# layers and the weight-gradient products of all four, 2 flops per
+# multiply-add (the 256 -> 1 output layer is not a tensor-core product)
+MLP_TRAIN_FLOPS_PER_ROW = 2 * (2 * (16 * 256 + 3 * 256 * 256) + 3 * 256 * 256)
+
+
+def run_mlp_train_bench(args):
+    """The surrogate's training loop alone: --steps Adam steps of 8,192 rows
+    in one lmosem_surrogate_train call (its CUDA-graph replay of a captured
+    step), timed with CUDA events; TFLOP/s of the products against the
+    measured sustained BF16 peak."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2002_12471_gb300.lmosem as L
+    from paper_2002_12471_gb300 import synthetic as S
+    n, B = 4_000_000, 8192
+    steps = max(1, args.steps) * 500
+    ph, g, *_ = S.workload("tiny16")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    rng = np.random.default_rng(1)
+    feat = torch.from_numpy(rng.standard_normal((n, 6)).astype(np.float32)).to(dev)
+    targ = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+    try:
+        blob = torch.from_numpy(L.surrogate_init(seed=3)).to(dev)
+        L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=max(1, args.warmup) * 100, batch=B, lr=1e-3, seed=5)
+        blob = torch.from_numpy(L.surrogate_init(seed=3)).to(dev)
+        clocks = ClockSampler(None)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        curve = L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=steps, batch=B, lr=1e-3, seed=5)
+        e1.record(stream)
+        e1.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        launches = L.lmosem_launch_count(ctx)
+    finally:
+        L.lmosem_destroy(ctx)
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    tflops = steps * B * MLP_TRAIN_FLOPS_PER_ROW / (ms * 1e-3) / 1e12
+    return {"metric": "surrogate training steps/s", "value": steps / (ms * 1e-3), "unit": "steps/s", "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+            "data": "synthetic (standard-normal features and targets)",
+            "config": {"workload": WORKLOAD_DESC, "batch": B, "samples": n},
+            "loss_first": float(curve[0]), "loss_last": float(np.mean(curve[-50:])),
+            "roofline": {"bound": "tensor", "kernel": "training step (tcgen05 products, transposes, Adam)",
+                         "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                         "traffic": None, "peak_kind": pk_kind + " sustained BF16"},
+            "clocks": clk, "gpu_launches": launches}
+
+
+def surrogate_baseline(blob, x):
+    """The blob's quadratic baseline c . phi(x) of the log scatter at scaled
+    inputs x (n x 6 torch tensor): phi = (1, x_i, x_i x_k for i <= k)."""
+    import torch
+    nb = 28
+    coef = torch.as_tensor(np.asarray(blob[-2 - nb:-2], dtype=np.float64), device=x.device)
+    cols = [torch.ones_like(x[:, 0])] + [x[:, i] for i in range(6)]
+    cols += [x[:, i] * x[:, k] for i in range(6) for k in range(i, 6)]
+    return torch.stack(cols, 1) @ coef
 
 
 def run_surrogate_bench(args):
@@ -1009,7 +1117,7 @@ def run_surrogate_bench(args):
     try:
         t_train = time.perf_counter()
         curve = L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=train_steps, batch=train_batch,
-                                         lr=1e-3, seed=5, target_floor=train_floor)
+                                         lr=1e-3, seed=5, target_floor=train_floor, residual_fit=True)
         t_train = time.perf_counter() - t_train
         # held out: exact log scatter of 200 events of the evaluation phantom
         nsup = L.lmosem_n_support(ctx)
@@ -1021,7 +1129,7 @@ def run_surrogate_bench(args):
         hy = torch.empty(hold * nsup, dtype=torch.float32, device=dev)
         L.lmosem_surrogate_infer(ctx, blob, hf, hy)
         _, mu_t, sigma_t = L.unpack_surrogate(blob.cpu().numpy())
-        pred = mu_t + sigma_t * hy.double()
+        pred = surrogate_baseline(blob.cpu().numpy(), hf.double()) + mu_t + sigma_t * hy.double()
         err = (pred - ht.double()).cpu().numpy()
         w_ho = ht.double().exp()
         ho_lin = float(torch.linalg.vector_norm(pred.exp() - w_ho) / torch.linalg.vector_norm(w_ho))
@@ -1139,7 +1247,7 @@ def run_surrogate_bench(args):
         "config": {"workload": WORKLOAD_DESC, "events": J, "support_pixels": nsup,
                    "train_pairs": n_train_pairs, "train_phantoms": len(SURR_TRAIN_SEEDS),
                    "train_steps": train_steps, "train_batch": train_batch,
-                   "train_target_floor": train_floor,
+                   "train_target_floor": train_floor, "train_residual_of_quadratic_baseline": True,
                    "l2": "model (%.1f GB) larger than L2; 256 MB flush before every step" % (J * nsup * 4 / 1e9)},
         "model_build_evals_per_s": {"surrogate": pairs / (sur_build_ms * 1e-3),
                                     "exact": pairs / (ex_build_ms * 1e-3),
@@ -1381,6 +1489,10 @@ def main():
         out = run_surrogate_bench(args)
     elif WORKLOAD == "mlp_infer":
         out = run_mlp_bench(args)
+    elif WORKLOAD == "ex2_peak":
+        out = run_ex2_bench(args)
+    elif WORKLOAD == "mlp_train":
+        out = run_mlp_train_bench(args)
     elif WORKLOAD == "windows64":
         out = run_windows_bench(args)
     elif WORKLOAD == "binned64":

@@ -114,9 +114,10 @@ typedef struct {
     int32_t pass_variant;
     int32_t ring_rows;
     int32_t ring_stages;
-    /* Scatter-surrogate inference: 0 = automatic (2), 1 = BF16 mma.sync
-     * product chain (the training kernels), 2 = fused tcgen05 kernel (one
-     * persistent CTA per SM, activations kept on chip, TMEM accumulators). */
+    /* Scatter-surrogate inference: 0 = automatic (2), 1 = the chain of
+     * separate tcgen05 products that training uses (activations through
+     * HBM), 2 = fused tcgen05 kernel (one persistent CTA per SM, activations
+     * kept on chip, TMEM accumulators). */
     int32_t surrogate_kernel;
 } lmosem_options;
 
@@ -145,15 +146,19 @@ typedef enum {
 
 /* Scatter surrogate parameters: one FP32 blob of LMOSEM_SURROGATE_PARAMS
  * values, in this order: W1 (256 x 6, row-major, out x in), b1 (256), W2, b2,
- * W3, b3 (256 x 256, 256), W4, b4, W5 (1 x 256), b5 (1), mu, sigma.  The
- * network (ReLU after every hidden layer) maps six inputs, each scaled as
- * (v - shift) / scale with shift, scale =
- *   pixel x (0, 100 mm), pixel y (0, 100 mm), detector angle (pi, pi rad),
- *   event position u (0, 100 mm), event energy (137.5, 37.5 keV),
- *   integral of mu(E0) from the pixel centre to the grid edge along the
- *   detector direction (1.5, 1.5),
- * to y with log p^scat_jn = mu + sigma y (natural log). */
-#define LMOSEM_SURROGATE_PARAMS 199427
+ * W3, b3 (256 x 256, 256), W4, b4, W5 (1 x 256), b5 (1), the 28 coefficients
+ * c of a quadratic baseline, mu, sigma.  The network (ReLU after every hidden
+ * layer) maps six inputs x, the event and the pixel in the detector frame of
+ * the event's angle theta (omega = (cos theta, sin theta), t = (-sin theta,
+ * cos theta), p the pixel centre, u_a(p) = p.t):
+ *   (u - u_a(p)) / 50 mm, p.omega / 100 mm, u_a(p) / 100 mm,
+ *   (theta - pi) / pi, (E - 137.5 keV) / 37.5 keV,
+ *   (integral of mu(E0) from the pixel centre to the grid edge along omega - 1.5) / 1.5,
+ * to y with
+ *   log p^scat_jn = c . phi(x) + mu + sigma y   (natural log),
+ * phi(x) = (1, x_1 .. x_6, x_i x_k for i <= k) in that order.  A blob with
+ * zero coefficients is the network alone. */
+#define LMOSEM_SURROGATE_PARAMS 199455
 
 /* Create a context: validate the problem, copy the mu-map and support to the
  * device and build the attenuation tables (integrals of mu along omega_a from
@@ -298,13 +303,18 @@ typedef struct {
     float target_floor; /* > 0: targets below (largest target - target_floor) are
                          * raised to that level, so that the fit is spent on the
                          * entries that carry the model (log units); 0: none      */
+    int32_t residual_fit; /* 1: fit the quadratic baseline to the (floored) targets
+                           * by least squares first and train the network on the
+                           * residual, whose smaller spread shrinks the error of
+                           * the BF16 arithmetic in log units; 0: zero baseline   */
 } lmosem_train_opts;
 
 /* Train the surrogate on n samples (features n x 6, targets n = log scatter)
  * with the library's tensor-core forward and backward kernels and Adam (FP32
  * parameters and moments, BF16 products, FP32 accumulation).  d_weights holds
- * the initial parameters on entry (mu and sigma are recomputed from the
- * (floored) targets) and the trained ones on return.  h_loss_curve (steps doubles, may
+ * the initial parameters on entry (the baseline coefficients are refitted or
+ * zeroed, and mu and sigma recomputed from the (floored) targets minus the
+ * baseline) and the trained ones on return.  h_loss_curve (steps doubles, may
  * be NULL) receives the minibatch loss of every step.  Synchronises. */
 lmosem_status lmosem_surrogate_train(lmosem_ctx* ctx, const float* d_features, const float* d_targets,
                                      int64_t n, const lmosem_train_opts* opts, float* d_weights,

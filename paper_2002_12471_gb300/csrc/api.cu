@@ -766,8 +766,9 @@ lmosem_status lmosem_surrogate_train(lmosem_ctx* c, const float* d_features, con
         !isfinite(opts->target_floor))
         return fail(c, LMOSEM_EINVAL,
                     "steps >= 1, batch a multiple of 64 in [64, 65536], lr > 0, target_floor >= 0");
+    if (opts->residual_fit != 0 && opts->residual_fit != 1) return fail(c, LMOSEM_EINVAL, "residual_fit is 0 or 1");
     return run_surrogate_train(c, d_features, d_targets, n, opts->steps, opts->batch, opts->lr, opts->seed,
-                               opts->target_floor, d_weights, h_loss_curve);
+                               opts->target_floor, opts->residual_fit != 0, d_weights, h_loss_curve);
 }
 
 lmosem_status lmosem_surrogate_grad(lmosem_ctx* c, const float* d_weights, const float* d_features,

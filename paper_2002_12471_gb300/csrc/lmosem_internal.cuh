@@ -113,7 +113,8 @@ struct lmosem_ctx {
     float* d_surrogate = nullptr;             // LMOSEM_SURROGATE_PARAMS FP32 parameters
     bool scatter_only = false;                // model build leaves the primary path out
     bool use_surrogate = false;               // model build takes the scatter part from the MLP
-    int surrogate_kernel = 0;                 // inference: 0 auto (tcgen05), 1 mma.sync, 2 tcgen05
+    int surrogate_kernel = 0;                 // inference: 0 auto (fused tcgen05), 1 product chain, 2 fused
+    bool gemm_attrs = false;                  // shared-memory opt-in of the training products is set
     // exact check of a surrogate build: rows recomputed by the path sum
     double sur_tol = 1e-2;                    // rel-L2 above which the model is rebuilt exactly (0: never)
     int sur_check_rows = 512;                 // sampled rows
@@ -283,8 +284,8 @@ lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int3
 lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* feat, const float* targ,
                                  int64_t n, float* grad_out, double* h_loss);
 lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
-                                  int steps, int B, float lr, uint64_t seed, float floor_below, float* blob,
-                                  double* h_loss_curve);
+                                  int steps, int B, float lr, uint64_t seed, float floor_below, bool residual_fit,
+                                  float* blob, double* h_loss_curve);
 lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float* feat, int64_t n,
                                   float* out);
 lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ);
@@ -296,6 +297,28 @@ lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max);
 // mlp_tc.cu: fused tcgen05 inference of M rows of BF16 inputs (M x 16)
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
                          const unsigned char* w234img, const __nv_bfloat16* X, float* y, int64_t M);
+// mlp_tc.cu: C = A B^T on the tensor cores (tcgen05, BF16 operands with K
+// contiguous, FP32 accumulation); epi 0: FP32 C (split z of K at
+// C + z split_stride), 1: bias + ReLU to BF16, 2: ReLU mask of `mask` to BF16.
+// K a multiple of 16, lda/ldb/ldc multiples of 8 elements.
+struct GemmTcArgs {
+    const __nv_bfloat16* A;
+    int64_t lda;
+    const __nv_bfloat16* B;
+    int64_t ldb;
+    void* C;
+    int64_t ldc;
+    int64_t split_stride;
+    const float* bias;
+    const __nv_bfloat16* mask;
+    int64_t ldm;
+    int64_t M;
+    int N, K, k_per_split;
+    int* status;
+    long long budget;
+};
+lmosem_status gemm_tc(lmosem_ctx* c, int epi, const GemmTcArgs& G, int splits);
+lmosem_status gemm_tc_setup(lmosem_ctx* c);  // once per context, before any stream capture
 // hidden weights to the chunked operand layout of forward_tc (3 x 128 KB)
 lmosem_status weights_img(lmosem_ctx* c, const __nv_bfloat16* w234, unsigned char* img);
 

@@ -11,10 +11,11 @@
 // out) and evaluated inside the model build, where p_jn = primary_jn +
 // exp(mu + sigma y_jn).
 //
-// Matrix products run on the tensor cores in BF16 with FP32 accumulation:
-// C[M x N] = A[M x K] B[N x K]^T with both operands K-contiguous (one kernel;
-// the backward products use explicit transposes), ldmatrix fragments and
-// mma.sync m16n8k16, fused bias / ReLU / ReLU-mask epilogues.  Parameters are
+// Matrix products run on the 5th-generation tensor cores (tcgen05, the
+// kernel in mlp_tc.cu) in BF16 with FP32 accumulation in TMEM:
+// C[M x N] = A[M x K] B[N x K]^T with both operands K-contiguous (the
+// backward products use explicit transposes; the weight gradients split K
+// over the SMs), fused bias / ReLU / ReLU-mask epilogues.  Parameters are
 // kept in FP32 (Adam state too) with BF16 copies for the products.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -39,127 +40,40 @@ constexpr int64_t kOffW4 = kOffB3 + kH;
 constexpr int64_t kOffB4 = kOffW4 + kH * kH;
 constexpr int64_t kOffW5 = kOffB4 + kH;
 constexpr int64_t kOffB5 = kOffW5 + kH;
-constexpr int64_t kOffMu = kOffB5 + 1;
+// coefficients of the quadratic baseline of the log target in the six scaled
+// inputs (1, x_i, x_i x_j for i <= j): 28 values, fitted by least squares, or
+// zero; the network learns the standardised residual
+constexpr int kBasis = 28;
+constexpr int64_t kOffBase = kOffB5 + 1;
+constexpr int64_t kOffMu = kOffBase + kBasis;
 constexpr int64_t kOffSigma = kOffMu + 1;
 constexpr int64_t kParams = kOffSigma + 1;
 static_assert(kParams == LMOSEM_SURROGATE_PARAMS, "parameter blob layout");
 
-// input scaling: (raw - shift) / scale for x, y, theta, u, E, attenuation
+__device__ __forceinline__ void basis(const float* x, float* phi) {
+    phi[0] = 1.0f;
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) phi[1 + i] = x[i];
+    int k = 1 + kIn;
+#pragma unroll
+    for (int i = 0; i < kIn; ++i)
+#pragma unroll
+        for (int j = i; j < kIn; ++j) phi[k++] = x[i] * x[j];
+}
 
-// ---------------------------------------------------------------- GEMM
+// the baseline of the log scatter at scaled inputs x (FP32)
+__device__ __forceinline__ float baseline(const float* __restrict__ blob, const float* x) {
+    float phi[kBasis];
+    basis(x, phi);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kBasis; ++k) s = fmaf(blob[kOffBase + k], phi[k], s);
+    return s;
+}
 
-constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;
+// ---------------------------------------------------------------- products
 
 enum Epi { EPI_F32 = 0, EPI_RELU_BF16 = 1, EPI_MASK_BF16 = 2 };
-
-__device__ __forceinline__ void cp16_zfill(void* dst, const void* src, bool ok) {
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    int n = ok ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n));
-}
-__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
-                                        const void* p) {
-    unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// C = A B^T (+ epilogue); K a multiple of 8; M, N arbitrary
-template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict__ A, int64_t lda,
-                                                 const __nv_bfloat16* __restrict__ B, int64_t ldb,
-                                                 void* __restrict__ C, int64_t ldc,
-                                                 const float* __restrict__ bias,
-                                                 const __nv_bfloat16* __restrict__ mask, int64_t ldm,
-                                                 int64_t M, int N, int K) {
-    __shared__ __align__(16) __nv_bfloat16 As[2][kBM][kLds];
-    __shared__ __align__(16) __nv_bfloat16 Bs[2][kBN][kLds];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int64_t m0 = (int64_t)blockIdx.x * kBM;
-    const int n0 = blockIdx.y * kBN;
-
-    auto load = [&](int kt, int buf) {
-        const int k0 = kt * kBK;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int c = tid + q * 128;       // 256 chunks of 8 elements per operand
-            const int row = c >> 2, kc = (c & 3) * 8;
-            const bool ka = k0 + kc < K;
-            const int64_t ar = m0 + row;
-            cp16_zfill(&As[buf][row][kc], A + (ar < M && ka ? ar * lda + k0 + kc : 0), ar < M && ka);
-            const int br = n0 + row;
-            cp16_zfill(&Bs[buf][row][kc], B + (br < N && ka ? (int64_t)br * ldb + k0 + kc : 0), br < N && ka);
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-    };
-
-    float acc[2][4][4] = {};
-    const int nk = (K + kBK - 1) / kBK;
-    load(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < nk) {
-            load(kt + 1, buf ^ 1);
-            asm volatile("cp.async.wait_group 1;\n" ::);
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kBK; kk += 16) {
-            unsigned af[2][4], bf[2][4];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-                ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3],
-                        &As[buf][wm * 32 + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-                ldsm_x4(bf[j][0], bf[j][1], bf[j][2], bf[j][3],
-                        &Bs[buf][wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16(acc[i][j], af[i], bf[j >> 1][(j & 1) * 2], bf[j >> 1][(j & 1) * 2 + 1]);
-        }
-        __syncthreads();
-    }
-    // epilogue: thread holds rows g, g+8 and columns 2t, 2t+1 of every m16n8 tile
-    const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t row = m0 + wm * 32 + i * 16 + g + h * 8;
-                const int col = n0 + wn * 32 + j * 8 + 2 * t4;
-                if (row >= M) continue;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    if (col + e >= N) continue;
-                    float v = acc[i][j][2 * h + e];
-                    if constexpr (EPI == EPI_F32) {
-                        reinterpret_cast<float*>(C)[row * ldc + col + e] = v;
-                    } else if constexpr (EPI == EPI_RELU_BF16) {
-                        v += bias[col + e];
-                        reinterpret_cast<__nv_bfloat16*>(C)[row * ldc + col + e] = __float2bfloat16_rn(fmaxf(v, 0.0f));
-                    } else {
-                        const bool on = __bfloat162float(mask[row * ldm + col + e]) > 0.0f;
-                        reinterpret_cast<__nv_bfloat16*>(C)[row * ldc + col + e] = __float2bfloat16_rn(on ? v : 0.0f);
-                    }
-                }
-            }
-}
 
 // out[c][r] = in[r][c] (BF16), 32 x 32 tiles
 __global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int64_t rows, int cols, int64_t ldi,
@@ -192,7 +106,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // minibatch rows (seeded, with replacement): scaled features as BF16 (padded
 // to 16 columns) and standardised targets
 // element index of input (row i, column k) in the row-major M x 16 layout of
-// the mma.sync chain or, for the tcgen05 kernel, the tile-major layout:
+// the chain of separate products or, for the fused tcgen05 kernel, the tile-major layout:
 // 128-row tiles of 2048 elements, each the K = 16 operand layout (row group g
 // of 8 rows at 128 elements, its two 8-column groups 64 elements apart)
 __device__ __forceinline__ int64_t x_index(int64_t i, int k, bool tiled) {
@@ -201,19 +115,23 @@ __device__ __forceinline__ int64_t x_index(int64_t i, int k, bool tiled) {
     return (i >> 7) * (128 * kInPad) + (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
 }
 
+// (step_ptr: the step index lives on the device, for a captured training step)
 __global__ void k_gather(const float* __restrict__ feat, const float* __restrict__ targ, int64_t n,
-                         int B, uint64_t seed, int step, const float* __restrict__ blob,
-                         const float* __restrict__ floor, __nv_bfloat16* __restrict__ X,
-                         float* __restrict__ t, bool tiled) {
+                         int B, uint64_t seed, int step, const int* __restrict__ step_ptr,
+                         const float* __restrict__ blob, const float* __restrict__ floor,
+                         __nv_bfloat16* __restrict__ X, float* __restrict__ t, bool tiled) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    if (step_ptr) step = *step_ptr;
     const int64_t i = seed == 0 ? (int64_t)b % n
                                 : (int64_t)(splitmix64(seed ^ ((uint64_t)step * 0x100000001B3ull + b)) % (uint64_t)n);
+    float x[kIn];
 #pragma unroll
-    for (int k = 0; k < kInPad; ++k)
-        X[x_index(b, k, tiled)] = __float2bfloat16_rn(k < kIn ? feat[i * kIn + k] : 0.0f);
+    for (int k = 0; k < kIn; ++k) x[k] = feat[i * kIn + k];
+#pragma unroll
+    for (int k = 0; k < kInPad; ++k) X[x_index(b, k, tiled)] = __float2bfloat16_rn(k < kIn ? x[k] : 0.0f);
     const float ti = floor ? fmaxf(targ[i], *floor) : targ[i];
-    t[b] = (ti - blob[kOffMu]) / blob[kOffSigma];
+    t[b] = (ti - baseline(blob, x) - blob[kOffMu]) / blob[kOffSigma];
 }
 
 // y = H4 w5 + b5 (one warp per row)
@@ -228,11 +146,14 @@ __global__ void k_out_fwd(const __nv_bfloat16* __restrict__ H, int64_t M, const 
     if (lane == 0) y[row] = s + blob[kOffB5];
 }
 
-// dy = 2 (y - t) / B; dz4 = dy w5 where H4 > 0; loss sum into *loss (FP64)
+// dy = 2 (y - t) / B; dz4 = dy w5 where H4 > 0; loss sum into loss[step]
+// (FP64; step = *step_ptr, or 0)
 __global__ void k_out_bwd(const float* __restrict__ y, const float* __restrict__ t,
                           const __nv_bfloat16* __restrict__ H4, int B, const float* __restrict__ blob,
-                          float* __restrict__ dy, __nv_bfloat16* __restrict__ dz4, double* __restrict__ loss) {
+                          float* __restrict__ dy, __nv_bfloat16* __restrict__ dz4, double* __restrict__ loss,
+                          const int* __restrict__ step_ptr) {
     const int b = blockIdx.x;
+    if (step_ptr) loss += *step_ptr;
     const float r = y[b] - t[b];
     const float d = 2.0f * r / (float)B;
     if (threadIdx.x == 0) {
@@ -245,13 +166,27 @@ __global__ void k_out_bwd(const float* __restrict__ y, const float* __restrict__
     }
 }
 
-// dW5[k] = sum_b dy_b H4[b][k], db5 = sum_b dy_b (fixed order per column)
-__global__ void k_out_wgrad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, int B,
-                            float* __restrict__ grad) {
+// dW5[k] = sum_b dy_b H4[b][k], db5 = sum_b dy_b: block z sums its share of
+// the rows (thread k = column k, coalesced across the block; thread kH the
+// bias) into part[z][k]; k_out_wgrad_sum adds the shares in order
+constexpr int kOutSplits = 32;
+__global__ void __launch_bounds__(kH + 32) k_out_wgrad(const float* __restrict__ dy,
+                                                       const __nv_bfloat16* __restrict__ H4, int B,
+                                                       float* __restrict__ part) {
+    const int k = threadIdx.x;
+    if (k > kH) return;
+    const int per = (B + kOutSplits - 1) / kOutSplits;
+    const int b0 = blockIdx.x * per, b1 = min(B, b0 + per);
+    float s = 0.0f;
+    for (int b = b0; b < b1; ++b) s += dy[b] * (k < kH ? __bfloat162float(H4[(int64_t)b * kH + k]) : 1.0f);
+    part[blockIdx.x * (kH + 1) + k] = s;
+}
+
+__global__ void k_out_wgrad_sum(const float* __restrict__ part, float* __restrict__ grad) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k > kH) return;
     float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += dy[b] * (k < kH ? __bfloat162float(H4[(int64_t)b * kH + k]) : 1.0f);
+    for (int z = 0; z < kOutSplits; ++z) s += part[z * (kH + 1) + k];
     grad[k < kH ? kOffW5 + k : kOffB5] = s;
 }
 
@@ -267,20 +202,37 @@ __global__ void k_rowsum(const __nv_bfloat16* __restrict__ ZT, int rows, int B, 
     if (lane == 0) out[r] = s;
 }
 
-// copy a gradient block [rows x cols] from a GEMM result with ld into the blob
-__global__ void k_copy_grad(const float* __restrict__ src, int rows, int cols, int64_t lds,
-                            float* __restrict__ dst) {
+// a gradient block [rows x cols] into the blob: the sum, in split order, of
+// the K splits of a GEMM result with ld (split_stride elements apart)
+__global__ void k_copy_grad(const float* __restrict__ src, int rows, int cols, int64_t lds, int splits,
+                            int64_t split_stride, float* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows * cols) return;
-    dst[i] = src[(int64_t)(i / cols) * lds + (i % cols)];
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += src[z * split_stride + (int64_t)(i / cols) * lds + (i % cols)];
+    dst[i] = s;
 }
 
-// Adam (bias-corrected moments) over the whole blob except (mu, sigma)
+// learning rate and Adam bias corrections of the step *step_ptr (the last
+// 20% of the steps at lr / 10): sc = (lr_s, 1 - b1^(s+1), 1 - b2^(s+1))
+__global__ void k_step_scalars(const int* __restrict__ step_ptr, int steps, float lr, float b1, float b2,
+                               float* __restrict__ sc) {
+    const int s = *step_ptr;
+    sc[0] = s < steps * 0.8 ? lr : lr * 0.1f;
+    sc[1] = (float)(1.0 - pow((double)b1, (double)(s + 1)));
+    sc[2] = (float)(1.0 - pow((double)b2, (double)(s + 1)));
+}
+
+// Adam (bias-corrected moments) over the whole blob except (mu, sigma); the
+// step's scalars from sc; thread 0 then advances the device step counter (no
+// later kernel of the step reads it)
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       float* __restrict__ v, int64_t n, const float* __restrict__ sc, float b1, float b2,
+                       float eps, int* __restrict__ step_ptr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *step_ptr += 1;
     if (i >= n) return;
+    const float lr = sc[0], c1 = sc[1], c2 = sc[2];
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -307,12 +259,9 @@ __global__ void k_weights_bf16(const float* __restrict__ blob, __nv_bfloat16* __
     }
 }
 
-// mean and standard deviation of the targets (FP64, one block, fixed order)
-// with floor_below > 0 the targets are first raised to (largest - floor_below),
-// that level written to *floor (else -FLT_MAX)
-__global__ void k_target_stats(const float* __restrict__ t, int64_t n, float floor_below,
-                               float* __restrict__ floor, float* __restrict__ blob) {
-    __shared__ double s1[256], s2[256];
+// with floor_below > 0 the targets are raised to (largest - floor_below):
+// that level into *floor (else -FLT_MAX); one block
+__global__ void k_target_floor(const float* __restrict__ t, int64_t n, float floor_below, float* __restrict__ floor) {
     __shared__ float smax[256];
     float fl = -FLT_MAX;
     if (floor_below > 0.0f) {
@@ -324,9 +273,17 @@ __global__ void k_target_stats(const float* __restrict__ t, int64_t n, float flo
         fl -= floor_below;
     }
     if (threadIdx.x == 0) *floor = fl;
+}
+
+// mean and standard deviation of the (floored) targets minus the baseline
+// (FP64, one block, fixed order) into the blob's mu and sigma
+__global__ void k_target_stats(const float* __restrict__ t, const float* __restrict__ feat, int64_t n,
+                               const float* __restrict__ floor, float* __restrict__ blob) {
+    __shared__ double s1[256], s2[256];
+    const float fl = *floor;
     double a = 0.0, b = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const double ti = fmaxf(t[i], fl);
+        const double ti = fmaxf(t[i], fl) - baseline(blob, feat + i * kIn);
         a += ti;
         b += ti * ti;
     }
@@ -343,6 +300,32 @@ __global__ void k_target_stats(const float* __restrict__ t, int64_t n, float flo
         const double var = fmax(Bq / n - mu * mu, 1e-12);
         blob[kOffMu] = (float)mu;
         blob[kOffSigma] = (float)sqrt(var);
+    }
+}
+
+// least squares of the baseline: for m rows evenly spaced over the samples,
+// block (i, j) (j <= i) sums phi_i phi_j and block (i, kBasis) sums phi_i t
+// (floored), FP64 in a fixed order
+__global__ void k_basis_normal(const float* __restrict__ feat, const float* __restrict__ t, int64_t n, int64_t m,
+                               const float* __restrict__ floor, double* __restrict__ out /* kBasis x (kBasis+1) */) {
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (bj < kBasis && bj > bi) return;
+    __shared__ double sh[256];
+    const float fl = *floor;
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+        const int64_t i = (int64_t)((double)r * (double)n / (double)m);
+        float phi[kBasis];
+        basis(feat + i * kIn, phi);
+        const double pj = bj < kBasis ? (double)phi[bj] : (double)fmaxf(t[i], fl);
+        acc += (double)phi[bi] * pj;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) s += sh[k];
+        out[bi * (kBasis + 1) + bj] = s;
     }
 }
 
@@ -409,7 +392,7 @@ __global__ void k_surr_inputs(FeatArgs F, int64_t r0, int64_t nrows, __nv_bfloat
 }
 
 // p_jn = primary_jn + exp(mu + sigma y_jn) into the FP32 model rows
-__global__ void k_surr_combine(const float* __restrict__ y, int64_t r0, int64_t nrows, int n_sup,
+__global__ void k_surr_combine(FeatArgs F, const float* __restrict__ y, int64_t r0, int64_t nrows, int n_sup,
                                int64_t ld, const int32_t* __restrict__ a_s, const float* __restrict__ u_s,
                                const float* __restrict__ e_s, const float4* __restrict__ ppar, int ld_w,
                                float e0, float sE0, float lE0, const float* __restrict__ blob,
@@ -425,7 +408,9 @@ __global__ void k_surr_combine(const float* __restrict__ y, int64_t r0, int64_t 
         const float te = (e_s[row] - e0) * sE0;
         const float t = (u_s[row] - pp.x) * pp.y;
         const float prim = ex2_approx(fmaf(-t, t, pp.z + fmaf(-te, te, lE0)));
-        const float ls = blob[kOffMu] + blob[kOffSigma] * y[(i / ld) * n_sup + q];
+        float x[kIn];
+        features(F, row, q, x);
+        const float ls = baseline(blob, x) + blob[kOffMu] + blob[kOffSigma] * y[(i / ld) * n_sup + q];
         v = prim + expf(ls);
     }
     model[row * ld + q] = v;
@@ -439,19 +424,29 @@ struct MlpBufs {
 };
 
 
+// the products run on the tcgen05 kernel (mlp_tc.cu); splits > 1 splits K,
+// each split writing its own FP32 slice of C (M ldc elements apart)
 lmosem_status gemm(lmosem_ctx* c, int epi, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B,
                    int64_t ldb, void* C, int64_t ldc, const float* bias, const __nv_bfloat16* mask,
-                   int64_t ldm, int64_t M, int N, int K) {
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + kBN - 1) / kBN));
-    LMOSEM_PROF_BEGIN(c);
-    if (epi == EPI_F32)
-        k_gemm_tn<EPI_F32><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
-    else if (epi == EPI_RELU_BF16)
-        k_gemm_tn<EPI_RELU_BF16><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
-    else
-        k_gemm_tn<EPI_MASK_BF16><<<grid, 128, 0, c->stream>>>(A, lda, B, ldb, C, ldc, bias, mask, ldm, M, N, K);
-    LMOSEM_LAUNCHED(c, LMOSEM_K_MLP);
-    return LMOSEM_OK;
+                   int64_t ldm, int64_t M, int N, int K, int splits = 1) {
+    GemmTcArgs G;
+    G.A = A;
+    G.lda = lda;
+    G.B = B;
+    G.ldb = ldb;
+    G.C = C;
+    G.ldc = ldc;
+    G.split_stride = M * ldc;
+    G.bias = bias;
+    G.mask = mask;
+    G.ldm = ldm;
+    G.M = M;
+    G.N = N;
+    G.K = K;
+    G.k_per_split = K;
+    G.status = nullptr;
+    G.budget = 0;
+    return gemm_tc(c, epi, G, splits);
 }
 
 lmosem_status transpose(lmosem_ctx* c, const __nv_bfloat16* in, int64_t rows, int cols, int64_t ldi,
@@ -497,17 +492,24 @@ lmosem_status forward(lmosem_ctx* c, const float* blob, const MlpBufs& w, const 
 }
 
 // inference: the tcgen05 kernel (mlp_tc.cu) unless the options select the
-// mma.sync product chain (surrogate_kernel == 1), which the training uses
+// chain of separate tcgen05 products (surrogate_kernel == 1), which the training uses
 lmosem_status forward_infer(lmosem_ctx* c, const float* blob, const MlpBufs& w, const __nv_bfloat16* X,
                             __nv_bfloat16* const H[4], float* y, int64_t M) {
     if (c->surrogate_kernel != 1) return forward_tc(c, blob, w.w1, w.wimg, X, y, M);
     return forward(c, blob, w, X, H, y, M);
 }
 
+// batch rows of the transposed operands (a multiple of the product's K step)
+inline int padded_batch(int B) { return (B + 15) / 16 * 16; }
+// K splits of the weight-gradient products (K = the batch): about 256 rows
+// each, so that the 2 x 2 output tiles of a layer occupy the SMs
+inline int wgrad_splits(int Bp) { return std::max(1, std::min(32, Bp / 256)); }
+
 struct TrainBufs {
     __nv_bfloat16 *X = nullptr, *XT = nullptr, *H = nullptr, *HT = nullptr, *dz = nullptr, *dzT = nullptr;
     float *t = nullptr, *y = nullptr, *dy = nullptr, *gtmp = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     double* loss = nullptr;
+    int* step = nullptr;  // device step counter of a captured training step (nullptr: loss[0])
 };
 
 // loss and gradient of one minibatch into tb.grad (blob layout)
@@ -517,26 +519,35 @@ lmosem_status loss_grad(lmosem_ctx* c, const float* blob, const MlpBufs& w, Trai
     if ((st = forward(c, blob, w, tb.X, H, tb.y, B))) return st;
     __nv_bfloat16* dz = tb.dz;                       // B x 256, current layer
     LMOSEM_PROF_BEGIN(c);
-    k_out_bwd<<<B, 128, 0, c->stream>>>(tb.y, tb.t, H[3], B, blob, tb.dy, dz, tb.loss);
+    k_out_bwd<<<B, 128, 0, c->stream>>>(tb.y, tb.t, H[3], B, blob, tb.dy, dz, tb.loss, tb.step);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     LMOSEM_PROF_BEGIN(c);
-    k_out_wgrad<<<2, 256, 0, c->stream>>>(tb.dy, H[3], B, tb.grad);
+    k_out_wgrad<<<kOutSplits, kH + 32, 0, c->stream>>>(tb.dy, H[3], B, tb.gtmp);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    LMOSEM_PROF_BEGIN(c);
+    k_out_wgrad_sum<<<2, 256, 0, c->stream>>>(tb.gtmp, tb.grad);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     for (int l = 3; l >= 0; --l) {                   // hidden layer l + 1 (0-based l)
         // dW = dz^T h_prev, db = row sums of dz^T
-        if ((st = transpose(c, dz, B, kH, kH, tb.dzT, B))) return st;
+        // (the transposes keep their rows Bp = B rounded up to 16 long; the
+        // tail columns stay zero, so K = Bp adds nothing)
+        const int Bp = padded_batch(B);
+        if ((st = transpose(c, dz, B, kH, kH, tb.dzT, Bp))) return st;
         const int in = l == 0 ? kInPad : kH;
         const __nv_bfloat16* hprev = l == 0 ? tb.X : H[l - 1];
-        if ((st = transpose(c, hprev, B, in, in, tb.HT, B))) return st;
-        if ((st = gemm(c, EPI_F32, tb.dzT, B, tb.HT, B, tb.gtmp, in, nullptr, nullptr, 0, kH, in, B))) return st;
+        if ((st = transpose(c, hprev, B, in, in, tb.HT, Bp))) return st;
+        const int splits = wgrad_splits(Bp);
+        if ((st = gemm(c, EPI_F32, tb.dzT, Bp, tb.HT, Bp, tb.gtmp, in, nullptr, nullptr, 0, kH, in, Bp, splits)))
+            return st;
         const int64_t offW = l == 0 ? kOffW1 : kOffW2 + (int64_t)(l - 1) * (kH * kH + kH);
         const int64_t offB = l == 0 ? kOffB1 : offW + kH * kH;
         const int cols = l == 0 ? kIn : kH;
         LMOSEM_PROF_BEGIN(c);
-        k_copy_grad<<<(kH * cols + 255) / 256, 256, 0, c->stream>>>(tb.gtmp, kH, cols, in, tb.grad + offW);
+        k_copy_grad<<<(kH * cols + 255) / 256, 256, 0, c->stream>>>(tb.gtmp, kH, cols, in, splits,
+                                                                     (int64_t)kH * in, tb.grad + offW);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         LMOSEM_PROF_BEGIN(c);
-        k_rowsum<<<kH / 8, 256, 0, c->stream>>>(tb.dzT, kH, B, B, tb.grad + offB);
+        k_rowsum<<<kH / 8, 256, 0, c->stream>>>(tb.dzT, kH, B, Bp, tb.grad + offB);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         if (l > 0) {
             // dz_prev = (dz W_l) where h_prev > 0
@@ -557,6 +568,7 @@ lmosem_status loss_grad(lmosem_ctx* c, const float* blob, const MlpBufs& w, Trai
 lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* feat, const float* targ,
                                  int64_t n, float* grad_out, double* h_loss) {
     lmosem_status st;
+    if ((st = gemm_tc_setup(c))) return st;
     const int B = (int)n;
     MlpBufs w;
     TrainBufs tb;
@@ -564,16 +576,19 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
         (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&tb.X, (size_t)B * kInPad)) ||
         (st = tmp.alloc(&tb.XT, (size_t)B * kInPad)) || (st = tmp.alloc(&tb.H, (size_t)4 * B * kH)) ||
-        (st = tmp.alloc(&tb.HT, (size_t)B * kH)) || (st = tmp.alloc(&tb.dz, (size_t)2 * B * kH)) ||
-        (st = tmp.alloc(&tb.dzT, (size_t)B * kH)) || (st = tmp.alloc(&tb.t, B)) ||
+        (st = tmp.alloc(&tb.HT, (size_t)padded_batch(B) * kH)) || (st = tmp.alloc(&tb.dz, (size_t)2 * B * kH)) ||
+        (st = tmp.alloc(&tb.dzT, (size_t)padded_batch(B) * kH)) || (st = tmp.alloc(&tb.t, B)) ||
         (st = tmp.alloc(&tb.y, B)) || (st = tmp.alloc(&tb.dy, B)) ||
-        (st = tmp.alloc(&tb.gtmp, (size_t)kH * kH)) || (st = tmp.alloc(&tb.loss, 1)))
+        (st = tmp.alloc(&tb.gtmp, (size_t)wgrad_splits(padded_batch(B)) * kH * kH)) || (st = tmp.alloc(&tb.loss, 1)))
         return st;
+    LMOSEM_CK(c, cudaMemsetAsync(tb.HT, 0, sizeof(__nv_bfloat16) * padded_batch(B) * kH, c->stream));
+    LMOSEM_CK(c, cudaMemsetAsync(tb.dzT, 0, sizeof(__nv_bfloat16) * padded_batch(B) * kH, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(grad_out, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(tb.loss, 0, sizeof(double), c->stream));
     if ((st = weights_bf16(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, blob, nullptr, tb.X, tb.t, false);
+    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, nullptr, blob, nullptr, tb.X, tb.t,
+                                                     false);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     tb.grad = grad_out;
     if ((st = loss_grad(c, blob, w, tb, B))) return st;
@@ -584,49 +599,154 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     return LMOSEM_OK;
 }
 
+// The quadratic baseline's coefficients into the blob: a least-squares fit
+// to the floored targets of up to 2^20 evenly spaced samples (FP64 normal
+// equations, Cholesky with a relative ridge of 1e-10), or zeros.
+lmosem_status fit_baseline(lmosem_ctx* c, const float* feat, const float* targ, int64_t n, const float* d_floor,
+                           bool fit, float* blob) {
+    float coef[kBasis] = {};
+    if (fit) {
+        const int64_t m = std::min<int64_t>(n, int64_t(1) << 20);
+        double* d_ne = nullptr;
+        Scratch tmp(c);
+        lmosem_status st;
+        if ((st = tmp.alloc(&d_ne, (size_t)kBasis * (kBasis + 1)))) return st;
+        LMOSEM_CK(c, cudaMemsetAsync(d_ne, 0, sizeof(double) * kBasis * (kBasis + 1), c->stream));
+        LMOSEM_PROF_BEGIN(c);
+        k_basis_normal<<<dim3(kBasis, kBasis + 1), 256, 0, c->stream>>>(feat, targ, n, m, d_floor, d_ne);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        double ne[kBasis * (kBasis + 1)];
+        LMOSEM_CK(c, cudaMemcpyAsync(ne, d_ne, sizeof(ne), cudaMemcpyDeviceToHost, c->stream));
+        LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+        // A = sum phi phi^T (lower triangle), r = sum phi t; A x = r by Cholesky
+        double A[kBasis][kBasis], L[kBasis][kBasis] = {}, r[kBasis], x[kBasis];
+        double tr = 0.0;
+        for (int i = 0; i < kBasis; ++i) {
+            for (int j = 0; j <= i; ++j) A[i][j] = A[j][i] = ne[i * (kBasis + 1) + j];
+            r[i] = ne[i * (kBasis + 1) + kBasis];
+            tr += A[i][i];
+        }
+        for (int i = 0; i < kBasis; ++i) A[i][i] += 1e-10 * tr / kBasis;
+        for (int i = 0; i < kBasis; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double sum = A[i][j];
+                for (int k = 0; k < j; ++k) sum -= L[i][k] * L[j][k];
+                if (i == j) {
+                    if (!(sum > 0.0)) return fail(c, LMOSEM_ENUMERIC, "baseline fit: singular normal equations");
+                    L[i][i] = sqrt(sum);
+                } else {
+                    L[i][j] = sum / L[j][j];
+                }
+            }
+        }
+        for (int i = 0; i < kBasis; ++i) {  // L z = r, then L^T x = z
+            double sum = r[i];
+            for (int k = 0; k < i; ++k) sum -= L[i][k] * x[k];
+            x[i] = sum / L[i][i];
+        }
+        for (int i = kBasis - 1; i >= 0; --i) {
+            double sum = x[i];
+            for (int k = i + 1; k < kBasis; ++k) sum -= L[k][i] * x[k];
+            x[i] = sum / L[i][i];
+        }
+        for (int i = 0; i < kBasis; ++i) coef[i] = (float)x[i];
+    }
+    LMOSEM_CK(c, cudaMemcpyAsync(blob + kOffBase, coef, sizeof(coef), cudaMemcpyHostToDevice, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));  // coef is on this stack frame
+    return LMOSEM_OK;
+}
+
 lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
-                                  int steps, int B, float lr, uint64_t seed, float floor_below, float* blob,
-                                  double* h_loss_curve) {
+                                  int steps, int B, float lr, uint64_t seed, float floor_below, bool residual_fit,
+                                  float* blob, double* h_loss_curve) {
     lmosem_status st;
+    if ((st = gemm_tc_setup(c))) return st;
     MlpBufs w;
     TrainBufs tb;
     double* d_curve = nullptr;
     float* d_floor = nullptr;
+    int* d_step = nullptr;
+    float* d_sc = nullptr;
     Scratch tmp(c);
     if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
         (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&tb.X, (size_t)B * kInPad)) ||
-        (st = tmp.alloc(&tb.H, (size_t)4 * B * kH)) || (st = tmp.alloc(&tb.HT, (size_t)B * kH)) ||
-        (st = tmp.alloc(&tb.dz, (size_t)2 * B * kH)) || (st = tmp.alloc(&tb.dzT, (size_t)B * kH)) ||
+        (st = tmp.alloc(&tb.H, (size_t)4 * B * kH)) || (st = tmp.alloc(&tb.HT, (size_t)padded_batch(B) * kH)) ||
+        (st = tmp.alloc(&tb.dz, (size_t)2 * B * kH)) || (st = tmp.alloc(&tb.dzT, (size_t)padded_batch(B) * kH)) ||
         (st = tmp.alloc(&tb.t, B)) || (st = tmp.alloc(&tb.y, B)) || (st = tmp.alloc(&tb.dy, B)) ||
-        (st = tmp.alloc(&tb.gtmp, (size_t)kH * kH)) || (st = tmp.alloc(&tb.grad, kParams)) ||
+        (st = tmp.alloc(&tb.gtmp, (size_t)wgrad_splits(padded_batch(B)) * kH * kH)) ||
+        (st = tmp.alloc(&tb.grad, kParams)) ||
         (st = tmp.alloc(&tb.m, kParams)) || (st = tmp.alloc(&tb.v, kParams)) ||
-        (st = tmp.alloc(&d_curve, std::max(1, steps))) || (st = tmp.alloc(&d_floor, 1)))
+        (st = tmp.alloc(&d_curve, std::max(1, steps))) || (st = tmp.alloc(&d_floor, 1)) ||
+        (st = tmp.alloc(&d_step, 1)) || (st = tmp.alloc(&d_sc, 3)))
         return st;
     LMOSEM_CK(c, cudaMemsetAsync(tb.m, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(tb.v, 0, sizeof(float) * kParams, c->stream));
     LMOSEM_CK(c, cudaMemsetAsync(d_curve, 0, sizeof(double) * std::max(1, steps), c->stream));
     LMOSEM_PROF_BEGIN(c);
-    k_target_stats<<<1, 256, 0, c->stream>>>(targ, n, floor_below, d_floor, blob);
+    k_target_floor<<<1, 256, 0, c->stream>>>(targ, n, floor_below, d_floor);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    if ((st = fit_baseline(c, feat, targ, n, d_floor, residual_fit, blob))) return st;
+    LMOSEM_PROF_BEGIN(c);
+    k_target_stats<<<1, 256, 0, c->stream>>>(targ, feat, n, d_floor, blob);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     const float b1 = 0.9f, b2 = 0.999f;
-    double p1 = 1.0, p2 = 1.0;
-    for (int s = 0; s < steps; ++s) {
-        if ((st = weights_bf16(c, blob, w))) return st;
+    // one training step: its scalars (minibatch index, loss slot, learning
+    // rate, bias corrections) come from the device step counter, so the step
+    // is captured once as a CUDA graph and replayed (direct launches on a
+    // stream that cannot be captured)
+    LMOSEM_CK(c, cudaMemsetAsync(d_step, 0, sizeof(int), c->stream));
+    if ((st = ensure_status(c))) return st;  // before any capture: the products report to it
+    tb.loss = d_curve;
+    tb.step = d_step;
+    auto enqueue_step = [&]() -> lmosem_status {
+        lmosem_status s2;
+        if ((s2 = weights_bf16(c, blob, w))) return s2;
         LMOSEM_PROF_BEGIN(c);
-        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, s, blob, d_floor, tb.X,
-                                                         tb.t, false);
+        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, 0, d_step, blob, d_floor,
+                                                         tb.X, tb.t, false);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
-        tb.loss = d_curve + s;
-        if ((st = loss_grad(c, blob, w, tb, B))) return st;
-        p1 *= b1;
-        p2 *= b2;
-        const float lr_s = s < steps * 0.8 ? lr : lr * 0.1f;
+        if ((s2 = loss_grad(c, blob, w, tb, B))) return s2;
         LMOSEM_PROF_BEGIN(c);
-        k_adam<<<(unsigned)((kOffMu + 255) / 256), 256, 0, c->stream>>>(blob, tb.grad, tb.m, tb.v, kOffMu, lr_s,
-                                                                       b1, b2, 1e-8f, (float)(1.0 - p1),
-                                                                       (float)(1.0 - p2));
+        k_step_scalars<<<1, 1, 0, c->stream>>>(d_step, steps, lr, b1, b2, d_sc);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        LMOSEM_PROF_BEGIN(c);
+        k_adam<<<(unsigned)((kOffBase + 255) / 256), 256, 0, c->stream>>>(blob, tb.grad, tb.m, tb.v, kOffBase, d_sc, b1,
+                                                                       b2, 1e-8f, d_step);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        return LMOSEM_OK;
+    };
+    cudaGraphExec_t exec = nullptr;
+    int64_t step_launches = 0;
+    if (steps > 1 && c->stream != nullptr && c->profile != 1 &&
+        cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const int64_t before = c->launches;
+        c->capturing = true;
+        st = enqueue_step();
+        c->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (!st && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st) return st;
+        if (e != cudaSuccess) return cuda_fail(c, e, "training-step graph");
+        step_launches = c->launches - before;
+        c->launches = before;
+    } else {
+        cudaGetLastError();
     }
+    for (int s = 0; s < steps; ++s) {
+        if (exec) {
+            cudaError_t e = cudaGraphLaunch(exec, c->stream);
+            if (e != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(c, e, "cudaGraphLaunch");
+            }
+            c->launches += step_launches;
+        } else if ((st = enqueue_step())) {
+            return st;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
     if (h_loss_curve && steps > 0)
         LMOSEM_CK(c, cudaMemcpyAsync(h_loss_curve, d_curve, sizeof(double) * steps, cudaMemcpyDeviceToHost,
                                      c->stream));
@@ -637,6 +757,7 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
 lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float* feat, int64_t n,
                                   float* out) {
     lmosem_status st;
+    if ((st = gemm_tc_setup(c))) return st;
     MlpBufs w;
     __nv_bfloat16 *X = nullptr, *H = nullptr;
     Scratch tmp(c);
@@ -646,7 +767,7 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
         return st;
     if ((st = infer_weights(c, blob, w, tmp))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, blob, nullptr, X, out,
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, nullptr, blob, nullptr, X, out,
                                                                  c->surrogate_kernel != 1);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
@@ -687,7 +808,8 @@ lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ) {
 // model rows with the surrogate scatter term, in chunks of whole rows
 lmosem_status build_model_surrogate(lmosem_ctx* c) {
     lmosem_status st;
-    // pairs per chunk: the mma.sync chain keeps two 256-wide BF16 activations
+    if ((st = gemm_tc_setup(c))) return st;
+    // pairs per chunk: the product chain keeps two 256-wide BF16 activations
     // per pair in HBM, the fused tcgen05 kernel none
     const int64_t max_pairs = int64_t(1) << (c->surrogate_kernel == 1 ? 20 : 24);
     const int64_t rows_per = std::max<int64_t>(1, max_pairs / c->n_sup);
@@ -714,7 +836,7 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
         if ((st = forward_infer(c, c->d_surrogate, w, X, Hs, y, m))) return st;
         LMOSEM_PROF_BEGIN(c);
         k_surr_combine<<<(unsigned)((nr * c->ld_model + 255) / 256), 256, 0, c->stream>>>(
-            y, r0, nr, c->n_sup, c->ld_model, c->d_a_s, c->d_u_s, c->d_e_s, c->d_ppar, c->ld_w, (float)c->e0,
+            feat_args(c), y, r0, nr, c->n_sup, c->ld_model, c->d_a_s, c->d_u_s, c->d_e_s, c->d_ppar, c->ld_w, (float)c->e0,
             (float)(0.8493218002880191 / se0), (float)(-log2(se0 * sqrt(2.0 * kPi))), c->d_surrogate,
             reinterpret_cast<float*>(c->d_model));
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);

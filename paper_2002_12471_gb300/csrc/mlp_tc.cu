@@ -440,6 +440,166 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcArgs A) {
     }
 }
 
+
+// ---------------------------------------------------------------- training products
+//
+// C[M x N] = A[M x K] B[N x K]^T on the tensor cores: BF16 operands with K
+// contiguous in global memory, FP32 accumulation in TMEM.  A CTA of four warps
+// computes a 128 x BN tile.  K is staged in chunks of 32 by cp.async into the
+// canonical K-major layout of the inference kernel (row group g at g * 512 B,
+// k group at 128 B), kGemmStages chunk buffers, so copies run three chunks
+// ahead of the tensor core; one thread issues the products (tcgen05.mma
+// kind::f16, M = 128, N = BN, K = 16, two per chunk) and commits each chunk to
+// an mbarrier that frees its buffer.  Epilogue: warp w reads TMEM lanes 32w..
+// (its 32 rows of the tile), 32 columns at a time, and applies bias + ReLU,
+// the ReLU mask of the layer input, or nothing (FP32).  gridDim.z splits K;
+// split z writes its own FP32 slice of C.  Waits are bounded: a timeout sets
+// the status word, the CTA drains its products and returns.
+constexpr int kGemmRows = 128, kGemmChunk = 32, kGemmStages = 4;
+
+__device__ __forceinline__ void cp_wait_upto(int n) {  // at most n of this thread's newest groups pending
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    }
+}
+
+template <int EPI, int BN>
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmTcArgs G) {
+    constexpr uint32_t kAStage = kGemmRows * kGemmChunk * 2;  // 8 KB
+    constexpr uint32_t kBStage = BN * kGemmChunk * 2;
+    constexpr uint32_t kStage = kAStage + kBStage;
+    constexpr uint32_t kCols = BN < 32 ? 32 : BN;             // TMEM columns (a power of two >= 32)
+    constexpr int S = kGemmStages;
+    extern __shared__ __align__(1024) unsigned char sm[];    // S chunk buffers
+    __shared__ __align__(8) uint64_t bars[S + 1];             // chunk buffer free (S), all products done
+    __shared__ uint32_t tslot;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * kGemmRows;
+    const int n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * G.k_per_split;
+    const int ke = min(G.K, kb + G.k_per_split);
+    const int nk = ke > kb ? (ke - kb + kGemmChunk - 1) / kGemmChunk : 0;
+    const uint32_t base = su32(sm);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tslot)),
+                     "n"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < S + 1; ++i) bar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tslot;
+    const uint32_t idesc = idesc_bf16(kGemmRows, BN);
+
+    auto load_chunk = [&](int c, int buf) {
+        const int k0 = kb + c * kGemmChunk;
+        const uint32_t a_s = base + (uint32_t)buf * kStage, b_s = a_s + kAStage;
+        for (int p = tid; p < kGemmRows * 4; p += 128) {  // 16-byte pieces: row r, k group kg
+            const int r = p >> 2, kg = p & 3, k = k0 + kg * 8;
+            const bool ok = m0 + r < G.M && k < ke;
+            cp16(a_s + (uint32_t)((r >> 3) * 512 + kg * 128 + (r & 7) * 16),
+                 G.A + (ok ? (m0 + r) * G.lda + k : 0), ok);
+        }
+        for (int p = tid; p < BN * 4; p += 128) {
+            const int r = p >> 2, kg = p & 3, k = k0 + kg * 8;
+            const bool ok = n0 + r < G.N && k < ke;
+            cp16(b_s + (uint32_t)((r >> 3) * 512 + kg * 128 + (r & 7) * 16),
+                 G.B + (ok ? (int64_t)(n0 + r) * G.ldb + k : 0), ok);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    bool ok = true;
+    int issued = 0;  // chunks whose copies were issued
+    for (; issued < min(S - 1, nk); ++issued) load_chunk(issued, issued);
+    for (int c = 0; c < nk; ++c) {
+        const int buf = c % S;
+        if (issued < nk) {
+            // chunk `issued` goes to the buffer of chunk c - 1: its products must be done
+            if (tid == 0) s_ok = c < 1 || bar_wait(&bars[(c - 1) % S], (uint32_t)((c - 1) / S) & 1u, G.budget, nullptr);
+            __syncthreads();
+            if (!s_ok) {
+                ok = false;
+                break;
+            }
+            load_chunk(issued, issued % S);
+            ++issued;
+        }
+        cp_wait_upto(issued - c - 1);  // chunk c's copies (this thread's) have landed
+        fence_async_smem();            // and are visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const uint32_t a_s = base + (uint32_t)buf * kStage, b_s = a_s + kAStage;
+            const int nmma = min(2, (ke - (kb + c * kGemmChunk) + 15) / 16);
+            for (int s2 = 0; s2 < nmma; ++s2)
+                mma_bf16_tc(tmem, smem_desc(a_s + s2 * 256, 128, 512), smem_desc(b_s + s2 * 256, 128, 512), idesc,
+                            (c | s2) ? 1u : 0u);
+            mma_commit(&bars[buf]);
+        }
+    }
+    if (!ok) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy outlives the CTA
+    if (tid == 0) {
+        mma_commit(&bars[S]);  // every product issued so far
+        s_ok = bar_wait(&bars[S], 0u, ok ? G.budget : kDrainCycles, nullptr) && ok;
+        if (!s_ok) atomicExch(G.status, 1);
+    }
+    __syncthreads();
+    fence_after();
+    if (s_ok) {  // (an empty K split still writes its slice: zeros)
+        const int row = warp * 32 + lane;
+        const int64_t gr = m0 + row;
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
+            if (nk > 0) {
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+                tmem_wait32(r);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) r[j] = 0u;
+            }
+            if (gr >= G.M) continue;
+            const int col0 = n0 + c0;
+            const int nv = min(32, G.N - col0);
+            if constexpr (EPI == 0) {
+                float* out = reinterpret_cast<float*>(G.C) + (int64_t)blockIdx.z * G.split_stride + gr * G.ldc + col0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < nv) out[j] = __uint_as_float(r[j]);
+            } else {
+                __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(G.C) + gr * G.ldc + col0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j >= nv) continue;
+                    float v = __uint_as_float(r[j]);
+                    if constexpr (EPI == 1) {
+                        v = fmaxf(v + G.bias[col0 + j], 0.0f);
+                    } else {
+                        v = __bfloat162float(G.mask[gr * G.ldm + col0 + j]) > 0.0f ? v : 0.0f;
+                    }
+                    out[j] = __float2bfloat16_rn(v);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kCols) : "memory");
+    }
+}
+
 }  // namespace
 
 static_assert(kSmBytes <= 227 * 1024, "shared memory of the fused kernel");
@@ -495,5 +655,52 @@ lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* 
     LMOSEM_LAUNCHED(c, LMOSEM_K_MLP);
     return LMOSEM_OK;
 }
+
+// the products' shared-memory opt-in, once per context and before any
+// stream capture (it is not a stream operation)
+lmosem_status gemm_tc_setup(lmosem_ctx* c) {
+    if (c->gemm_attrs) return LMOSEM_OK;
+    const int s128 = kGemmStages * (kGemmRows + 128) * kGemmChunk * 2;
+    const int s256 = kGemmStages * (kGemmRows + 256) * kGemmChunk * 2;
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_gemm_tc<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_gemm_tc<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_gemm_tc<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128));
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_gemm_tc<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256));
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_gemm_tc<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256));
+    LMOSEM_CK(c, cudaFuncSetAttribute(k_gemm_tc<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256));
+    c->gemm_attrs = true;
+    return LMOSEM_OK;
+}
+
+lmosem_status gemm_tc(lmosem_ctx* c, int epi, const GemmTcArgs& G0, int splits) {
+    lmosem_status st;
+    if ((st = ensure_status(c))) return st;
+    GemmTcArgs G = G0;
+    G.status = c->d_status;
+    G.budget = c->wait_budget;
+    splits = std::max(1, splits);
+    G.k_per_split = (G.K + splits - 1) / splits;
+    G.k_per_split = (G.k_per_split + 15) / 16 * 16;
+    const int bn = G.N <= 16 ? 16 : (G.N <= 128 ? 128 : 256);
+    // 128-column tiles when the 128-row tiles alone leave SMs idle
+    const int64_t mt = (G.M + kGemmRows - 1) / kGemmRows;
+    const int bnu = (bn == 256 && mt < 152) ? 128 : bn;
+    dim3 grid((unsigned)mt, (unsigned)((G.N + bnu - 1) / bnu), (unsigned)splits);
+    const int smem = kGemmStages * (kGemmRows + bnu) * kGemmChunk * 2;  // the chunk buffers of A and B
+    if (!c->gemm_attrs) return fail(c, LMOSEM_ESTATE, "gemm_tc_setup was not called");
+    LMOSEM_PROF_BEGIN(c);
+#define LMOSEM_GEMM_TC(E, BNV) k_gemm_tc<E, BNV><<<grid, 128, smem, c->stream>>>(G)
+    if (bnu == 16) {
+        if (epi == 0) LMOSEM_GEMM_TC(0, 16); else if (epi == 1) LMOSEM_GEMM_TC(1, 16); else LMOSEM_GEMM_TC(2, 16);
+    } else if (bnu == 128) {
+        if (epi == 0) LMOSEM_GEMM_TC(0, 128); else if (epi == 1) LMOSEM_GEMM_TC(1, 128); else LMOSEM_GEMM_TC(2, 128);
+    } else {
+        if (epi == 0) LMOSEM_GEMM_TC(0, 256); else if (epi == 1) LMOSEM_GEMM_TC(1, 256); else LMOSEM_GEMM_TC(2, 256);
+    }
+#undef LMOSEM_GEMM_TC
+    LMOSEM_LAUNCHED(c, LMOSEM_K_MLP);
+    return LMOSEM_OK;
+}
+
 
 }  // namespace lmosem

@@ -181,6 +181,7 @@ struct PathSumArgs {
     const int32_t* tile_prefix;  // cumulative event tiles, tile_prefix[0] = 0
     int n_ent;
     int pt0, n_pt;               // column tiles pt0 .. pt0 + n_pt - 1 in this launch
+    int n_tiles;                 // event tiles of this launch (all entries)
     int nq_tail;                 // narrow form: live 4-column groups of its tile
     const float* wtab;
     int ld_w, n_scat;
@@ -589,7 +590,10 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     int* mlist = reinterpret_cast<int*>(sm + kWOffList);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float2* sUw = reinterpret_cast<float2*>(sm + kWOffU) + warp * kStage * 8;
-    const TileInfo T = tile_setup(A, blockIdx.x / A.n_pt, A.pt0 + blockIdx.x % A.n_pt, ev_u, ev_e, misc,
+    // the event tile is the fast index: the CTAs resident at one time share a
+    // column tile, whose planes for an angle (12 B x 128 per scatter pixel, a
+    // few MB) stay in L2 for all of that angle's event tiles
+    const TileInfo T = tile_setup(A, blockIdx.x % A.n_tiles, A.pt0 + blockIdx.x / A.n_tiles, ev_u, ev_e, misc,
                                   mlist);
 
     // accumulators (pairs of adjacent support pixels), initialised with the
@@ -1102,6 +1106,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.n_ent = g_first[gi + 1] - e0;
         P.pt0 = 0;
         P.n_pt = n_wide;
+        P.n_tiles = tiles;
         P.nq_tail = nq_tail;
         P.wtab = wtab;
         P.ld_w = c->ld_w;
@@ -1162,7 +1167,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
 
 namespace {
 
-__global__ void k_gather_events(const int32_t* __restrict__ a_s, const float* __restrict__ u_s,
+__global__ void k_judge_gather(const int32_t* __restrict__ a_s, const float* __restrict__ u_s,
                                 const float* __restrict__ e_s, const int64_t* __restrict__ rows, int64_t K,
                                 int32_t* __restrict__ a_o, float* __restrict__ u_o, float* __restrict__ e_o) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1234,7 +1239,7 @@ lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max) {
         return st;
     LMOSEM_CK(c, cudaMemcpyAsync(d_rows, rows.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     LMOSEM_PROF_BEGIN(c);
-    k_gather_events<<<(unsigned)((K + 255) / 256), 256, 0, c->stream>>>(c->d_a_s, c->d_u_s, c->d_e_s, d_rows, K,
+    k_judge_gather<<<(unsigned)((K + 255) / 256), 256, 0, c->stream>>>(c->d_a_s, c->d_u_s, c->d_e_s, d_rows, K,
                                                                         d_a, d_u, d_e);
     LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
     std::vector<int32_t> h_a(K);

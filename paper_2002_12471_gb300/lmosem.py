@@ -55,14 +55,15 @@ class Options(ctypes.Structure):
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
                   "other", "surrogate", "mlp"]
-SURROGATE_PARAMS = 199427
+SURROGATE_PARAMS = 199455
+SURROGATE_BASIS = 28
 MODEL_SURROGATE_FP32 = 3
 FORMATS["surrogate"] = MODEL_SURROGATE_FP32
 
 
 class TrainOpts(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("target_floor", ctypes.c_float)]
+                ("seed", ctypes.c_uint64), ("target_floor", ctypes.c_float), ("residual_fit", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -365,11 +366,11 @@ def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_sc
 
 
 def lmosem_surrogate_train(ctx, d_features, d_targets, d_weights, steps=2000, batch=4096, lr=1e-3,
-                           seed=1, target_floor=0.0):
+                           seed=1, target_floor=0.0, residual_fit=False):
     """Trains in place; returns the per-step minibatch loss curve."""
     n = int(d_targets.numel())
     curve = np.zeros(int(steps), dtype=np.float64)
-    o = TrainOpts(int(steps), int(batch), float(lr), int(seed), float(target_floor))
+    o = TrainOpts(int(steps), int(batch), float(lr), int(seed), float(target_floor), int(bool(residual_fit)))
     _check(ctx, load().lmosem_surrogate_train(ctx, _ptr(d_features), _ptr(d_targets), n, ctypes.byref(o),
                                               _ptr(d_weights), curve.ctypes.data))
     return curve
@@ -418,10 +419,12 @@ def surrogate_init(seed=0, layers=(6, 256, 256, 256, 256, 1)):
     return pack_surrogate(params)
 
 
-def pack_surrogate(params, mu=0.0, sigma=1.0):
-    """Flatten [[W, b], ...] (the oracle's layout) into the library's blob."""
+def pack_surrogate(params, mu=0.0, sigma=1.0, baseline=None):
+    """Flatten [[W, b], ...] (the oracle's layout) into the library's blob;
+    the baseline coefficients default to zero (the network alone)."""
     parts = [np.asarray(a, dtype=np.float64).ravel() for layer in params for a in layer]
-    blob = np.concatenate(parts + [np.array([mu, sigma])]).astype(np.float32)
+    base = np.zeros(SURROGATE_BASIS) if baseline is None else np.asarray(baseline, dtype=np.float64)
+    blob = np.concatenate(parts + [base, np.array([mu, sigma])]).astype(np.float32)
     assert blob.size == SURROGATE_PARAMS, blob.size
     return blob
 
@@ -435,6 +438,7 @@ def unpack_surrogate(blob, layers=(6, 256, 256, 256, 256, 1)):
         b = blob[k:k + fo]
         k += fo
         params.append([W, b])
+    k += SURROGATE_BASIS  # the baseline coefficients
     return params, float(blob[k]), float(blob[k + 1])
 
 

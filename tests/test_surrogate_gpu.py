@@ -129,10 +129,11 @@ def _mirrored_forward(params, X, round_last):
 
 
 @pytest.mark.parametrize("n", [1, 129, 10007, 3 * 152 * 128 + 5])
-def test_tcgen05_inference_matches_mma_and_oracle(L, n):
+def test_tcgen05_inference_matches_product_chain_and_oracle(L, n):
     """The fused tcgen05 inference kernel (persistent over 128-row tiles, a
-    ragged last tile) against the mma.sync product chain and against the FP64
-    forward with the same BF16 rounding points."""
+    ragged last tile) against the chain of separate tcgen05 products (the
+    training kernels, activations through HBM) and against the FP64 forward
+    with the same BF16 rounding points."""
     import torch
     dev = torch.device("cuda:0")
     ph, g, *_ = S.workload("tiny16")
@@ -263,9 +264,9 @@ def test_training_converges_and_generalises(trained):
 
 
 def test_surrogate_model_rows_agree_across_kernels(L, trained):
-    """Model rows built with the surrogate scatter term through the tcgen05
-    kernel and through the mma.sync chain agree to the BF16 rounding of the
-    last hidden layer."""
+    """Model rows built with the surrogate scatter term through the fused
+    tcgen05 kernel and through the chain of separate products agree to the
+    BF16 rounding of the last hidden layer."""
     import torch
     dev = torch.device("cuda:0")
     ph, g, ns = trained["ph"], trained["g"], trained["ns"]
