@@ -1082,7 +1082,7 @@ def run_surrogate_bench(args):
 
     # ---- training set: exact log scatter of every (event, support pixel)
     t_samples = time.perf_counter()
-    feats, targs = [], []
+    feats, targs, rels = [], [], []
     for (seed, _, _), (a, u, e) in zip(jobs[:len(SURR_TRAIN_SEEDS)], parts):
         ph = surrogate_phantom(seed)
         ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
@@ -1090,16 +1090,19 @@ def run_surrogate_bench(args):
             nsup = L.lmosem_n_support(ctx)
             feat = torch.empty((len(a) * nsup, 6), dtype=torch.float32, device=dev)
             targ = torch.empty(len(a) * nsup, dtype=torch.float32, device=dev)
+            rel = torch.empty(len(a) * nsup, dtype=torch.float32, device=dev)
             L.lmosem_surrogate_samples(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(u).to(dev),
-                                       torch.from_numpy(e).to(dev), feat, targ)
+                                       torch.from_numpy(e).to(dev), feat, targ, rel)
             feats.append(feat)
             targs.append(targ)
+            rels.append(rel)
         finally:
             L.lmosem_destroy(ctx)
     feat = torch.cat(feats)
     targ = torch.cat(targs)
+    rel = torch.cat(rels)
     n_train_pairs = int(targ.numel())
-    del feats, targs
+    del feats, targs, rels
     torch.cuda.synchronize()
     t_samples = time.perf_counter() - t_samples
 
@@ -1111,13 +1114,15 @@ def run_surrogate_bench(args):
     J = len(a_h)
     a_d, u_d, e_d = a_h.to(dev), u_h.to(dev), e_h.to(dev)
 
-    train_steps, train_batch, train_floor = 60000, 8192, 10.0
+    # pairs drawn in proportion to (scatter / its row's largest scatter)^1
+    train_steps, train_batch, train_floor, train_power = 60000, 8192, 14.0, 1.0
     blob = torch.from_numpy(L.surrogate_init(seed=3)).to(dev)
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
     try:
         t_train = time.perf_counter()
         curve = L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=train_steps, batch=train_batch,
-                                         lr=1e-3, seed=5, target_floor=train_floor, residual_fit=True)
+                                         lr=1e-3, seed=5, target_floor=train_floor, residual_fit=True,
+                                         d_rel_log=rel, magnitude_power=train_power)
         t_train = time.perf_counter() - t_train
         # held out: exact log scatter of 200 events of the evaluation phantom
         nsup = L.lmosem_n_support(ctx)
@@ -1248,6 +1253,8 @@ def run_surrogate_bench(args):
                    "train_pairs": n_train_pairs, "train_phantoms": len(SURR_TRAIN_SEEDS),
                    "train_steps": train_steps, "train_batch": train_batch,
                    "train_target_floor": train_floor, "train_residual_of_quadratic_baseline": True,
+                   "train_sampling": "pairs drawn with probability proportional to (scatter / row maximum)^%g"
+                                     % train_power,
                    "l2": "model (%.1f GB) larger than L2; 256 MB flush before every step" % (J * nsup * 4 / 1e9)},
         "model_build_evals_per_s": {"surrogate": pairs / (sur_build_ms * 1e-3),
                                     "exact": pairs / (ex_build_ms * 1e-3),

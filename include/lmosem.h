@@ -100,9 +100,9 @@ typedef struct {
      * LMOSEM_ETIMEOUT; the context stays usable.  Tests set a tiny budget
      * (here or with lmosem_set_wait_budget) to exercise that path. */
     int64_t wait_budget_cycles;
-    /* Streaming-pass implementation (tuning knobs; 0 = automatic, which is
-     * 4 for lmosem_iterate without per-iteration log-likelihoods and 1 or 3
-     * otherwise): 1 = rows double-buffered in registers, 2 = rows staged in a
+    /* Streaming-pass implementation (tuning knobs; 0 = automatic: 3 for FP32
+     * rows of 6 or more 16-byte vectors per thread, 1 otherwise):
+     * 1 = rows double-buffered in registers, 2 = rows staged in a
      * shared-memory ring by bulk (TMA) copies, ring_rows rows per stage
      * (1..8) and ring_stages stages (2..8), 3 = each thread's row vectors
      * staged in its own slots of a shared-memory ring by cp.async (several
@@ -119,6 +119,10 @@ typedef struct {
      * HBM), 2 = fused tcgen05 kernel (one persistent CTA per SM, activations
      * kept on chip, TMEM accumulators). */
     int32_t surrogate_kernel;
+    /* Register pass (pass_variant 1): row groups fetched into L2 ahead of
+     * their register loads by bulk prefetches, this many groups ahead;
+     * -1 = none, 0 = automatic, 1..16. */
+    int32_t prefetch_groups;
 } lmosem_options;
 
 /* Kernel classes reported by lmosem_profile_read. */
@@ -290,10 +294,14 @@ lmosem_status lmosem_binned_support(lmosem_ctx* ctx, const int32_t* d_angle, con
  * afterwards) and writes, for every (event k, support pixel q) at row
  * k * N_nz + q: the six scaled inputs (d_features, 6 floats per row) and the
  * natural log of the exact scatter entry (d_log_scatter; entries below 1e-30
- * are clamped).  Synchronises.  EINVAL as lmosem_build_model. */
+ * are clamped).  d_rel_log (may be NULL) receives each entry's log minus the
+ * largest log of its event's row (<= 0), which lmosem_surrogate_train can use
+ * to draw training pairs in proportion to their share of their row: the EM
+ * update weighs every event alike, and most pairs of a row carry little of
+ * it.  Synchronises.  EINVAL as lmosem_build_model. */
 lmosem_status lmosem_surrogate_samples(lmosem_ctx* ctx, const int32_t* d_angle, const float* d_u_mm,
                                        const float* d_e_kev, int64_t n_events, float* d_features,
-                                       float* d_log_scatter);
+                                       float* d_log_scatter, float* d_rel_log);
 
 typedef struct {
     int32_t steps;     /* Adam steps (>= 1)                                        */
@@ -305,11 +313,14 @@ typedef struct {
                          * entries that carry the model (log units); 0: none      */
     int32_t residual_fit; /* 1: fit the quadratic baseline to the (floored) targets
                            * by least squares first and train the network on the
-                           * residual, whose smaller spread shrinks the error of
-                           * the BF16 arithmetic in log units; 0: zero baseline   */
+                           * residual; 0: zero baseline                           */
+    float magnitude_power; /* alpha > 0 with d_rel_log: minibatch rows drawn with
+                            * probability proportional to exp(alpha rel_log), i.e.
+                            * (entry / largest entry of its row)^alpha; 0: uniform */
 } lmosem_train_opts;
 
-/* Train the surrogate on n samples (features n x 6, targets n = log scatter)
+/* Train the surrogate on n samples (features n x 6, targets n = log scatter,
+ * d_rel_log n or NULL: see lmosem_surrogate_samples and magnitude_power)
  * with the library's tensor-core forward and backward kernels and Adam (FP32
  * parameters and moments, BF16 products, FP32 accumulation).  d_weights holds
  * the initial parameters on entry (the baseline coefficients are refitted or
@@ -317,8 +328,8 @@ typedef struct {
  * baseline) and the trained ones on return.  h_loss_curve (steps doubles, may
  * be NULL) receives the minibatch loss of every step.  Synchronises. */
 lmosem_status lmosem_surrogate_train(lmosem_ctx* ctx, const float* d_features, const float* d_targets,
-                                     int64_t n, const lmosem_train_opts* opts, float* d_weights,
-                                     double* h_loss_curve);
+                                     const float* d_rel_log, int64_t n, const lmosem_train_opts* opts,
+                                     float* d_weights, double* h_loss_curve);
 
 /* Gradient of the mean squared error of the network output against the
  * standardised targets ((t - mu) / sigma with the blob's mu, sigma) over all

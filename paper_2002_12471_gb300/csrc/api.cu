@@ -324,6 +324,11 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
             return LMOSEM_EINVAL;
         }
         c->surrogate_kernel = opts->surrogate_kernel;
+        if (opts->prefetch_groups < -1 || opts->prefetch_groups > 16) {
+            delete c;
+            return LMOSEM_EINVAL;
+        }
+        c->prefetch_groups = opts->prefetch_groups;
     }
 
     std::vector<float> mu(c->npix);
@@ -740,7 +745,7 @@ lmosem_status lmosem_binned_support(lmosem_ctx* c, const int32_t* d_angle, const
 
 lmosem_status lmosem_surrogate_samples(lmosem_ctx* c, const int32_t* d_angle, const float* d_u_mm,
                                        const float* d_e_kev, int64_t n_events, float* d_features,
-                                       float* d_log_scatter) {
+                                       float* d_log_scatter, float* d_rel_log) {
     if (!c) return LMOSEM_EINVAL;
     if (!d_features || !d_log_scatter) return fail(c, LMOSEM_EINVAL, "null output");
     lmosem_status st = check_events_args(c, d_angle, d_u_mm, d_e_kev, n_events, 1, LMOSEM_MODEL_FP32);
@@ -749,15 +754,15 @@ lmosem_status lmosem_surrogate_samples(lmosem_ctx* c, const int32_t* d_angle, co
     st = build_model_common(c, d_angle, d_u_mm, d_e_kev, n_events, 1, LMOSEM_MODEL_FP32, nullptr, 1);
     c->scatter_only = false;
     if (st) return st;
-    st = run_surrogate_samples(c, d_features, d_log_scatter);
+    st = run_surrogate_samples(c, d_features, d_log_scatter, d_rel_log);
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
     free_model(c);
     return st;
 }
 
 lmosem_status lmosem_surrogate_train(lmosem_ctx* c, const float* d_features, const float* d_targets,
-                                     int64_t n, const lmosem_train_opts* opts, float* d_weights,
-                                     double* h_loss_curve) {
+                                     const float* d_rel_log, int64_t n, const lmosem_train_opts* opts,
+                                     float* d_weights, double* h_loss_curve) {
     if (!c) return LMOSEM_EINVAL;
     if (!d_features || !d_targets || !d_weights || !opts || n < 1)
         return fail(c, LMOSEM_EINVAL, "bad training arguments");
@@ -767,8 +772,11 @@ lmosem_status lmosem_surrogate_train(lmosem_ctx* c, const float* d_features, con
         return fail(c, LMOSEM_EINVAL,
                     "steps >= 1, batch a multiple of 64 in [64, 65536], lr > 0, target_floor >= 0");
     if (opts->residual_fit != 0 && opts->residual_fit != 1) return fail(c, LMOSEM_EINVAL, "residual_fit is 0 or 1");
-    return run_surrogate_train(c, d_features, d_targets, n, opts->steps, opts->batch, opts->lr, opts->seed,
-                               opts->target_floor, opts->residual_fit != 0, d_weights, h_loss_curve);
+    if (!(opts->magnitude_power >= 0.0f) || !isfinite(opts->magnitude_power))
+        return fail(c, LMOSEM_EINVAL, "magnitude_power must be finite and >= 0");
+    return run_surrogate_train(c, d_features, d_targets, d_rel_log, n, opts->steps, opts->batch, opts->lr,
+                               opts->seed, opts->target_floor, opts->residual_fit != 0, opts->magnitude_power,
+                               d_weights, h_loss_curve);
 }
 
 lmosem_status lmosem_surrogate_grad(lmosem_ctx* c, const float* d_weights, const float* d_features,

@@ -114,6 +114,7 @@ struct lmosem_ctx {
     bool scatter_only = false;                // model build leaves the primary path out
     bool use_surrogate = false;               // model build takes the scatter part from the MLP
     int surrogate_kernel = 0;                 // inference: 0 auto (fused tcgen05), 1 product chain, 2 fused
+    int prefetch_groups = 0;                  // register pass: groups prefetched into L2 ahead (-1 none, 0 auto)
     bool gemm_attrs = false;                  // shared-memory opt-in of the training products is set
     // exact check of a surrogate build: rows recomputed by the path sum
     double sur_tol = 1e-2;                    // rel-L2 above which the model is rebuilt exactly (0: never)
@@ -283,12 +284,12 @@ lmosem_status run_autotune_batch(lmosem_ctx* c, double T, const float* d_f, int3
 // mlp.cu
 lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* feat, const float* targ,
                                  int64_t n, float* grad_out, double* h_loss);
-lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
-                                  int steps, int B, float lr, uint64_t seed, float floor_below, bool residual_fit,
-                                  float* blob, double* h_loss_curve);
+lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, const float* rel,
+                                  int64_t n, int steps, int B, float lr, uint64_t seed, float floor_below,
+                                  bool residual_fit, float magnitude_power, float* blob, double* h_loss_curve);
 lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float* feat, int64_t n,
                                   float* out);
-lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ);
+lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ, float* rel);
 lmosem_status build_model_surrogate(lmosem_ctx* c);
 // model.cu: exact rows of an evenly spaced sample of the model's events
 // against the rows the surrogate built (relative L2 over the sampled rows,

@@ -116,15 +116,32 @@ __device__ __forceinline__ int64_t x_index(int64_t i, int k, bool tiled) {
 }
 
 // (step_ptr: the step index lives on the device, for a captured training step)
+// (cdf: inclusive prefix sums of sampling weights, n FP64 values: row i is
+// drawn with probability weight_i / total, by bisection; nullptr: uniform)
 __global__ void k_gather(const float* __restrict__ feat, const float* __restrict__ targ, int64_t n,
                          int B, uint64_t seed, int step, const int* __restrict__ step_ptr,
-                         const float* __restrict__ blob, const float* __restrict__ floor,
-                         __nv_bfloat16* __restrict__ X, float* __restrict__ t, bool tiled) {
+                         const double* __restrict__ cdf, const float* __restrict__ blob,
+                         const float* __restrict__ floor, __nv_bfloat16* __restrict__ X, float* __restrict__ t,
+                         bool tiled) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     if (step_ptr) step = *step_ptr;
-    const int64_t i = seed == 0 ? (int64_t)b % n
-                                : (int64_t)(splitmix64(seed ^ ((uint64_t)step * 0x100000001B3ull + b)) % (uint64_t)n);
+    const uint64_t h = seed == 0 ? 0 : splitmix64(seed ^ ((uint64_t)step * 0x100000001B3ull + b));
+    int64_t i;
+    if (seed == 0) {
+        i = (int64_t)b % n;
+    } else if (cdf) {
+        const double x = (double)(h >> 11) * 0x1.0p-53 * cdf[n - 1];
+        int64_t lo = 0, hi = n - 1;  // smallest i with cdf[i] > x
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cdf[mid] > x) hi = mid;
+            else lo = mid + 1;
+        }
+        i = lo;
+    } else {
+        i = (int64_t)(h % (uint64_t)n);
+    }
     float x[kIn];
 #pragma unroll
     for (int k = 0; k < kIn; ++k) x[k] = feat[i * kIn + k];
@@ -380,6 +397,59 @@ __global__ void k_samples(FeatArgs F, const float* __restrict__ model, int64_t l
     targ[i] = logf(fmaxf(model[row * ld + q], 1e-30f));
 }
 
+// rel[k * n_sup + q] = targ[k * n_sup + q] - max over q' of targ[k * n_sup + q']
+// (one block per event row)
+__global__ void k_row_rel(const float* __restrict__ targ, int n_sup, float* __restrict__ rel) {
+    __shared__ float sm[256];
+    const float* row = targ + (int64_t)blockIdx.x * n_sup;
+    float m = -FLT_MAX;
+    for (int q = threadIdx.x; q < n_sup; q += blockDim.x) m = fmaxf(m, row[q]);
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    m = sm[0];
+    for (int q = threadIdx.x; q < n_sup; q += blockDim.x) rel[(int64_t)blockIdx.x * n_sup + q] = row[q] - m;
+}
+
+// inclusive prefix sums of w_i = exp(alpha rel_i) in FP64: per-chunk sums,
+// their scan (one block, in order), then each chunk's scan from its offset
+constexpr int kCdfChunk = 4096;
+__global__ void k_cdf_chunks(const float* __restrict__ rel, int64_t n, float alpha, double* __restrict__ csum) {
+    __shared__ double sh[256];
+    const int64_t c0 = (int64_t)blockIdx.x * kCdfChunk;
+    double a = 0.0;
+    for (int64_t i = c0 + threadIdx.x; i < min(n, c0 + kCdfChunk); i += blockDim.x) a += exp((double)alpha * rel[i]);
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) s += sh[k];
+        csum[blockIdx.x] = s;
+    }
+}
+__global__ void k_cdf_offsets(double* __restrict__ csum, int64_t nchunks) {
+    if (threadIdx.x != 0) return;
+    double acc = 0.0;  // exclusive scan in place
+    for (int64_t k = 0; k < nchunks; ++k) {
+        const double v = csum[k];
+        csum[k] = acc;
+        acc += v;
+    }
+}
+__global__ void k_cdf_fill(const float* __restrict__ rel, int64_t n, float alpha, const double* __restrict__ off,
+                           double* __restrict__ cdf) {
+    if (threadIdx.x != 0) return;  // one thread per chunk, in order
+    const int64_t c0 = (int64_t)blockIdx.x * kCdfChunk;
+    double acc = off[blockIdx.x];
+    for (int64_t i = c0; i < min(n, c0 + kCdfChunk); ++i) {
+        acc += exp((double)alpha * rel[i]);
+        cdf[i] = acc;
+    }
+}
+
 // surrogate inputs of rows [r0, r0 + nrows) x all support pixels, BF16
 __global__ void k_surr_inputs(FeatArgs F, int64_t r0, int64_t nrows, __nv_bfloat16* __restrict__ X,
                               bool tiled) {
@@ -587,8 +657,8 @@ lmosem_status run_surrogate_grad(lmosem_ctx* c, const float* blob, const float* 
     LMOSEM_CK(c, cudaMemsetAsync(tb.loss, 0, sizeof(double), c->stream));
     if ((st = weights_bf16(c, blob, w))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, nullptr, blob, nullptr, tb.X, tb.t,
-                                                     false);
+    k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, 0, 0, nullptr, nullptr, blob, nullptr, tb.X,
+                                                     tb.t, false);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     tb.grad = grad_out;
     if ((st = loss_grad(c, blob, w, tb, B))) return st;
@@ -656,9 +726,9 @@ lmosem_status fit_baseline(lmosem_ctx* c, const float* feat, const float* targ, 
     return LMOSEM_OK;
 }
 
-lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, int64_t n,
-                                  int steps, int B, float lr, uint64_t seed, float floor_below, bool residual_fit,
-                                  float* blob, double* h_loss_curve) {
+lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float* targ, const float* rel,
+                                  int64_t n, int steps, int B, float lr, uint64_t seed, float floor_below,
+                                  bool residual_fit, float magnitude_power, float* blob, double* h_loss_curve) {
     lmosem_status st;
     if ((st = gemm_tc_setup(c))) return st;
     MlpBufs w;
@@ -667,6 +737,7 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
     float* d_floor = nullptr;
     int* d_step = nullptr;
     float* d_sc = nullptr;
+    double *d_cdf = nullptr, *d_csum = nullptr;
     Scratch tmp(c);
     if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
         (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&tb.X, (size_t)B * kInPad)) ||
@@ -696,14 +767,27 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
     // stream that cannot be captured)
     LMOSEM_CK(c, cudaMemsetAsync(d_step, 0, sizeof(int), c->stream));
     if ((st = ensure_status(c))) return st;  // before any capture: the products report to it
+    if (rel && magnitude_power > 0.0f) {    // sampling weights (entry / row maximum)^alpha
+        const int64_t nchunks = (n + kCdfChunk - 1) / kCdfChunk;
+        if ((st = tmp.alloc(&d_cdf, (size_t)n)) || (st = tmp.alloc(&d_csum, (size_t)nchunks))) return st;
+        LMOSEM_PROF_BEGIN(c);
+        k_cdf_chunks<<<(unsigned)nchunks, 256, 0, c->stream>>>(rel, n, magnitude_power, d_csum);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        LMOSEM_PROF_BEGIN(c);
+        k_cdf_offsets<<<1, 32, 0, c->stream>>>(d_csum, nchunks);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        LMOSEM_PROF_BEGIN(c);
+        k_cdf_fill<<<(unsigned)nchunks, 32, 0, c->stream>>>(rel, n, magnitude_power, d_csum, d_cdf);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    }
     tb.loss = d_curve;
     tb.step = d_step;
     auto enqueue_step = [&]() -> lmosem_status {
         lmosem_status s2;
         if ((s2 = weights_bf16(c, blob, w))) return s2;
         LMOSEM_PROF_BEGIN(c);
-        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, 0, d_step, blob, d_floor,
-                                                         tb.X, tb.t, false);
+        k_gather<<<(B + 255) / 256, 256, 0, c->stream>>>(feat, targ, n, B, seed | 1ull, 0, d_step, d_cdf, blob,
+                                                         d_floor, tb.X, tb.t, false);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         if ((s2 = loss_grad(c, blob, w, tb, B))) return s2;
         LMOSEM_PROF_BEGIN(c);
@@ -767,7 +851,7 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
         return st;
     if ((st = infer_weights(c, blob, w, tmp))) return st;
     LMOSEM_PROF_BEGIN(c);
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, nullptr, blob, nullptr, X, out,
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(feat, feat, n, (int)n, 0, 0, nullptr, nullptr, blob, nullptr, X, out,
                                                                  c->surrogate_kernel != 1);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
     __nv_bfloat16* Hs[4] = {H, H + n * kH, H + 2 * n * kH, H + 3 * n * kH};
@@ -795,13 +879,18 @@ FeatArgs feat_args(lmosem_ctx* c) {
 
 // features and log exact scatter of every (event, support pixel) of the
 // current (scatter-only, FP32) model, in the caller's event order
-lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ) {
+lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ, float* rel) {
     const int64_t total = c->J * c->n_sup;
     // the sort's rank maps the caller's event k to its model row
     LMOSEM_PROF_BEGIN(c);
     k_samples<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
         feat_args(c), reinterpret_cast<const float*>(c->d_model), c->ld_model, c->d_rank, c->J, feat, targ);
     LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    if (rel) {
+        LMOSEM_PROF_BEGIN(c);
+        k_row_rel<<<(unsigned)c->J, 256, 0, c->stream>>>(targ, c->n_sup, rel);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    }
     return LMOSEM_OK;
 }
 

@@ -106,7 +106,22 @@ struct PassArgs {
     double log_T;
     float* bpart;            // [cta][n_sup]
     double* llpart;          // [cta]
+    int prefetch;            // register pass: row groups fetched into L2 this many groups ahead (0: none)
 };
+
+// rows [r, min(r + R, re)) of the model into L2, one bulk prefetch per row
+// (the row's nvec 16-byte vectors: 16-byte aligned start and size)
+template <int R>
+__device__ __forceinline__ void prefetch_rows_l2(const char* model, int64_t ld_bytes, int64_t nvec, int64_t r,
+                                                 int64_t re, int warp, int nwarps, int lane) {
+    if (lane != 0) return;
+    for (int i = warp; i < R; i += nwarps) {
+        if (r + i >= re) return;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(model + (r + i) * ld_bytes),
+                     "r"((unsigned)(nvec * 16))
+                     : "memory");
+    }
+}
 
 // One pass over rows [r0, r1): thread t owns the 16-byte column vectors
 // t, t + NT, ... (VPT of them); groups of R rows are double-buffered in
@@ -240,13 +255,21 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
         }
     };
 
+    // register double buffer: group g + 1 loads while group g is processed;
+    // with A.prefetch = D, group g + 1 + D is requested into L2 at the same
+    // time, so D more groups are in flight than the registers hold
+    const int64_t ahead = (int64_t)A.prefetch * R;
     uint4 P0[R][VPT], P1[R][VPT];
     if (rb < re) load(rb, P0);
+    for (int64_t k = 1; k <= A.prefetch; ++k)
+        prefetch_rows_l2<R>(model, A.ld_bytes, A.nvec, rb + k * R, re, warp, NW, lane);
     load_f();
     for (int64_t r = rb; r < re; r += 2 * R) {
+        if (ahead) prefetch_rows_l2<R>(model, A.ld_bytes, A.nvec, r + R + ahead, re, warp, NW, lane);
         if (r + R < re) load(r + R, P1);
         process(r, P0, 0);
         if (r + R >= re) break;
+        if (ahead) prefetch_rows_l2<R>(model, A.ld_bytes, A.nvec, r + 2 * R + ahead, re, warp, NW, lane);
         if (r + 2 * R < re) load(r + 2 * R, P0);
         process(r + R, P1, 1);
     }
@@ -299,6 +322,9 @@ __device__ __forceinline__ void cpa_wait(int n) {
     }
 }
 constexpr int kCpaMaxStages = 8;
+// row groups the register pass prefetches into L2 ahead of its loads, unless
+// the context sets another distance
+constexpr int kAutoPrefetch = 0;
 
 template <typename H, int VPT, int R, bool BACK, bool W>
 __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass_cpa(PassArgs A, int S) {
@@ -1244,6 +1270,7 @@ lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f,
     A.log_T = log(T);
     A.bpart = c->d_bpart;
     A.llpart = c->d_llpart;
+    A.prefetch = c->prefetch_groups < 0 ? 0 : (c->prefetch_groups > 0 ? c->prefetch_groups : kAutoPrefetch);
     if (c->d_weight) {  // binned rows: FP32 only
         if (c->fmt != LMOSEM_MODEL_FP32) return fail(c, LMOSEM_ESTATE, "binned rows are FP32");
         return launch_pass_h<float, BACK, true>(c, A, rows, s);
@@ -1616,6 +1643,7 @@ extern "C" lmosem_status lmosem_osem_subiter_noalloc(const float* d_rows, int64_
     A.log_T = 0.0;
     A.bpart = scratch;
     A.llpart = nullptr;
+    A.prefetch = 0;
     int grid = 0;
     cudaError_t e;
     switch (vpt) {

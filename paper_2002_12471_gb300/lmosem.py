@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
     _fields_ = [("k_sigma", ctypes.c_float), ("table_budget_bytes", ctypes.c_int64),
                 ("profile", ctypes.c_int32), ("wait_budget_cycles", ctypes.c_int64),
                 ("pass_variant", ctypes.c_int32), ("ring_rows", ctypes.c_int32),
-                ("ring_stages", ctypes.c_int32), ("surrogate_kernel", ctypes.c_int32)]
+                ("ring_stages", ctypes.c_int32), ("surrogate_kernel", ctypes.c_int32),
+                ("prefetch_groups", ctypes.c_int32)]
 
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
@@ -63,7 +64,8 @@ FORMATS["surrogate"] = MODEL_SURROGATE_FP32
 
 class TrainOpts(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("target_floor", ctypes.c_float), ("residual_fit", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("target_floor", ctypes.c_float), ("residual_fit", ctypes.c_int32),
+                ("magnitude_power", ctypes.c_float)]
 
 
 _vp = ctypes.c_void_p
@@ -104,8 +106,8 @@ SIGNATURES = {
     "lmosem_set_batch_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
     "lmosem_binned_support": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_double, ctypes.c_int32, _vp, _vp]),
-    "lmosem_surrogate_samples": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
-    "lmosem_surrogate_train": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(TrainOpts), _vp, _vp]),
+    "lmosem_surrogate_samples": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "lmosem_surrogate_train": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(TrainOpts), _vp, _vp]),
     "lmosem_surrogate_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "lmosem_surrogate_infer": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
     "lmosem_surrogate_load": (ctypes.c_int, [_vp, _vp]),
@@ -160,7 +162,7 @@ def _check(ctx, st):
 
 def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                   table_budget_bytes=0, stream=None, profile=False, wait_budget_cycles=0,
-                  pass_variant=0, ring_rows=0, ring_stages=0, surrogate_kernel=0):
+                  pass_variant=0, ring_rows=0, ring_stages=0, surrogate_kernel=0, prefetch_groups=0):
     """Create a context.  ``mu_per_mm`` is an (ny, nx) host array at the
     photopeak, ``geom`` holds the scanner and energy fields of
     ``include/lmosem.h``; ``stream`` is a torch.cuda.Stream or a raw handle."""
@@ -179,7 +181,7 @@ def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                float(geom["e_hi_kev"]))
     o = Options(float(k_sigma), int(table_budget_bytes), int(profile),
                 int(wait_budget_cycles), int(pass_variant), int(ring_rows), int(ring_stages),
-                int(surrogate_kernel))
+                int(surrogate_kernel), int(prefetch_groups))
     h = _vp()
     s = getattr(stream, "cuda_stream", stream)
     st = L.lmosem_create(ctypes.byref(obj), ctypes.byref(g), ctypes.byref(e), ctypes.byref(o),
@@ -359,20 +361,23 @@ def lmosem_binned_support(ctx, d_angle, d_u_mm, d_e_kev, n_subsets=4, n_iters=3,
     return mask
 
 
-def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_scatter):
+def lmosem_surrogate_samples(ctx, d_angle, d_u_mm, d_e_kev, d_features, d_log_scatter, d_rel_log=None):
     n = _n_events(d_angle, d_u_mm, d_e_kev)
     _check(ctx, load().lmosem_surrogate_samples(ctx, _ptr(d_angle), _ptr(d_u_mm), _ptr(d_e_kev), n,
-                                                _ptr(d_features), _ptr(d_log_scatter)))
+                                                _ptr(d_features), _ptr(d_log_scatter),
+                                                _ptr(d_rel_log) if d_rel_log is not None else None))
 
 
 def lmosem_surrogate_train(ctx, d_features, d_targets, d_weights, steps=2000, batch=4096, lr=1e-3,
-                           seed=1, target_floor=0.0, residual_fit=False):
+                           seed=1, target_floor=0.0, residual_fit=False, d_rel_log=None, magnitude_power=0.0):
     """Trains in place; returns the per-step minibatch loss curve."""
     n = int(d_targets.numel())
     curve = np.zeros(int(steps), dtype=np.float64)
-    o = TrainOpts(int(steps), int(batch), float(lr), int(seed), float(target_floor), int(bool(residual_fit)))
-    _check(ctx, load().lmosem_surrogate_train(ctx, _ptr(d_features), _ptr(d_targets), n, ctypes.byref(o),
-                                              _ptr(d_weights), curve.ctypes.data))
+    o = TrainOpts(int(steps), int(batch), float(lr), int(seed), float(target_floor), int(bool(residual_fit)),
+                  float(magnitude_power))
+    _check(ctx, load().lmosem_surrogate_train(ctx, _ptr(d_features), _ptr(d_targets),
+                                              _ptr(d_rel_log) if d_rel_log is not None else None, n,
+                                              ctypes.byref(o), _ptr(d_weights), curve.ctypes.data))
     return curve
 
 

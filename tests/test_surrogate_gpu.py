@@ -207,12 +207,17 @@ def test_training_targets_match_oracle_scatter(L):
         nsup = L.lmosem_n_support(ctx)
         feat = torch.zeros((len(ev) * nsup, 6), dtype=torch.float32, device=dev)
         targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
+        rel = torch.full((len(ev) * nsup,), np.nan, dtype=torch.float32, device=dev)
         L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
-                                   torch.from_numpy(ev.e_kev).to(dev), feat, targ)
+                                   torch.from_numpy(ev.e_kev).to(dev), feat, targ, rel)
         f = feat.cpu().numpy().astype(np.float64).reshape(len(ev), nsup, 6)
-        p_gpu = np.exp(targ.cpu().numpy().astype(np.float64)).reshape(len(ev), nsup)
+        t32 = targ.cpu().numpy().reshape(len(ev), nsup)
+        p_gpu = np.exp(t32.astype(np.float64))
+        r32 = rel.cpu().numpy().reshape(len(ev), nsup)
     finally:
         L.lmosem_destroy(ctx)
+    # each log's offset from its row's largest log, one FP32 subtraction
+    np.testing.assert_array_equal(r32, t32 - t32.max(axis=1, keepdims=True))
     scat = P.model(ev.angle, ev.u_mm, ev.e_kev, primary=False)
     assert row_close(p_gpu, scat) <= 1.0
     # inputs: pixel centre, angle, position, energy, attenuation to the edge
@@ -221,6 +226,39 @@ def test_training_targets_match_oracle_scatter(L):
     ref = mlp.features(xs[None, :], ys[None, :], th[:, None], ev.u_mm[:, None].astype(np.float64),
                        ev.e_kev[:, None].astype(np.float64), P.l_edge[ev.angle][:, P.support])
     np.testing.assert_allclose(f, ref, rtol=1e-5, atol=1e-5)
+
+
+def test_training_draws_pairs_by_magnitude_weight(L):
+    """With magnitude_power, minibatch rows are drawn in proportion to
+    exp(alpha rel_log).  Half the rows carry target a and weight 1, the other
+    half target b and weight exp(-60) (never drawn in practice); the inputs are
+    noise.  The normalised targets are -1 and +1 (mean and deviation over all
+    rows), so a network that sees only the weighted rows drives its loss to 0,
+    while uniform draws leave it at 1, the variance of the two."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, J, ns, ni = S.workload("tiny16")
+    n = 1 << 16
+    gen = torch.Generator().manual_seed(7)
+    feat = torch.rand((n, 6), generator=gen).to(dev)
+    heavy = torch.rand(n, generator=gen) < 0.5
+    targ = torch.where(heavy, torch.tensor(-3.0), torch.tensor(1.0)).to(dev)
+    rel = torch.where(heavy, torch.tensor(0.0), torch.tensor(-60.0)).to(dev)
+    ctx = _ctx(L, ph, g)
+    try:
+        last = {}
+        for power in (0.0, 1.0):
+            blob = torch.from_numpy(L.pack_surrogate(mlp.init_params(3))).to(dev)
+            curve = L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=600, batch=1024, lr=1e-3, seed=9,
+                                             d_rel_log=rel, magnitude_power=power)
+            last[power] = float(np.mean(curve[-100:]))
+        with pytest.raises(RuntimeError):
+            L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=1, batch=1024, d_rel_log=rel,
+                                     magnitude_power=-1.0)
+    finally:
+        L.lmosem_destroy(ctx)
+    assert last[1.0] < 0.02, last
+    assert 0.8 < last[0.0] < 1.2, last
 
 
 @pytest.fixture(scope="module")
