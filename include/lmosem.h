@@ -100,9 +100,8 @@ typedef struct {
      * LMOSEM_ETIMEOUT; the context stays usable.  Tests set a tiny budget
      * (here or with lmosem_set_wait_budget) to exercise that path. */
     int64_t wait_budget_cycles;
-    /* Streaming-pass implementation (tuning knobs; 0 = automatic: 3 for FP32
-     * rows of 6 or more 16-byte vectors per thread, 1 otherwise):
-     * 1 = rows double-buffered in registers, 2 = rows staged in a
+    /* Streaming-pass implementation (tuning knobs; 0 = automatic, which is
+     * 1): 1 = rows double-buffered in registers, 2 = rows staged in a
      * shared-memory ring by bulk (TMA) copies, ring_rows rows per stage
      * (1..8) and ring_stages stages (2..8), 3 = each thread's row vectors
      * staged in its own slots of a shared-memory ring by cp.async (several
@@ -121,7 +120,8 @@ typedef struct {
     int32_t surrogate_kernel;
     /* Register pass (pass_variant 1): row groups fetched into L2 ahead of
      * their register loads by bulk prefetches, this many groups ahead;
-     * -1 = none, 0 = automatic, 1..16. */
+     * -1 = none, 0 = automatic (rows wide enough to be processed one at a
+     * time: about 48 KB ahead per CTA; none otherwise), 1..16. */
     int32_t prefetch_groups;
 } lmosem_options;
 
@@ -310,7 +310,9 @@ typedef struct {
     uint64_t seed;     /* minibatch sampling (rows drawn with replacement)         */
     float target_floor; /* > 0: targets below (largest target - target_floor) are
                          * raised to that level, so that the fit is spent on the
-                         * entries that carry the model (log units); 0: none      */
+                         * entries that carry the model (log units); with
+                         * d_rel_log the largest target of the same event's row
+                         * (every event then keeps its row's shape); 0: none     */
     int32_t residual_fit; /* 1: fit the quadratic baseline to the (floored) targets
                            * by least squares first and train the network on the
                            * residual; 0: zero baseline                           */

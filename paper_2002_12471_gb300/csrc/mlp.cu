@@ -414,6 +414,16 @@ __global__ void k_row_rel(const float* __restrict__ targ, int n_sup, float* __re
     for (int q = threadIdx.x; q < n_sup; q += blockDim.x) rel[(int64_t)blockIdx.x * n_sup + q] = row[q] - m;
 }
 
+// targets floored per event row: t_i raised to (its row's largest - F), the
+// row maximum being t_i - rel_i
+__global__ void k_row_floor(const float* __restrict__ t, const float* __restrict__ rel, int64_t n, float F,
+                            float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float ti = t[i];
+        out[i] = rel[i] < -F ? ti - rel[i] - F : ti;
+    }
+}
+
 // inclusive prefix sums of w_i = exp(alpha rel_i) in FP64: per-chunk sums,
 // their scan (one block, in order), then each chunk's scan from its offset
 constexpr int kCdfChunk = 4096;
@@ -739,6 +749,16 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
     float* d_sc = nullptr;
     double *d_cdf = nullptr, *d_csum = nullptr;
     Scratch tmp(c);
+    if (rel && floor_below > 0.0f) {  // floor per event row: the targets floored once
+        float* tf = nullptr;
+        if ((st = tmp.alloc(&tf, (size_t)n))) return st;
+        LMOSEM_PROF_BEGIN(c);
+        k_row_floor<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(targ, rel, n,
+                                                                                               floor_below, tf);
+        LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+        targ = tf;
+        floor_below = 0.0f;
+    }
     if ((st = tmp.alloc(&w.w1, kH * kInPad)) || (st = tmp.alloc(&w.w234, 3 * kH * kH)) ||
         (st = tmp.alloc(&w.w234t, 3 * kH * kH)) || (st = tmp.alloc(&tb.X, (size_t)B * kInPad)) ||
         (st = tmp.alloc(&tb.H, (size_t)4 * B * kH)) || (st = tmp.alloc(&tb.HT, (size_t)padded_batch(B) * kH)) ||

@@ -322,9 +322,21 @@ __device__ __forceinline__ void cpa_wait(int n) {
     }
 }
 constexpr int kCpaMaxStages = 8;
-// row groups the register pass prefetches into L2 ahead of its loads, unless
-// the context sets another distance
-constexpr int kAutoPrefetch = 0;
+// Row groups the register pass prefetches into L2 ahead of its loads, unless
+// the context sets a distance: for one-row groups (the wide rows), about
+// 48 KB ahead per CTA, as measured on GB300 (ms per OSEM iteration, one box,
+// 1M events at 128x128): FP16 rows (12 KB) 2.50 without, 1.98 / 1.89 / 1.87 /
+// 1.88 / 2.09 ms at 1 / 2 / 4 / 6 / 12 rows ahead; FP32 rows (24 KB) 3.41 ms
+// at 2 rows ahead and 3.47 at 4, against 3.64 for the cp.async ring.  The
+// 64x64 FP32 groups of 4 rows gain nothing (0.266 ms without, 0.267 / 0.269 /
+// 0.281 at 1 / 2 / 4 groups ahead): none there.
+constexpr int64_t kPrefetchBytes = 48 << 10;
+inline int auto_prefetch(int requested, int rows_per_group, int64_t ld_bytes) {
+    if (requested < 0) return 0;
+    if (requested > 0) return requested;
+    if (rows_per_group != 1) return 0;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, (kPrefetchBytes + ld_bytes / 2) / ld_bytes));
+}
 
 template <typename H, int VPT, int R, bool BACK, bool W>
 __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass_cpa(PassArgs A, int S) {
@@ -1136,6 +1148,7 @@ lmosem_status launch_pass_reg_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt)
     A.rows_per_cta = (A.rows_per_cta + R - 1) / R * R;
     grid = std::max<int64_t>(1, (rows + A.rows_per_cta - 1) / A.rows_per_cta);
     c->pass_grid = (int)grid;
+    A.prefetch = auto_prefetch(A.prefetch, R, A.ld_bytes);
     LMOSEM_PROF_BEGIN(c);
     LMOSEM_CK(c, launch_pdl(kern, dim3((unsigned)grid), dim3(nt), 0, c->stream, A));
     LMOSEM_LAUNCHED(c, LMOSEM_K_PASS);
@@ -1176,13 +1189,10 @@ lmosem_status launch_pass_cpa_t(lmosem_ctx* c, PassArgs A, int64_t rows, int nt)
 // bulk-copy ring pass (pass_variant 2)
 template <typename H, int VPT, bool BACK, bool W>
 lmosem_status launch_pass_t(lmosem_ctx* c, PassArgs A0, int64_t rows, int nt) {
-    // automatic: wide FP32 rows (6 or 8 vectors per thread) stream faster
-    // through the cp.async ring (128x128 FP32: 0.98 vs 1.03 ms per iteration,
-    // 90% of HBM); the register pass is faster for every other shape measured
-    // (64x64 FP32 0.25 vs 0.34 ms, 2-byte rows 0.70 vs 0.92 ms at 128x128)
-    constexpr bool kWideF32 = std::is_same<H, float>::value && VPT >= 6;
-    if (c->pass_variant == 3 || (c->pass_variant == 0 && kWideF32))
-        return launch_pass_cpa_t<H, VPT, BACK, W>(c, A0, rows, nt);
+    // automatic: the register pass, with its L2 prefetch for wide rows (at
+    // 128x128 FP32 3.41 ms per iteration against 3.64 for the cp.async ring;
+    // without the prefetch the ring was the faster of the two)
+    if (c->pass_variant == 3) return launch_pass_cpa_t<H, VPT, BACK, W>(c, A0, rows, nt);
     if (c->pass_variant != 2) return launch_pass_reg_t<H, VPT, BACK, W>(c, A0, rows, nt);
     auto kern = k_pass_ring<H, VPT, BACK>;
     // ring shape: stages of G rows (~24 KB), ~96 KB of stages per CTA unless set
@@ -1270,7 +1280,7 @@ lmosem_status launch_pass(lmosem_ctx* c, int64_t r0, int64_t r1, const float* f,
     A.log_T = log(T);
     A.bpart = c->d_bpart;
     A.llpart = c->d_llpart;
-    A.prefetch = c->prefetch_groups < 0 ? 0 : (c->prefetch_groups > 0 ? c->prefetch_groups : kAutoPrefetch);
+    A.prefetch = c->prefetch_groups;  // resolved by the register pass's launch
     if (c->d_weight) {  // binned rows: FP32 only
         if (c->fmt != LMOSEM_MODEL_FP32) return fail(c, LMOSEM_ESTATE, "binned rows are FP32");
         return launch_pass_h<float, BACK, true>(c, A, rows, s);

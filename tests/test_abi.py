@@ -31,7 +31,7 @@ def test_status_strings(lib):
     assert lib.lmosem_status_string(6) == b"called out of order"
 
 
-def _call_create(mu, g, nx=None, pixel=4.0, k_sigma=0.0, support=None):
+def _call_create(mu, g, nx=None, pixel=4.0, k_sigma=0.0, support=None, **knobs):
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     ny, nx0 = mu.shape
     obj = L.Object(nx if nx is not None else nx0, ny, pixel,
@@ -40,6 +40,8 @@ def _call_create(mu, g, nx=None, pixel=4.0, k_sigma=0.0, support=None):
                      g["coll_fwhm0_mm"], g["coll_fwhm_slope"])
     en = L.Energy(g["e0_kev"], g["fwhm_frac_e0"], g["e_lo_kev"], g["e_hi_kev"])
     opt = L.Options(k_sigma, 0)
+    for k, v in knobs.items():
+        setattr(opt, k, v)
     h = ctypes.c_void_p()
     st = L.load().lmosem_create(ctypes.byref(obj), ctypes.byref(geo), ctypes.byref(en),
                                 ctypes.byref(opt), None, ctypes.byref(h))
@@ -137,3 +139,15 @@ def test_device_calls_reject_mismatched_event_arrays():
                  lambda: L.lmosem_build_model_batch(None, a, e, e, [0, 6], 1)):
         with pytest.raises(ValueError):
             call()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(profile=3), dict(pass_variant=5), dict(pass_variant=-1), dict(ring_rows=-1),
+    dict(surrogate_kernel=3), dict(prefetch_groups=-2), dict(prefetch_groups=17),
+])
+def test_create_rejects_bad_tuning_options(lib, bad):
+    """Out-of-range tuning knobs are refused before any device work."""
+    ph = S.disk_phantom()
+    g = S.geometry(32, 16, 8.0, 80.0)
+    st, h = _call_create(ph.mu, g, pixel=ph.pixel_mm, **bad)
+    assert st == L.EINVAL and not h

@@ -475,15 +475,20 @@ def test_cpasync_ring_pass_bitwise(fmt):
     assert np.array_equal(reg["loglik"], cpa["loglik"])
 
 
-def test_wide_fp32_rows_take_the_cpasync_pass_bitwise():
-    """128 x 128 FP32 rows (6 vectors per thread) take the cp.async ring pass
-    automatically; it matches the register pass bit for bit."""
+@pytest.mark.parametrize("fmt", ["fp32", "fp16"])
+def test_wide_rows_prefetch_and_ring_passes_bitwise(fmt):
+    """128 x 128 rows (one row per pipeline step) take the register pass with
+    its L2 prefetch automatically; without the prefetch, at another distance
+    and through the cp.async ring the images and log-likelihoods are the same
+    bits."""
     ph, g, J, ns, ni = S.workload("dat128")
     ev = S.simulate_events(ph, g, 3000, seed=35)
-    auto = gpu_reconstruct(ph, g, ev, ns, 2, loglik=True)
-    reg = gpu_reconstruct(ph, g, ev, ns, 2, loglik=True, pass_variant=1)
-    assert np.array_equal(auto["f"], reg["f"])
-    assert np.array_equal(auto["loglik"], reg["loglik"])
+    auto = gpu_reconstruct(ph, g, ev, ns, 2, fmt=fmt, loglik=True)
+    for kw in (dict(pass_variant=1, prefetch_groups=-1), dict(pass_variant=1, prefetch_groups=7),
+               dict(pass_variant=3)):
+        other = gpu_reconstruct(ph, g, ev, ns, 2, fmt=fmt, loglik=True, **kw)
+        assert np.array_equal(auto["f"], other["f"]), kw
+        assert np.array_equal(auto["loglik"], other["loglik"]), kw
 
 
 def test_introspection_and_error_messages():

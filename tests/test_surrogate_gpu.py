@@ -261,6 +261,36 @@ def test_training_draws_pairs_by_magnitude_weight(L):
     assert 0.8 < last[0.0] < 1.2, last
 
 
+def test_target_floor_per_row_with_row_offsets(L):
+    """target_floor F raises the targets below (largest - F): with the row
+    offsets given, the largest of the same event's row, else the largest of
+    all.  The blob's mean and deviation are those of the floored targets
+    (FP64 sums, no baseline)."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, J, ns, ni = S.workload("tiny16")
+    rng = np.random.default_rng(11)
+    rows, width, F = 256, 64, 5.0
+    t = (rng.uniform(-30.0, 0.0, (rows, 1)) + rng.uniform(-12.0, 0.0, (rows, width))).astype(np.float32)
+    rel = t - t.max(axis=1, keepdims=True)
+    feat = torch.from_numpy(rng.uniform(-1, 1, (rows * width, 6)).astype(np.float32)).to(dev)
+    want = {"row": np.where(rel < -F, t - rel - np.float32(F), t).astype(np.float64),
+            "all": np.maximum(t, t.max() - np.float32(F)).astype(np.float64)}
+    ctx = _ctx(L, ph, g)
+    try:
+        for kind in ("row", "all"):
+            blob = torch.from_numpy(L.pack_surrogate(mlp.init_params(3))).to(dev)
+            L.lmosem_surrogate_train(ctx, feat, torch.from_numpy(t.reshape(-1)).to(dev), blob, steps=1, batch=64,
+                                     target_floor=F,
+                                     d_rel_log=torch.from_numpy(rel.reshape(-1)).to(dev) if kind == "row" else None)
+            _, mu, sigma = L.unpack_surrogate(blob.cpu().numpy())
+            w = want[kind]
+            assert mu == pytest.approx(w.mean(), rel=1e-6), kind
+            assert sigma == pytest.approx(w.std(), rel=1e-5), kind
+    finally:
+        L.lmosem_destroy(ctx)
+
+
 @pytest.fixture(scope="module")
 def trained(L):
     """Surrogate trained on exact scatter sums of 400 events of the 32 x 32
