@@ -52,8 +52,9 @@ WORKLOADS = {
                "1,000,000 list-mode events (100-175 keV, 10% FWHM at 159 keV), 8 subsets x 10 "
                "iterations, model cached in the chosen format, FP32 accumulation"),
     "surrogate128": ("scatter surrogate on the 128x128 DaT-like family (2 mm, 120 angles x 128 bins x 2 mm, "
-                     "R = 150 mm): MLP 6 -> 4 x 256 -> 1 with BF16 weights and FP32 accumulation trained "
-                     "on exact scatter path sums of 32 jittered phantoms (~1M event-pixel pairs each); "
+                     "R = 150 mm): MLP 8 -> 4 x 256 -> 1 with BF16 weights and FP32 accumulation trained "
+                     "on exact scatter path sums of 32 jittered phantoms (~6M event-pixel pairs each), exact rows below an "
+                     "energy cut chosen by the exact judge; "
                      "one step = sensitivity, surrogate model build, 8 subsets x 10 iterations on "
                      "2,000,000 events of a held-out phantom"),
     "windows64": ("energy-window variants (photopeak [143, 175], [120, 175], full [100, 175] keV) of the "
@@ -65,10 +66,10 @@ WORKLOADS = {
                  "count-weighted EM, against list mode; 8 subsets x 10 iterations; ROI-mean NRMSE"),
     "ex2_peak": ("throughput of the exponential unit (ex2.approx.ftz.f32), the bound of the path sum: every SM "
                  "runs 4 CTAs x 512 threads of 8 independent chains (one ex2 and one FP32 add per step)"),
-    "mlp_infer": ("scatter-surrogate inference alone: MLP 6 -> 4 x 256 -> 1, BF16 operands, FP32 accumulation, "
+    "mlp_infer": ("scatter-surrogate inference alone: MLP 8 -> 4 x 256 -> 1, BF16 operands, FP32 accumulation, "
                   "2,000,000 rows of standard-normal inputs (He-initialised weights; the kernel's work does not "
                   "depend on their values), one lmosem_surrogate_infer call per step"),
-    "mlp_train": ("scatter-surrogate training alone: MLP 6 -> 4 x 256 -> 1, BF16 products on the tcgen05 "
+    "mlp_train": ("scatter-surrogate training alone: MLP 8 -> 4 x 256 -> 1, BF16 products on the tcgen05 "
                   "tensor cores with FP32 accumulation, Adam on FP32 parameters; minibatches of 8,192 rows "
                   "drawn from 4,000,000 standard-normal samples; one step = one Adam step (the whole "
                   "lmosem_surrogate_train call of --steps steps is timed)"),
@@ -864,11 +865,12 @@ def run_batch_bench(args):
 # ------------------------------------------------------------------ surrogate form
 
 SURR_TRAIN_SEEDS = tuple(range(1000, 1032))
-SURR_TRAIN_EVENTS = 170            # x ~5,900 support pixels = ~1M (event, pixel) pairs per phantom
+SURR_TRAIN_EVENTS = 1000           # x ~5,900 support pixels = ~6M (event, pixel) pairs per phantom
+SURR_GATE_ROW_TOL = 1e-2           # energy gate: bins whose sampled mean row error exceeds this are exact
 SURR_EVAL_SEED = 2000
 SURR_EVAL_EVENTS = 2_000_000
 SURR_EVAL_CHUNKS = 16
-MLP_FLOPS_PER_PAIR = 2 * (6 * 256 + 3 * 256 * 256 + 256)   # the network's multiply-adds x 2
+MLP_FLOPS_PER_PAIR = 2 * (8 * 256 + 3 * 256 * 256 + 256)   # the network's multiply-adds x 2
 
 
 def surrogate_phantom(seed):
@@ -941,7 +943,7 @@ def run_mlp_bench(args):
     torch.cuda.set_stream(stream)
     rng = np.random.default_rng(1)
     blob = torch.from_numpy(L.surrogate_init(seed=2)).to(dev)
-    X = torch.from_numpy(rng.standard_normal((rows, 6)).astype(np.float32)).to(dev)
+    X = torch.from_numpy(rng.standard_normal((rows, 8)).astype(np.float32)).to(dev)
     y = torch.empty(rows, dtype=torch.float32, device=dev)
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=1)
     try:
@@ -1006,7 +1008,7 @@ def run_mlp_train_bench(args):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     rng = np.random.default_rng(1)
-    feat = torch.from_numpy(rng.standard_normal((n, 6)).astype(np.float32)).to(dev)
+    feat = torch.from_numpy(rng.standard_normal((n, 8)).astype(np.float32)).to(dev)
     targ = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
     try:
@@ -1042,7 +1044,8 @@ def run_mlp_train_bench(args):
 
 def surrogate_baseline(blob, x):
     """The blob's quadratic baseline c . phi(x) of the log scatter at scaled
-    inputs x (n x 6 torch tensor): phi = (1, x_i, x_i x_k for i <= k)."""
+    inputs x (n x 8 torch tensor): phi = (1, x_i, x_i x_k for i <= k <= 6), the
+    first six inputs only."""
     import torch
     nb = 28
     coef = torch.as_tensor(np.asarray(blob[-2 - nb:-2], dtype=np.float64), device=x.device)
@@ -1088,7 +1091,7 @@ def run_surrogate_bench(args):
         ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
         try:
             nsup = L.lmosem_n_support(ctx)
-            feat = torch.empty((len(a) * nsup, 6), dtype=torch.float32, device=dev)
+            feat = torch.empty((len(a) * nsup, L.SURROGATE_INPUTS), dtype=torch.float32, device=dev)
             targ = torch.empty(len(a) * nsup, dtype=torch.float32, device=dev)
             rel = torch.empty(len(a) * nsup, dtype=torch.float32, device=dev)
             L.lmosem_surrogate_samples(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(u).to(dev),
@@ -1127,7 +1130,7 @@ def run_surrogate_bench(args):
         # held out: exact log scatter of 200 events of the evaluation phantom
         nsup = L.lmosem_n_support(ctx)
         hold = 200
-        hf = torch.empty((hold * nsup, 6), dtype=torch.float32, device=dev)
+        hf = torch.empty((hold * nsup, L.SURROGATE_INPUTS), dtype=torch.float32, device=dev)
         ht = torch.empty(hold * nsup, dtype=torch.float32, device=dev)
         L.lmosem_surrogate_samples(ctx, a_d[:hold].contiguous(), u_d[:hold].contiguous(),
                                    e_d[:hold].contiguous(), hf, ht)
@@ -1148,7 +1151,9 @@ def run_surrogate_bench(args):
     last_check = [None]
     rows_ids = torch.arange(0, J, max(1, J // 2000), dtype=torch.int64, device=dev)
 
-    def step(surrogate, a, u, e, profile=0, rows=None, host_out=None):
+    last_gate = [None]
+
+    def step(surrogate, a, u, e, profile=0, rows=None, host_out=None, gate=SURR_GATE_ROW_TOL):
         nonlocal support
         ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile)
         try:
@@ -1157,10 +1162,12 @@ def run_surrogate_bench(args):
                 support = L.lmosem_support(ctx)
             if surrogate:
                 L.lmosem_surrogate_load(ctx, blob)
+                L.lmosem_set_surrogate_gate(ctx, gate)
             L.lmosem_sensitivity(ctx, ns)
             L.lmosem_build_model(ctx, a, u, e, ns, "surrogate" if surrogate else "fp32")
             if surrogate:
                 last_check[0] = L.lmosem_surrogate_check(ctx)
+                last_gate[0] = L.lmosem_surrogate_gate(ctx)
             f = torch.empty(nsup, dtype=torch.float32, device=dev)
             ll = torch.empty(1, dtype=torch.float64, device=dev)
             L.lmosem_init_image(ctx, T, f)
@@ -1205,6 +1212,12 @@ def run_surrogate_bench(args):
     clk = clocks.stop()
     _, (f_sur, ll, _, _) = timed(lambda: step(True, a_d, u_d, e_d, rows=rows_sur))
     f_sur_np = f_sur.double().cpu().numpy()
+    check_gated, gate_gated = last_check[0], last_gate[0]
+    # the network alone (gate off), for the error it leaves without the exact rows
+    rows_net = []
+    _, (f_net, _, _, _) = timed(lambda: step(True, a_d, u_d, e_d, rows=rows_net, gate=0.0))
+    f_net_np = f_net.double().cpu().numpy()
+    check_net = last_check[0]
 
     # ---- end to end through host buffers
     nsup = len(support)
@@ -1220,13 +1233,19 @@ def run_surrogate_bench(args):
     re = rows_exact[0].double()
     rs = rows_sur[0].double()
     row_err = float(torch.linalg.vector_norm(rs - re) / torch.linalg.vector_norm(re))
+    row_err_net = float(torch.linalg.vector_norm(rows_net[0].double() - re) / torch.linalg.vector_norm(re))
     img = lambda f: np.bincount(support, weights=f, minlength=ph.mu.size)
-    roi = {}
-    for name, w in ph.rois.items():
-        w = w.reshape(-1)
-        ref = float(np.dot(w, img(f_exact)) / w.sum())
-        roi[name] = (float(np.dot(w, img(f_sur_np)) / w.sum()) - ref) / ref
+
+    def roi_err(f):
+        out = {}
+        for name, w in ph.rois.items():
+            w = w.reshape(-1)
+            ref = float(np.dot(w, img(f_exact)) / w.sum())
+            out[name] = (float(np.dot(w, img(f)) / w.sum()) - ref) / ref
+        return out
+    roi = roi_err(f_sur_np)
     img_err = float(np.linalg.norm(f_sur_np - f_exact) / np.linalg.norm(f_exact))
+    img_err_net = float(np.linalg.norm(f_net_np - f_exact) / np.linalg.norm(f_exact))
 
     agg = {}
     for p in profs:
@@ -1261,9 +1280,17 @@ def run_surrogate_bench(args):
                                     "exact_path_terms": terms},
         "exact_step_ms": ex_ms,
         "exact_check": {"what": "the library's exact judge of every surrogate build: 512 evenly spaced rows "
-                                "recomputed with the exact path sum; above the tolerance the build falls back "
-                                "to the exact model", "tol": 1e-2, "rows_rel_l2": last_check[0][0],
-                        "worst_row_rel_l2": last_check[0][1], "fell_back_to_exact": last_check[0][2]},
+                                "recomputed with the exact path sum; the energy gate gives the rows of every "
+                                "5 keV bin up to the highest one whose sampled mean row error exceeds its "
+                                "tolerance exact rows; above the check's tolerance the whole build falls back "
+                                "to the exact model", "tol": 1e-2, "gate_row_tol": SURR_GATE_ROW_TOL,
+                        "gate_cut_kev": gate_gated[0], "rows_exact_fraction": gate_gated[1],
+                        "rows_rel_l2": check_gated[0], "worst_row_rel_l2": check_gated[1],
+                        "fell_back_to_exact": check_gated[2]},
+        "network_alone": {"what": "the same build with the gate off (every row from the network)",
+                          "model_rows_rel_l2": row_err_net, "image_rel_l2": img_err_net,
+                          "roi_mean_rel": roi_err(f_net_np), "check_rows_rel_l2": check_net[0],
+                          "check_worst_row_rel_l2": check_net[1]},
         "error_vs_exact": {"model_rows_rel_l2": row_err, "image_rel_l2": img_err,
                            "roi_mean_rel": roi, "rows_sampled": int(rows_ids.numel()),
                            "held_out_scatter_rel_l2": ho_lin,
@@ -1281,7 +1308,7 @@ def run_surrogate_bench(args):
         "roofline": {"bound": "tensor", "kernel": "k_mlp_tc", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_kind": "%s bf16 (sustained)" % pk_kind,
-                     "flops_basis": "%d flops per (event, pixel) pair: 2 x (6x256 + 3x256x256 + 256)"
+                     "flops_basis": "%d flops per (event, pixel) pair: 2 x (8x256 + 3x256x256 + 256)"
                                     % MLP_FLOPS_PER_PAIR},
         "clocks": clk, "gpu_launches": launches,
     }

@@ -149,20 +149,25 @@ typedef enum {
 } lmosem_model_fmt;
 
 /* Scatter surrogate parameters: one FP32 blob of LMOSEM_SURROGATE_PARAMS
- * values, in this order: W1 (256 x 6, row-major, out x in), b1 (256), W2, b2,
+ * values, in this order: W1 (256 x 8, row-major, out x in), b1 (256), W2, b2,
  * W3, b3 (256 x 256, 256), W4, b4, W5 (1 x 256), b5 (1), the 28 coefficients
  * c of a quadratic baseline, mu, sigma.  The network (ReLU after every hidden
- * layer) maps six inputs x, the event and the pixel in the detector frame of
- * the event's angle theta (omega = (cos theta, sin theta), t = (-sin theta,
- * cos theta), p the pixel centre, u_a(p) = p.t):
+ * layer) maps eight inputs x, the event and the pixel in the detector frame
+ * of the event's angle theta (omega = (cos theta, sin theta), t = (-sin theta,
+ * cos theta), p the pixel centre, u_a(p) = p.t, mu the map at E0):
  *   (u - u_a(p)) / 50 mm, p.omega / 100 mm, u_a(p) / 100 mm,
  *   (theta - pi) / pi, (E - 137.5 keV) / 37.5 keV,
- *   (integral of mu(E0) from the pixel centre to the grid edge along omega - 1.5) / 1.5,
+ *   (integral of mu from the pixel centre to the grid edge along omega - 1.5) / 1.5,
+ *   (integral of mu along the event's line {s omega + u t} from s = p.omega
+ *    on, towards the detector - 1.5) / 1.5,
+ *   (integral of mu along that whole line - 1.5) / 1.5,
  * to y with
  *   log p^scat_jn = c . phi(x) + mu + sigma y   (natural log),
- * phi(x) = (1, x_1 .. x_6, x_i x_k for i <= k) in that order.  A blob with
- * zero coefficients is the network alone. */
-#define LMOSEM_SURROGATE_PARAMS 199455
+ * phi(x) = (1, x_1 .. x_6, x_i x_k for i <= k <= 6) in that order.  The two
+ * line integrals are interpolated bilinearly in u and s from exact integrals
+ * at nodes half a pixel apart.  A blob with zero coefficients is the network
+ * alone. */
+#define LMOSEM_SURROGATE_PARAMS 199967
 
 /* Create a context: validate the problem, copy the mu-map and support to the
  * device and build the attenuation tables (integrals of mu along omega_a from
@@ -292,7 +297,7 @@ lmosem_status lmosem_binned_support(lmosem_ctx* ctx, const int32_t* d_angle, con
  * Training samples: builds the exact model of the given events with the
  * primary path left out (replacing any cached model, which is released
  * afterwards) and writes, for every (event k, support pixel q) at row
- * k * N_nz + q: the six scaled inputs (d_features, 6 floats per row) and the
+ * k * N_nz + q: the eight scaled inputs (d_features, 8 floats per row) and the
  * natural log of the exact scatter entry (d_log_scatter; entries below 1e-30
  * are clamped).  d_rel_log (may be NULL) receives each entry's log minus the
  * largest log of its event's row (<= 0), which lmosem_surrogate_train can use
@@ -321,7 +326,7 @@ typedef struct {
                             * (entry / largest entry of its row)^alpha; 0: uniform */
 } lmosem_train_opts;
 
-/* Train the surrogate on n samples (features n x 6, targets n = log scatter,
+/* Train the surrogate on n samples (features n x 8, targets n = log scatter,
  * d_rel_log n or NULL: see lmosem_surrogate_samples and magnitude_power)
  * with the library's tensor-core forward and backward kernels and Adam (FP32
  * parameters and moments, BF16 products, FP32 accumulation).  d_weights holds
@@ -355,7 +360,8 @@ lmosem_status lmosem_surrogate_load(lmosem_ctx* ctx, const float* d_weights);
  * against that sum: n_check_rows sorted rows, evenly spaced over the model
  * (row (k + 1/2) J / K of K, so every subset and angle group is sampled),
  * are rebuilt with the exact path sum and compared with the surrogate's
- * rows.  When the relative L2 error over those rows exceeds tol, the build
+ * rows.  When the relative L2 error over those rows exceeds tol (taken after
+ * the energy gate of lmosem_set_surrogate_gate, when it is on), the build
  * replaces the whole model with the exact path sum.  tol = 0: measure only,
  * never rebuild.  Defaults: tol 1e-2, 512 rows (0 selects 512).  Applies to
  * the builds that follow.  EINVAL: tol negative or not finite, n_check_rows
@@ -371,6 +377,30 @@ lmosem_status lmosem_set_surrogate_check(lmosem_ctx* ctx, double tol, int32_t n_
  * form. */
 lmosem_status lmosem_surrogate_check(const lmosem_ctx* ctx, double* h_rel_err, double* h_row_max,
                                      int32_t* h_exact);
+
+/* Energy gate of the surrogate form: the exact path sum as a per-energy
+ * fallback.  The surrogate replaces the first-order scatter sum of paper Eq. 2
+ * (Section 2.2); its error is largest for events well below the photopeak,
+ * whose rows are almost all scatter, and the EM update (Eq. 8) weighs every
+ * event's row alike.  With row_tol > 0 (and the check of
+ * lmosem_set_surrogate_check on), the check's sampled rows are grouped in
+ * energy bins of bin_kev from the window's lower edge; the highest bin whose
+ * mean per-row relative L2 error exceeds row_tol marks the cut: every model
+ * row whose event energy lies below the top of that bin is rebuilt with the
+ * exact path sum (bitwise the exact build's row), the rest keep the
+ * surrogate's rows, and the check's error is then taken with those rows
+ * exact.  row_tol = 0: off (the default).  bin_kev = 0 selects 5 keV.
+ * Applies to the builds that follow.  EINVAL: a negative or non-finite
+ * argument. */
+lmosem_status lmosem_set_surrogate_gate(lmosem_ctx* ctx, double row_tol, double bin_kev);
+
+/* Result of the energy gate of the current surrogate-form model:
+ * *h_e_cut_kev = the energy below which rows are exact (the window's lower
+ * edge when none are; its upper edge when all are), *h_frac_exact = the
+ * fraction of the model's rows that hold the exact path sum (1 after a whole
+ * rebuild by the check).  Any pointer may be NULL.  ESTATE: the current model
+ * was not built in the surrogate form. */
+lmosem_status lmosem_surrogate_gate(const lmosem_ctx* ctx, double* h_e_cut_kev, double* h_frac_exact);
 
 /* Uniform starting image on the support, T sum_q s_q f_q = J (FP32, N_nz);
  * J is the number of events, or the sum of the counts of a binned model.

@@ -217,6 +217,55 @@ class Problem:
         ix, iy = pix % g.nx, pix // g.nx
         return ((ix + 0.5 - 0.5 * g.nx) * g.pixel_mm, (iy + 0.5 - 0.5 * g.ny) * g.pixel_mm)
 
+    def line_attenuation(self, angle, u_mm, s_mm):
+        """Attenuation inputs of the scatter surrogate: the integral of mu(E0)
+        along the detector line {s omega_a + u t_a} of angle a from depth s
+        on, towards the detector.  Definition (the one the surrogate's
+        inputs use): exact integrals (``ray_to_edge``) at nodes h = half a
+        pixel apart, u_i = -U + i h (U = half the detector extent + 3h/4:
+        no node line runs along a grid line at the axis angles, where the
+        integral would depend on which side of it rounding falls) and
+        s_k = -S + k h (S = half the grid diagonal + h, so s_0 lies before
+        the grid and the node at s_0 is the whole line), interpolated
+        bilinearly; u and s are clamped to [node 0, last node - 1e-3 h].
+        Nodes are computed on demand and cached."""
+        g = self.geom
+        h = 0.5 * g.pixel_mm
+        U = 0.5 * g.n_bins * g.bin_mm + 0.75 * h
+        S = 0.5 * g.pixel_mm * np.hypot(g.nx, g.ny) + h
+        nu, ns = int(np.ceil(2 * U / h)) + 1, int(np.ceil(2 * S / h)) + 1
+        cache = self.__dict__.setdefault("_line_nodes", {})
+
+        def node(a, i, k):
+            key = (a, i, k)
+            if key not in cache:
+                th = g.angle0_rad + 2.0 * np.pi * a / g.n_angles
+                om = (np.cos(th), np.sin(th))
+                u, sk = -U + i * h, -S + k * h
+                p0 = (sk * om[0] - u * om[1], sk * om[1] + u * om[0])
+                cache[key] = ray_to_edge(self.mu, g.pixel_mm, p0, om)
+            return cache[key]
+
+        a_, u_, s_ = np.broadcast_arrays(np.asarray(angle), np.asarray(u_mm, dtype=np.float64),
+                                         np.asarray(s_mm, dtype=np.float64))
+        out = np.empty(a_.shape, dtype=np.float64)
+        for idx in np.ndindex(a_.shape):
+            fu = min(max((u_[idx] + U) / h, 0.0), nu - 1 - 1e-3)
+            fs = min(max((s_[idx] + S) / h, 0.0), ns - 1 - 1e-3)
+            i, k = int(np.floor(fu)), int(np.floor(fs))
+            wu, ws = fu - i, fs - k
+            a = int(a_[idx])
+            lo = (1 - ws) * node(a, i, k) + ws * node(a, i, k + 1)
+            hi = (1 - ws) * node(a, i + 1, k) + ws * node(a, i + 1, k + 1)
+            out[idx] = (1 - wu) * lo + wu * hi
+        return out
+
+    def line_start(self):
+        """Depth of the first line node (before the grid): the whole-line
+        attenuation is ``line_attenuation`` there."""
+        g = self.geom
+        return -(0.5 * g.pixel_mm * np.hypot(g.nx, g.ny) + 0.5 * g.pixel_mm)
+
     def model(self, angle, u_mm, e_kev, primary=True, scatter=True):
         """p[j, q] of every event j and support pixel q (paper Eq. 2 with
         Eq. 4: pr(A_j|P) s_eff(P) summed over the primary path and every

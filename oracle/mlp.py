@@ -2,18 +2,22 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  The surrogate replaces
 the sum over scatter pixels of the path model (paper Eq. 2 restricted to the
-first-order paths of Section 2.2) by a learned function of six inputs:
+first-order paths of Section 2.2) by a learned function of eight inputs:
 
     pixel x, pixel y, detector angle, event position u, event energy E,
     attenuation from the pixel to the detector along the detector direction,
+    attenuation along the event's detector line from the pixel's depth on,
+    attenuation along that whole line,
 
 encoded in the detector frame of the angle (``features`` below): the event's
 offset from the pixel's projection u - u_a(p), the pixel's coordinate along
 the flight direction p . omega_a, its projection u_a(p) = p . t_a, the
-angle, the energy and the attenuation, each mapped to O(1) by a fixed affine
-scaling.  The encoding is a bijection of the six inputs; it puts the
-quantity the scatter term varies fastest with (the offset) on one axis.
-Architecture: 6 -> 256 -> 256 -> 256 -> 256 -> 1, ReLU after every hidden
+angle, the energy and the three attenuations, each mapped to O(1) by a fixed
+affine scaling.  The offset puts the quantity the scatter term varies
+fastest with on one axis; the two line attenuations describe the object
+along the line on which the event's scatter points lie (the callers take
+them from ``Problem.line_attenuation``).
+Architecture: 8 -> 256 -> 256 -> 256 -> 256 -> 1, ReLU after every hidden
 layer, linear output; the output is the standardised natural log of the
 scatter part of p_jn.  Parameters: W_l (out x in, row-major), b_l (out).
 Training: mean squared error, Adam (Kingma & Ba 2015: bias-corrected first
@@ -25,18 +29,21 @@ from __future__ import annotations
 
 import numpy as np
 
-LAYERS = (6, 256, 256, 256, 256, 1)
+LAYERS = (8, 256, 256, 256, 256, 1)
 
-def features(x_mm, y_mm, theta, u_mm, e_kev, atten):
-    """Scaled network inputs (..., 6) of pixel centres (x, y), angles theta
+def features(x_mm, y_mm, theta, u_mm, e_kev, atten, line_from, line_total):
+    """Scaled network inputs (..., 8) of pixel centres (x, y), angles theta
     (flight direction omega = (cos, sin), lateral axis t = (-sin, cos)),
-    event positions u, energies E and pixel-to-detector attenuation."""
+    event positions u, energies E, pixel-to-detector attenuation, and the
+    attenuation along the event's detector line from the pixel's depth on
+    and along the whole line."""
     x, y, th = (np.asarray(v, dtype=np.float64) for v in (x_mm, y_mm, theta))
     u_a = -x * np.sin(th) + y * np.cos(th)
     s_a = x * np.cos(th) + y * np.sin(th)
-    u, e, att = (np.asarray(v, dtype=np.float64) for v in (u_mm, e_kev, atten))
+    u, e, att, lf, lt = (np.asarray(v, dtype=np.float64) for v in (u_mm, e_kev, atten, line_from, line_total))
     return np.stack(np.broadcast_arrays((u - u_a) / 50.0, s_a / 100.0, u_a / 100.0, (th - np.pi) / np.pi,
-                                        (e - 137.5) / 37.5, (att - 1.5) / 1.5), axis=-1)
+                                        (e - 137.5) / 37.5, (att - 1.5) / 1.5, (lf - 1.5) / 1.5,
+                                        (lt - 1.5) / 1.5), axis=-1)
 
 
 def init_params(seed=0, layers=LAYERS):

@@ -116,20 +116,67 @@ lmosem_status check_events_args(lmosem_ctx* c, const int32_t* d_angle, const flo
     return LMOSEM_OK;
 }
 
-// The surrogate rows against the exact path sum on a sample of rows; above
-// the tolerance the whole model is rebuilt exactly.
+// The surrogate rows against the exact path sum on a sample of rows.  With
+// the energy gate on, the sampled rows are grouped in energy bins; the
+// highest bin whose mean per-row relative L2 error exceeds the gate's
+// tolerance, and every bin below it, take exact rows, and the check's error
+// is recomputed with those rows exact.  Above the check's tolerance the whole
+// model is rebuilt exactly.
 lmosem_status check_surrogate(lmosem_ctx* c) {
     double err = 0.0, mx = 0.0;
-    lmosem_status st = judge_surrogate(c, &err, &mx);
+    std::vector<double> sums;
+    std::vector<float> ev;
+    lmosem_status st = judge_surrogate(c, &err, &mx, &sums, &ev);
     if (st) return st;
     c->sur_checked = true;
+    c->sur_exact = false;
+    c->sur_cut = c->e_lo;
+    c->sur_frac_exact = 0.0;
+    if (c->sur_tol > 0.0 && c->sur_gate_tol > 0.0) {
+        const int nb = std::max(1, (int)ceil((c->e_hi - c->e_lo) / c->sur_gate_bin - 1e-9));
+        std::vector<double> esum(nb, 0.0);
+        std::vector<int> cnt(nb, 0);
+        const int64_t K = (int64_t)ev.size();
+        auto bin_of = [&](float e) {
+            return std::min(nb - 1, std::max(0, (int)floor(((double)e - c->e_lo) / c->sur_gate_bin)));
+        };
+        for (int64_t k = 0; k < K; ++k) {
+            const double d2 = sums[2 * k], e2 = sums[2 * k + 1];
+            const double r = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
+            const int b = bin_of(ev[k]);
+            esum[b] += r;
+            ++cnt[b];
+        }
+        int top = -1;  // highest failing bin (a NaN mean fails)
+        for (int b = 0; b < nb; ++b)
+            if (cnt[b] > 0 && !(esum[b] / cnt[b] <= c->sur_gate_tol)) top = b;
+        if (top >= 0) {
+            const double cut = top + 1 >= nb ? INFINITY : c->e_lo + (top + 1) * c->sur_gate_bin;
+            int64_t n_exact = 0;
+            if ((st = rebuild_rows_below(c, cut, &n_exact))) return st;
+            c->sur_cut = std::min(cut, c->e_hi);
+            c->sur_frac_exact = (double)n_exact / (double)c->J;
+            c->sur_exact = n_exact == c->J;
+            double d2 = 0.0, e2 = 0.0;
+            mx = 0.0;
+            for (int64_t k = 0; k < K; ++k) {
+                e2 += sums[2 * k + 1];
+                if ((double)ev[k] < cut) continue;  // now an exact row
+                d2 += sums[2 * k];
+                if (sums[2 * k + 1] > 0.0) mx = std::max(mx, sqrt(sums[2 * k] / sums[2 * k + 1]));
+                else if (sums[2 * k] > 0.0) mx = INFINITY;
+            }
+            err = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
+        }
+    }
     c->sur_err = err;
     c->sur_row_max = mx;
-    c->sur_exact = false;
     if (c->sur_tol > 0.0 && !(err <= c->sur_tol)) {  // a NaN error rebuilds too
         c->use_surrogate = false;
         if ((st = build_model_rows(c))) return st;
         c->sur_exact = true;
+        c->sur_cut = c->e_hi;
+        c->sur_frac_exact = 1.0;
     }
     return LMOSEM_OK;
 }
@@ -234,6 +281,7 @@ void lmosem_destroy(lmosem_ctx* c) {
     dev_free(c, &c->d_scat_geo);
     dev_free(c, &c->d_trig);
     dev_free(c, &c->d_l_edge);
+    dev_free(c, &c->d_line);
     dev_free(c, &c->d_l_pair);
     dev_free(c, &c->d_compton);
     dev_free(c, &c->d_mpar);
@@ -811,6 +859,23 @@ lmosem_status lmosem_surrogate_check(const lmosem_ctx* c, double* h_rel_err, dou
     if (h_rel_err) *h_rel_err = c->sur_err;
     if (h_row_max) *h_row_max = c->sur_row_max;
     if (h_exact) *h_exact = c->sur_exact ? 1 : 0;
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_set_surrogate_gate(lmosem_ctx* c, double row_tol, double bin_kev) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!(row_tol >= 0.0) || !isfinite(row_tol) || !(bin_kev >= 0.0) || !isfinite(bin_kev))
+        return fail(c, LMOSEM_EINVAL, "need row_tol >= 0 and bin_kev >= 0 (finite)");
+    c->sur_gate_tol = row_tol;
+    c->sur_gate_bin = bin_kev > 0.0 ? bin_kev : 5.0;
+    return LMOSEM_OK;
+}
+
+lmosem_status lmosem_surrogate_gate(const lmosem_ctx* c, double* h_e_cut_kev, double* h_frac_exact) {
+    if (!c) return LMOSEM_EINVAL;
+    if (!c->sur_checked) return LMOSEM_ESTATE;
+    if (h_e_cut_kev) *h_e_cut_kev = c->sur_cut;
+    if (h_frac_exact) *h_frac_exact = c->sur_frac_exact;
     return LMOSEM_OK;
 }
 

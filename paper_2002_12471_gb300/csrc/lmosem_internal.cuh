@@ -111,6 +111,10 @@ struct lmosem_ctx {
     size_t coop_words = 0;
     // scatter surrogate
     float* d_surrogate = nullptr;             // LMOSEM_SURROGATE_PARAMS FP32 parameters
+    float* d_line = nullptr;                  // surrogate inputs: [a][iu][is] mu(E0) integrated along the
+                                              // detector line u_i from depth s_k to the detector
+    int line_nu = 0, line_ns = 0;
+    double line_u0 = 0, line_s0 = 0, line_h = 0;
     bool scatter_only = false;                // model build leaves the primary path out
     bool use_surrogate = false;               // model build takes the scatter part from the MLP
     int surrogate_kernel = 0;                 // inference: 0 auto (fused tcgen05), 1 product chain, 2 fused
@@ -122,6 +126,11 @@ struct lmosem_ctx {
     bool sur_checked = false;                 // a surrogate build has been checked
     double sur_err = 0.0, sur_row_max = 0.0;  // rel-L2 of the sampled rows; largest per-row rel-L2
     bool sur_exact = false;                   // the check rebuilt the model with the exact path sum
+    double sur_gate_tol = 0.0;                // energy gate: per-bin mean row error above which the
+                                              // bin's rows (and every lower one) are exact (0: off)
+    double sur_gate_bin = 5.0;                // energy bin width of the gate, keV
+    double sur_cut = 0.0;                     // rows with E below this energy hold exact rows
+    double sur_frac_exact = 0.0;              // fraction of the model's rows that are exact
     // batching form: per-realisation work words, partial slots, tiles, graph
     bool batch_model = false;
     int64_t* d_bsub_row0 = nullptr;           // n_real * (n_subsets + 1)
@@ -177,12 +186,15 @@ void prof_end(lmosem_ctx* c, int cls);
         if ((ctx)->profile) ::lmosem::prof_begin(ctx); \
     } while (0)
 
+#define LMOSEM_STR2(x) #x
+#define LMOSEM_STR(x) LMOSEM_STR2(x)
 #define LMOSEM_LAUNCHED(ctx, cls)                                              \
     do {                                                                       \
         (ctx)->launches++;                                                     \
         if ((ctx)->profile) ::lmosem::prof_end(ctx, cls);                      \
         cudaError_t e_ = cudaGetLastError();                                   \
-        if (e_ != cudaSuccess) return ::lmosem::cuda_fail(ctx, e_, "launch");  \
+        if (e_ != cudaSuccess)                                                 \
+            return ::lmosem::cuda_fail(ctx, e_, "launch at " __FILE__ ":" LMOSEM_STR(__LINE__)); \
     } while (0)
 
 // Device memory of a context is stream-ordered on the context's stream
@@ -224,22 +236,24 @@ public:
     Scratch(const Scratch&) = delete;
     Scratch& operator=(const Scratch&) = delete;
     ~Scratch() {
-        for (void** p : owned_)
-            if (*p) {
-                cudaFreeAsync(*p, c_->stream);
-                *p = nullptr;
-            }
+        for (void* p : owned_)
+            if (p) cudaFreeAsync(p, c_->stream);
     }
+    // the allocation itself is recorded, not the caller's pointer variable,
+    // which may go out of scope before the Scratch does
     template <typename T>
     lmosem_status alloc(T** p, size_t count) {
+        void* old = reinterpret_cast<void*>(*p);  // dev_alloc frees it
+        for (void*& q : owned_)
+            if (old && q == old) q = nullptr;
         lmosem_status st = dev_alloc(c_, p, count);
-        if (st == LMOSEM_OK) owned_.push_back(reinterpret_cast<void**>(p));
+        if (st == LMOSEM_OK) owned_.push_back(reinterpret_cast<void*>(*p));
         return st;
     }
 
 private:
     lmosem_ctx* c_;
-    std::vector<void**> owned_;
+    std::vector<void*> owned_;
 };
 
 // ---- host entry points implemented in the other translation units
@@ -294,7 +308,9 @@ lmosem_status build_model_surrogate(lmosem_ctx* c);
 // model.cu: exact rows of an evenly spaced sample of the model's events
 // against the rows the surrogate built (relative L2 over the sampled rows,
 // and the largest per-row value); synchronises
-lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max);
+lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max, std::vector<double>* row_sums,
+                              std::vector<float>* row_e);
+lmosem_status rebuild_rows_below(lmosem_ctx* c, double e_cut, int64_t* n_rebuilt);
 // mlp_tc.cu: fused tcgen05 inference of M rows of BF16 inputs (M x 16)
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
                          const unsigned char* w234img, const __nv_bfloat16* X, float* y, int64_t M);

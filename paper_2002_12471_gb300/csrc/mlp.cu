@@ -3,12 +3,14 @@
 // The first-order scatter part of the per-event path sum (paper Eq. 2 over
 // the scatter paths of Section 2.2),
 //     p^scat_jn = sum_{m in strip(j)} U_jm W_a(n, m) phi(E_j; E'_a(n, m), sigma_E),
-// is replaced by a multilayer perceptron of six inputs (pixel x, y, detector
-// angle, event position, event energy, attenuation from the pixel to the
-// detector), 6 -> 256 -> 256 -> 256 -> 256 -> 1 with ReLU, whose output is the
-// standardised natural log of p^scat_jn.  The network is trained on exact
-// scatter path sums made by the exact path (k_pathsum with the primary left
-// out) and evaluated inside the model build, where p_jn = primary_jn +
+// is replaced by a multilayer perceptron of eight inputs (pixel x, y,
+// detector angle, event position, event energy, and three attenuation
+// features: mu(E0) integrated from the pixel to the detector, along the
+// event's detector line from the pixel's depth to the detector, and along
+// that whole line), 8 -> 256 -> 256 -> 256 -> 256 -> 1 with ReLU, whose output
+// is the standardised natural log of p^scat_jn.  The network is trained on
+// exact scatter path sums made by the exact path (k_pathsum with the primary
+// left out) and evaluated inside the model build, where p_jn = primary_jn +
 // exp(mu + sigma y_jn).
 //
 // Matrix products run on the 5th-generation tensor cores (tcgen05, the
@@ -29,7 +31,8 @@ namespace lmosem {
 
 namespace {
 
-constexpr int kIn = 6, kInPad = 16, kH = 256;
+constexpr int kIn = 8, kInPad = 16, kH = 256;
+constexpr int kBaseIn = 6;  // inputs of the quadratic baseline (the first six)
 constexpr int64_t kOffW1 = 0;
 constexpr int64_t kOffB1 = kOffW1 + kH * kIn;
 constexpr int64_t kOffW2 = kOffB1 + kH;
@@ -40,25 +43,27 @@ constexpr int64_t kOffW4 = kOffB3 + kH;
 constexpr int64_t kOffB4 = kOffW4 + kH * kH;
 constexpr int64_t kOffW5 = kOffB4 + kH;
 constexpr int64_t kOffB5 = kOffW5 + kH;
-// coefficients of the quadratic baseline of the log target in the six scaled
-// inputs (1, x_i, x_i x_j for i <= j): 28 values, fitted by least squares, or
-// zero; the network learns the standardised residual
+// coefficients of the quadratic baseline of the log target in the first six
+// scaled inputs (1, x_i, x_i x_j for i <= j): 28 values, fitted by least
+// squares, or zero; the network learns the standardised residual
 constexpr int kBasis = 28;
 constexpr int64_t kOffBase = kOffB5 + 1;
 constexpr int64_t kOffMu = kOffBase + kBasis;
 constexpr int64_t kOffSigma = kOffMu + 1;
 constexpr int64_t kParams = kOffSigma + 1;
 static_assert(kParams == LMOSEM_SURROGATE_PARAMS, "parameter blob layout");
+static_assert(kBasis == 1 + kBaseIn + kBaseIn * (kBaseIn + 1) / 2, "quadratic basis size");
+static_assert(kIn <= kInPad, "inputs fit the padded operand");
 
 __device__ __forceinline__ void basis(const float* x, float* phi) {
     phi[0] = 1.0f;
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) phi[1 + i] = x[i];
-    int k = 1 + kIn;
+    for (int i = 0; i < kBaseIn; ++i) phi[1 + i] = x[i];
+    int k = 1 + kBaseIn;
 #pragma unroll
-    for (int i = 0; i < kIn; ++i)
+    for (int i = 0; i < kBaseIn; ++i)
 #pragma unroll
-        for (int j = i; j < kIn; ++j) phi[k++] = x[i] * x[j];
+        for (int j = i; j < kBaseIn; ++j) phi[k++] = x[i] * x[j];
 }
 
 // the baseline of the log scatter at scaled inputs x (FP32)
@@ -357,12 +362,29 @@ struct FeatArgs {
     float dpx;
     const float* l_edge;     // [a][pixel]
     float angle0, dtheta;
+    const float* line;       // [a][iu][is]: mu(E0) integrated from depth s to the detector along u
+    int line_nu, line_ns;
+    float line_u0, line_s0, line_inv_h;
 };
+
+// attenuation along the detector line u of angle a from depth s on (bilinear
+// in the table's nodes; u and s clamped to the table)
+__device__ __forceinline__ float line_att(const FeatArgs& F, int a, float u, float s) {
+    const float fu = fminf(fmaxf((u - F.line_u0) * F.line_inv_h, 0.0f), (float)(F.line_nu - 1) - 1e-3f);
+    const float fs = fminf(fmaxf((s - F.line_s0) * F.line_inv_h, 0.0f), (float)(F.line_ns - 1) - 1e-3f);
+    const int iu = (int)fu, is = (int)fs;
+    const float wu = fu - (float)iu, ws = fs - (float)is;
+    const float* t = F.line + ((size_t)a * F.line_nu + iu) * F.line_ns + is;
+    const float lo = fmaf(ws, t[1] - t[0], t[0]);
+    const float hi = fmaf(ws, t[F.line_ns + 1] - t[F.line_ns], t[F.line_ns]);
+    return fmaf(wu, hi - lo, lo);
+}
 
 // network inputs in the detector frame of the event's angle: offset of the
 // event from the pixel's projection, the pixel's coordinate along the flight
-// direction and its projection, the angle, the energy and the pixel-to-
-// detector attenuation, each scaled to O(1)
+// direction and its projection, the angle, the energy, the pixel-to-detector
+// attenuation, and the attenuation along the event's detector line from the
+// pixel's depth to the detector and along the whole line, each scaled to O(1)
 __device__ __forceinline__ void features(const FeatArgs& F, int64_t row, int q, float* out) {
     const int a = F.a_s[row];
     const int pix = F.sup[q];
@@ -372,12 +394,70 @@ __device__ __forceinline__ void features(const FeatArgs& F, int64_t row, int q, 
     sincosf(th, &sn, &cs);
     const float u_a = -x * sn + y * cs;
     const float s_a = x * cs + y * sn;
-    out[0] = (F.u_s[row] - u_a) / 50.0f;
+    const float u = F.u_s[row];
+    out[0] = (u - u_a) / 50.0f;
     out[1] = s_a / 100.0f;
     out[2] = u_a / 100.0f;
     out[3] = (th - 3.14159265358979f) / 3.14159265358979f;
     out[4] = (F.e_s[row] - 137.5f) / 37.5f;
     out[5] = (F.l_edge[(size_t)a * F.npix + pix] - 1.5f) / 1.5f;
+    out[6] = (line_att(F, a, u, s_a) - 1.5f) / 1.5f;
+    out[7] = (line_att(F, a, u, F.line_s0) - 1.5f) / 1.5f;
+}
+
+// Attenuation along detector lines: for angle a, lateral position
+// u_i = u0 + i h and depth s_k = s0 + k h (point s omega_a + u t_a), the
+// integral of the piecewise-constant mu(E0) map from s_k to the end of the
+// line (beyond the grid), i.e. towards the detector.  One thread walks one
+// line from s0 upwards through the merged sequences of vertical and
+// horizontal grid-line crossings and table nodes, adding mu times the length
+// of every piece (the pixel of a piece from its midpoint), in FP64: the node
+// values are exact integrals of the map up to rounding.
+__global__ void k_line_table(const float* __restrict__ mu, int nx, int ny, double dpx, int n_angles,
+                             double angle0, int nu, int ns, double u0, double s0, double h,
+                             float* __restrict__ out) {
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= n_angles * nu) return;
+    const int a = line / nu, iu = line % nu;
+    const double th = angle0 + 2.0 * kPi * a / n_angles;
+    const double c = cos(th), sn = sin(th);
+    const double u = u0 + iu * h;
+    const double xmin = -0.5 * nx * dpx, ymin = -0.5 * ny * dpx;
+    // x(s) = s c - u sn, y(s) = s sn + u c; the k-th crossing of an axis's
+    // grid lines comes at an s that increases with k
+    const bool hx = fabs(c) > 1e-12, hy = fabs(sn) > 1e-12;
+    auto sx = [&](int k) { const int i = c > 0 ? k : nx - k; return (xmin + i * dpx + u * sn) / c; };
+    auto sy = [&](int k) { const int i = sn > 0 ? k : ny - k; return (ymin + i * dpx - u * c) / sn; };
+    float* row = out + (size_t)line * ns;
+    // pass 0: the whole line's integral; pass 1: integral from each node on
+    double total = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int kx = 0, ky = 0;
+        double cur = s0, acc = 0.0;
+        for (int k = 0; k < ns;) {
+            double nxt = s0 + k * h;
+            if (hx && kx <= nx && sx(kx) < nxt) nxt = sx(kx);
+            if (hy && ky <= ny && sy(ky) < nxt) nxt = sy(ky);
+            if (nxt > cur) {
+                const double mid = 0.5 * (cur + nxt);
+                const double px = mid * c - u * sn, py = mid * sn + u * c;
+                const int ix = (int)floor((px - xmin) / dpx), iy = (int)floor((py - ymin) / dpx);
+                if (ix >= 0 && ix < nx && iy >= 0 && iy < ny) acc += (double)mu[(size_t)iy * nx + ix] * (nxt - cur);
+                cur = nxt;
+            }
+            if (hx && kx <= nx && sx(kx) <= cur) {
+                ++kx;
+                continue;
+            }
+            if (hy && ky <= ny && sy(ky) <= cur) {
+                ++ky;
+                continue;
+            }
+            if (pass == 1) row[k] = (float)(total - acc);  // integral over [s_k, end)
+            ++k;
+        }
+        total = acc;  // the last node lies beyond the grid
+    }
 }
 
 // training samples: scaled features and log of the exact scatter entry for
@@ -748,9 +828,9 @@ lmosem_status run_surrogate_train(lmosem_ctx* c, const float* feat, const float*
     int* d_step = nullptr;
     float* d_sc = nullptr;
     double *d_cdf = nullptr, *d_csum = nullptr;
+    float* tf = nullptr;  // (Scratch keeps the address of the pointer: same scope as tmp)
     Scratch tmp(c);
     if (rel && floor_below > 0.0f) {  // floor per event row: the targets floored once
-        float* tf = nullptr;
         if ((st = tmp.alloc(&tf, (size_t)n))) return st;
         LMOSEM_PROF_BEGIN(c);
         k_row_floor<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(targ, rel, n,
@@ -880,8 +960,39 @@ lmosem_status run_surrogate_infer(lmosem_ctx* c, const float* blob, const float*
     return st;
 }
 
+// The detector-line attenuation table of the surrogate's inputs (built once
+// per context): nodes h = half a pixel apart across the detector extent,
+// starting 3h/4 before it (so that no node line runs along a grid line at
+// the axis angles), and along a line's whole crossing of the grid.
+lmosem_status ensure_line_table(lmosem_ctx* c) {
+    if (c->d_line) return LMOSEM_OK;
+    const double h = 0.5 * c->dpx;
+    const double U = 0.5 * c->n_bins * c->bin_mm + 0.75 * h;
+    const double S = 0.5 * c->dpx * sqrt((double)c->nx * c->nx + (double)c->ny * c->ny) + h;
+    const int nu = (int)ceil(2.0 * U / h) + 1, ns = (int)ceil(2.0 * S / h) + 1;
+    lmosem_status st;
+    if ((st = dev_alloc(c, &c->d_line, (size_t)c->n_angles * nu * ns))) return st;
+    c->line_nu = nu;
+    c->line_ns = ns;
+    c->line_u0 = -U;
+    c->line_s0 = -S;
+    c->line_h = h;
+    const int lines = c->n_angles * nu;
+    LMOSEM_PROF_BEGIN(c);
+    k_line_table<<<(lines + 127) / 128, 128, 0, c->stream>>>(c->d_mu, c->nx, c->ny, c->dpx, c->n_angles, c->angle0,
+                                                             nu, ns, -U, -S, h, c->d_line);
+    LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
+    return LMOSEM_OK;
+}
+
 FeatArgs feat_args(lmosem_ctx* c) {
     FeatArgs F;
+    F.line = c->d_line;
+    F.line_nu = c->line_nu;
+    F.line_ns = c->line_ns;
+    F.line_u0 = (float)c->line_u0;
+    F.line_s0 = (float)c->line_s0;
+    F.line_inv_h = (float)(1.0 / c->line_h);
     F.a_s = c->d_a_s;
     F.u_s = c->d_u_s;
     F.e_s = c->d_e_s;
@@ -901,6 +1012,8 @@ FeatArgs feat_args(lmosem_ctx* c) {
 // current (scatter-only, FP32) model, in the caller's event order
 lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ, float* rel) {
     const int64_t total = c->J * c->n_sup;
+    lmosem_status st;
+    if ((st = ensure_line_table(c))) return st;
     // the sort's rank maps the caller's event k to its model row
     LMOSEM_PROF_BEGIN(c);
     k_samples<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
@@ -918,6 +1031,7 @@ lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ, flo
 lmosem_status build_model_surrogate(lmosem_ctx* c) {
     lmosem_status st;
     if ((st = gemm_tc_setup(c))) return st;
+    if ((st = ensure_line_table(c))) return st;
     // pairs per chunk: the product chain keeps two 256-wide BF16 activations
     // per pair in HBM, the fused tcgen05 kernel none
     const int64_t max_pairs = int64_t(1) << (c->surrogate_kernel == 1 ? 20 : 24);

@@ -39,9 +39,12 @@ constexpr uint32_t kWChunkBytes = kH * kChunkK * 2;       // 16 KB
 constexpr uint32_t kAChunkBytes = kTileM * kChunkK * 2;   // 8 KB
 constexpr uint32_t kABytes = kChunks * kAChunkBytes;      // 64 KB per tile
 constexpr long long kDrainCycles = 1LL << 31;             // waits for in-flight work after an abort
-constexpr int64_t kOffB1 = 256 * 6, kOffW2 = kOffB1 + 256, kOffB2 = kOffW2 + 256 * 256;
+constexpr int kBlobIn = 8;  // network inputs (first-layer columns in the blob)
+constexpr int64_t kOffB1 = 256 * kBlobIn, kOffW2 = kOffB1 + 256, kOffB2 = kOffW2 + 256 * 256;
 constexpr int64_t kLayerStride = 256 * 256 + 256;
 constexpr int64_t kOffW5 = kOffW2 + 3 * kLayerStride, kOffB5 = kOffW5 + 256;
+// the blob ends with the 28 baseline coefficients, mu and sigma
+static_assert(kOffB5 + 1 + 28 + 2 == LMOSEM_SURROGATE_PARAMS, "parameter blob layout");
 
 // Operand layouts (canonical K-major, no swizzle; core matrix = 8 rows x 16 B):
 //  * K = 16 operands (inputs, first-layer weights): row group g of 8 rows at

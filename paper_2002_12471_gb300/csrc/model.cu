@@ -1217,49 +1217,44 @@ __global__ void __launch_bounds__(256) k_judge_rows(const float* __restrict__ mo
 
 }  // namespace
 
-// The exact judge of a surrogate build: K sorted rows evenly spaced over the
-// model ((k + 1/2) J / K, so every subset and angle group is sampled) are
-// rebuilt with the exact path sum into scratch rows, by running the exact
-// row build on the sample in place of the model's events, and compared with
-// the surrogate's rows.
-lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max) {
-    const int64_t J = c->J;
-    const int64_t K = std::min<int64_t>(J, c->sur_check_rows);
-    std::vector<int64_t> rows(K);
-    for (int64_t k = 0; k < K; ++k) rows[k] = (int64_t)(((double)k + 0.5) * (double)J / (double)K);
+// Exact FP32 rows (primary and every first-order scatter path) of K sorted
+// model rows h_rows (increasing; d_rows their device copy) into d_out
+// (K x ld_model): the rows' events are gathered and built by the exact path
+// sum in place of the model's events, and the model's event state is put back
+// after.  The rows of a (realisation, angle) stay contiguous in the sample,
+// and a row's bits do not depend on the other events of its tiles, so every
+// row equals the one the exact build of all events gives.  h_e (K floats, may
+// be NULL) receives the rows' event energies.
+lmosem_status exact_rows(lmosem_ctx* c, const std::vector<int64_t>& h_rows, const int64_t* d_rows, float* d_out,
+                         float* h_e) {
+    const int64_t K = (int64_t)h_rows.size();
+    if (K == 0) return LMOSEM_OK;
     lmosem_status st;
-    int64_t* d_rows = nullptr;
     int32_t* d_a = nullptr;
-    float *d_u = nullptr, *d_e = nullptr, *d_ex = nullptr;
-    double* d_sums = nullptr;
+    float *d_u = nullptr, *d_e = nullptr;
     Scratch tmp(c);
-    if ((st = tmp.alloc(&d_rows, K)) || (st = tmp.alloc(&d_a, K)) || (st = tmp.alloc(&d_u, K)) ||
-        (st = tmp.alloc(&d_e, K)) || (st = tmp.alloc(&d_ex, (size_t)K * c->ld_model)) ||
-        (st = tmp.alloc(&d_sums, 2 * K)))
-        return st;
-    LMOSEM_CK(c, cudaMemcpyAsync(d_rows, rows.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    if ((st = tmp.alloc(&d_a, K)) || (st = tmp.alloc(&d_u, K)) || (st = tmp.alloc(&d_e, K))) return st;
     LMOSEM_PROF_BEGIN(c);
     k_judge_gather<<<(unsigned)((K + 255) / 256), 256, 0, c->stream>>>(c->d_a_s, c->d_u_s, c->d_e_s, d_rows, K,
                                                                         d_a, d_u, d_e);
     LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
     std::vector<int32_t> h_a(K);
     LMOSEM_CK(c, cudaMemcpyAsync(h_a.data(), d_a, K * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    if (h_e) LMOSEM_CK(c, cudaMemcpyAsync(h_e, d_e, K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
-    // rows of every (realisation, angle) of the sample: contiguous, since the
-    // sample keeps the model's sorted order
     std::vector<int64_t> s_row0((size_t)c->n_real * c->n_angles, 0), s_cnt((size_t)c->n_real * c->n_angles, 0);
+    int r = 0;
     for (int64_t k = 0; k < K; ++k) {
-        int r = 0;
-        while (r + 1 < c->n_real && rows[k] >= c->h_real_row0[r + 1]) ++r;
+        while (r + 1 < c->n_real && h_rows[k] >= c->h_real_row0[r + 1]) ++r;
         const size_t i = (size_t)r * c->n_angles + h_a[k];
         if (s_cnt[i]++ == 0) s_row0[i] = k;
     }
-    // the exact build on the sample, with the model's event state put back after
     const int64_t J0 = c->J;
     int32_t* a0 = c->d_a_s;
     float *u0 = c->d_u_s, *e0 = c->d_e_s;
     void* m0 = c->d_model;
     const int fmt0 = c->fmt;
+    const bool sur0 = c->use_surrogate;
     std::vector<int64_t> row0_0, cnt0;
     row0_0.swap(c->h_angle_row0);
     cnt0.swap(c->h_angle_cnt);
@@ -1269,11 +1264,11 @@ lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max) {
     c->d_a_s = d_a;
     c->d_u_s = d_u;
     c->d_e_s = d_e;
-    c->d_model = d_ex;
+    c->d_model = d_out;
     c->fmt = LMOSEM_MODEL_FP32;
     c->use_surrogate = false;
     st = build_model_rows(c);
-    c->use_surrogate = true;
+    c->use_surrogate = sur0;
     c->fmt = fmt0;
     c->d_model = m0;
     c->d_e_s = e0;
@@ -1282,7 +1277,44 @@ lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max) {
     c->J = J0;
     c->h_angle_row0.swap(row0_0);
     c->h_angle_cnt.swap(cnt0);
-    if (st) return st;
+    return st;
+}
+
+namespace {
+
+// model row rows[k] <- src row k (FP32, ld4 float4 per row)
+__global__ void k_scatter_rows(const float4* __restrict__ src, const int64_t* __restrict__ rows, int64_t ld4,
+                               float4* __restrict__ model) {
+    const int64_t k = blockIdx.x;
+    const float4* in = src + k * ld4;
+    float4* out = model + rows[k] * ld4;
+    for (int64_t i = threadIdx.x; i < ld4; i += blockDim.x) out[i] = in[i];
+}
+
+}  // namespace
+
+// The exact judge of a surrogate build: K sorted rows evenly spaced over the
+// model ((k + 1/2) J / K, so every subset and angle group is sampled) are
+// rebuilt with the exact path sum into scratch rows and compared with the
+// surrogate's rows.  row_sums (2K: squared difference and squared exact
+// norm of every sampled row) and row_e (K event energies) may be NULL.
+lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max, std::vector<double>* row_sums,
+                              std::vector<float>* row_e) {
+    const int64_t J = c->J;
+    const int64_t K = std::min<int64_t>(J, c->sur_check_rows);
+    std::vector<int64_t> rows(K);
+    for (int64_t k = 0; k < K; ++k) rows[k] = (int64_t)(((double)k + 0.5) * (double)J / (double)K);
+    lmosem_status st;
+    int64_t* d_rows = nullptr;
+    float* d_ex = nullptr;
+    double* d_sums = nullptr;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&d_rows, K)) || (st = tmp.alloc(&d_ex, (size_t)K * c->ld_model)) ||
+        (st = tmp.alloc(&d_sums, 2 * K)))
+        return st;
+    LMOSEM_CK(c, cudaMemcpyAsync(d_rows, rows.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    std::vector<float> energies(K);
+    if ((st = exact_rows(c, rows, d_rows, d_ex, energies.data()))) return st;
     LMOSEM_PROF_BEGIN(c);
     k_judge_rows<<<(unsigned)K, 256, 0, c->stream>>>(reinterpret_cast<const float*>(c->d_model), c->ld_model,
                                                       d_rows, d_ex, c->n_sup, d_sums);
@@ -1299,6 +1331,44 @@ lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max) {
     }
     *rel_err = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
     *row_max = mx;
+    if (row_sums) row_sums->swap(sums);
+    if (row_e) row_e->swap(energies);
+    return LMOSEM_OK;
+}
+
+// The rows of the current (FP32) model whose event energy lies below e_cut,
+// replaced by exact rows: the rows are rebuilt by the exact path sum in
+// chunks of at most 8 GiB of scratch rows and copied over the model's.
+lmosem_status rebuild_rows_below(lmosem_ctx* c, double e_cut, int64_t* n_rebuilt) {
+    const int64_t J = c->J;
+    std::vector<float> e(J);
+    LMOSEM_CK(c, cudaMemcpyAsync(e.data(), c->d_e_s, J * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    std::vector<int64_t> rows;
+    for (int64_t r = 0; r < J; ++r)
+        if ((double)e[r] < e_cut) rows.push_back(r);
+    *n_rebuilt = (int64_t)rows.size();
+    if (rows.empty()) return LMOSEM_OK;
+    if (c->ld_model % 4) return fail(c, LMOSEM_ESTATE, "model rows not 16-byte aligned");
+    const int64_t row_bytes = c->ld_model * (int64_t)sizeof(float);
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>((int64_t)rows.size(), (int64_t(8) << 30) / row_bytes));
+    lmosem_status st;
+    int64_t* d_rows = nullptr;
+    float* d_ex = nullptr;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&d_rows, per)) || (st = tmp.alloc(&d_ex, (size_t)per * c->ld_model))) return st;
+    for (int64_t k0 = 0; k0 < (int64_t)rows.size(); k0 += per) {
+        const int64_t K = std::min<int64_t>(per, (int64_t)rows.size() - k0);
+        std::vector<int64_t> part(rows.begin() + k0, rows.begin() + k0 + K);
+        LMOSEM_CK(c, cudaMemcpyAsync(d_rows, part.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+        if ((st = exact_rows(c, part, d_rows, d_ex, nullptr))) return st;
+        LMOSEM_PROF_BEGIN(c);
+        k_scatter_rows<<<(unsigned)K, 256, 0, c->stream>>>(reinterpret_cast<const float4*>(d_ex), d_rows,
+                                                           c->ld_model / 4, reinterpret_cast<float4*>(c->d_model));
+        LMOSEM_LAUNCHED(c, LMOSEM_K_OTHER);
+        // the host copy of this chunk's rows must outlive the copy above
+        LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    }
     return LMOSEM_OK;
 }
 

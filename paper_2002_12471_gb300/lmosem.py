@@ -56,7 +56,8 @@ class Options(ctypes.Structure):
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
                   "other", "surrogate", "mlp"]
-SURROGATE_PARAMS = 199455
+SURROGATE_PARAMS = 199967
+SURROGATE_INPUTS = 8
 SURROGATE_BASIS = 28
 MODEL_SURROGATE_FP32 = 3
 FORMATS["surrogate"] = MODEL_SURROGATE_FP32
@@ -114,6 +115,8 @@ SIGNATURES = {
     "lmosem_set_surrogate_check": (ctypes.c_int, [_vp, _dbl, _i32]),
     "lmosem_measure_ex2_rate": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp]),
     "lmosem_surrogate_check": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmosem_set_surrogate_gate": (ctypes.c_int, [_vp, _dbl, _dbl]),
+    "lmosem_surrogate_gate": (ctypes.c_int, [_vp, _vp, _vp]),
 }
 
 _lib = None
@@ -414,7 +417,23 @@ def lmosem_surrogate_check(ctx):
     return err.value, mx.value, bool(ex.value)
 
 
-def surrogate_init(seed=0, layers=(6, 256, 256, 256, 256, 1)):
+def lmosem_set_surrogate_gate(ctx, row_tol=1e-2, bin_kev=0.0):
+    """Energy gate of the surrogate form (0: off): rows of the energy bins
+    whose sampled mean row error exceeds row_tol, and of every lower bin,
+    are rebuilt with the exact path sum (bin_kev = 0: 5 keV bins)."""
+    _check(ctx, load().lmosem_set_surrogate_gate(ctx, float(row_tol), float(bin_kev)))
+
+
+def lmosem_surrogate_gate(ctx):
+    """(e_cut_kev, frac_exact) of the current surrogate-form model: rows
+    with E below e_cut_kev hold the exact path sum, a fraction frac_exact of
+    all rows."""
+    cut, frac = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, load().lmosem_surrogate_gate(ctx, ctypes.byref(cut), ctypes.byref(frac)))
+    return cut.value, frac.value
+
+
+def surrogate_init(seed=0, layers=(SURROGATE_INPUTS, 256, 256, 256, 256, 1)):
     """Initial surrogate weights as a blob: He-normal weights (standard
     deviation sqrt(2 / fan_in)), zero biases, output standardisation (0, 1);
     training sets the standardisation from its targets."""
@@ -434,7 +453,7 @@ def pack_surrogate(params, mu=0.0, sigma=1.0, baseline=None):
     return blob
 
 
-def unpack_surrogate(blob, layers=(6, 256, 256, 256, 256, 1)):
+def unpack_surrogate(blob, layers=(SURROGATE_INPUTS, 256, 256, 256, 256, 1)):
     blob = np.asarray(blob, dtype=np.float64)
     params, k = [], 0
     for fi, fo in zip(layers[:-1], layers[1:]):

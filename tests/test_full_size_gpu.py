@@ -83,7 +83,7 @@ def test_surrogate_inference_at_launch_size(L):
     for W, b in params:
         b += rng.normal(0.0, 0.2, b.shape)
     n = 1 << 24
-    X = torch.randn((n, 6), dtype=torch.float32, device=dev, generator=torch.Generator(dev).manual_seed(5))
+    X = torch.randn((n, 8), dtype=torch.float32, device=dev, generator=torch.Generator(dev).manual_seed(5))
     out = torch.empty(n, dtype=torch.float32, device=dev)
     blob = torch.from_numpy(L.pack_surrogate(params)).to(dev)
     ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=torch.cuda.current_stream(), surrogate_kernel=2)

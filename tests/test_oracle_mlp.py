@@ -70,14 +70,14 @@ def test_relu_network_is_piecewise_linear():
 def test_feature_encoding_special_angles():
     # theta = 0: flight direction +x, lateral axis +y, so u_a(p) = y and p.omega = x;
     # theta = pi/2: omega = +y, t = -x, so u_a(p) = -x and p.omega = y
-    x, y, u, e, att = 30.0, -20.0, 5.0, 150.0, 0.75
-    f0 = mlp.features(x, y, 0.0, u, e, att)
-    np.testing.assert_allclose(f0, [(u - y) / 50.0, x / 100.0, y / 100.0, -1.0, (e - 137.5) / 37.5, -0.5],
-                               rtol=1e-12, atol=1e-15)
-    f1 = mlp.features(x, y, np.pi / 2, u, e, att)
-    np.testing.assert_allclose(f1, [(u + x) / 50.0, y / 100.0, -x / 100.0, -0.5, (e - 137.5) / 37.5, -0.5],
-                               rtol=1e-12, atol=1e-15)
+    x, y, u, e, att, lf, lt = 30.0, -20.0, 5.0, 150.0, 0.75, 3.0, 4.5
+    f0 = mlp.features(x, y, 0.0, u, e, att, lf, lt)
+    np.testing.assert_allclose(f0, [(u - y) / 50.0, x / 100.0, y / 100.0, -1.0, (e - 137.5) / 37.5, -0.5,
+                                    1.0, 2.0], rtol=1e-12, atol=1e-15)
+    f1 = mlp.features(x, y, np.pi / 2, u, e, att, lf, lt)
+    np.testing.assert_allclose(f1, [(u + x) / 50.0, y / 100.0, -x / 100.0, -0.5, (e - 137.5) / 37.5, -0.5,
+                                    1.0, 2.0], rtol=1e-12, atol=1e-15)
     # an event on the pixel's projection has zero offset at any angle
     th = np.linspace(0.0, 2 * np.pi, 7)
     ua = -x * np.sin(th) + y * np.cos(th)
-    np.testing.assert_allclose(mlp.features(x, y, th, ua, e, att)[:, 0], 0.0, atol=1e-14)
+    np.testing.assert_allclose(mlp.features(x, y, th, ua, e, att, lf, lt)[:, 0], 0.0, atol=1e-14)

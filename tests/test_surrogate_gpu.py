@@ -51,7 +51,7 @@ def test_gradients_match_oracle(L):
     params = _perturbed_params(7)
     rng = np.random.default_rng(8)
     n = 512
-    X = rng.normal(0.0, 1.0, (n, 6))
+    X = rng.normal(0.0, 1.0, (n, 8))
     t = rng.normal(0.0, 1.0, n)
     blob = L.pack_surrogate(params)
     ctx = _ctx(L, ph, g)
@@ -73,16 +73,16 @@ def test_gradients_match_oracle(L):
     Xq = bf16(X.astype(np.float32))
     tq = t.astype(np.float32).astype(np.float64)
     # (1) the plain FP64 oracle: the GPU also rounds every hidden activation and
-    # every back-propagated delta to BF16 (2^-9 relative each) and ReLU masks of
-    # pre-activations within that rounding of zero can flip, so the bound is 3e-2
+    # every back-propagated delta to BF16 (2^-9 relative each), and ReLU masks
+    # of pre-activations within that rounding of zero can flip; the size of
+    # that effect depends on the draw, so it is measured on the CPU (the
+    # oracle at the GPU's rounding points, (2) below, against the plain one)
+    # and the GPU may differ from the plain oracle by it plus 2e-3, and by 5e-2
+    # at most
     loss_ref, g_ref = mlp.mse_loss_and_grad(pq, Xq, tq)
     y_ref, _ = mlp.forward(pq, Xq)
     assert loss == pytest.approx(loss_ref, rel=2e-2)
     assert oracle.rel_l2(y_gpu, y_ref) <= 2e-2
-    for l in range(5):
-        for i in range(2):
-            err = oracle.rel_l2(np.ravel(g_gpu[l][i]), np.ravel(g_ref[l][i]))
-            assert err <= 3e-2, (l, i, err)
     # (2) FP64 with the GPU's BF16 rounding points: only the FP32 accumulation
     # order remains
     hs, zs, h = [], [], Xq
@@ -108,6 +108,9 @@ def test_gradients_match_oracle(L):
         for i in range(2):
             err = oracle.rel_l2(np.ravel(g_gpu[l][i]), np.ravel(gm[l][i]))
             assert err <= 2e-3, ("bf16-mirrored", l, i, err)
+            bf16_effect = oracle.rel_l2(np.ravel(gm[l][i]), np.ravel(g_ref[l][i]))
+            err = oracle.rel_l2(np.ravel(g_gpu[l][i]), np.ravel(g_ref[l][i]))
+            assert err <= min(bf16_effect + 2e-3, 5e-2), (l, i, err, bf16_effect)
 
 
 def _mirrored_forward(params, X, round_last):
@@ -138,7 +141,7 @@ def test_tcgen05_inference_matches_product_chain_and_oracle(L, n):
     dev = torch.device("cuda:0")
     ph, g, *_ = S.workload("tiny16")
     params = _perturbed_params(11)
-    X = np.random.default_rng(12).normal(0.0, 1.0, (n, 6))
+    X = np.random.default_rng(12).normal(0.0, 1.0, (n, 8))
     blob = torch.from_numpy(L.pack_surrogate(params)).to(dev)
     Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
     ys = {}
@@ -174,7 +177,7 @@ def test_tcgen05_bounded_wait_reports_timeout(L):
     ph, g, *_ = S.workload("tiny16")
     params = _perturbed_params(13)
     n = 4 * 128 + 3
-    X = np.random.default_rng(14).normal(0.0, 1.0, (n, 6))
+    X = np.random.default_rng(14).normal(0.0, 1.0, (n, 8))
     blob = torch.from_numpy(L.pack_surrogate(params)).to(dev)
     Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
     out = torch.zeros(n, dtype=torch.float32, device=dev)
@@ -205,12 +208,12 @@ def test_training_targets_match_oracle_scatter(L):
     ctx = _ctx(L, ph, g)
     try:
         nsup = L.lmosem_n_support(ctx)
-        feat = torch.zeros((len(ev) * nsup, 6), dtype=torch.float32, device=dev)
+        feat = torch.zeros((len(ev) * nsup, L.SURROGATE_INPUTS), dtype=torch.float32, device=dev)
         targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
         rel = torch.full((len(ev) * nsup,), np.nan, dtype=torch.float32, device=dev)
         L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
                                    torch.from_numpy(ev.e_kev).to(dev), feat, targ, rel)
-        f = feat.cpu().numpy().astype(np.float64).reshape(len(ev), nsup, 6)
+        f = feat.cpu().numpy().astype(np.float64).reshape(len(ev), nsup, L.SURROGATE_INPUTS)
         t32 = targ.cpu().numpy().reshape(len(ev), nsup)
         p_gpu = np.exp(t32.astype(np.float64))
         r32 = rel.cpu().numpy().reshape(len(ev), nsup)
@@ -220,11 +223,17 @@ def test_training_targets_match_oracle_scatter(L):
     np.testing.assert_array_equal(r32, t32 - t32.max(axis=1, keepdims=True))
     scat = P.model(ev.angle, ev.u_mm, ev.e_kev, primary=False)
     assert row_close(p_gpu, scat) <= 1.0
-    # inputs: pixel centre, angle, position, energy, attenuation to the edge
+    # inputs: pixel centre, angle, position, energy, attenuation to the edge,
+    # and along the event's detector line from the pixel's depth and whole
     xs, ys = P.pixel_centres(P.support)
     th = g["angle0_rad"] + 2 * np.pi * ev.angle / g["n_angles"]
-    ref = mlp.features(xs[None, :], ys[None, :], th[:, None], ev.u_mm[:, None].astype(np.float64),
-                       ev.e_kev[:, None].astype(np.float64), P.l_edge[ev.angle][:, P.support])
+    u = ev.u_mm[:, None].astype(np.float64)
+    depth = xs[None, :] * np.cos(th)[:, None] + ys[None, :] * np.sin(th)[:, None]
+    a2 = np.broadcast_to(ev.angle[:, None], depth.shape)
+    line_from = P.line_attenuation(a2, np.broadcast_to(u, depth.shape), depth)
+    line_total = P.line_attenuation(ev.angle, ev.u_mm.astype(np.float64), np.full(len(ev), P.line_start()))
+    ref = mlp.features(xs[None, :], ys[None, :], th[:, None], u, ev.e_kev[:, None].astype(np.float64),
+                       P.l_edge[ev.angle][:, P.support], line_from, line_total[:, None])
     np.testing.assert_allclose(f, ref, rtol=1e-5, atol=1e-5)
 
 
@@ -240,7 +249,7 @@ def test_training_draws_pairs_by_magnitude_weight(L):
     ph, g, J, ns, ni = S.workload("tiny16")
     n = 1 << 16
     gen = torch.Generator().manual_seed(7)
-    feat = torch.rand((n, 6), generator=gen).to(dev)
+    feat = torch.rand((n, 8), generator=gen).to(dev)
     heavy = torch.rand(n, generator=gen) < 0.5
     targ = torch.where(heavy, torch.tensor(-3.0), torch.tensor(1.0)).to(dev)
     rel = torch.where(heavy, torch.tensor(0.0), torch.tensor(-60.0)).to(dev)
@@ -273,7 +282,7 @@ def test_target_floor_per_row_with_row_offsets(L):
     rows, width, F = 256, 64, 5.0
     t = (rng.uniform(-30.0, 0.0, (rows, 1)) + rng.uniform(-12.0, 0.0, (rows, width))).astype(np.float32)
     rel = t - t.max(axis=1, keepdims=True)
-    feat = torch.from_numpy(rng.uniform(-1, 1, (rows * width, 6)).astype(np.float32)).to(dev)
+    feat = torch.from_numpy(rng.uniform(-1, 1, (rows * width, 8)).astype(np.float32)).to(dev)
     want = {"row": np.where(rel < -F, t - rel - np.float32(F), t).astype(np.float64),
             "all": np.maximum(t, t.max() - np.float32(F)).astype(np.float64)}
     ctx = _ctx(L, ph, g)
@@ -302,7 +311,7 @@ def trained(L):
     ctx = _ctx(L, ph, g)
     try:
         nsup = L.lmosem_n_support(ctx)
-        feat = torch.zeros((len(ev) * nsup, 6), dtype=torch.float32, device=dev)
+        feat = torch.zeros((len(ev) * nsup, L.SURROGATE_INPUTS), dtype=torch.float32, device=dev)
         targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
         L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
                                    torch.from_numpy(ev.e_kev).to(dev), feat, targ)
@@ -476,3 +485,123 @@ def test_untrained_surrogate_falls_back_to_the_exact_model(L):
     s = P.sensitivity(ns)
     f_ref, _ = oracle.osem(p, ev.angle, s, ni, oracle.initial_image(J, s.sum(0)))
     assert oracle.rel_l2(f_gpu, f_ref) <= 1e-4
+
+
+def _gated_rows(L, ph, g, ns, blob, ev, row_tol, check_tol=1.0):
+    """Model rows (original event order) of a surrogate build with the
+    energy gate at row_tol, and the gate's and the check's results."""
+    import torch
+    dev = torch.device("cuda:0")
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        L.lmosem_surrogate_load(ctx, blob)
+        L.lmosem_set_surrogate_check(ctx, check_tol)
+        L.lmosem_set_surrogate_gate(ctx, row_tol)
+        a, u, e = (torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev))
+        L.lmosem_build_model(ctx, a, u, e, ns, "surrogate")
+        return _model_rows(L, ctx, len(ev), nsup), L.lmosem_surrogate_gate(ctx), L.lmosem_surrogate_check(ctx)
+    finally:
+        L.lmosem_destroy(ctx)
+
+
+def test_energy_gate_takes_exact_rows_below_its_cut(L, trained):
+    """The energy gate of the surrogate form: rows of events below the cut
+    are bitwise the exact path sum's, the others bitwise the surrogate's; the
+    cut sits on a bin edge of the window; a tolerance no bin meets makes every
+    row exact, one every bin meets none."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, ns = trained["ph"], trained["g"], trained["ns"]
+    ev = S.simulate_events(ph, g, 6000, seed=55)
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        a, u, e = (torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev))
+        L.lmosem_build_model(ctx, a, u, e, ns, "fp32")
+        exact = _model_rows(L, ctx, len(ev), nsup)
+    finally:
+        L.lmosem_destroy(ctx)
+    sur, (cut0, frac0), _ = _gated_rows(L, ph, g, ns, trained["blob"], ev, 0.0)
+    assert cut0 == g["e_lo_kev"] and frac0 == 0.0
+    assert not np.array_equal(sur, exact)
+    for tol in (3e-2, 1e-2, 3e-3):
+        rows, (cut, frac), (err, row_max, all_exact) = _gated_rows(L, ph, g, ns, trained["blob"], ev, tol)
+        k = (cut - g["e_lo_kev"]) / 5.0
+        assert abs(k - round(k)) < 1e-9 and g["e_lo_kev"] <= cut <= g["e_hi_kev"], cut
+        low = ev.e_kev < cut
+        assert frac == pytest.approx(low.mean(), abs=1e-12)
+        assert np.array_equal(rows[low], exact[low])
+        assert np.array_equal(rows[~low], sur[~low])
+        assert all_exact == (frac == 1.0)
+    # every sampled bin fails: the cut is the top edge of the highest one
+    rows, (cut, frac), (err, _, all_exact) = _gated_rows(L, ph, g, ns, trained["blob"], ev, 1e-12)
+    low = ev.e_kev < cut
+    assert cut >= g["e_hi_kev"] - 5.0 and frac > 0.99 and err == 0.0
+    assert frac == pytest.approx(low.mean(), abs=1e-12) and all_exact == (frac == 1.0)
+    assert np.array_equal(rows[low], exact[low])
+    rows, (cut, frac), _ = _gated_rows(L, ph, g, ns, trained["blob"], ev, 1e12)
+    assert cut == g["e_lo_kev"] and frac == 0.0
+    assert np.array_equal(rows, sur)
+
+
+@pytest.fixture(scope="module")
+def trained_dat32(L):
+    """Surrogate trained as the benchmark trains it (pairs drawn by
+    magnitude, alpha = 1; per-row floor 14; quadratic residual baseline) on
+    exact scatter sums of 3,000 events of the 32 x 32 brain workload
+    (20,000 steps, about 10 s)."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, J, ns, ni = S.workload("dat32")
+    ev = S.simulate_events(ph, g, 3000, seed=61)
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        feat = torch.zeros((len(ev) * nsup, L.SURROGATE_INPUTS), dtype=torch.float32, device=dev)
+        targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
+        rel = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                                   torch.from_numpy(ev.e_kev).to(dev), feat, targ, rel)
+        blob = torch.from_numpy(L.surrogate_init(seed=3)).to(dev)
+        L.lmosem_surrogate_train(ctx, feat, targ, blob, steps=20000, batch=4096, lr=1e-3, seed=5,
+                                 target_floor=14.0, residual_fit=True, d_rel_log=rel, magnitude_power=1.0)
+    finally:
+        L.lmosem_destroy(ctx)
+    return dict(ph=ph, g=g, ns=ns, blob=blob)
+
+
+def test_surrogate_form_reconstructs_within_the_bound(L, trained_dat32):
+    """The surrogate form as the library builds it (energy gate at a mean
+    row error of 1e-2, exact check at 1e-2) reconstructs 20,000 events of the
+    32 x 32 brain (6 subsets x 10 iterations) within 1e-2 relative L2 of the
+    exact model's image, with striatal ROI means within 1%, while the
+    surrogate still serves part of the rows."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, ns = trained_dat32["ph"], trained_dat32["g"], trained_dat32["ns"]
+    ni = 10
+    ev = S.simulate_events(ph, g, 20000, seed=62)
+    exact = gpu_reconstruct(ph, g, ev, ns, ni)
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        L.lmosem_surrogate_load(ctx, trained_dat32["blob"])
+        L.lmosem_set_surrogate_gate(ctx, 1e-2)
+        L.lmosem_sensitivity(ctx, ns)
+        a, u, e = (torch.from_numpy(x).to(dev) for x in (ev.angle, ev.u_mm, ev.e_kev))
+        L.lmosem_build_model(ctx, a, u, e, ns, "surrogate")
+        cut, frac = L.lmosem_surrogate_gate(ctx)
+        f = torch.zeros(nsup, dtype=torch.float32, device=dev)
+        L.lmosem_init_image(ctx, 1.0, f)
+        L.lmosem_iterate(ctx, ni, 1.0, f)
+        f_sur = f.cpu().numpy().astype(np.float64)
+    finally:
+        L.lmosem_destroy(ctx)
+    assert frac < 1.0, (cut, frac)
+    assert oracle.rel_l2(f_sur, exact["f"]) <= 1e-2, (cut, frac)
+    img = lambda f: np.bincount(exact["support"], weights=f, minlength=ph.mu.size)
+    for name, roi in ph.rois.items():
+        w = roi.reshape(-1)
+        ref = np.dot(w, img(exact["f"]))
+        assert abs(np.dot(w, img(f_sur)) - ref) <= 1e-2 * ref, name
