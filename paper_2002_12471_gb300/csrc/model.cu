@@ -578,6 +578,41 @@ constexpr int kWOffMisc = kWOffEv + 2 * kTJ;                     // 16 ints
 constexpr int kWOffList = kWOffMisc + 16;                        // n_scat ints
 static_assert(kWOffMp % 4 == 0 && kWOffU % 4 == 0, "16-byte aligned stage buffers");
 static_assert(kTJ == 8 * kWarps && kStage == 16, "8 events per warp; 16-bit live masks; 4 U per lane");
+static_assert(kBuildThreads == 256 && kTN == 128 && kStage == 2 * kWarps, "one column group, two stage rows per thread");
+
+// The wide form's staging: the copies of stage_issue with the per-thread
+// parts of the addresses hoisted out of the stage loop.  Thread t copies the
+// 16-byte column group t % 32 of stage rows t / 32 and t / 32 + 8 of the
+// three planes (tab_q = the table row start + that group's offset, dst_q =
+// its slot in plane 0 of buffer 0); threads t < kStage the position
+// parameters of stage row t.
+__device__ __forceinline__ void stage_issue_wide(const TileInfo& T, const int* mlist, const float* tab_q,
+                                                 size_t plane, int ld_w, const float4* mp_a, float* dst_q,
+                                                 float4* mp, int c0, int buf) {
+    const int tid = threadIdx.x, mc0 = tid >> 5;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int mc = mc0 + 8 * h;
+        float* d = dst_q + (buf * 3 * kStage + 8 * h) * kTN;
+        if (c0 + mc < T.nm) {
+            const float* src = tab_q + (size_t)mlist[c0 + mc] * ld_w;
+            cp_async16(d, src);
+            cp_async16(d + kPlaneF, src + plane);
+            cp_async16(d + 2 * kPlaneF, src + 2 * plane);
+        } else {
+            const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            *reinterpret_cast<float4*>(d) = z;
+            *reinterpret_cast<float4*>(d + kPlaneF) = z;
+            *reinterpret_cast<float4*>(d + 2 * kPlaneF) = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+        }
+    }
+    if (tid < kStage) {
+        float4* dst = mp + buf * kStage + tid;
+        if (c0 + tid < T.nm) cp_async16(dst, mp_a + mlist[c0 + tid]);
+        else *dst = make_float4(0.0f, 0.0f, -INFINITY, -1.0f);  // cut < 0: U = 0
+    }
+    cp_async_commit();
+}
 
 __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     extern __shared__ float4 smem4[];
@@ -617,8 +652,10 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
     const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
     const int nchunks = (T.nm + kStage - 1) / kStage;
+    const float* tab_q = tab + 4 * lane;
+    float* dst_q = planes + warp * kTN + 4 * lane;
     for (int q = 0; q < min(2, nchunks); ++q)
-        stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, q * kStage, q, kTN / 4);
+        stage_issue_wide(T, mlist, tab_q, plane, A.ld_w, mp_a, dst_q, mp, q * kStage, q);
     const float uw = ev_u[8 * warp + (lane & 7)];  // this lane's event in the U step
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c % kWBuf;
@@ -626,8 +663,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         else cp_async_wait<0>();
         __syncthreads();  // stage c landed everywhere; every warp is done with stage c - 1
         if (c + 2 < nchunks)
-            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 2) * kStage, (c + 2) % kWBuf,
-                        kTN / 4);
+            stage_issue_wide(T, mlist, tab_q, plane, A.ld_w, mp_a, dst_q, mp, (c + 2) * kStage, (c + 2) % kWBuf);
         // U_jm of this warp's events: lane holds event lane % 8 at scatter
         // pixels lane / 8 + 4 i
         unsigned live = 0;
