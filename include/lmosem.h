@@ -389,9 +389,10 @@ lmosem_status lmosem_surrogate_check(const lmosem_ctx* ctx, double* h_rel_err, d
  * row whose event energy lies below the top of that bin is rebuilt with the
  * exact path sum (bitwise the exact build's row), the rest keep the
  * surrogate's rows, and the check's error is then taken with those rows
- * exact.  row_tol = 0: off (the default).  bin_kev = 0 selects 5 keV.
- * Applies to the builds that follow.  EINVAL: a negative or non-finite
- * argument. */
+ * exact.  The rebuilt rows pass through device scratch of at most 8 GiB at a
+ * time (ENOMEM from the build when that does not fit).  row_tol = 0: off
+ * (the default).  bin_kev = 0 selects 5 keV.  Applies to the builds that
+ * follow.  EINVAL: a negative or non-finite argument. */
 lmosem_status lmosem_set_surrogate_gate(lmosem_ctx* ctx, double row_tol, double bin_kev);
 
 /* Result of the energy gate of the current surrogate-form model:
