@@ -59,9 +59,10 @@ __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
 template <int VPT>
 __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs A) {
     constexpr int R = VPT >= 3 ? 2 : 4;
-    __shared__ float red[2][R][kBatchThreads / 32];
+    static_assert(kBatchThreads == 256, "eight per-warp partials per row, every slot written");
+    __shared__ __align__(16) float red[2][R][kBatchThreads / 32];
     __shared__ int s_r, s_e, s_c, s_last;
-    const int NT = blockDim.x, NW = NT >> 5;
+    const int NT = blockDim.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     int rot = blockIdx.x % A.n_real;
     long long idle_since = -1;
@@ -171,8 +172,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs A) {
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                float y = 0.0f;
-                for (int w = 0; w < NW; ++w) y += red[rbuf][k][w];
+                const float y = sum8_in_order(red[rbuf][k]);
                 const float inv = (row + k < re && y > 0.0f) ? 1.0f / y : 0.0f;
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {

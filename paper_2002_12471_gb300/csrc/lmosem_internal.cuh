@@ -256,6 +256,25 @@ private:
     std::vector<void*> owned_;
 };
 
+// The sum v[0] + v[1] + ... + v[7], added in index order from 0, read with
+// two 16-byte shared-memory loads (v: the per-warp partials of one row, 16-
+// byte aligned; the slots of absent warps hold +0, and adding +0 leaves a
+// sum's bits unchanged except that -0 becomes +0)
+__device__ __forceinline__ float sum8_in_order(const float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(v);
+    const float4 b = *reinterpret_cast<const float4*>(v + 4);
+    float y = 0.0f;
+    y += a.x;
+    y += a.y;
+    y += a.z;
+    y += a.w;
+    y += b.x;
+    y += b.y;
+    y += b.z;
+    y += b.w;
+    return y;
+}
+
 // ---- host entry points implemented in the other translation units
 lmosem_status build_tables(lmosem_ctx* c);                      // siddon.cu
 // h_offsets: n_real + 1 event offsets of the realisations (nullptr: one)

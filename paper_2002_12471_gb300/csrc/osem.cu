@@ -152,11 +152,16 @@ constexpr int pass_rows() {
 template <typename H, int VPT, int R, bool BACK, bool W>
 __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass(PassArgs A) {
     constexpr int EPV = Vec<H>::N;
-    __shared__ float red[2][R][kMaxPassThreads / 32];
+    static_assert(kMaxPassThreads / 32 == 8, "eight per-warp partials per row");
+    __shared__ __align__(16) float red[2][R][kMaxPassThreads / 32];
     __shared__ double llred[kMaxPassThreads / 32];
     const int NT = blockDim.x, NW = NT >> 5;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const char* model = reinterpret_cast<const char*>(A.model);
+    // the partial slots no warp writes hold +0 (read by sum8_in_order; the
+    // first row group's barrier orders these stores before any read)
+    for (int k = t; k < 2 * R * 8; k += NT)
+        if ((k & 7) >= NW) (&red[0][0][0])[k] = 0.0f;
 
     float fr[VPT][EPV], br[VPT][EPV];
 #pragma unroll
@@ -220,8 +225,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            float y = 0.0f;
-            for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
+            const float y = sum8_in_order(red[rb_][i]);
             const bool ok = r + i < re && y > 0.0f;
             if constexpr (BACK) {
                 float inv = ok ? 1.0f / y : 0.0f;
@@ -342,11 +346,16 @@ template <typename H, int VPT, int R, bool BACK, bool W>
 __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pass_cpa(PassArgs A, int S) {
     constexpr int EPV = Vec<H>::N;
     extern __shared__ __align__(128) unsigned char cring[];
-    __shared__ float red[2][R][kMaxPassThreads / 32];
+    static_assert(kMaxPassThreads / 32 == 8, "eight per-warp partials per row");
+    __shared__ __align__(16) float red[2][R][kMaxPassThreads / 32];
     __shared__ double llred[kMaxPassThreads / 32];
     const int NT = blockDim.x, NW = NT >> 5;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const char* model = reinterpret_cast<const char*>(A.model);
+    // the partial slots no warp writes hold +0 (read by sum8_in_order; the
+    // first row group's barrier orders these stores before any read)
+    for (int k = t; k < 2 * R * 8; k += NT)
+        if ((k & 7) >= NW) (&red[0][0][0])[k] = 0.0f;
 
     float fr[VPT][EPV], br[VPT][EPV];
 #pragma unroll
@@ -429,8 +438,7 @@ __global__ void __launch_bounds__(kMaxPassThreads, pass_min_ctas<H, VPT>()) k_pa
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            float y = 0.0f;
-            for (int w = 0; w < NW; ++w) y += red[rb_][i][w];
+            const float y = sum8_in_order(red[rb_][i]);
             const bool ok = r + i < re && y > 0.0f;
             if constexpr (BACK) {
                 float inv = ok ? 1.0f / y : 0.0f;
