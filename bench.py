@@ -550,7 +550,7 @@ def run_ours(args, rank, world, local_rank):
     terms_per_launch = terms / max(1, ps_n / args.steps)
     achieved = terms_per_launch / (ps_launch_ms * 1e-3) / 1e9          # Gterm/s
     peak = MUFU_EX2_PER_CLK_SM * sms * sm_max * 1e6 / 1e9             # Gterm/s (1 ex2 / term)
-    traffic = read_traffic("k_pathsum", WORKLOAD)
+    traffic = read_traffic("k_pathsum", "%s_%gM" % (WORKLOAD, J / 1e6))
     value = aggregate_rate(evals, world, ms_step)
     e2e_ms = statistics.mean(e2e_times)
     R = runs[chosen]
@@ -629,8 +629,9 @@ def kernel_source_sha1():
 
 
 def read_traffic(kernel, workload):
-    """DRAM bytes per launch of a kernel on a workload from the committed ncu
-    summary, if the kernel's source has not changed since it was taken."""
+    """DRAM bytes per launch of a kernel on a workload (name and event count,
+    e.g. dat128_1M) from the committed ncu summary, if the kernel's source has
+    not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -638,7 +639,7 @@ def read_traffic(kernel, workload):
     for ln in open(path):
         parts = dict(p.split("=", 1) for p in ln.split() if "=" in p)
         if (parts.get("kernel") == kernel and parts.get("source_sha1") == h
-                and parts.get("workload", "").split("_")[0] == workload):
+                and parts.get("workload", "") == workload):
             try:
                 return float(parts["dram_bytes_per_launch"])
             except (KeyError, ValueError):

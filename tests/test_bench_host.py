@@ -126,12 +126,15 @@ def test_traffic_figure_is_gated_on_the_path_sum_source():
     rec = [dict(p.split("=", 1) for p in ln.split() if "=" in p) for ln in open(path)]
     mine = [r for r in rec if r.get("kernel") == "k_pathsum"]
     assert mine, "no k_pathsum traffic line"
-    for wl in ("dat64", "dat128"):
+    for wl in ("dat64_0.2M", "dat128_1M", "dat128_0.06M"):
         t = bench.read_traffic("k_pathsum", wl)
-        match = [r for r in mine if r["source_sha1"] == h and r.get("workload", "").split("_")[0] == wl]
+        match = [r for r in mine if r["source_sha1"] == h and r.get("workload", "") == wl]
         if match:
             assert t == float(match[0]["dram_bytes_per_launch"])
         else:
             assert t is None
+    # the figure of the 1M-event benchmark is not reported for a smaller run
+    assert bench.read_traffic("k_pathsum", "dat128_0.06M") is None
+    assert "%s_%gM" % ("dat128", 1000000 / 1e6) == "dat128_1M"
     assert bench.read_traffic("no_such_kernel", "dat64") is None
     assert bench.read_traffic("k_pathsum", "no_such_workload") is None
