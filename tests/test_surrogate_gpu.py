@@ -605,3 +605,35 @@ def test_surrogate_form_reconstructs_within_the_bound(L, trained_dat32):
         w = roi.reshape(-1)
         ref = np.dot(w, img(exact["f"]))
         assert abs(np.dot(w, img(f_sur)) - ref) <= 1e-2 * ref, name
+
+
+def test_inputs_match_oracle_at_the_benchmark_geometry(L):
+    """All eight surrogate inputs at the 128 x 128 benchmark geometry (2 mm
+    pixels, 120 angles, 128 bins) for 12 events against the oracle's
+    encoding, with the two line attenuations from its own exact node
+    integrals."""
+    import torch
+    dev = torch.device("cuda:0")
+    ph, g, *_ = S.workload("dat128")
+    ev = S.simulate_events(ph, g, 12, seed=71)
+    P = oracle_problem(ph, g)
+    ctx = _ctx(L, ph, g)
+    try:
+        nsup = L.lmosem_n_support(ctx)
+        feat = torch.zeros((len(ev) * nsup, L.SURROGATE_INPUTS), dtype=torch.float32, device=dev)
+        targ = torch.zeros(len(ev) * nsup, dtype=torch.float32, device=dev)
+        L.lmosem_surrogate_samples(ctx, torch.from_numpy(ev.angle).to(dev), torch.from_numpy(ev.u_mm).to(dev),
+                                   torch.from_numpy(ev.e_kev).to(dev), feat, targ)
+        f = feat.cpu().numpy().astype(np.float64).reshape(len(ev), nsup, L.SURROGATE_INPUTS)
+    finally:
+        L.lmosem_destroy(ctx)
+    xs, ys = P.pixel_centres(P.support)
+    th = g["angle0_rad"] + 2 * np.pi * ev.angle / g["n_angles"]
+    u = ev.u_mm[:, None].astype(np.float64)
+    depth = xs[None, :] * np.cos(th)[:, None] + ys[None, :] * np.sin(th)[:, None]
+    line_from = P.line_attenuation(np.broadcast_to(ev.angle[:, None], depth.shape),
+                                   np.broadcast_to(u, depth.shape), depth)
+    line_total = P.line_attenuation(ev.angle, ev.u_mm.astype(np.float64), np.full(len(ev), P.line_start()))
+    ref = mlp.features(xs[None, :], ys[None, :], th[:, None], u, ev.e_kev[:, None].astype(np.float64),
+                       P.l_edge[ev.angle][:, P.support], line_from, line_total[:, None])
+    np.testing.assert_allclose(f, ref, rtol=1e-5, atol=1e-5)
