@@ -383,14 +383,14 @@ lmosem_status lmosem_surrogate_check(const lmosem_ctx* ctx, double* h_rel_err, d
  * (Section 2.2); its error is largest for events well below the photopeak,
  * whose rows are almost all scatter, and the EM update (Eq. 8) weighs every
  * event's row alike.  With row_tol > 0 (and the check of
- * lmosem_set_surrogate_check on), the check's sampled rows are grouped in
- * energy bins of bin_kev from the window's lower edge; the highest bin whose
- * mean per-row relative L2 error exceeds row_tol marks the cut: every model
- * row whose event energy lies below the top of that bin is rebuilt with the
- * exact path sum (bitwise the exact build's row), the rest keep the
- * surrogate's rows, and the check's error is then taken with those rows
- * exact.  The rebuilt rows pass through device scratch of at most 8 GiB at a
- * time (ENOMEM from the build when that does not fit).  row_tol = 0: off
+ * lmosem_set_surrogate_check on), the network builds the check's sampled
+ * rows first and the check groups them in energy bins of bin_kev from the
+ * window's lower edge; the highest bin whose mean per-row relative L2 error
+ * exceeds row_tol marks the cut.  Every model row whose event energy lies
+ * below the top of that bin is then built by the exact path sum (bitwise the
+ * exact build's row), the others by the network, and the check's error is
+ * taken with the former exact.  The exact rows pass through device scratch of
+ * at most 8 GiB at a time (ENOMEM from the build when that does not fit).  row_tol = 0: off
  * (the default).  bin_kev = 0 selects 5 keV.  Applies to the builds that
  * follow.  EINVAL: a negative or non-finite argument. */
 lmosem_status lmosem_set_surrogate_gate(lmosem_ctx* ctx, double row_tol, double bin_kev);

@@ -116,58 +116,76 @@ lmosem_status check_events_args(lmosem_ctx* c, const int32_t* d_angle, const flo
     return LMOSEM_OK;
 }
 
-// The surrogate rows against the exact path sum on a sample of rows.  With
-// the energy gate on, the sampled rows are grouped in energy bins; the
-// highest bin whose mean per-row relative L2 error exceeds the gate's
-// tolerance, and every bin below it, take exact rows, and the check's error
-// is recomputed with those rows exact.  Above the check's tolerance the whole
-// model is rebuilt exactly.
-lmosem_status check_surrogate(lmosem_ctx* c) {
+// The energy gate's cut from the judge's sampled rows (squared difference
+// and squared exact norm per row, and the rows' event energies): the top of
+// the highest bin whose mean per-row relative L2 error exceeds the gate's
+// tolerance (a NaN mean fails), infinity when that is the window's last bin,
+// the window's lower edge when no bin fails.
+double gate_cut(const lmosem_ctx* c, const std::vector<double>& sums, const std::vector<float>& ev) {
+    const int nb = std::max(1, (int)ceil((c->e_hi - c->e_lo) / c->sur_gate_bin - 1e-9));
+    std::vector<double> esum(nb, 0.0);
+    std::vector<int> cnt(nb, 0);
+    for (size_t k = 0; k < ev.size(); ++k) {
+        const double d2 = sums[2 * k], e2 = sums[2 * k + 1];
+        const double r = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
+        const int b = std::min(nb - 1, std::max(0, (int)floor(((double)ev[k] - c->e_lo) / c->sur_gate_bin)));
+        esum[b] += r;
+        ++cnt[b];
+    }
+    int top = -1;
+    for (int b = 0; b < nb; ++b)
+        if (cnt[b] > 0 && !(esum[b] / cnt[b] <= c->sur_gate_tol)) top = b;
+    if (top < 0) return c->e_lo;
+    return top + 1 >= nb ? INFINITY : c->e_lo + (top + 1) * c->sur_gate_bin;
+}
+
+// The surrogate-form model and its exact check.  The judge compares the
+// network's rows with the exact path sum's on a sample of rows.  Without the
+// energy gate every row is built by the network first.  With it the sample's
+// rows are built first; the judge's cut then decides which rows the network
+// builds (event energy at or above the cut) and which the exact path sum
+// builds (below), and the check's error is taken with the latter exact.
+// Above the check's tolerance the whole model is rebuilt exactly.
+lmosem_status build_checked_surrogate(lmosem_ctx* c) {
+    const bool gate = c->sur_tol > 0.0 && c->sur_gate_tol > 0.0;
+    lmosem_status st;
+    if (!gate) {
+        if ((st = build_model_rows(c))) return st;
+    } else {
+        const std::vector<int64_t> rows = judge_sample_rows(c);
+        int64_t* d_rows = nullptr;
+        Scratch tmp(c);
+        if ((st = tmp.alloc(&d_rows, rows.size()))) return st;
+        LMOSEM_CK(c, cudaMemcpyAsync(d_rows, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                     c->stream));
+        if ((st = build_model_surrogate_rows(c, d_rows, (int64_t)rows.size()))) return st;
+    }
     double err = 0.0, mx = 0.0;
     std::vector<double> sums;
     std::vector<float> ev;
-    lmosem_status st = judge_surrogate(c, &err, &mx, &sums, &ev);
-    if (st) return st;
+    if ((st = judge_surrogate(c, &err, &mx, &sums, &ev))) return st;
     c->sur_checked = true;
     c->sur_exact = false;
     c->sur_cut = c->e_lo;
     c->sur_frac_exact = 0.0;
-    if (c->sur_tol > 0.0 && c->sur_gate_tol > 0.0) {
-        const int nb = std::max(1, (int)ceil((c->e_hi - c->e_lo) / c->sur_gate_bin - 1e-9));
-        std::vector<double> esum(nb, 0.0);
-        std::vector<int> cnt(nb, 0);
-        const int64_t K = (int64_t)ev.size();
-        auto bin_of = [&](float e) {
-            return std::min(nb - 1, std::max(0, (int)floor(((double)e - c->e_lo) / c->sur_gate_bin)));
-        };
-        for (int64_t k = 0; k < K; ++k) {
-            const double d2 = sums[2 * k], e2 = sums[2 * k + 1];
-            const double r = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
-            const int b = bin_of(ev[k]);
-            esum[b] += r;
-            ++cnt[b];
+    if (gate) {
+        const double cut = gate_cut(c, sums, ev);
+        int64_t n_net = 0, n_exact = 0;
+        if ((st = build_surrogate_rows_above(c, cut, &n_net))) return st;
+        if ((st = rebuild_rows_below(c, cut, &n_exact))) return st;
+        c->sur_cut = std::min(cut, c->e_hi);
+        c->sur_frac_exact = (double)n_exact / (double)c->J;
+        c->sur_exact = n_exact == c->J;
+        double d2 = 0.0, e2 = 0.0;
+        mx = 0.0;
+        for (size_t k = 0; k < ev.size(); ++k) {
+            e2 += sums[2 * k + 1];
+            if ((double)ev[k] < cut) continue;  // an exact row
+            d2 += sums[2 * k];
+            if (sums[2 * k + 1] > 0.0) mx = std::max(mx, sqrt(sums[2 * k] / sums[2 * k + 1]));
+            else if (sums[2 * k] > 0.0) mx = INFINITY;
         }
-        int top = -1;  // highest failing bin (a NaN mean fails)
-        for (int b = 0; b < nb; ++b)
-            if (cnt[b] > 0 && !(esum[b] / cnt[b] <= c->sur_gate_tol)) top = b;
-        if (top >= 0) {
-            const double cut = top + 1 >= nb ? INFINITY : c->e_lo + (top + 1) * c->sur_gate_bin;
-            int64_t n_exact = 0;
-            if ((st = rebuild_rows_below(c, cut, &n_exact))) return st;
-            c->sur_cut = std::min(cut, c->e_hi);
-            c->sur_frac_exact = (double)n_exact / (double)c->J;
-            c->sur_exact = n_exact == c->J;
-            double d2 = 0.0, e2 = 0.0;
-            mx = 0.0;
-            for (int64_t k = 0; k < K; ++k) {
-                e2 += sums[2 * k + 1];
-                if ((double)ev[k] < cut) continue;  // now an exact row
-                d2 += sums[2 * k];
-                if (sums[2 * k + 1] > 0.0) mx = std::max(mx, sqrt(sums[2 * k] / sums[2 * k + 1]));
-                else if (sums[2 * k] > 0.0) mx = INFINITY;
-            }
-            err = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
-        }
+        err = e2 > 0.0 ? sqrt(d2 / e2) : (d2 > 0.0 ? INFINITY : 0.0);
     }
     c->sur_err = err;
     c->sur_row_max = mx;
@@ -216,7 +234,7 @@ lmosem_status build_model_common(lmosem_ctx* c, const int32_t* d_angle, const fl
         free_model(c);
         return st;
     }
-    if ((st = build_model_rows(c)) || (sur && (st = check_surrogate(c)))) {
+    if ((st = sur ? build_checked_surrogate(c) : build_model_rows(c))) {
         free_model(c);
         return st;
     }

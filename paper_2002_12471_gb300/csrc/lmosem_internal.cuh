@@ -330,6 +330,9 @@ lmosem_status build_model_surrogate(lmosem_ctx* c);
 lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max, std::vector<double>* row_sums,
                               std::vector<float>* row_e);
 lmosem_status rebuild_rows_below(lmosem_ctx* c, double e_cut, int64_t* n_rebuilt);
+std::vector<int64_t> judge_sample_rows(const lmosem_ctx* c);
+lmosem_status build_surrogate_rows_above(lmosem_ctx* c, double e_cut, int64_t* n_built);
+lmosem_status build_model_surrogate_rows(lmosem_ctx* c, const int64_t* d_rows, int64_t n);
 // mlp_tc.cu: fused tcgen05 inference of M rows of BF16 inputs (M x 16)
 lmosem_status forward_tc(lmosem_ctx* c, const float* blob, const __nv_bfloat16* w1,
                          const unsigned char* w234img, const __nv_bfloat16* X, float* y, int64_t M);

@@ -540,26 +540,29 @@ __global__ void k_cdf_fill(const float* __restrict__ rel, int64_t n, float alpha
     }
 }
 
-// surrogate inputs of rows [r0, r0 + nrows) x all support pixels, BF16
-__global__ void k_surr_inputs(FeatArgs F, int64_t r0, int64_t nrows, __nv_bfloat16* __restrict__ X,
-                              bool tiled) {
+// surrogate inputs of rows [r0, r0 + nrows) x all support pixels, BF16; with
+// a row list, of its entries r0 .. r0 + nrows - 1 instead
+__global__ void k_surr_inputs(FeatArgs F, const int64_t* __restrict__ rows, int64_t r0, int64_t nrows,
+                              __nv_bfloat16* __restrict__ X, bool tiled) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows * F.n_sup) return;
+    const int64_t k = r0 + i / F.n_sup;
     float f[kIn];
-    features(F, r0 + i / F.n_sup, (int)(i % F.n_sup), f);
+    features(F, rows ? rows[k] : k, (int)(i % F.n_sup), f);
 #pragma unroll
     for (int k = 0; k < kInPad; ++k) X[x_index(i, k, tiled)] = __float2bfloat16_rn(k < kIn ? f[k] : 0.0f);
 }
 
-// p_jn = primary_jn + exp(mu + sigma y_jn) into the FP32 model rows
-__global__ void k_surr_combine(FeatArgs F, const float* __restrict__ y, int64_t r0, int64_t nrows, int n_sup,
-                               int64_t ld, const int32_t* __restrict__ a_s, const float* __restrict__ u_s,
-                               const float* __restrict__ e_s, const float4* __restrict__ ppar, int ld_w,
-                               float e0, float sE0, float lE0, const float* __restrict__ blob,
-                               float* __restrict__ model) {
+// p_jn = primary_jn + exp(mu + sigma y_jn) into the FP32 model rows (rows as
+// in k_surr_inputs)
+__global__ void k_surr_combine(FeatArgs F, const int64_t* __restrict__ rows, const float* __restrict__ y,
+                               int64_t r0, int64_t nrows, int n_sup, int64_t ld, const int32_t* __restrict__ a_s,
+                               const float* __restrict__ u_s, const float* __restrict__ e_s,
+                               const float4* __restrict__ ppar, int ld_w, float e0, float sE0, float lE0,
+                               const float* __restrict__ blob, float* __restrict__ model) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows * ld) return;
-    const int64_t row = r0 + i / ld;
+    const int64_t row = rows ? rows[r0 + i / ld] : r0 + i / ld;
     const int q = (int)(i % ld);
     float v = 0.0f;
     if (q < n_sup) {
@@ -1027,9 +1030,11 @@ lmosem_status run_surrogate_samples(lmosem_ctx* c, float* feat, float* targ, flo
     return LMOSEM_OK;
 }
 
-// model rows with the surrogate scatter term, in chunks of whole rows
-lmosem_status build_model_surrogate(lmosem_ctx* c) {
+// model rows with the surrogate scatter term, in chunks of whole rows: all J
+// rows (d_rows == nullptr) or the n sorted rows d_rows lists
+lmosem_status build_model_surrogate_rows(lmosem_ctx* c, const int64_t* d_rows, int64_t n) {
     lmosem_status st;
+    const int64_t n_rows = d_rows ? n : c->J;
     if ((st = gemm_tc_setup(c))) return st;
     if ((st = ensure_line_table(c))) return st;
     // pairs per chunk: the product chain keeps two 256-wide BF16 activations
@@ -1049,17 +1054,17 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double se0 = fw2s * c->fwhm_frac * c->e0;
     __nv_bfloat16* Hs[4] = {H, H + M * kH, H, H + M * kH};  // ping-pong
-    for (int64_t r0 = 0; r0 < c->J; r0 += rows_per) {
-        const int64_t nr = std::min(rows_per, c->J - r0);
+    for (int64_t r0 = 0; r0 < n_rows; r0 += rows_per) {
+        const int64_t nr = std::min(rows_per, n_rows - r0);
         const int64_t m = nr * c->n_sup;
         LMOSEM_PROF_BEGIN(c);
-        k_surr_inputs<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(feat_args(c), r0, nr, X,
+        k_surr_inputs<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(feat_args(c), d_rows, r0, nr, X,
                                                                           c->surrogate_kernel != 1);
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
         if ((st = forward_infer(c, c->d_surrogate, w, X, Hs, y, m))) return st;
         LMOSEM_PROF_BEGIN(c);
         k_surr_combine<<<(unsigned)((nr * c->ld_model + 255) / 256), 256, 0, c->stream>>>(
-            feat_args(c), y, r0, nr, c->n_sup, c->ld_model, c->d_a_s, c->d_u_s, c->d_e_s, c->d_ppar, c->ld_w, (float)c->e0,
+            feat_args(c), d_rows, y, r0, nr, c->n_sup, c->ld_model, c->d_a_s, c->d_u_s, c->d_e_s, c->d_ppar, c->ld_w, (float)c->e0,
             (float)(0.8493218002880191 / se0), (float)(-log2(se0 * sqrt(2.0 * kPi))), c->d_surrogate,
             reinterpret_cast<float*>(c->d_model));
         LMOSEM_LAUNCHED(c, LMOSEM_K_SURROGATE);
@@ -1067,5 +1072,7 @@ lmosem_status build_model_surrogate(lmosem_ctx* c) {
     st = take_status(c);   // synchronises
     return st;
 }
+
+lmosem_status build_model_surrogate(lmosem_ctx* c) { return build_model_surrogate_rows(c, nullptr, 0); }
 
 }  // namespace lmosem

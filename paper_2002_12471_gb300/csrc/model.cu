@@ -1337,12 +1337,18 @@ __global__ void k_scatter_rows(const float4* __restrict__ src, const int64_t* __
 // rebuilt with the exact path sum into scratch rows and compared with the
 // surrogate's rows.  row_sums (2K: squared difference and squared exact
 // norm of every sampled row) and row_e (K event energies) may be NULL.
-lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max, std::vector<double>* row_sums,
-                              std::vector<float>* row_e) {
+std::vector<int64_t> judge_sample_rows(const lmosem_ctx* c) {
     const int64_t J = c->J;
     const int64_t K = std::min<int64_t>(J, c->sur_check_rows);
     std::vector<int64_t> rows(K);
     for (int64_t k = 0; k < K; ++k) rows[k] = (int64_t)(((double)k + 0.5) * (double)J / (double)K);
+    return rows;
+}
+
+lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max, std::vector<double>* row_sums,
+                              std::vector<float>* row_e) {
+    const std::vector<int64_t> rows = judge_sample_rows(c);
+    const int64_t K = (int64_t)rows.size();
     lmosem_status st;
     int64_t* d_rows = nullptr;
     float* d_ex = nullptr;
@@ -1373,6 +1379,32 @@ lmosem_status judge_surrogate(lmosem_ctx* c, double* rel_err, double* row_max, s
     if (row_sums) row_sums->swap(sums);
     if (row_e) row_e->swap(energies);
     return LMOSEM_OK;
+}
+
+// The sorted rows whose event energy lies at or above e_cut (every row when
+// e_cut is the window's lower edge), built by the surrogate network.
+lmosem_status build_surrogate_rows_above(lmosem_ctx* c, double e_cut, int64_t* n_built) {
+    const int64_t J = c->J;
+    if (e_cut <= c->e_lo) {
+        *n_built = J;
+        return build_model_surrogate_rows(c, nullptr, 0);
+    }
+    std::vector<float> e(J);
+    LMOSEM_CK(c, cudaMemcpyAsync(e.data(), c->d_e_s, J * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    std::vector<int64_t> rows;
+    for (int64_t r = 0; r < J; ++r)
+        if (!((double)e[r] < e_cut)) rows.push_back(r);
+    *n_built = (int64_t)rows.size();
+    if (rows.empty()) return LMOSEM_OK;
+    lmosem_status st;
+    int64_t* d_rows = nullptr;
+    Scratch tmp(c);
+    if ((st = tmp.alloc(&d_rows, rows.size()))) return st;
+    LMOSEM_CK(c, cudaMemcpyAsync(d_rows, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 c->stream));
+    st = build_model_surrogate_rows(c, d_rows, (int64_t)rows.size());  // synchronises before rows is freed
+    return st;
 }
 
 // The rows of the current (FP32) model whose event energy lies below e_cut,
