@@ -672,13 +672,10 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
             const int mc = (lane >> 3) + 4 * i;
             const float U = strip_weight(uw, mp[buf * kStage + mc]);
             sUw[mc * 8 + (lane & 7)] = make_float2(U, U);
-            // byte g of the ballot (lanes 8g .. 8g + 7: scatter pixel g + 4i)
-            // folded into its bit 8g, then the four bits gathered
-            unsigned t = __ballot_sync(0xffffffffu, U != 0.0f);
-            t |= t >> 4;
-            t |= t >> 2;
-            t |= t >> 1;
-            live |= ((t & 1u) | ((t >> 7) & 2u) | ((t >> 14) & 4u) | ((t >> 21) & 8u)) << (4 * i);
+            const unsigned bal = __ballot_sync(0xffffffffu, U != 0.0f);
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if ((bal >> (8 * g)) & 0xffu) live |= 1u << (g + 4 * i);
         }
         __syncwarp();
         const float* pS = planes + (buf * 3 + 0) * kPlaneF + 4 * lane;
