@@ -68,37 +68,43 @@ struct WTabArgs {
     float* wtab;                // [slot - s0][plane s, b, -lw][m][ld_w]
 };
 
-// planes (s, b, -lw) of the scatter path (n, m) at the angle of one slot
-__global__ void k_wtable(WTabArgs A) {
+// planes (s, b, -lw) of the scatter path (n, m) at the angles of the group's
+// slots: one thread per (n, m) walks the slots, so the angle-free inputs
+// (the pair integral, the scatter pixel) are read once for all of them
+__global__ void k_wtable(WTabArgs A, int n_slots) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     int k = blockIdx.y;
-    int g = blockIdx.z;
     if (n >= A.ld_w) return;
-    float s = 0.0f, b = 0.0f, nlw = INFINITY;
-    if (n < A.n_sup) {
-        int a = A.slot_angle[A.s0 + g];
-        int pn = A.sup[n];
-        const float4 gm = __ldg(A.scat_geo + k);
-        const int pm = __float_as_int(gm.w);
-        float cpsi, rinv;
-        if (path_geometry_xy(pixel_x(pn, A.nx, A.dpx), pixel_y(pn, A.nx, A.ny, A.dpx), gm.x, gm.y,
-                             pn == pm, A.trig[a], &cpsi, &rinv)) {
-            float P, kt;
-            compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
-            float e1 = A.e0 * P;
-            float ratio = compton_lookup(A.compton, cpsi).x;
-            float att = fmaf(ratio, A.l_edge[(size_t)a * A.npix + pm], A.l_pair[(size_t)k * A.n_sup + n]);
-            float ri = rsqrtf(e1);
-            nlw = fmaf(att, kLog2e, -__log2f(A.w_const * gm.z * kt * rinv * ri));
-            s = A.cE * ri;
-            b = -e1 * s;
+    const size_t plane = (size_t)A.n_scat * A.ld_w;
+    float* base = A.wtab + (size_t)k * A.ld_w + n;
+    const bool real = n < A.n_sup;
+    const int pn = real ? A.sup[n] : 0;
+    const float4 gm = __ldg(A.scat_geo + k);
+    const int pm = __float_as_int(gm.w);
+    const float lpair = real ? A.l_pair[(size_t)k * A.n_sup + n] : 0.0f;
+    const float xn = pixel_x(pn, A.nx, A.dpx), yn = pixel_y(pn, A.nx, A.ny, A.dpx);
+    for (int g = 0; g < n_slots; ++g) {
+        float s = 0.0f, b = 0.0f, nlw = INFINITY;
+        if (real) {
+            int a = A.slot_angle[A.s0 + g];
+            float cpsi, rinv;
+            if (path_geometry_xy(xn, yn, gm.x, gm.y, pn == pm, A.trig[a], &cpsi, &rinv)) {
+                float P, kt;
+                compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
+                float e1 = A.e0 * P;
+                float ratio = compton_lookup(A.compton, cpsi).x;
+                float att = fmaf(ratio, A.l_edge[(size_t)a * A.npix + pm], lpair);
+                float ri = rsqrtf(e1);
+                nlw = fmaf(att, kLog2e, -__log2f(A.w_const * gm.z * kt * rinv * ri));
+                s = A.cE * ri;
+                b = -e1 * s;
+            }
         }
+        float* out = base + (size_t)g * 3 * plane;
+        out[0] = s;
+        out[plane] = b;
+        out[2 * plane] = nlw;
     }
-    size_t plane = (size_t)A.n_scat * A.ld_w;
-    float* base = A.wtab + (size_t)g * 3 * plane + (size_t)k * A.ld_w + n;
-    base[0] = s;
-    base[plane] = b;
-    base[2 * plane] = nlw;
 }
 
 // Every angle's planes (s, b, -lw) (indexed by angle) and, in the same pass,
@@ -1124,7 +1130,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         if (!pre) {
             WTabArgs W = wtab_args(c, c->d_wtab, d_slot_angle, s0);
             LMOSEM_PROF_BEGIN(c);
-            k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, s1 - s0), 256, 0, c->stream>>>(W);
+            k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat), 256, 0, c->stream>>>(W, s1 - s0);
             LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
         }
 
@@ -1493,7 +1499,7 @@ lmosem_status build_binned_rows(lmosem_ctx* c, const int32_t* d_rowmap, int n_eb
         if (!pre) {
             WTabArgs W = wtab_args(c, c->d_wtab, d_ang, a0);
             LMOSEM_PROF_BEGIN(c);
-            k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat, na), 256, 0, c->stream>>>(W);
+            k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat), 256, 0, c->stream>>>(W, na);
             LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
         }
         B.wtab = pre ? c->d_wtab_all : c->d_wtab;
