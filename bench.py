@@ -108,6 +108,9 @@ def parse():
     ap.add_argument("--table-budget-mb", type=int, default=0,
                     help="device budget of the scatter-weight tables (0: the library's 4 GiB); "
                          "small profiling captures keep one angle group resident")
+    ap.add_argument("--e-sigma", type=float, default=0.0,
+                    help="energy cut of the path sum in energy sigmas (0: the library's 6; "
+                         "negative: every term, the exact sum)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dat128")
     args = ap.parse_args()
     if args.fmt is None:
@@ -370,13 +373,17 @@ def run_ours(args, rank, world, local_rank):
 
     budget = args.table_budget_mb << 20
 
-    def step(fmt, a, u, e, profile=0):
-        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=profile,
+    kept_terms = {}
+
+    def step(fmt, a, u, e, profile=0, count=False):
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, e_sigma=args.e_sigma, profile=profile,
                               table_budget_bytes=budget)
         try:
             nsup = L.lmosem_n_support(ctx)
             L.lmosem_sensitivity(ctx, ns)
             L.lmosem_build_model(ctx, a, u, e, ns, fmt)
+            if count:   # untimed steps only: the count synchronises the stream
+                kept_terms[fmt] = L.lmosem_model_terms(ctx)
             f = torch.empty(nsup, dtype=torch.float32, device=dev)
             ll = torch.empty(1, dtype=torch.float64, device=dev)
             L.lmosem_init_image(ctx, T, f)
@@ -389,8 +396,8 @@ def run_ours(args, rank, world, local_rank):
             L.lmosem_destroy(ctx)
 
     for fmt in forms:
-        for _ in range(args.warmup):
-            step(fmt, a_d, u_d, e_d)
+        for w in range(max(1, args.warmup)):   # the first untimed step also counts the path terms
+            step(fmt, a_d, u_d, e_d, count=w == 0)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region, one block of steps per model format
@@ -438,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+        ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, e_sigma=args.e_sigma)
         try:
             L.lmosem_reconstruct(ctx, a_h, u_h, e_h, ns, ni, T, chosen, f_h, ll_h)
         finally:
@@ -454,7 +461,7 @@ def run_ours(args, rank, world, local_rank):
     for fmt in forms:
         it_times = []
         for prof_level in (0, 1):
-            ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, profile=prof_level)
+            ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, e_sigma=args.e_sigma, profile=prof_level)
             try:
                 L.lmosem_sensitivity(ctx, ns)
                 L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, fmt)
@@ -488,7 +495,7 @@ def run_ours(args, rank, world, local_rank):
     # without a preceding sensitivity pass builds the tables itself) + the
     # subset passes and updates.
     otf_times = []
-    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream)
+    ctx = L.lmosem_create(ph.mu, ph.pixel_mm, g, stream=stream, e_sigma=args.e_sigma)
     try:
         L.lmosem_sensitivity(ctx, ns)
         L.lmosem_build_model(ctx, a_d, u_d, e_d, ns, chosen)
@@ -509,7 +516,10 @@ def run_ours(args, rank, world, local_rank):
             if rank == 0 and WORKLOAD == "dat64" else None)
     errors = (oracle_subset_errors(L, stream, dev)
               if rank == 0 and WORKLOAD == "dat128" and os.path.exists(GOLDEN_128) else None)
-    terms, n_nz = strip_terms(ph, g, ev)
+    # path terms: those of the exact sum (host enumeration of the position
+    # strips) and those the kernels formed after the energy cut (device count)
+    terms_exact, n_nz = strip_terms(ph, g, ev)
+    terms = kept_terms[chosen]
     evals = J * n_nz
     pk, pk_kind = peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -579,6 +589,9 @@ def run_ours(args, rank, world, local_rank):
         "kernel_share": {k: v[0] / tot_kernel_ms for k, v in agg.items() if v[1]},
         "model_build_evals_per_s": evals / (ps_launch_ms * ps_n / args.steps * 1e-3),
         "path_terms_per_step": terms,
+        "path_terms_exact_sum_per_step": terms_exact,
+        "energy_cut_kept_frac": terms / terms_exact,
+        "energy_cut_sigma": (args.e_sigma if args.e_sigma > 0 else 6.0) if args.e_sigma >= 0 else None,
         "os_vs_mlem": osml,
         "loglik_final": ll_final,
         "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": UNIT,
@@ -587,7 +600,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "k_pathsum", "achieved": achieved, "peak": peak,
                      "unit": "Gterm/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "%d MUFU ex2 per clock per SM x %d SMs x %.0f MHz; one ex2 and "
-                                   "three FP32 FMAs per path term" % (MUFU_EX2_PER_CLK_SM, sms, sm_max)},
+                                   "three FP32 FMAs per path term" % (MUFU_EX2_PER_CLK_SM, sms, sm_max),
+                     "units": "path terms the position and energy cuts keep (counted by the kernels)"},
         "roofline_pass": {"bound": "hbm", "kernel": "k_osem_coop" if pass_n < 10 else "k_pass",
                           "units": "model rows once per iteration plus the image once per subset",
                           "achieved": pass_gbs,

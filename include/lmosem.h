@@ -123,6 +123,14 @@ typedef struct {
      * -1 = none, 0 = automatic (rows wide enough to be processed one at a
      * time: about 48 KB ahead per CTA; none otherwise), 1..16. */
     int32_t prefetch_groups;
+    /* Energy cut of the scatter terms: a term U_jm W_a(n, m) phi(E_j; E', sigma_E)
+     * of the sum of paper Eq. 2 is left out when the event energy E_j lies
+     * farther than e_sigma energy sigmas sigma_E(E') from the Compton energy
+     * E'_a(n', m) of every support pixel n' of the 128-pixel column tile
+     * that holds n.  Every term left out is below 2^(-e_sigma^2 log2(e) / 2)
+     * of its value at E_j = E' (1.5e-8 at 6).  0 selects the default 6;
+     * a negative value keeps every term (the exact sum); EINVAL above 20. */
+    float e_sigma;
 } lmosem_options;
 
 /* Kernel classes reported by lmosem_profile_read. */
@@ -459,6 +467,15 @@ int64_t lmosem_model_bytes(const lmosem_ctx* ctx);
 
 /* Number of kernel launches this context has enqueued so far. */
 int64_t lmosem_launch_count(const lmosem_ctx* ctx);
+
+/* Path terms of the last exact model build (paper Eq. 2 with Eq. 4: one
+ * term per (event, support pixel) for the primary path and one per (event,
+ * support pixel, scatter pixel) whose term the position cut (k_sigma) and
+ * the energy cut (e_sigma) keep), counted by the path-sum kernels.  Padding
+ * columns are not counted.  Synchronises the context stream.  EINVAL: no
+ * exact model has been built (a surrogate build counts only the rows the
+ * path sum made). */
+lmosem_status lmosem_model_terms(lmosem_ctx* ctx, int64_t* h_terms);
 
 /* Change the clock-cycle budget of the bounded device waits (see
  * lmosem_options.wait_budget_cycles; 0 restores 2e9) for the calls that

@@ -276,6 +276,16 @@ lmosem_status lmosem_set_wait_budget(lmosem_ctx* c, int64_t cycles) {
     return LMOSEM_OK;
 }
 
+lmosem_status lmosem_model_terms(lmosem_ctx* c, int64_t* h_terms) {
+    if (!c || !h_terms) return LMOSEM_EINVAL;
+    if (!c->terms_valid || !c->d_terms) return fail(c, LMOSEM_EINVAL, "no exact model build to count");
+    unsigned long long v = 0;
+    LMOSEM_CK(c, cudaMemcpyAsync(&v, c->d_terms, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    LMOSEM_CK(c, cudaStreamSynchronize(c->stream));
+    *h_terms = (int64_t)v;
+    return LMOSEM_OK;
+}
+
 int64_t lmosem_model_bytes(const lmosem_ctx* ctx) {
     if (!ctx || ctx->fmt < 0) return 0;
     int64_t elem = ctx->fmt == LMOSEM_MODEL_FP32 ? 4 : 2;
@@ -312,6 +322,7 @@ void lmosem_destroy(lmosem_ctx* c) {
     c->coop_words = 0;
     dev_free(c, &c->d_llpart);
     dev_free(c, &c->d_scalar);
+    dev_free(c, &c->d_terms);
     dev_free(c, &c->d_status);
     dev_free(c, &c->d_surrogate);
     for (auto& r : c->prof) {
@@ -340,6 +351,8 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
         return LMOSEM_EINVAL;
     float ks = opts && opts->k_sigma != 0.0f ? opts->k_sigma : 6.0f;
     if (!(ks > 0.0f && ks <= 20.0f)) return LMOSEM_EINVAL;
+    float es = opts && opts->e_sigma != 0.0f ? opts->e_sigma : 6.0f;
+    if (!(es <= 20.0f)) return LMOSEM_EINVAL;  // also rejects NaN
 
     lmosem_ctx* c = new (std::nothrow) lmosem_ctx();
     if (!c) return LMOSEM_ENOMEM;
@@ -369,6 +382,7 @@ lmosem_status lmosem_create(const lmosem_object* obj, const lmosem_geometry* geo
     c->e_lo = en->e_lo_kev;
     c->e_hi = en->e_hi_kev;
     c->k_sigma = ks;
+    c->e_sigma = es > 0.0f ? es : 0.0f;
     if (opts && opts->table_budget_bytes > 0) c->table_budget = opts->table_budget_bytes;
     c->profile = opts ? opts->profile : 0;
     if (c->profile < 0 || c->profile > 2) {

@@ -41,6 +41,7 @@ struct lmosem_ctx {
     double angle0 = 0, bin_mm = 0, radius = 0, fwhm0 = 0, fwhm_slope = 0;
     double e0 = 0, fwhm_frac = 0, e_lo = 0, e_hi = 0;
     float k_sigma = 6.0f;
+    float e_sigma = 6.0f;         // energy cut of the scatter terms (sigmas); <= 0: none
     int64_t table_budget = int64_t(4) << 30;
 
     int n_sup = 0, n_scat = 0, ld_w = 0;  // ld_w: support padded to kTN
@@ -103,6 +104,8 @@ struct lmosem_ctx {
     float* d_bpart = nullptr;     // pass_ctas x n_sup
     double* d_llpart = nullptr;   // pass_ctas
     double* d_scalar = nullptr;   // small FP64 scratch
+    unsigned long long* d_terms = nullptr;  // path terms of the last model build (path-sum kernels)
+    bool terms_valid = false;
     int* d_status = nullptr;      // [0] = 1 after a bounded device wait ran out
     long long wait_budget = 2000000000LL;  // clock cycles per bounded wait
     int pass_variant = 0;         // 0 auto, 1 register pipeline, 2 bulk-copy ring, 3 cp.async ring,

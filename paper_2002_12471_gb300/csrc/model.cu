@@ -30,6 +30,14 @@
 // last column tile with few live columns runs in a tail form (one event per
 // thread); both leave every result bit unchanged.
 //
+// Energy cut: the table kernels also record, per scatter pixel m and column
+// tile, the hull [lo, hi] of E' -/+ e_sigma sigma_E(E') over the tile's paths
+// (n, m).  An event whose energy lies outside it takes U_jm = 0 for the tile:
+// each term so dropped is below 2^(-e_sigma^2 log2(e) / 2) of its value at
+// E_j = E' (1.5e-8 at the default 6 sigma, the same width as the position
+// cut).  It drops the backscatter paths of photopeak events; the event sort
+// puts the photopeak class in tiles of its own, so whole warps skip them.
+//
 // The binned form (paper Section 4) integrates the same model over position
 // and energy bins; it reads the same planes (k_binned, below).
 #include <cuda_bf16.h>
@@ -66,7 +74,32 @@ struct WTabArgs {
     float w_const;              // D^2 / (2 pi sqrt(2 pi kappa)), sigma_E^2 = kappa E
     float cE;                   // s = cE / sqrt(E')
     float* wtab;                // [slot - s0][plane s, b, -lw][m][ld_w]
+    // energy hull of the scatter pixel m over the support pixels of a column
+    // tile: [slot - s0][column tile][m] = (bits of lo, ~bits of hi), where
+    // [lo, hi] covers E' -/+ e_sigma sigma_E(E') of every path (n, m) of the
+    // tile; both words start at 0xffffffff and take atomicMin (the bits of
+    // non-negative floats order as unsigned integers)
+    uint2* hull;
+    int n_ptiles;
+    float hK;                   // e_sigma sqrt(kappa): half-width = hK sqrt(E'); inf: no cut
 };
+
+// (lo, hi) of one path in hull encoding
+__device__ __forceinline__ uint2 hull_bits(float e1, float ri, float hK) {
+    const float h = hK * (e1 * ri);  // e_sigma sigma_E(E'), sigma_E^2 = kappa E'
+    return make_uint2(__float_as_uint(fmaxf(e1 - h, 0.0f)), ~__float_as_uint(e1 + h));
+}
+
+// warp-combine the lanes' hull words (lanes without a path hold 0xffffffff)
+// and fold them into the table entry
+__device__ __forceinline__ void hull_fold(uint2* dst, uint2 v) {
+    const unsigned lo = __reduce_min_sync(0xffffffffu, v.x);
+    const unsigned hi = __reduce_min_sync(0xffffffffu, v.y);
+    if ((threadIdx.x & 31) == 0) {
+        if (lo != 0xffffffffu) atomicMin(&dst->x, lo);
+        if (hi != 0xffffffffu) atomicMin(&dst->y, hi);
+    }
+}
 
 // planes (s, b, -lw) of the scatter path (n, m) at the angles of the group's
 // slots: one thread per (n, m) walks the slots, so the angle-free inputs
@@ -85,6 +118,7 @@ __global__ void k_wtable(WTabArgs A, int n_slots) {
     const float xn = pixel_x(pn, A.nx, A.dpx), yn = pixel_y(pn, A.nx, A.ny, A.dpx);
     for (int g = 0; g < n_slots; ++g) {
         float s = 0.0f, b = 0.0f, nlw = INFINITY;
+        uint2 hb = make_uint2(0xffffffffu, 0xffffffffu);
         if (real) {
             int a = A.slot_angle[A.s0 + g];
             float cpsi, rinv;
@@ -98,12 +132,16 @@ __global__ void k_wtable(WTabArgs A, int n_slots) {
                 nlw = fmaf(att, kLog2e, -__log2f(A.w_const * gm.z * kt * rinv * ri));
                 s = A.cE * ri;
                 b = -e1 * s;
+                hb = hull_bits(e1, ri, A.hK);
             }
         }
         float* out = base + (size_t)g * 3 * plane;
         out[0] = s;
         out[plane] = b;
         out[2 * plane] = nlw;
+        // whole warps share k and a 32-column slice of one tile (ld_w is a
+        // multiple of kTN and the grid's surplus threads are whole warps)
+        hull_fold(A.hull + ((size_t)g * A.n_ptiles + n / kTN) * A.n_scat + k, hb);
     }
 }
 
@@ -126,22 +164,18 @@ __global__ void k_wtable_sens(WSensArgs S) {
     const WTabArgs& A = S.w;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
-    if (n >= A.ld_w) return;
+    if (n >= A.ld_w) return;  // never splits a warp: ld_w is a multiple of kTN
     const size_t plane = (size_t)A.n_scat * A.ld_w;
     float* base = A.wtab + (size_t)a * 3 * plane + n;
-    if (n >= A.n_sup) {  // padding columns: no path
-        for (int k = 0; k < A.n_scat; ++k) {
-            base[(size_t)k * A.ld_w] = 0.0f;
-            base[plane + (size_t)k * A.ld_w] = 0.0f;
-            base[2 * plane + (size_t)k * A.ld_w] = INFINITY;
-        }
-        return;
-    }
-    const int pn = A.sup[n];
+    uint2* hull = A.hull + ((size_t)a * A.n_ptiles + n / kTN) * A.n_scat;
+    const bool real = n < A.n_sup;  // padding columns: no path, but they join the warp's hull fold
+    const int pn = real ? A.sup[n] : 0;
     const float xn = pixel_x(pn, A.nx, A.dpx), yn = pixel_y(pn, A.nx, A.ny, A.dpx);
     const float2 trig = A.trig[a];
-    double acc = (double)(expf(-A.l_edge[(size_t)a * A.npix + pn]) * S.ppar[(size_t)a * A.ld_w + n].w * S.de0);
-    const float* lp = A.l_pair + n;
+    double acc = 0.0;
+    if (real)
+        acc = (double)(expf(-A.l_edge[(size_t)a * A.npix + pn]) * S.ppar[(size_t)a * A.ld_w + n].w * S.de0);
+    const float* lp = A.l_pair + (real ? n : 0);
     const float* le = A.l_edge + (size_t)a * A.npix;
     const float* du = S.du_m + (size_t)a * A.n_scat;
     float part = 0.0f;
@@ -149,8 +183,9 @@ __global__ void k_wtable_sens(WSensArgs S) {
         const float4 gm = __ldg(A.scat_geo + k);
         const int pm = __float_as_int(gm.w);
         float s = 0.0f, b = 0.0f, nlw = INFINITY;
+        uint2 hb = make_uint2(0xffffffffu, 0xffffffffu);
         float cpsi, rinv;
-        if (path_geometry_xy(xn, yn, gm.x, gm.y, pn == pm, trig, &cpsi, &rinv)) {
+        if (real && path_geometry_xy(xn, yn, gm.x, gm.y, pn == pm, trig, &cpsi, &rinv)) {
             float P, kt;
             compton(cpsi, A.eps0, A.inv_kbar, &P, &kt);
             const float2 cr = compton_lookup(A.compton, cpsi);  // (mu ratio, window mass)
@@ -161,19 +196,21 @@ __global__ void k_wtable_sens(WSensArgs S) {
             nlw = fmaf(att, kLog2e, -__log2f(A.w_const * mu * kt * rinv * ri));
             s = A.cE * ri;
             b = -e1 * s;
+            hb = hull_bits(e1, ri, A.hK);
             const float w = S.w_const_sens * mu * kt * rinv * __expf(-att);
             part = fmaf(w, __ldg(du + k) * cr.y, part);
         }
         base[(size_t)k * A.ld_w] = s;
         base[plane + (size_t)k * A.ld_w] = b;
         base[2 * plane + (size_t)k * A.ld_w] = nlw;
+        hull_fold(hull + k, hb);
         if ((k & 31) == 31) {
             acc += (double)part;
             part = 0.0f;
         }
     }
     acc += (double)part;
-    S.sens_angle[(size_t)a * A.n_sup + n] = acc;
+    if (real) S.sens_angle[(size_t)a * A.n_sup + n] = acc;
 }
 
 struct PathSumArgs {
@@ -199,7 +236,42 @@ struct PathSumArgs {
     int64_t row_base;            // out row = sorted row - row_base
     int n_store;                 // columns to store (padded row width)
     int scatter_only;            // 1: leave the primary path out
+    // energy cut: hull of each scatter pixel over a column tile's paths,
+    // [slot][column tile][m] (see WTabArgs); an event whose energy lies
+    // outside it takes U_jm = 0 for that tile, so its terms there are exact
+    // zeros in every form
+    const uint2* hull;
+    int n_ptiles;
+    int e_cut;                   // 1: apply the energy cut
+    int n_sup;                   // real support columns (for the term count)
+    unsigned long long* n_terms; // terms kept by both cuts, summed over the launch
 };
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+
+// true when energy e lies outside the staged hull h (lo, ~hi bits): every
+// term of the event at this scatter pixel and column tile is then dropped
+__device__ __forceinline__ bool energy_cut(float e, uint2 h) {
+    return e < __uint_as_float(h.x) || e > __uint_as_float(~h.y);
+}
+
+// hull words of stage rows c0 .. c0 + kStage - 1 into hl[buf * kStage + t],
+// one row per thread t in [0, kStage) (padded rows: no cut, their U is 0)
+template <typename TI>
+__device__ __forceinline__ void stage_hull(int t, const TI& T, const int* mlist, const uint2* hull_a, uint2* hl,
+                                           int c0, int buf) {
+    if (t >= 0 && t < kStage) {
+        uint2* dst = hl + buf * kStage + t;
+        if (c0 + t < T.nm) cp_async8(dst, hull_a + mlist[c0 + t]);
+        else *dst = make_uint2(0u, 0u);
+    }
+}
+
+// real support columns of the column tile starting at n0
+__device__ __forceinline__ int tile_cols(const PathSumArgs& A, int n0) { return max(0, min(kTN, A.n_sup - n0)); }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     float2 d;
@@ -360,7 +432,8 @@ constexpr int kPlaneF = kStage * kTN;                 // one plane of one stage
 constexpr int kOffPlanes = 0;                         // [2][3][kStage][kTN]
 constexpr int kOffU = kOffPlanes + 2 * 3 * kPlaneF;   // [kStage][kTJ] float2
 constexpr int kOffMp = kOffU + 2 * kStage * kTJ;      // [2][kStage] float4
-constexpr int kOffEv = kOffMp + 2 * kStage * 4;       // u[kTJ], e[kTJ]
+constexpr int kOffHl = kOffMp + 2 * kStage * 4;       // [2][kStage] uint2 (energy hull)
+constexpr int kOffEv = kOffHl + 2 * kStage * 2;       // u[kTJ], e[kTJ]
 constexpr int kOffMisc = kOffEv + 2 * kTJ;            // 16 ints
 constexpr int kOffList = kOffMisc + 16;               // n_scat ints
 
@@ -371,7 +444,8 @@ constexpr int kOffList = kOffMisc + 16;               // n_scat ints
 template <int NT = kBuildThreads>
 __device__ __forceinline__ void stage_issue(const TileInfo& T, const int* mlist, const float* tab,
                                             size_t plane, int ld_w, const float4* mp_a, float* planes,
-                                            float4* mp, int c0, int buf, int nq, int row = kTN) {
+                                            float4* mp, int c0, int buf, int nq, int row = kTN,
+                                            const uint2* hull_a = nullptr, uint2* hl = nullptr) {
     const int tid = threadIdx.x;
     for (int k = tid; k < 3 * kStage * nq; k += NT) {
         const int p = k / (kStage * nq);
@@ -390,6 +464,7 @@ __device__ __forceinline__ void stage_issue(const TileInfo& T, const int* mlist,
         if (c0 + tid < T.nm) cp_async16(dst, mp_a + mlist[c0 + tid]);
         else *dst = make_float4(0.0f, 0.0f, -INFINITY, -1.0f);  // cut < 0: U = 0
     }
+    if (hull_a) stage_hull(tid - kStage, T, mlist, hull_a, hl, c0, buf);
     cp_async_commit();
 }
 
@@ -407,12 +482,14 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs
     float* planes = sm + kOffPlanes;
     float2* sU = reinterpret_cast<float2*>(sm + kOffU);
     float4* mp = reinterpret_cast<float4*>(sm + kOffMp);
+    uint2* hl = reinterpret_cast<uint2*>(sm + kOffHl);
     float* ev_u = sm + kOffEv;
     float* ev_e = ev_u + kTJ;
     int* misc = reinterpret_cast<int*>(sm + kOffMisc);
     int* mlist = reinterpret_cast<int*>(sm + kOffList);
     const int tid = threadIdx.x;
     const TileInfo T = tile_setup(A, blockIdx.x, A.pt0, ev_u, ev_e, misc, mlist);
+    const uint2* hull_a = A.hull + ((size_t)A.ent_wpos[T.ent] * A.n_ptiles + T.n0 / kTN) * A.n_scat;
     const int nq = A.nq_tail;
     constexpr int kQ = kNarrowQ / 4;
     const int jn = tid & (kTJ - 1), qs = tid / kTJ;  // event, first column group
@@ -435,11 +512,13 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs
     const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
     const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
     const int nchunks = (T.nm + kStage - 1) / kStage;
-    if (nchunks > 0) stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, 0, 0, nq);
+    unsigned kept = 0;  // (event, scatter pixel) pairs with U != 0 formed by this thread
+    if (nchunks > 0) stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, 0, 0, nq, kTN, hull_a, hl);
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c & 1;
         if (c + 1 < nchunks) {
-            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 1) * kStage, buf ^ 1, nq);
+            stage_issue(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 1) * kStage, buf ^ 1, nq, kTN, hull_a,
+                        hl);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -447,7 +526,9 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs
         __syncthreads();
         for (int k = tid; k < kStage * kTJ; k += kBuildThreads) {
             const int mc = k / kTJ, j = k - mc * kTJ;
-            const float U = strip_weight(ev_u[j], mp[buf * kStage + mc]);
+            const float U = (A.e_cut && energy_cut(ev_e[j], hl[buf * kStage + mc])) ? 0.0f
+                                                                        : strip_weight(ev_u[j], mp[buf * kStage + mc]);
+            kept += U != 0.0f;
             sU[mc * kTJ + j] = make_float2(U, U);
         }
         __syncthreads();
@@ -468,6 +549,12 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum_narrow(PathSumArgs
             }
         }
         __syncthreads();
+    }
+    if (A.n_terms) {
+        const unsigned long long cols = (unsigned long long)tile_cols(A, T.n0);
+        const unsigned w = __reduce_add_sync(0xffffffffu, kept);
+        if ((tid & 31) == 0 && w) atomicAdd(A.n_terms, cols * w);
+        if (tid == 0 && !A.scatter_only) atomicAdd(A.n_terms, cols * (unsigned long long)T.nr);
     }
 
     if (jn >= T.nr) return;
@@ -493,7 +580,8 @@ constexpr int kTailQ = 4;
 constexpr int kTRow = 4 * kTailQ;                                 // floats per staged plane row
 constexpr int kTOffPlanes = 0;                                    // [3][3][kStage][kTRow]
 constexpr int kTOffMp = kTOffPlanes + 3 * 3 * kStage * kTRow;     // [3][kStage] float4
-constexpr int kTOffEv = kTOffMp + 3 * kStage * 4;                 // u[kTJ], e[kTJ]
+constexpr int kTOffHl = kTOffMp + 3 * kStage * 4;                 // [3][kStage] uint2 (energy hull)
+constexpr int kTOffEv = kTOffHl + 3 * kStage * 2;                 // u[kTJ], e[kTJ]
 constexpr int kTOffMisc = kTOffEv + 2 * kTJ;                      // 16 ints
 constexpr int kTOffList = kTOffMisc + 16;                         // n_scat ints
 
@@ -502,12 +590,14 @@ __global__ void __launch_bounds__(kTJ) k_pathsum_tail(PathSumArgs A) {
     float* sm = reinterpret_cast<float*>(smem4);
     float* planes = sm + kTOffPlanes;
     float4* mp = reinterpret_cast<float4*>(sm + kTOffMp);
+    uint2* hl = reinterpret_cast<uint2*>(sm + kTOffHl);
     float* ev_u = sm + kTOffEv;
     float* ev_e = ev_u + kTJ;
     int* misc = reinterpret_cast<int*>(sm + kTOffMisc);
     int* mlist = reinterpret_cast<int*>(sm + kTOffList);
     const int j = threadIdx.x;
     const TileInfo T = tile_setup<kTJ>(A, blockIdx.x, A.pt0, ev_u, ev_e, misc, mlist);
+    const uint2* hull_a = A.hull + ((size_t)A.ent_wpos[T.ent] * A.n_ptiles + T.n0 / kTN) * A.n_scat;
     const int nq = A.nq_tail;
     const float uj = ev_u[j], ej = ev_e[j];
     const float2 E2 = make_float2(ej, ej);
@@ -528,8 +618,9 @@ __global__ void __launch_bounds__(kTJ) k_pathsum_tail(PathSumArgs A) {
     const float* tab = A.wtab + (size_t)A.ent_wpos[T.ent] * 3 * plane + T.n0;
     const float4* mp_a = A.mpar + (size_t)T.a * A.n_scat;
     const int nchunks = (T.nm + kStage - 1) / kStage;
+    unsigned kept = 0;  // scatter pixels with U != 0 for this thread's event
     for (int q = 0; q < min(2, nchunks); ++q)
-        stage_issue<kTJ>(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, q * kStage, q, nq, kTRow);
+        stage_issue<kTJ>(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, q * kStage, q, nq, kTRow, hull_a, hl);
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c % 3;
         if (c + 1 < nchunks) cp_async_wait<1>();
@@ -537,13 +628,15 @@ __global__ void __launch_bounds__(kTJ) k_pathsum_tail(PathSumArgs A) {
         __syncthreads();  // stage c landed everywhere; every thread is done with stage c - 1
         if (c + 2 < nchunks)
             stage_issue<kTJ>(T, mlist, tab, plane, A.ld_w, mp_a, planes, mp, (c + 2) * kStage, (c + 2) % 3, nq,
-                             kTRow);
+                             kTRow, hull_a, hl);
         const float* pS = planes + (buf * 3 + 0) * kStage * kTRow;
         const float* pB = planes + (buf * 3 + 1) * kStage * kTRow;
         const float* pW = planes + (buf * 3 + 2) * kStage * kTRow;
         for (int mc = 0; mc < kStage; ++mc) {
-            const float U = strip_weight(uj, mp[buf * kStage + mc]);
+            const float U =
+                (A.e_cut && energy_cut(ej, hl[buf * kStage + mc])) ? 0.0f : strip_weight(uj, mp[buf * kStage + mc]);
             if (U == 0.0f) continue;
+            ++kept;
             const float2 U2 = make_float2(U, U);
 #pragma unroll
             for (int q = 0; q < kTailQ; ++q) {
@@ -553,6 +646,13 @@ __global__ void __launch_bounds__(kTJ) k_pathsum_tail(PathSumArgs A) {
                        *reinterpret_cast<const float4*>(pW + o), acc[q][0], acc[q][1]);
             }
         }
+    }
+
+    if (A.n_terms) {  // 64 threads: two whole warps
+        const unsigned long long cols = (unsigned long long)tile_cols(A, T.n0);
+        const unsigned w = __reduce_add_sync(0xffffffffu, kept);
+        if ((j & 31) == 0 && w) atomicAdd(A.n_terms, cols * w);
+        if (j == 0 && !A.scatter_only) atomicAdd(A.n_terms, cols * (unsigned long long)T.nr);
     }
 
     if (j >= T.nr) return;
@@ -578,11 +678,12 @@ constexpr int kWBuf = 3;
 constexpr int kWarps = kBuildThreads / 32;
 constexpr int kWOffPlanes = 0;                                   // [kWBuf][3][kStage][kTN]
 constexpr int kWOffMp = kWOffPlanes + kWBuf * 3 * kPlaneF;       // [kWBuf][kStage] float4
-constexpr int kWOffU = kWOffMp + kWBuf * kStage * 4;             // [warp][kStage][8] float2
+constexpr int kWOffHl = kWOffMp + kWBuf * kStage * 4;            // [kWBuf][kStage] uint2 (energy hull)
+constexpr int kWOffU = kWOffHl + kWBuf * kStage * 2;             // [warp][kStage][8] float2
 constexpr int kWOffEv = kWOffU + kWarps * kStage * 8 * 2;        // u[kTJ], e[kTJ]
 constexpr int kWOffMisc = kWOffEv + 2 * kTJ;                     // 16 ints
 constexpr int kWOffList = kWOffMisc + 16;                        // n_scat ints
-static_assert(kWOffMp % 4 == 0 && kWOffU % 4 == 0, "16-byte aligned stage buffers");
+static_assert(kWOffMp % 4 == 0 && kWOffU % 4 == 0 && kWOffHl % 2 == 0, "aligned stage buffers");
 static_assert(kTJ == 8 * kWarps && kStage == 16, "8 events per warp; 16-bit live masks; 4 U per lane");
 static_assert(kBuildThreads == 256 && kTN == 128 && kStage == 2 * kWarps, "one column group, two stage rows per thread");
 
@@ -594,7 +695,7 @@ static_assert(kBuildThreads == 256 && kTN == 128 && kStage == 2 * kWarps, "one c
 // parameters of stage row t.
 __device__ __forceinline__ void stage_issue_wide(const TileInfo& T, const int* mlist, const float* tab_q,
                                                  size_t plane, int ld_w, const float4* mp_a, float* dst_q,
-                                                 float4* mp, int c0, int buf) {
+                                                 float4* mp, const uint2* hull_a, uint2* hl, int c0, int buf) {
     const int tid = threadIdx.x, mc0 = tid >> 5;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -617,6 +718,7 @@ __device__ __forceinline__ void stage_issue_wide(const TileInfo& T, const int* m
         if (c0 + tid < T.nm) cp_async16(dst, mp_a + mlist[c0 + tid]);
         else *dst = make_float4(0.0f, 0.0f, -INFINITY, -1.0f);  // cut < 0: U = 0
     }
+    stage_hull(tid - kStage, T, mlist, hull_a, hl, c0, buf);
     cp_async_commit();
 }
 
@@ -625,6 +727,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     float* sm = reinterpret_cast<float*>(smem4);
     float* planes = sm + kWOffPlanes;
     float4* mp = reinterpret_cast<float4*>(sm + kWOffMp);
+    uint2* hl = reinterpret_cast<uint2*>(sm + kWOffHl);
     float* ev_u = sm + kWOffEv;
     float* ev_e = ev_u + kTJ;
     int* misc = reinterpret_cast<int*>(sm + kWOffMisc);
@@ -636,7 +739,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     // few MB) stay in L2 for all of that angle's event tiles
     const TileInfo T = tile_setup(A, blockIdx.x % A.n_tiles, A.pt0 + blockIdx.x / A.n_tiles, ev_u, ev_e, misc,
                                   mlist);
-
+    const uint2* hull_a = A.hull + ((size_t)A.ent_wpos[T.ent] * A.n_ptiles + T.n0 / kTN) * A.n_scat;
     // accumulators (pairs of adjacent support pixels), initialised with the
     // primary path
     float2 E2[8];
@@ -661,24 +764,29 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
     const float* tab_q = tab + 4 * lane;
     float* dst_q = planes + warp * kTN + 4 * lane;
     for (int q = 0; q < min(2, nchunks); ++q)
-        stage_issue_wide(T, mlist, tab_q, plane, A.ld_w, mp_a, dst_q, mp, q * kStage, q);
+        stage_issue_wide(T, mlist, tab_q, plane, A.ld_w, mp_a, dst_q, mp, hull_a, hl, q * kStage, q);
     const float uw = ev_u[8 * warp + (lane & 7)];  // this lane's event in the U step
+    const float ew = ev_e[8 * warp + (lane & 7)];
+    unsigned kept = 0;  // (event, scatter pixel) pairs of the warp with U != 0
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c % kWBuf;
         if (c + 1 < nchunks) cp_async_wait<1>();
         else cp_async_wait<0>();
         __syncthreads();  // stage c landed everywhere; every warp is done with stage c - 1
         if (c + 2 < nchunks)
-            stage_issue_wide(T, mlist, tab_q, plane, A.ld_w, mp_a, dst_q, mp, (c + 2) * kStage, (c + 2) % kWBuf);
+            stage_issue_wide(T, mlist, tab_q, plane, A.ld_w, mp_a, dst_q, mp, hull_a, hl, (c + 2) * kStage,
+                             (c + 2) % kWBuf);
         // U_jm of this warp's events: lane holds event lane % 8 at scatter
         // pixels lane / 8 + 4 i
         unsigned live = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int mc = (lane >> 3) + 4 * i;
-            const float U = strip_weight(uw, mp[buf * kStage + mc]);
+            const float U =
+                (A.e_cut && energy_cut(ew, hl[buf * kStage + mc])) ? 0.0f : strip_weight(uw, mp[buf * kStage + mc]);
             sUw[mc * 8 + (lane & 7)] = make_float2(U, U);
             const unsigned bal = __ballot_sync(0xffffffffu, U != 0.0f);
+            kept += __popc(bal);
 #pragma unroll
             for (int g = 0; g < 4; ++g)
                 if ((bal >> (8 * g)) & 0xffu) live |= 1u << (g + 4 * i);
@@ -706,6 +814,12 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_pathsum(PathSumArgs A) {
         }
     }
 
+    if (A.n_terms && lane == 0) {
+        const unsigned long long cols = (unsigned long long)tile_cols(A, T.n0);
+        const int real = max(0, min(8, T.nr - 8 * warp));
+        const unsigned long long t = cols * (kept + (A.scatter_only ? 0u : (unsigned)real));
+        if (t) atomicAdd(A.n_terms, t);
+    }
     const int n = T.n0 + 4 * lane;
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
@@ -962,7 +1076,10 @@ __global__ void __launch_bounds__(kBuildThreads, 2) k_binned(BinnedArgs A) {
     }
 }
 
-WTabArgs wtab_args(const lmosem_ctx* c, float* wtab, const int32_t* slot_angle, int s0) {
+int64_t wtab_angle_floats(const lmosem_ctx* c);
+
+// planes of a buffer of n_buf slots, followed by the slots' energy hulls
+WTabArgs wtab_args(const lmosem_ctx* c, float* wtab, int n_buf, const int32_t* slot_angle, int s0) {
     const double fw2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
     const double kappa = pow(c->fwhm_frac * fw2s, 2.0) * c->e0;
     WTabArgs W;
@@ -989,10 +1106,23 @@ WTabArgs wtab_args(const lmosem_ctx* c, float* wtab, const int32_t* slot_angle, 
     W.w_const = (float)(c->dpx * c->dpx / (2.0 * kPi * sqrt(2.0 * kPi * kappa)));
     W.cE = (float)sqrt(1.4426950408889634 / (2.0 * kappa));
     W.wtab = wtab;
+    W.n_ptiles = c->ld_w / kTN;
+    W.hull = reinterpret_cast<uint2*>(wtab + (size_t)n_buf * 3 * c->n_scat * c->ld_w);
+    W.hK = c->e_sigma > 0.0f ? (float)(c->e_sigma * sqrt(kappa)) : INFINITY;
     return W;
 }
 
-int64_t wtab_angle_floats(const lmosem_ctx* c) { return (int64_t)3 * c->n_scat * c->ld_w; }
+// per angle: three planes of n_scat x ld_w floats, then the energy hulls of
+// n_scat x (ld_w / kTN) column tiles (two words each)
+int64_t wtab_angle_floats(const lmosem_ctx* c) {
+    return (int64_t)3 * c->n_scat * c->ld_w + (int64_t)2 * c->n_scat * (c->ld_w / kTN);
+}
+
+// hull words of n slots to their starting value (0xffffffff: no path yet)
+lmosem_status hull_reset(lmosem_ctx* c, const WTabArgs& W, int n) {
+    LMOSEM_CK(c, cudaMemsetAsync(W.hull, 0xff, sizeof(uint2) * (size_t)n * W.n_ptiles * c->n_scat, c->stream));
+    return LMOSEM_OK;
+}
 
 }  // namespace
 
@@ -1004,7 +1134,8 @@ lmosem_status wtab_all_with_sens(lmosem_ctx* c, double* sens_angle, float w_cons
     lmosem_status st;
     if ((st = dev_alloc(c, &c->d_wtab_all, (size_t)c->n_angles * wtab_angle_floats(c)))) return st;
     WSensArgs S;
-    S.w = wtab_args(c, c->d_wtab_all, nullptr, 0);
+    S.w = wtab_args(c, c->d_wtab_all, c->n_angles, nullptr, 0);
+    if ((st = hull_reset(c, S.w, c->n_angles))) return st;
     S.ppar = c->d_ppar;
     S.du_m = c->d_du_m;
     S.w_const_sens = w_const_sens;
@@ -1042,6 +1173,9 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     const int64_t per_angle = wtab_angle_floats(c) * (int64_t)sizeof(float);
     const int gsz = pre ? ns : (int)std::max<int64_t>(1, std::min<int64_t>(ns, c->table_budget / per_angle));
     const int n_groups = (ns + gsz - 1) / gsz;
+    if (!c->d_terms && (st = dev_alloc(c, &c->d_terms, 1))) return st;
+    LMOSEM_CK(c, cudaMemsetAsync(c->d_terms, 0, sizeof(unsigned long long), c->stream));
+    c->terms_valid = true;
 
     // launch entries (realisation, angle) of every group, in sorted-row order
     // within a realisation; one host array for all groups, copied once
@@ -1102,6 +1236,7 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
 
     if (!pre && (st = dev_alloc(c, &c->d_wtab, (size_t)gsz * wtab_angle_floats(c)))) return st;
     float* wtab = pre ? c->d_wtab_all : c->d_wtab;
+    const uint2* hull = wtab_args(c, wtab, pre ? c->n_angles : gsz, nullptr, 0).hull;
     const bool scaled = c->fmt != LMOSEM_MODEL_FP32;
     if (scaled) {
         // scaled rows are staged per group: one realisation, contiguous rows
@@ -1128,7 +1263,8 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
     for (int gi = 0; gi < n_groups; ++gi) {
         const int s0 = gi * gsz, s1 = std::min(ns, s0 + gsz);
         if (!pre) {
-            WTabArgs W = wtab_args(c, c->d_wtab, d_slot_angle, s0);
+            WTabArgs W = wtab_args(c, c->d_wtab, gsz, d_slot_angle, s0);
+            if ((st = hull_reset(c, W, s1 - s0))) return st;
             LMOSEM_PROF_BEGIN(c);
             k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat), 256, 0, c->stream>>>(W, s1 - s0);
             LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);
@@ -1161,6 +1297,11 @@ lmosem_status build_model_rows(lmosem_ctx* c) {
         P.ld_out = c->ld_model;
         P.n_store = (int)c->ld_model;
         P.scatter_only = c->scatter_only ? 1 : 0;
+        P.hull = hull;
+        P.n_ptiles = n_ptiles;
+        P.e_cut = c->e_sigma > 0.0f ? 1 : 0;
+        P.n_sup = c->n_sup;
+        P.n_terms = c->d_terms;
         const int64_t grow0 = g_row0[gi], grows = g_rows[gi];
         if (scaled) {
             P.out = c->d_stage;
@@ -1497,7 +1638,8 @@ lmosem_status build_binned_rows(lmosem_ctx* c, const int32_t* d_rowmap, int n_eb
     for (int a0 = 0; a0 < c->n_angles; a0 += gsz) {
         const int na = std::min(gsz, c->n_angles - a0);
         if (!pre) {
-            WTabArgs W = wtab_args(c, c->d_wtab, d_ang, a0);
+            WTabArgs W = wtab_args(c, c->d_wtab, gsz, d_ang, a0);
+            if ((st = hull_reset(c, W, na))) return st;  // written by the table kernel, unused here
             LMOSEM_PROF_BEGIN(c);
             k_wtable<<<dim3((c->ld_w + 255) / 256, c->n_scat), 256, 0, c->stream>>>(W, na);
             LMOSEM_LAUNCHED(c, LMOSEM_K_WTABLE);

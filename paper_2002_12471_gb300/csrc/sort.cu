@@ -1,11 +1,15 @@
 // Event ordering: validate the list-mode events and sort them by
-// (subset, angle, position bin) with two stable counting-sort passes.
-// Subsets are formed from detector angles (paper Section 2.2): subset i
-// holds the angles a with a mod N_s == i, so after sorting every subset, and
-// every angle within it, is a contiguous range of model rows; events of one
-// angle are ordered by position so that a tile of consecutive events needs a
-// narrow strip of scatter pixels.  Both passes are stable, so the order is a
-// deterministic function of the input.
+// (subset, angle, energy class, position bin) with two stable counting-sort
+// passes.  Subsets are formed from detector angles (paper Section 2.2):
+// subset i holds the angles a with a mod N_s == i, so after sorting every
+// subset, and every angle within it, is a contiguous range of model rows.
+// Within an angle the events below the photopeak class (E < E0 (1 - f_E / 2),
+// the lower half-maximum of the photopeak) come first, then those in it, each
+// class ordered by position: a tile of consecutive events then needs a
+// narrow strip of scatter pixels, and its events share an energy class, so
+// that the path sum's energy cut (which drops the backscatter paths of
+// photopeak events) drops them for whole warps alike.  Both passes are
+// stable, so the order is a deterministic function of the input.
 #include "lmosem_internal.cuh"
 
 namespace lmosem {
@@ -39,17 +43,19 @@ __device__ __forceinline__ int realisation_of(const int64_t* off, int n_real, in
 
 // digit of the event at original index i
 struct Digit {
-    int mode;  // 0: position bin, 1: subset-major angle slot, 2: realisation
+    int mode;  // 0: (energy class, position bin), 1: subset-major angle slot, 2: realisation
     const int32_t* a;
     const float* u;
     float half;
     int n_subsets, group;
     const int64_t* off;
     int n_real;
+    const float* e;
+    float e_class;  // lower edge of the photopeak class
     __device__ int operator()(int64_t i) const {
         if (mode == 0) {
             int b = (int)floorf((u[i] + half) * ((float)kUBins / (2.0f * half)));
-            return min(max(b, 0), kUBins - 1);
+            return min(max(b, 0), kUBins - 1) + (e[i] >= e_class ? kUBins : 0);
         }
         if (mode == 2) return realisation_of(off, n_real, i);
         int ai = a[i];
@@ -231,7 +237,7 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
     // the stable scatter keeps one count per (warp, digit) in 48 KB of shared memory
     if (ndig_a > 1536 || n_real > 1536)
         return fail(c, LMOSEM_EINVAL, "too many angles or realisations for the event sort");
-    int ndig = ndig_a > kUBins ? ndig_a : kUBins;
+    int ndig = ndig_a > 2 * kUBins ? ndig_a : 2 * kUBins;
     ndig = ndig > n_real ? ndig : n_real;
     const int nblk = (int)((n + kSortThreads - 1) / kSortThreads);
     const int64_t hn = (int64_t)ndig * nblk;
@@ -255,12 +261,13 @@ lmosem_status sort_events(lmosem_ctx* c, const int32_t* d_angle, const float* d_
                                      cudaMemcpyHostToDevice, c->stream));
     }
 
-    // stable passes, least significant key first: position bin, angle slot
-    // and, for several realisations, the realisation
-    Digit d0{0, d_angle, d_u, half, n_subsets, group, d_off, n_real};
-    Digit d1{1, d_angle, d_u, half, n_subsets, group, d_off, n_real};
-    Digit d2{2, d_angle, d_u, half, n_subsets, group, d_off, n_real};
-    if ((st = counting_pass(c, d0, kUBins, nullptr, p1, n, H, tot))) return st;
+    // stable passes, least significant key first: (energy class, position
+    // bin), angle slot and, for several realisations, the realisation
+    const float e_class = (float)(c->e0 * (1.0 - 0.5 * c->fwhm_frac));
+    Digit d0{0, d_angle, d_u, half, n_subsets, group, d_off, n_real, d_e, e_class};
+    Digit d1{1, d_angle, d_u, half, n_subsets, group, d_off, n_real, d_e, e_class};
+    Digit d2{2, d_angle, d_u, half, n_subsets, group, d_off, n_real, d_e, e_class};
+    if ((st = counting_pass(c, d0, 2 * kUBins, nullptr, p1, n, H, tot))) return st;
     if (n_real > 1) {
         if ((st = counting_pass(c, d1, ndig_a, p1, p2, n, H, tot))) return st;
         if ((st = counting_pass(c, d2, n_real, p2, c->d_perm, n, H, tot))) return st;

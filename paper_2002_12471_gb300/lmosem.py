@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("wait_budget_cycles", ctypes.c_int64),
                 ("pass_variant", ctypes.c_int32), ("ring_rows", ctypes.c_int32),
                 ("ring_stages", ctypes.c_int32), ("surrogate_kernel", ctypes.c_int32),
-                ("prefetch_groups", ctypes.c_int32)]
+                ("prefetch_groups", ctypes.c_int32), ("e_sigma", ctypes.c_float)]
 
 
 KERNEL_CLASSES = ["tables", "sort", "wtable", "pathsum", "quantize", "sens", "pass", "update",
@@ -95,6 +95,7 @@ SIGNATURES = {
     "lmosem_model_rows": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
     "lmosem_model_bytes": (_i64, [_vp]),
     "lmosem_launch_count": (_i64, [_vp]),
+    "lmosem_model_terms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     "lmosem_set_wait_budget": (ctypes.c_int, [_vp, _i64]),
     "lmosem_subset_totals": (ctypes.c_int, [_vp, _dbl, _vp, _vp]),
     "lmosem_profile_read": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -165,7 +166,8 @@ def _check(ctx, st):
 
 def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                   table_budget_bytes=0, stream=None, profile=False, wait_budget_cycles=0,
-                  pass_variant=0, ring_rows=0, ring_stages=0, surrogate_kernel=0, prefetch_groups=0):
+                  pass_variant=0, ring_rows=0, ring_stages=0, surrogate_kernel=0, prefetch_groups=0,
+                  e_sigma=0.0):
     """Create a context.  ``mu_per_mm`` is an (ny, nx) host array at the
     photopeak, ``geom`` holds the scanner and energy fields of
     ``include/lmosem.h``; ``stream`` is a torch.cuda.Stream or a raw handle."""
@@ -184,7 +186,7 @@ def lmosem_create(mu_per_mm, pixel_mm, geom: dict, support=None, k_sigma=0.0,
                float(geom["e_hi_kev"]))
     o = Options(float(k_sigma), int(table_budget_bytes), int(profile),
                 int(wait_budget_cycles), int(pass_variant), int(ring_rows), int(ring_stages),
-                int(surrogate_kernel), int(prefetch_groups))
+                int(surrogate_kernel), int(prefetch_groups), float(e_sigma))
     h = _vp()
     s = getattr(stream, "cuda_stream", stream)
     st = L.lmosem_create(ctypes.byref(obj), ctypes.byref(g), ctypes.byref(e), ctypes.byref(o),
@@ -298,6 +300,13 @@ def lmosem_model_bytes(ctx):
 
 def lmosem_launch_count(ctx):
     return int(load().lmosem_launch_count(ctx))
+
+
+def lmosem_model_terms(ctx):
+    """Path terms the path-sum kernels formed in the last exact model build."""
+    n = ctypes.c_int64(0)
+    _check(ctx, load().lmosem_model_terms(ctx, ctypes.byref(n)))
+    return int(n.value)
 
 
 def lmosem_set_wait_budget(ctx, cycles):

@@ -32,6 +32,10 @@ def gpu_reconstruct(ph, g, ev, n_subsets, n_iters, fmt="fp32", T=1.0, support=No
         sens = torch.zeros((n_subsets, nsup), dtype=torch.float64, device=dev)
         L.lmosem_sensitivity(ctx, n_subsets, sens)
         L.lmosem_build_model(ctx, a, u, e, n_subsets, fmt)
+        try:
+            out["terms"] = L.lmosem_model_terms(ctx)
+        except L.LmosemError:   # a build without path-sum rows
+            out["terms"] = None
         if rows is not None:
             ids = torch.as_tensor(np.asarray(rows, dtype=np.int64), device=dev)
             buf = torch.zeros((len(rows), nsup), dtype=torch.float32, device=dev)

@@ -74,6 +74,8 @@ def test_create_rejects_bad_object(lib):
     nan[2, 2] = np.nan
     assert _call_create(nan, g, pixel=ph.pixel_mm)[0] == L.EINVAL
     assert _call_create(ph.mu, g, pixel=ph.pixel_mm, k_sigma=-1.0)[0] == L.EINVAL
+    assert _call_create(ph.mu, g, pixel=ph.pixel_mm, e_sigma=25.0)[0] == L.EINVAL
+    assert _call_create(ph.mu, g, pixel=ph.pixel_mm, e_sigma=float("nan"))[0] == L.EINVAL
 
 
 def test_null_context_calls_fail_cleanly(lib):
