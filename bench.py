@@ -601,7 +601,11 @@ def run_ours(args, rank, world, local_rank):
                      "unit": "Gterm/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "%d MUFU ex2 per clock per SM x %d SMs x %.0f MHz; one ex2 and "
                                    "three FP32 FMAs per path term" % (MUFU_EX2_PER_CLK_SM, sms, sm_max),
-                     "units": "path terms the position and energy cuts keep (counted by the kernels)"},
+                     "units": "path terms the position and energy cuts keep (counted by the kernels)",
+                     "exact_sum_terms_frac": achieved * (terms_exact / terms) / peak,
+                     "exact_sum_terms_note": "the exact sum's terms (position strip only) per second of "
+                                             "the same kernel time, over the same peak: the rate at "
+                                             "which the cut delivers the exact sum's result"},
         "roofline_pass": {"bound": "hbm", "kernel": "k_osem_coop" if pass_n < 10 else "k_pass",
                           "units": "model rows once per iteration plus the image once per subset",
                           "achieved": pass_gbs,
