@@ -468,13 +468,16 @@ int64_t lmosem_model_bytes(const lmosem_ctx* ctx);
 /* Number of kernel launches this context has enqueued so far. */
 int64_t lmosem_launch_count(const lmosem_ctx* ctx);
 
-/* Path terms of the last exact model build (paper Eq. 2 with Eq. 4: one
- * term per (event, support pixel) for the primary path and one per (event,
- * support pixel, scatter pixel) whose term the position cut (k_sigma) and
- * the energy cut (e_sigma) keep), counted by the path-sum kernels.  Padding
- * columns are not counted.  Synchronises the context stream.  EINVAL: no
- * exact model has been built (a surrogate build counts only the rows the
- * path sum made). */
+/* Path terms that the path-sum kernels formed in their last row build on
+ * this context (paper Eq. 2 with Eq. 4: one term per (event, support pixel)
+ * for the primary path and one per (event, support pixel, scatter pixel)
+ * whose term the position cut (k_sigma) and the energy cut (e_sigma) keep).
+ * After lmosem_build_model or lmosem_build_model_batch with an FP32, FP16
+ * or BF16 format that is the whole model.  A surrogate build runs the path
+ * sum on the rows its exact judge and energy gate recompute, one set of
+ * rows at a time, and the count covers the last such set.  Padding columns
+ * are not counted.  Synchronises the context stream.  EINVAL: the path sum
+ * has not run on this context. */
 lmosem_status lmosem_model_terms(lmosem_ctx* ctx, int64_t* h_terms);
 
 /* Change the clock-cycle budget of the bounded device waits (see
