@@ -136,7 +136,7 @@ typedef struct {
 /* Kernel classes reported by lmosem_profile_read. */
 typedef enum {
     LMOSEM_K_TABLES = 0,   /* attenuation line integrals and per-angle parameters */
-    LMOSEM_K_SORT = 1,     /* event check and (subset, angle, position) sort      */
+    LMOSEM_K_SORT = 1,     /* event check and (subset, angle, class, position) sort */
     LMOSEM_K_WTABLE = 2,   /* per-angle scatter weight tables                     */
     LMOSEM_K_PATHSUM = 3,  /* per-event path-sum model build                      */
     LMOSEM_K_QUANTIZE = 4, /* row scaling to FP16/BF16                            */
@@ -213,8 +213,9 @@ lmosem_status lmosem_sensitivity(lmosem_ctx* ctx, int32_t n_subsets, double* d_s
  * primary path plus every first-order in-plane Compton path (q, m) with
  * attenuation, Klein-Nishina weight, energy blur and collimator response).
  * Events are three device arrays of length n_events (angle index, position
- * in mm, energy in keV).  The context sorts them by (subset, angle, u) and
- * keeps the sorted copy; the caller's arrays are not modified and may be
+ * in mm, energy in keV).  The context sorts them by (subset, angle, energy
+ * class, u), the class splitting at E0 (1 - fwhm_frac_e0 / 2), and keeps
+ * the sorted copy; the caller's arrays are not modified and may be
  * freed on return.  Synchronises the stream (input check).
  * EINVAL: n_events < 1 or >= 2^31, n_subsets not in [1, n_angles], an angle
  * outside [0, n_angles), |u| > extent/2, E outside [e_lo, e_hi], NaN.
